@@ -1,0 +1,328 @@
+"""ctypes front end of the CPU oracle (``rmlt_oracle.c``).
+
+TEST INFRASTRUCTURE: only the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg import this package.  The CUDA
+library and its Python binding never import it.
+
+The oracle is a plain binary64 restatement of Regional Adaptive Metropolis
+Light Transport (Alg. 1 and Secs. 3.2, 5.2-5.4 of the paper) in primary sample
+space; see the header of ``rmlt_oracle.c`` for the readings it takes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "rmlt_oracle.c"
+_LIB_PATH = _HERE / "_build" / "liboracle.so"
+_lib = None
+
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (no FMA contraction, IEEE semantics)."""
+    _LIB_PATH.parent.mkdir(exist_ok=True)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < max(
+            _SRC.stat().st_mtime, (_HERE / "rmlt_oracle.h").stat().st_mtime):
+        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.run(["gcc", *CFLAGS, str(_SRC), "-o", str(tmp), "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrParams(C.Structure):
+    _fields_ = [
+        ("n_chains", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+        ("region_px", C.c_int32), ("max_depth", C.c_int32), ("epoch_len", C.c_int32),
+        ("L", C.c_int32), ("target_mode", C.c_int32), ("n_bootstrap", C.c_int64),
+        ("seed", C.c_uint64), ("p_large", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
+        ("alpha_star", C.c_double), ("gamma_max", C.c_double), ("gamma_scale", C.c_double),
+        ("lambda_init", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
+        ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("pad_", C.c_int32),
+    ]
+
+
+MUT_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_uint32, C.c_uint64, C.POINTER(C.c_uint32), C.c_int32,
+                       C.c_int32, C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double),
+                       C.POINTER(C.c_double), C.POINTER(C.c_int32))
+UPD_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
+                       C.POINTER(C.c_int32))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = C.CDLL(str(build()))
+    P = C.POINTER
+    f32p, f64p, u32p, i32p = P(C.c_float), P(C.c_double), P(C.c_uint32), P(C.c_int32)
+    sig = {
+        "or_philox4x32_10": (None, [u32p, u32p, u32p]),
+        "or_exp2_f32": (C.c_float, [C.c_float]),
+        "or_kelemen_delta": (C.c_int64, [C.c_uint32, C.c_float, C.c_float]),
+        "or_scene_create": (C.c_void_p, [C.c_int32, f32p, C.c_int32, u32p, u32p, C.c_int32, i32p,
+                                         f32p, f32p, f32p, f32p, C.c_int32]),
+        "or_scene_create_toy": (C.c_void_p, [f64p]),
+        "or_scene_destroy": (None, [C.c_void_p]),
+        "or_scene_scale": (C.c_double, [C.c_void_p]),
+        "or_closest_hit": (C.c_int32, [C.c_void_p, f64p, f64p, C.c_double, C.c_double, C.c_int32,
+                                       f64p, i32p, f64p]),
+        "or_any_hit": (C.c_int32, [C.c_void_p, f64p, f64p, C.c_double, C.c_double, C.c_int32, f64p]),
+        "or_path_eval": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, u32p, f64p, f64p,
+                                     P(C.c_uint64)]),
+        "or_ctx_create": (C.c_void_p, [C.c_void_p, P(OrParams)]),
+        "or_ctx_destroy": (None, [C.c_void_p]),
+        "or_set_hooks": (None, [C.c_void_p, MUT_HOOK, UPD_HOOK, C.c_void_p]),
+        "or_init": (C.c_int32, [C.c_void_p]),
+        "or_run_epochs": (C.c_int32, [C.c_void_p, C.c_int64]),
+        "or_read_image": (None, [C.c_void_p, f64p]),
+        "or_dims": (C.c_int32, [C.c_void_p]),
+        "or_regions": (C.c_int32, [C.c_void_p]),
+        "or_region_of": (C.c_int32, [C.c_void_p, u32p]),
+        "or_mutations_done": (C.c_uint64, [C.c_void_p]),
+        "or_bhat": (C.c_double, [C.c_void_p]),
+        "or_stats": (None, [C.c_void_p, P(C.c_uint64)]),
+        "or_accept_prob": (C.c_double, [C.c_void_p, u32p, u32p, C.c_double, C.c_double, C.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    for name in ("or_state_q", "or_state_f", "or_state_pi", "or_state_k", "or_boot_choice",
+                 "or_lambda", "or_n_updates", "or_visits", "or_accsum", "or_hist", "or_weight",
+                 "or_sigma", "or_image_acc"):
+        fn = getattr(L, name)
+        fn.restype = C.c_void_p
+        fn.argtypes = [C.c_void_p]
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(o, C.c_uint32))
+    return o
+
+
+def exp2_f32(t: float) -> np.float32:
+    return np.float32(lib().or_exp2_f32(C.c_float(t)))
+
+
+def kelemen_delta(xmag: int, sigma_s2: float, log2_ratio: float) -> int:
+    return int(lib().or_kelemen_delta(xmag, C.c_float(sigma_s2), C.c_float(log2_ratio)))
+
+
+class Scene:
+    """An oracle scene built from a scene dict (see the package's scenes module)."""
+
+    def __init__(self, scene: dict | None = None, use_bvh: bool = True, toy=None):
+        L = lib()
+        if toy is not None:
+            self._toy = np.ascontiguousarray(toy, np.float64)
+            self.h = L.or_scene_create_toy(_ptr(self._toy, C.c_double))
+        else:
+            self._keep = {k: np.ascontiguousarray(v) for k, v in scene.items()}
+            s = self._keep
+            v = np.ascontiguousarray(s["verts"], np.float32)
+            t = np.ascontiguousarray(s["tris"], np.uint32)
+            self._keep.update(verts=v, tris=t)
+            self.h = L.or_scene_create(
+                len(v), _ptr(v, C.c_float), len(t), _ptr(t, C.c_uint32),
+                _ptr(np.ascontiguousarray(s["mat_id"], np.uint32), C.c_uint32), len(s["mat_type"]),
+                _ptr(np.ascontiguousarray(s["mat_type"], np.int32), C.c_int32),
+                _ptr(np.ascontiguousarray(s["albedo"], np.float32), C.c_float),
+                _ptr(np.ascontiguousarray(s["emission"], np.float32), C.c_float),
+                _ptr(np.ascontiguousarray(s["roughness"], np.float32), C.c_float),
+                _ptr(np.ascontiguousarray(s["camera"], np.float32), C.c_float), int(use_bvh))
+        if not self.h:
+            raise ValueError("oracle rejected the scene")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_scene_destroy(self.h)
+            self.h = None
+
+    @property
+    def scale(self) -> float:
+        return lib().or_scene_scale(self.h)
+
+    def closest_hit(self, o, d, tmin=0.0, tmax=float("inf"), brute=False, margin=False):
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        t = C.c_double()
+        tri = C.c_int32()
+        m = C.c_double(float("inf"))
+        hit = lib().or_closest_hit(self.h, _ptr(o, C.c_double), _ptr(d, C.c_double), tmin, tmax,
+                                   int(brute), C.byref(t), C.byref(tri),
+                                   C.byref(m) if margin else None)
+        return bool(hit), t.value, tri.value, m.value
+
+    def any_hit(self, o, d, tmin, tmax, brute=False):
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        return bool(lib().or_any_hit(self.h, _ptr(o, C.c_double), _ptr(d, C.c_double), tmin, tmax,
+                                     int(brute), None))
+
+    def path_eval(self, q, width, height, max_depth):
+        q = np.ascontiguousarray(q, np.uint32)
+        f = np.zeros(3)
+        m = C.c_double(float("inf"))
+        cnt = np.zeros(3, np.uint64)
+        ok = lib().or_path_eval(self.h, width, height, max_depth, _ptr(q, C.c_uint32),
+                                _ptr(f, C.c_double), C.byref(m), _ptr(cnt, C.c_uint64))
+        return f, m.value, bool(ok), int(cnt[0])
+
+
+DEFAULT_PARAMS = dict(
+    n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
+    target_mode=0, n_bootstrap=1 << 14, seed=1, p_large=0.3, s1=1.0 / 1024.0, s2=1.0 / 64.0,
+    alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
+    lambda_max=None, w_floor=1e-3, debug_flags=0,
+)
+
+
+def lambda_max_default(s2: float) -> float:
+    """Upper clamp of lambda: sigma s2 <= 1/2, the largest offset on the torus."""
+    import math
+    return 2.0 * math.log(1.0 / (2.0 * s2))
+
+
+def make_params(**kw) -> OrParams:
+    p = dict(DEFAULT_PARAMS)
+    p.update(kw)
+    if p["lambda_max"] is None:
+        p["lambda_max"] = lambda_max_default(p["s2"])
+    return OrParams(**p)
+
+
+class Chains:
+    """The oracle's chain population (Alg. 1 over many independent chains)."""
+
+    def __init__(self, scene: Scene, **params):
+        self.scene = scene
+        self.params = make_params(**params)
+        self.h = lib().or_ctx_create(scene.h, C.byref(self.params))
+        if not self.h:
+            raise ValueError("oracle rejected the parameters")
+        self.D = lib().or_dims(self.h)
+        self.m = lib().or_regions(self.h)
+        self.C = self.params.n_chains
+        self._hooks = None
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_ctx_destroy(self.h)
+            self.h = None
+
+    def _arr(self, name, ct, shape):
+        addr = getattr(lib(), name)(self.h)
+        n = int(np.prod(shape))
+        return np.ctypeslib.as_array((ct * n).from_address(addr)).reshape(shape)
+
+    def init(self):
+        if lib().or_init(self.h) != 0:
+            raise RuntimeError("or_init failed")
+
+    def run_epochs(self, n: int):
+        if lib().or_run_epochs(self.h, int(n)) != 0:
+            raise RuntimeError("or_run_epochs failed")
+
+    def set_hooks(self, mut_fn=None, upd_fn=None):
+        mh = MUT_HOOK(mut_fn) if mut_fn else MUT_HOOK()
+        uh = UPD_HOOK(upd_fn) if upd_fn else UPD_HOOK()
+        self._hooks = (mh, uh)
+        lib().or_set_hooks(self.h, mh, uh, None)
+
+    def image(self) -> np.ndarray:
+        out = np.zeros((self.params.height, self.params.width, 3))
+        lib().or_read_image(self.h, _ptr(out, C.c_double))
+        return out
+
+    def accept_prob(self, qx, qy, pi_x, pi_y, large=False) -> float:
+        qx = np.ascontiguousarray(qx, np.uint32)
+        qy = np.ascontiguousarray(qy, np.uint32)
+        return float(lib().or_accept_prob(self.h, _ptr(qx, C.c_uint32), _ptr(qy, C.c_uint32),
+                                          float(pi_x), float(pi_y), int(large)))
+
+    def region_of(self, q) -> int:
+        q = np.ascontiguousarray(q, np.uint32)
+        return lib().or_region_of(self.h, _ptr(q, C.c_uint32))
+
+    @property
+    def mutations_done(self) -> int:
+        return int(lib().or_mutations_done(self.h))
+
+    @property
+    def bhat(self) -> float:
+        return float(lib().or_bhat(self.h))
+
+    def stats(self) -> dict:
+        o = np.zeros(8, np.uint64)
+        lib().or_stats(self.h, _ptr(o, C.c_uint64))
+        keys = ("mutations", "accepted", "large", "small", "early_reject", "invalid", "rays", "boot")
+        return {k: int(v) for k, v in zip(keys, o)}
+
+    # live views of the oracle's state arrays
+    @property
+    def q(self):
+        return self._arr("or_state_q", C.c_uint32, (self.C, self.D))
+
+    @property
+    def f(self):
+        return self._arr("or_state_f", C.c_double, (self.C, 3))
+
+    @property
+    def pi(self):
+        return self._arr("or_state_pi", C.c_double, (self.C,))
+
+    @property
+    def k(self):
+        return self._arr("or_state_k", C.c_int32, (self.C,))
+
+    @property
+    def boot_choice(self):
+        return self._arr("or_boot_choice", C.c_int64, (self.C,))
+
+    @property
+    def lam(self):
+        return self._arr("or_lambda", C.c_double, (self.m,))
+
+    @property
+    def n_updates(self):
+        return self._arr("or_n_updates", C.c_int64, (self.m,))
+
+    @property
+    def visits(self):
+        return self._arr("or_visits", C.c_uint64, (self.m,))
+
+    @property
+    def accsum(self):
+        return self._arr("or_accsum", C.c_uint64, (self.m,))
+
+    @property
+    def hist(self):
+        return self._arr("or_hist", C.c_uint64, (self.m,))
+
+    @property
+    def weight(self):
+        return self._arr("or_weight", C.c_double, (self.m,))
+
+    @property
+    def sigma(self):
+        return self._arr("or_sigma", C.c_float, (self.m,))
+
+    @property
+    def image_acc(self):
+        return self._arr("or_image_acc", C.c_double, (self.params.height, self.params.width, 3))

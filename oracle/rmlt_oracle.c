@@ -1,0 +1,1052 @@
+/*
+ * CPU oracle for Regional Adaptive Metropolis Light Transport, restated in
+ * primary sample space (PSS).  TEST INFRASTRUCTURE: only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg load it; the CUDA product path
+ * shares no code with it.
+ *
+ * Plain binary64 C.  Readings of the paper that this file takes (where the
+ * paper is silent, garbled or inconsistent) are marked "Reading:".
+ *
+ * parity pins: Philox against an independent library generator; closest hit
+ * against brute force; the region update against a literal sequential
+ * transcription of Alg. 1; the furnace and uniform-emitter closed forms; the
+ * toy integrand's closed-form region masses (App. B); detailed balance of the
+ * state-dependent acceptance on an enumerated torus.  See tests/test_oracle_*.
+ */
+#include "rmlt_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_DIM 256
+#define OR_WIN 1e-3            /* scene-relative window of the decision margin */
+#define OR_INF (1.0 / 0.0)
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: ten rounds of two 32x32->64 multiplies, key bumped by the  */
+/* Weyl constants after each round (Salmon et al., SC'11, Sec. 3.2).         */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* A uniform in [0,1) from the top 24 bits of a word; exact in binary32/64. */
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+/* Counter layout of the draws (the paper does not specify its RNG):
+ *   mutation draws  ctr = {mut lo, mut hi, chain, call}, key = {seed lo, seed hi}
+ *   bootstrap draws ctr = {sample lo, sample hi, 0xFFFFFFFF, 0x8000 + call}   */
+static void draw(uint64_t seed, uint64_t a, uint32_t b, uint32_t call, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), b, call};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* binary32 quantities that decide integers (proposal offsets, sigma_k)     */
+/* ------------------------------------------------------------------------ */
+float or_exp2_f32(float t)
+{
+    /* t = n + r, n = rint(t), |r| <= 1/2; 2^r by its Taylor series
+     * sum_i (ln 2)^i r^i / i!, i <= 7, Horner with fused multiply-adds. */
+    float n = rintf(t);
+    float r = t - n;
+    float p = 1.525273365e-05f;
+    p = fmaf(p, r, 1.540352969e-04f);
+    p = fmaf(p, r, 1.333355787e-03f);
+    p = fmaf(p, r, 9.618128650e-03f);
+    p = fmaf(p, r, 5.550410971e-02f);
+    p = fmaf(p, r, 2.402265072e-01f);
+    p = fmaf(p, r, 6.931471825e-01f);
+    p = fmaf(p, r, 1.0f);
+    int32_t e = (int32_t)n + 127;
+    uint32_t bits = (uint32_t)e << 23;
+    float s;
+    memcpy(&s, &bits, sizeof s);
+    return p * s;
+}
+
+/* Kelemen et al. (2002) small step: offset magnitude sigma s2 (s1/s2)^xi,
+ * i.e. log-uniform on [sigma s1, sigma s2]; scaled by 2^32 and rounded to an
+ * integer number of PSS quanta.  sigma_s2 = fl(sigma_k * fl(s2 * 2^32)),
+ * log2_ratio = fl(log2(s2 / s1)). */
+int64_t or_kelemen_delta(uint32_t xmag, float sigma_s2, float log2_ratio)
+{
+    float xi = (float)(xmag >> 8) * 5.9604644775390625e-08f;
+    float t = -(xi * log2_ratio);
+    float m = sigma_s2 * or_exp2_f32(t);
+    return (int64_t)llrintf(m);
+}
+
+/* sigma_k = sqrt(exp(lambda_k)) = 2^(lambda_k / (2 ln 2))  (Alg. 1; Sec. 5.3) */
+static float sigma_of_lambda(double lambda)
+{
+    return or_exp2_f32((float)(lambda * 0.7213475204444817));
+}
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                      */
+/* ------------------------------------------------------------------------ */
+static void v_sub(const double a[3], const double b[3], double o[3]) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static double v_dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void v_cross(const double a[3], const double b[3], double o[3])
+{
+    double x = a[1] * b[2] - a[2] * b[1];
+    double y = a[2] * b[0] - a[0] * b[2];
+    double z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x; o[1] = y; o[2] = z;
+}
+static double v_len(const double a[3]) { return sqrt(v_dot(a, a)); }
+static void v_norm(double a[3]) { double l = v_len(a); a[0] /= l; a[1] /= l; a[2] /= l; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+static double dmax(double a, double b) { return a > b ? a : b; }
+
+/* Luminance l(f) (Sec. 3.2 leaves l unspecified; Rec. 709 weights). */
+static double luminance(const double f[3]) { return 0.2126 * f[0] + 0.7152 * f[1] + 0.0722 * f[2]; }
+
+/* ------------------------------------------------------------------------ */
+/* scene                                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double v0[3], e1[3], e2[3], n[3];
+    double area2;                 /* |e1 x e2| */
+    double h_u, h_v, h_w;         /* area2 / |edge opposite to each weight|  */
+    int32_t mat;
+} or_tri;
+
+typedef struct {
+    int32_t type;                 /* 0 Lambert, 1 GGX */
+    double albedo[3], emission[3], rough;
+    int32_t emissive, black;
+} or_mat;
+
+typedef struct {
+    double lo[3], hi[3];
+    int32_t left, right, first, count;   /* leaf iff count > 0 */
+} or_node;
+
+struct or_scene {
+    int32_t toy;
+    double toy_p[10];
+    int32_t nt, nm;
+    or_tri* tri;
+    or_mat* mat;
+    int32_t nl;
+    int32_t* light;
+    double* light_cdf;            /* cumulative area / total, last = 1 */
+    double light_area;
+    double cam_pos[3], cam_fwd[3], cam_right[3], cam_up[3], tan_half;
+    double scale, eps;
+    int32_t use_bvh, n_node;
+    or_node* node;
+    int32_t* idx;
+};
+
+static const double* g_cent;
+static int g_axis;
+static int cmp_idx(const void* a, const void* b)
+{
+    double ka = g_cent[3 * *(const int32_t*)a + g_axis], kb = g_cent[3 * *(const int32_t*)b + g_axis];
+    if (ka < kb) return -1;
+    if (ka > kb) return 1;
+    return (*(const int32_t*)a) - (*(const int32_t*)b);
+}
+
+/* Median-split BVH, leaves of <= 4 triangles, boxes inflated by the margin
+ * window so that every near-miss candidate is visited. */
+static int32_t bvh_build(or_scene* s, double* cent, int32_t first, int32_t count)
+{
+    int32_t id = s->n_node++;
+    or_node* nd = &s->node[id];
+    double infl = OR_WIN * s->scale;
+    for (int a = 0; a < 3; ++a) { nd->lo[a] = OR_INF; nd->hi[a] = -OR_INF; }
+    double clo[3] = {OR_INF, OR_INF, OR_INF}, chi[3] = {-OR_INF, -OR_INF, -OR_INF};
+    for (int32_t i = first; i < first + count; ++i) {
+        const or_tri* t = &s->tri[s->idx[i]];
+        for (int a = 0; a < 3; ++a) {
+            double p0 = t->v0[a], p1 = t->v0[a] + t->e1[a], p2 = t->v0[a] + t->e2[a];
+            nd->lo[a] = dmin(nd->lo[a], dmin(p0, dmin(p1, p2)));
+            nd->hi[a] = dmax(nd->hi[a], dmax(p0, dmax(p1, p2)));
+            double c = cent[3 * s->idx[i] + a];
+            clo[a] = dmin(clo[a], c);
+            chi[a] = dmax(chi[a], c);
+        }
+    }
+    for (int a = 0; a < 3; ++a) { nd->lo[a] -= infl; nd->hi[a] += infl; }
+    if (count <= 4) {
+        nd->first = first; nd->count = count; nd->left = nd->right = -1;
+        return id;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a) if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+    g_cent = cent;
+    g_axis = axis;
+    qsort(s->idx + first, (size_t)count, sizeof(int32_t), cmp_idx);
+    int32_t half = count / 2;
+    nd->count = 0;
+    nd->first = -1;
+    int32_t l = bvh_build(s, cent, first, half);
+    int32_t r = bvh_build(s, cent, first + half, count - half);
+    s->node[id].left = l;
+    s->node[id].right = r;
+    return id;
+}
+
+or_scene* or_scene_create(int32_t nv, const float* verts, int32_t nt, const uint32_t* tris,
+                          const uint32_t* mat_id, int32_t nm, const int32_t* mat_type,
+                          const float* albedo, const float* emission, const float* roughness,
+                          const float* camera, int32_t use_bvh)
+{
+    if (nt <= 0 || nv <= 0 || nm <= 0) return NULL;
+    or_scene* s = (or_scene*)calloc(1, sizeof(or_scene));
+    s->nt = nt; s->nm = nm;
+    s->tri = (or_tri*)calloc((size_t)nt, sizeof(or_tri));
+    s->mat = (or_mat*)calloc((size_t)nm, sizeof(or_mat));
+    for (int32_t m = 0; m < nm; ++m) {
+        or_mat* M = &s->mat[m];
+        M->type = mat_type[m];
+        for (int a = 0; a < 3; ++a) { M->albedo[a] = albedo[3 * m + a]; M->emission[a] = emission[3 * m + a]; }
+        M->rough = roughness[m];
+        M->emissive = (M->emission[0] > 0 || M->emission[1] > 0 || M->emission[2] > 0);
+        M->black = (M->albedo[0] <= 0 && M->albedo[1] <= 0 && M->albedo[2] <= 0);
+    }
+    double lo[3] = {OR_INF, OR_INF, OR_INF}, hi[3] = {-OR_INF, -OR_INF, -OR_INF};
+    for (int32_t i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) { lo[a] = dmin(lo[a], verts[3 * i + a]); hi[a] = dmax(hi[a], verts[3 * i + a]); }
+    double diag[3];
+    v_sub(hi, lo, diag);
+    s->scale = v_len(diag);
+    s->eps = 1e-4 * s->scale;
+    s->nl = 0;
+    for (int32_t i = 0; i < nt; ++i) {
+        or_tri* T = &s->tri[i];
+        double p[3][3];
+        for (int j = 0; j < 3; ++j) {
+            uint32_t vi = tris[3 * i + j];
+            if ((int64_t)vi >= nv) { or_scene_destroy(s); return NULL; }
+            for (int a = 0; a < 3; ++a) p[j][a] = verts[3 * vi + a];
+        }
+        if ((int64_t)mat_id[i] >= nm) { or_scene_destroy(s); return NULL; }
+        for (int a = 0; a < 3; ++a) { T->v0[a] = p[0][a]; T->e1[a] = p[1][a] - p[0][a]; T->e2[a] = p[2][a] - p[0][a]; }
+        double c[3];
+        v_cross(T->e1, T->e2, c);
+        T->area2 = v_len(c);
+        if (T->area2 > 0) { T->n[0] = c[0] / T->area2; T->n[1] = c[1] / T->area2; T->n[2] = c[2] / T->area2; }
+        double e3[3];
+        v_sub(T->e2, T->e1, e3);
+        T->h_u = T->area2 / dmax(v_len(T->e2), 1e-300);
+        T->h_v = T->area2 / dmax(v_len(T->e1), 1e-300);
+        T->h_w = T->area2 / dmax(v_len(e3), 1e-300);
+        T->mat = (int32_t)mat_id[i];
+        if (s->mat[T->mat].emissive && T->area2 > 0) s->nl++;
+    }
+    /* light list, sampled proportionally to area */
+    s->light = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s->nl > 0 ? s->nl : 1));
+    s->light_cdf = (double*)malloc(sizeof(double) * (size_t)(s->nl > 0 ? s->nl : 1));
+    double acc = 0;
+    int32_t li = 0;
+    for (int32_t i = 0; i < nt; ++i) {
+        if (s->mat[s->tri[i].mat].emissive && s->tri[i].area2 > 0) {
+            acc += 0.5 * s->tri[i].area2;
+            s->light[li] = i;
+            s->light_cdf[li] = acc;
+            li++;
+        }
+    }
+    s->light_area = acc;
+    for (int32_t j = 0; j < s->nl; ++j) s->light_cdf[j] /= acc;
+    if (s->nl > 0) s->light_cdf[s->nl - 1] = 1.0;
+    /* pinhole camera */
+    double pos[3] = {camera[0], camera[1], camera[2]}, look[3] = {camera[3], camera[4], camera[5]};
+    double up[3] = {camera[6], camera[7], camera[8]};
+    memcpy(s->cam_pos, pos, sizeof pos);
+    v_sub(look, pos, s->cam_fwd);
+    v_norm(s->cam_fwd);
+    v_cross(s->cam_fwd, up, s->cam_right);
+    v_norm(s->cam_right);
+    v_cross(s->cam_right, s->cam_fwd, s->cam_up);
+    s->tan_half = tan((double)camera[9] * OR_PI / 360.0);
+    s->use_bvh = use_bvh;
+    s->idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)nt);
+    for (int32_t i = 0; i < nt; ++i) s->idx[i] = i;
+    if (use_bvh) {
+        double* cent = (double*)malloc(sizeof(double) * 3 * (size_t)nt);
+        for (int32_t i = 0; i < nt; ++i)
+            for (int a = 0; a < 3; ++a)
+                cent[3 * i + a] = s->tri[i].v0[a] + (s->tri[i].e1[a] + s->tri[i].e2[a]) / 3.0;
+        s->node = (or_node*)calloc((size_t)(2 * nt + 1), sizeof(or_node));
+        s->n_node = 0;
+        bvh_build(s, cent, 0, nt);
+        free(cent);
+    }
+    return s;
+}
+
+or_scene* or_scene_create_toy(const double* p)
+{
+    or_scene* s = (or_scene*)calloc(1, sizeof(or_scene));
+    s->toy = 1;
+    memcpy(s->toy_p, p, sizeof(double) * 10);
+    s->scale = 1.0;
+    return s;
+}
+
+void or_scene_destroy(or_scene* s)
+{
+    if (!s) return;
+    free(s->tri); free(s->mat); free(s->light); free(s->light_cdf); free(s->node); free(s->idx);
+    free(s);
+}
+
+double or_scene_scale(const or_scene* s) { return s->scale; }
+
+/* ------------------------------------------------------------------------ */
+/* ray casting                                                               */
+/* ------------------------------------------------------------------------ */
+/* Moller-Trumbore: plane parameter t and barycentrics (u, v) of the hit.  */
+static int tri_plane(const or_tri* T, const double o[3], const double d[3], double* t, double* u, double* v)
+{
+    double p[3], s[3], q[3];
+    v_cross(d, T->e2, p);
+    double det = v_dot(T->e1, p);
+    if (det == 0.0 || !isfinite(det)) return 0;
+    double inv = 1.0 / det;
+    v_sub(o, T->v0, s);
+    *u = v_dot(s, p) * inv;
+    v_cross(s, T->e1, q);
+    *v = v_dot(d, q) * inv;
+    *t = v_dot(T->e2, q) * inv;
+    return 1;
+}
+
+/* signed distance (world units) of the plane hit from the nearest edge line;
+ * positive inside the triangle */
+static double edge_dist(const or_tri* T, double u, double v)
+{
+    double w = 1.0 - u - v;
+    return dmin(u * T->h_u, dmin(v * T->h_v, w * T->h_w));
+}
+
+static int box_hit(const or_node* n, const double o[3], const double d[3], double t0, double t1)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (o[a] < n->lo[a] || o[a] > n->hi[a]) return 0;
+            continue;
+        }
+        double inv = 1.0 / d[a];
+        double ta = (n->lo[a] - o[a]) * inv, tb = (n->hi[a] - o[a]) * inv;
+        if (ta > tb) { double x = ta; ta = tb; tb = x; }
+        t0 = dmax(t0, ta);
+        t1 = dmin(t1, tb);
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+typedef int (*tri_visit)(void* st, int32_t tri);   /* returns 1 to stop */
+
+/* visit every triangle whose (inflated) box the segment (t0, t1) touches;
+ * t1 may shrink during the walk through *t1p */
+static void walk(const or_scene* s, const double o[3], const double d[3], double t0, double* t1p,
+                 int brute, tri_visit fn, void* st, uint64_t* nodes, uint64_t* tests)
+{
+    if (brute || !s->use_bvh) {
+        for (int32_t i = 0; i < s->nt; ++i) { if (tests) (*tests)++; if (fn(st, i)) return; }
+        return;
+    }
+    int32_t stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const or_node* n = &s->node[stack[--sp]];
+        if (nodes) (*nodes)++;
+        if (!box_hit(n, o, d, t0, *t1p)) continue;
+        if (n->count > 0) {
+            for (int32_t i = n->first; i < n->first + n->count; ++i) {
+                if (tests) (*tests)++;
+                if (fn(st, s->idx[i])) return;
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
+typedef struct {
+    const or_scene* s;
+    const double *o, *d;
+    double tmin, t1;
+    int32_t best;
+    double bt, win, m;
+    int pass;
+} hit_state;
+
+static int closest_visit(void* vs, int32_t i)
+{
+    hit_state* h = (hit_state*)vs;
+    const or_tri* T = &h->s->tri[i];
+    double t, u, v;
+    if (!tri_plane(T, h->o, h->d, &t, &u, &v)) return 0;
+    if (h->pass == 0) {
+        if (u >= 0 && v >= 0 && u + v <= 1.0 && t > h->tmin && t < h->t1) {
+            h->t1 = t;
+            h->best = i;
+            h->bt = t;
+        }
+        return 0;
+    }
+    /* pass 1: margin of the closest-hit decision */
+    if (!(t > h->tmin) || t > h->t1) return 0;
+    double ed = edge_dist(T, u, v);
+    if (ed < -h->win) return 0;
+    double sc = h->s->scale;
+    if (i == h->best) h->m = dmin(h->m, ed / sc);
+    else if (ed >= 0) h->m = dmin(h->m, fabs(t - h->bt) / sc);
+    else h->m = dmin(h->m, -ed / sc);
+    return 0;
+}
+
+int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3],
+                       double tmin, double tmax, int32_t brute,
+                       double* t_out, int32_t* tri_out, double* margin)
+{
+    hit_state h = {s, o, d, tmin, tmax, -1, tmax, OR_WIN * s->scale, OR_INF, 0};
+    walk(s, o, d, tmin, &h.t1, brute, closest_visit, &h, NULL, NULL);
+    if (margin) {
+        h.pass = 1;
+        h.t1 = (h.best >= 0 ? h.bt : tmax) + h.win;
+        double t1 = h.t1;
+        walk(s, o, d, tmin, &t1, brute, closest_visit, &h, NULL, NULL);
+        *margin = dmin(*margin, h.m);
+    }
+    if (t_out) *t_out = h.bt;
+    if (tri_out) *tri_out = h.best;
+    return h.best >= 0;
+}
+
+typedef struct {
+    const or_scene* s;
+    const double *o, *d;
+    double tmin, tmax, win, m;
+    int occ, want_margin;
+} any_state;
+
+static int any_visit(void* vs, int32_t i)
+{
+    any_state* h = (any_state*)vs;
+    const or_tri* T = &h->s->tri[i];
+    double t, u, v;
+    if (!tri_plane(T, h->o, h->d, &t, &u, &v)) return 0;
+    if (u >= 0 && v >= 0 && u + v <= 1.0 && t > h->tmin && t < h->tmax) h->occ = 1;
+    if (!h->want_margin) return h->occ;
+    if (t <= h->tmin - h->win || t >= h->tmax + h->win) return 0;
+    double ed = edge_dist(T, u, v);
+    if (ed < -h->win) return 0;
+    double sc = h->s->scale;
+    h->m = dmin(h->m, fabs(ed) / sc);
+    if (ed >= 0) h->m = dmin(h->m, dmin(fabs(t - h->tmax), fabs(t - h->tmin)) / sc);
+    return 0;
+}
+
+int32_t or_any_hit(const or_scene* s, const double o[3], const double d[3],
+                   double tmin, double tmax, int32_t brute, double* margin)
+{
+    any_state h = {s, o, d, tmin, tmax, OR_WIN * s->scale, OR_INF, 0, margin != NULL};
+    double t1 = tmax + h.win;
+    walk(s, o, d, tmin - h.win, &t1, brute, any_visit, &h, NULL, NULL);
+    if (margin) *margin = dmin(*margin, h.m);
+    return h.occ;
+}
+
+/* ------------------------------------------------------------------------ */
+/* path map  u -> f(u): pinhole camera, d surface interactions, next-event  */
+/* estimation at each, BSDF sampling in between (PT + NEE in PSS).          */
+/* ------------------------------------------------------------------------ */
+/* orthonormal frame around n (switches helper axis at |n_z| = 0.9) */
+static void frame(const double n[3], double t[3], double b[3], double* margin)
+{
+    double az = fabs(n[2]);
+    if (margin) *margin = dmin(*margin, fabs(az - 0.9));
+    if (az < 0.9) { t[0] = -n[1]; t[1] = n[0]; t[2] = 0.0; }
+    else { t[0] = 0.0; t[1] = -n[2]; t[2] = n[1]; }
+    v_norm(t);
+    v_cross(n, t, b);
+}
+
+static void to_world(const double l[3], const double t[3], const double b[3], const double n[3], double w[3])
+{
+    for (int a = 0; a < 3; ++a) w[a] = l[0] * t[a] + l[1] * b[a] + l[2] * n[a];
+}
+
+/* Smith G1 for GGX */
+static double ggx_g1(double c, double a2)
+{
+    if (c <= 0) return 0.0;
+    return 2.0 * c / (c + sqrt(a2 + (1.0 - a2) * c * c));
+}
+
+static void bsdf_eval(const or_mat* M, const double wo[3], const double wi[3], const double n[3], double fr[3])
+{
+    if (M->type == 0) {
+        for (int a = 0; a < 3; ++a) fr[a] = M->albedo[a] / OR_PI;
+        return;
+    }
+    double co = v_dot(n, wo), ci = v_dot(n, wi);
+    if (co <= 0 || ci <= 0) { fr[0] = fr[1] = fr[2] = 0; return; }
+    double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
+    v_norm(h);
+    double ch = v_dot(n, h), a2 = M->rough * M->rough;
+    double den = 1.0 + (a2 - 1.0) * ch * ch;
+    double D = a2 / (OR_PI * den * den);
+    double G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+    double c5 = pow(1.0 - v_dot(wi, h), 5.0);
+    for (int a = 0; a < 3; ++a) {
+        double F = M->albedo[a] + (1.0 - M->albedo[a]) * c5;
+        fr[a] = F * D * G / (4.0 * co * ci);
+    }
+}
+
+static double toy_eval(const double* p, double u0, double u1)
+{
+    double f = p[0];
+    if (u0 >= p[2] && u0 < p[3] && u1 >= p[4] && u1 < p[5]) f += p[1];
+    double dx = u0 - p[7], dy = u1 - p[8];
+    f += p[6] * exp(-(dx * dx + dy * dy) / (2.0 * p[9] * p[9]));
+    return f;
+}
+
+int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                     const uint32_t* q, double f[3], double* margin, uint64_t counts[3])
+{
+    double mloc = OR_INF;
+    double* mp = margin ? &mloc : NULL;
+    f[0] = f[1] = f[2] = 0.0;
+    if (s->toy) {
+        double v = toy_eval(s->toy_p, u24(q[0]), u24(q[1]));
+        f[0] = f[1] = f[2] = v;
+        if (margin) *margin = OR_INF;
+        return 1;
+    }
+    double L[3] = {0, 0, 0}, T[3] = {1, 1, 1};
+    double aspect = (double)width / (double)height;
+    double sx = (2.0 * u24(q[0]) - 1.0) * s->tan_half * aspect;
+    double sy = (1.0 - 2.0 * u24(q[1])) * s->tan_half;
+    double o[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+        o[a] = s->cam_pos[a];
+        d[a] = s->cam_fwd[a] + sx * s->cam_right[a] + sy * s->cam_up[a];
+    }
+    v_norm(d);
+    for (int b = 0; b < max_depth; ++b) {
+        double t;
+        int32_t ti;
+        if (counts) counts[0]++;
+        if (!or_closest_hit(s, o, d, 0.0, OR_INF, 0, &t, &ti, mp)) break;
+        const or_tri* Tr = &s->tri[ti];
+        const or_mat* M = &s->mat[Tr->mat];
+        double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        double cosi = -v_dot(Tr->n, d);
+        mloc = dmin(mloc, fabs(cosi));
+        double ns[3];
+        for (int a = 0; a < 3; ++a) ns[a] = cosi > 0 ? Tr->n[a] : -Tr->n[a];
+        if (b == 0 && M->emissive && cosi > 0)
+            for (int a = 0; a < 3; ++a) L[a] += T[a] * M->emission[a];
+        if (M->black) break;
+        double wo[3] = {-d[0], -d[1], -d[2]};
+        /* next-event estimation: light triangle by area, uniform point on it */
+        if (s->nl > 0) {
+            double ls = u24(q[2 + 5 * b]), lu = u24(q[3 + 5 * b]), lv = u24(q[4 + 5 * b]);
+            int32_t lo = 0, hi = s->nl - 1;
+            while (lo < hi) { int32_t mid = (lo + hi) / 2; if (s->light_cdf[mid] > ls) hi = mid; else lo = mid + 1; }
+            mloc = dmin(mloc, s->light_cdf[lo] - ls);
+            if (lo > 0) mloc = dmin(mloc, ls - s->light_cdf[lo - 1]);
+            const or_tri* LT = &s->tri[s->light[lo]];
+            const or_mat* LM = &s->mat[LT->mat];
+            double su = sqrt(lu), b1 = su * (1.0 - lv), b2 = su * lv;
+            double p[3], wi[3];
+            for (int a = 0; a < 3; ++a) p[a] = LT->v0[a] + b1 * LT->e1[a] + b2 * LT->e2[a];
+            v_sub(p, x, wi);
+            double dist2 = v_dot(wi, wi), dist = sqrt(dist2);
+            for (int a = 0; a < 3; ++a) wi[a] /= dist;
+            double cx = v_dot(ns, wi), cl = -v_dot(LT->n, wi);
+            if (cx > 0 && cl > 0) {
+                double xo[3], sd[3];
+                for (int a = 0; a < 3; ++a) xo[a] = x[a] + s->eps * ns[a];
+                v_sub(p, xo, sd);
+                double sdist = v_len(sd);
+                if (sdist > 2.0 * s->eps) {
+                    for (int a = 0; a < 3; ++a) sd[a] /= sdist;
+                    if (counts) counts[0]++;
+                    if (!or_any_hit(s, xo, sd, 0.0, sdist - s->eps, 0, mp)) {
+                        double fr[3];
+                        bsdf_eval(M, wo, wi, ns, fr);
+                        double g = cx * cl / dist2 * s->light_area;
+                        for (int a = 0; a < 3; ++a) L[a] += T[a] * fr[a] * LM->emission[a] * g;
+                    }
+                }
+            }
+        }
+        if (b == max_depth - 1) break;
+        /* continue by sampling the BSDF with the bounce's last two dimensions */
+        double bu = u24(q[5 + 5 * b]), bv = u24(q[6 + 5 * b]);
+        double ft[3], fb[3], wi[3], loc[3];
+        frame(ns, ft, fb, mp);
+        double phi = 2.0 * OR_PI * bv;
+        if (M->type == 0) {
+            double r = sqrt(bu);
+            loc[0] = r * cos(phi); loc[1] = r * sin(phi); loc[2] = sqrt(dmax(0.0, 1.0 - bu));
+            to_world(loc, ft, fb, ns, wi);
+            for (int a = 0; a < 3; ++a) T[a] *= M->albedo[a];
+        } else {
+            /* half vector with density D(m) cos(theta_m) (Walter et al. 2007) */
+            double a2 = M->rough * M->rough;
+            double tan2 = a2 * bu / (1.0 - bu);
+            double cm = 1.0 / sqrt(1.0 + tan2);
+            double sm = sqrt(dmax(0.0, 1.0 - cm * cm));
+            double mv[3];
+            loc[0] = sm * cos(phi); loc[1] = sm * sin(phi); loc[2] = cm;
+            to_world(loc, ft, fb, ns, mv);
+            double dom = v_dot(wo, mv);
+            if (dom <= 0) break;
+            for (int a = 0; a < 3; ++a) wi[a] = 2.0 * dom * mv[a] - wo[a];
+            double ci = v_dot(wi, ns), co = v_dot(wo, ns);
+            if (ci <= 0) break;
+            double G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+            double c5 = pow(1.0 - dom, 5.0);
+            for (int a = 0; a < 3; ++a) {
+                double F = M->albedo[a] + (1.0 - M->albedo[a]) * c5;
+                T[a] *= F * G * dom / (co * cm);
+            }
+        }
+        for (int a = 0; a < 3; ++a) { o[a] = x[a] + s->eps * ns[a]; d[a] = wi[a]; }
+    }
+    int ok = isfinite(L[0]) && isfinite(L[1]) && isfinite(L[2]);
+    if (ok) { f[0] = L[0]; f[1] = L[1]; f[2] = L[2]; }
+    if (margin) *margin = mloc;
+    return ok;
+}
+
+/* ------------------------------------------------------------------------ */
+/* chains                                                                    */
+/* ------------------------------------------------------------------------ */
+struct or_ctx {
+    const or_scene* s;
+    or_params p;
+    int32_t D, m, nx;
+    uint32_t T_large;
+    float S1, S2, log2_ratio;
+    uint32_t* q;
+    double* f;
+    double* pi;
+    int32_t* k;
+    int64_t* boot;
+    double* lam;
+    int64_t* n;
+    uint64_t *i, *A, *h, *h_prev;
+    double *w, *Rc;
+    float* sig;
+    double* img;
+    double* Bk;                   /* sum of pi over uniform samples landing in region k */
+    uint64_t nU;                  /* number of uniform samples (bootstrap + large steps) */
+    double bhat;
+    uint64_t mut;
+    uint64_t st[8];
+    int inited;
+    or_mut_hook mh;
+    or_upd_hook uh;
+    void* user;
+};
+
+or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
+{
+    if (!s || !p) return NULL;
+    int32_t D = 2 + 5 * p->max_depth;
+    if (D > OR_MAX_DIM || p->n_chains <= 0 || p->width <= 0 || p->height <= 0 || p->region_px <= 0)
+        return NULL;
+    or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
+    c->s = s;
+    c->p = *p;
+    c->D = D;
+    c->nx = (p->width + p->region_px - 1) / p->region_px;
+    int32_t ny = (p->height + p->region_px - 1) / p->region_px;
+    c->m = c->nx * ny;
+    double tl = ceil(p->p_large * 16777216.0);
+    c->T_large = (uint32_t)(tl < 0 ? 0 : (tl > 16777216.0 ? 16777216.0 : tl));
+    c->S1 = (float)(p->s1 * 4294967296.0);
+    c->S2 = (float)(p->s2 * 4294967296.0);
+    c->log2_ratio = (float)log2(p->s2 / p->s1);
+    size_t C = (size_t)p->n_chains, m = (size_t)c->m;
+    c->q = (uint32_t*)calloc(C * (size_t)D, sizeof(uint32_t));
+    c->f = (double*)calloc(C * 3, sizeof(double));
+    c->pi = (double*)calloc(C, sizeof(double));
+    c->k = (int32_t*)calloc(C, sizeof(int32_t));
+    c->boot = (int64_t*)calloc(C, sizeof(int64_t));
+    c->lam = (double*)calloc(m, sizeof(double));
+    c->n = (int64_t*)calloc(m, sizeof(int64_t));
+    c->i = (uint64_t*)calloc(m, sizeof(uint64_t));
+    c->A = (uint64_t*)calloc(m, sizeof(uint64_t));
+    c->h = (uint64_t*)calloc(m, sizeof(uint64_t));
+    c->h_prev = (uint64_t*)calloc(m, sizeof(uint64_t));
+    c->w = (double*)calloc(m, sizeof(double));
+    c->Rc = (double*)calloc(m, sizeof(double));
+    c->sig = (float*)calloc(m, sizeof(float));
+    c->img = (double*)calloc((size_t)p->width * (size_t)p->height * 3, sizeof(double));
+    c->Bk = (double*)calloc(m, sizeof(double));
+    return c;
+}
+
+void or_ctx_destroy(or_ctx* c)
+{
+    if (!c) return;
+    free(c->q); free(c->f); free(c->pi); free(c->k); free(c->boot); free(c->lam); free(c->n);
+    free(c->i); free(c->A); free(c->h); free(c->h_prev); free(c->w); free(c->Rc); free(c->sig);
+    free(c->img); free(c->Bk);
+    free(c);
+}
+
+void or_set_hooks(or_ctx* c, or_mut_hook mh, or_upd_hook uh, void* user)
+{
+    c->mh = mh; c->uh = uh; c->user = user;
+}
+
+static void pixel_of(const or_ctx* c, const uint32_t* q, int32_t* px, int32_t* py)
+{
+    *px = (int32_t)(((uint64_t)(q[0] >> 8) * (uint64_t)c->p.width) >> 24);
+    *py = (int32_t)(((uint64_t)(q[1] >> 8) * (uint64_t)c->p.height) >> 24);
+}
+
+/* region of a state: the 2-D screen-space grid partition of Sec. 5.4 / 6.1 */
+int32_t or_region_of(const or_ctx* c, const uint32_t* q)
+{
+    int32_t px, py;
+    pixel_of(c, q, &px, &py);
+    return px / c->p.region_px + (py / c->p.region_px) * c->nx;
+}
+
+static double weight_of(const or_ctx* c, int32_t k) { return c->p.target_mode ? c->w[k] : 1.0; }
+
+/* Large step: an independent uniform point of the PSS cube. */
+static void large_step(const or_ctx* c, uint32_t chain, uint64_t mut, uint32_t* qy)
+{
+    for (int32_t j = 0; 4 * j < c->D; ++j) {
+        uint32_t r[4];
+        draw(c->p.seed, mut, chain, 1u + (uint32_t)j, r);
+        for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) qy[4 * j + a] = r[a];
+    }
+}
+
+/* Small step: every dimension perturbed with the one scale sigma_{k(x)}
+ * (Alg. 1 lines 8-10; Sec. 5.2 proposal of the current state's region). */
+static void small_step(const or_ctx* c, uint32_t chain, uint64_t mut, int32_t kx,
+                       const uint32_t* qx, uint32_t* qy)
+{
+    float sigS2 = c->sig[kx] * c->S2;
+    for (int32_t j = 0; 2 * j < c->D; ++j) {
+        uint32_t r[4];
+        draw(c->p.seed, mut, chain, 1u + (uint32_t)j, r);
+        for (int a = 0; a < 2 && 2 * j + a < c->D; ++a) {
+            int64_t dq = or_kelemen_delta(r[2 * a], sigS2, c->log2_ratio);
+            uint32_t off = (uint32_t)(uint64_t)dq;
+            int32_t dim = 2 * j + a;
+            qy[dim] = (r[2 * a + 1] >> 31) ? qx[dim] - off : qx[dim] + off;
+        }
+    }
+}
+
+/* Ratio T_{k(y)}(x|y) / T_{k(x)}(y|x) of the state-dependent mixture
+ * (Sec. 5.2, eq. regional_proposal_mixture) for the Kelemen kernel.  Its
+ * magnitude density 1 / (|delta| ln(s2/s1)) does not depend on sigma inside
+ * its support [sigma s1, sigma s2], so the ratio is the indicator that every
+ * offset lies in the reverse kernel's support.  Reading: the paper writes
+ * only the generic MH ratio (Sec. 3.2); the reverse kernel is the one of the
+ * proposal's region. */
+static int reverse_support(const or_ctx* c, int32_t kx, int32_t ky, const uint32_t* qx, const uint32_t* qy)
+{
+    if (c->sig[ky] == c->sig[kx]) return 1;
+    float lo = c->sig[ky] * c->S1, hi = c->sig[ky] * c->S2;
+    for (int32_t d = 0; d < c->D; ++d) {
+        int64_t dd = (int64_t)(int32_t)(qy[d] - qx[d]);
+        float mag = (float)(dd < 0 ? -dd : dd);
+        if (!(mag >= lo && mag <= hi)) return 0;
+    }
+    return 1;
+}
+
+/* MH acceptance of the mixture (Sec. 3.2, strategy-mixture form; Sec. 5.2):
+ * a = min(1, pi~(y) T_{k(y)}(x|y) s(j|y) / (pi~(x) T_{k(x)}(y|x) s(j|x))),
+ * pi~ = pi / w_k (w = 1 in plain mode).  The strategy probabilities s do not
+ * depend on the state and cancel; R is the kernel ratio (1 for the large step,
+ * whose density is uniform).  A zero-contribution current state (possible only
+ * at initialisation) accepts any proposal the reverse kernel can undo. */
+static double accept_prob(const or_ctx* c, int32_t kx, int32_t ky, double pix, double piy, int32_t R)
+{
+    if (!R) return 0.0;
+    double ptx = pix / weight_of(c, kx), pty = piy / weight_of(c, ky);
+    if (!(ptx > 0)) return 1.0;
+    return dmin(1.0, pty / ptx);
+}
+
+double or_accept_prob(const or_ctx* c, const uint32_t* qx, const uint32_t* qy,
+                      double pix, double piy, int32_t large)
+{
+    int32_t kx = or_region_of(c, qx), ky = or_region_of(c, qy);
+    int32_t R = large ? 1 : reverse_support(c, kx, ky, qx, qy);
+    return accept_prob(c, kx, ky, pix, piy, R);
+}
+
+/* splat f(x) / pi(x) of the chain's current state at its pixel */
+static void splat(or_ctx* c, int32_t chain)
+{
+    if (!(c->pi[chain] > 0)) return;
+    int32_t px, py;
+    pixel_of(c, &c->q[(size_t)chain * c->D], &px, &py);
+    size_t o = ((size_t)py * c->p.width + px) * 3;
+    for (int a = 0; a < 3; ++a) c->img[o + a] += c->f[3 * chain + a] / c->pi[chain];
+}
+
+/* One Metropolis-Hastings mutation of chain `chain` (Alg. 1 lines 8-12, 19). */
+static void mutate(or_ctx* c, uint32_t chain)
+{
+    int32_t D = c->D;
+    uint32_t r0[4], qy[OR_MAX_DIM];
+    uint32_t* qx = &c->q[(size_t)chain * D];
+    draw(c->p.seed, c->mut, chain, 0u, r0);
+    int32_t large = (r0[0] >> 8) < c->T_large;
+    double xi = u24(r0[1]);
+    int32_t kx = c->k[chain];
+    if (large) large_step(c, chain, c->mut, qy);
+    else small_step(c, chain, c->mut, kx, qx, qy);
+    int32_t ky = or_region_of(c, qy);
+    int32_t R = large ? 1 : reverse_support(c, kx, ky, qx, qy);
+    if (c->p.debug_flags & 1) R = 1;   /* planted mistake for negative-control tests */
+    double fy[3] = {0, 0, 0}, margin = OR_INF;
+    if (R) {
+        uint64_t cnt[3] = {0, 0, 0};
+        if (!or_path_eval(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy,
+                          c->mh ? &margin : NULL, cnt))
+            c->st[5]++;
+        c->st[6] += cnt[0];
+    } else {
+        c->st[4]++;
+    }
+    double piy = luminance(fy);
+    double pty = piy / weight_of(c, ky);
+    double a = accept_prob(c, kx, ky, c->pi[chain], piy, R);
+    int32_t acc = xi < a;
+    if (c->mh) {
+        c->mh(c->user, chain, c->mut, qy, D, large, !R, margin, xi, fy, &a, &acc);
+        piy = luminance(fy);
+        pty = piy / weight_of(c, ky);
+    }
+    if (large) {
+        c->st[2]++;
+        c->Bk[ky] += piy;
+        c->nU++;
+    } else {
+        /* adaptation statistics of the current state's region (Alg. 1 l. 11-12) */
+        c->st[3]++;
+        c->i[kx] += 1;
+        c->A[kx] += (uint64_t)llrint(a * 4294967296.0);
+    }
+    if (acc) {
+        memcpy(qx, qy, sizeof(uint32_t) * (size_t)D);
+        for (int x = 0; x < 3; ++x) c->f[3 * chain + x] = fy[x];
+        c->pi[chain] = piy;
+        c->k[chain] = ky;
+        c->st[1]++;
+    }
+    c->h[c->k[chain]] += 1;
+    c->st[0]++;
+    /* splat the chain's current state (estimator of Sec. 3.2) */
+    splat(c, chain);
+}
+
+/* Region-parameter update at an epoch boundary (Alg. 1 lines 13-18).
+ * Reading: the trigger is i_k >= L and alpha_hat = A_k / i_k, which equals
+ * eq. est_exp_acc (Alg. 1 tests i_k > L but divides by L).  The update follows
+ * eq. update_lambda as printed: lambda grows when the acceptance estimate is
+ * above the target (the prose after it states the opposite direction; the
+ * equation agrees with adaptive scaling).  lambda is clamped to
+ * [lambda_min, lambda_max] (Sec. 7.1 limits it below by -30).  At most one
+ * update per region per epoch. */
+static void region_update(or_ctx* c)
+{
+    const or_params* p = &c->p;
+    for (int32_t k = 0; k < c->m; ++k) {
+        if (c->i[k] >= (uint64_t)p->L) {
+            double ah = (double)c->A[k] / (4294967296.0 * (double)c->i[k]);
+            int32_t sg = ah > p->alpha_star ? 1 : (ah < p->alpha_star ? -1 : 0);
+            if (c->uh) c->uh(c->user, k, c->i[k], c->A[k], ah, &sg);
+            double g = dmin(p->gamma_max, p->gamma_scale / sqrt((double)c->n[k]));  /* eq. step_size_n */
+            double lam = c->lam[k] + g * (double)sg;                                  /* eq. update_lambda */
+            if (lam < p->lambda_min) lam = p->lambda_min;
+            if (lam > p->lambda_max) lam = p->lambda_max;
+            c->lam[k] = lam;
+            c->n[k] += 1;
+            c->i[k] = 0;
+            c->A[k] = 0;
+        }
+        c->sig[k] = sigma_of_lambda(c->lam[k]);
+    }
+}
+
+/* Region-weighted target (extension, not in the paper; modelled on two-stage
+ * MLT, Sec. 8): w_k tracks the region's share of the true target, so pi / w
+ * spreads the chains evenly over the regions.  Binary64, fixed region order. */
+static void weight_update(or_ctx* c)
+{
+    double m = (double)c->m, S = 0.0;
+    for (int32_t k = 0; k < c->m; ++k) S += c->w[k] * (double)(c->h[k] - c->h_prev[k]);
+    if (S > 0) {
+        for (int32_t k = 0; k < c->m; ++k) c->Rc[k] += c->w[k] * (double)(c->h[k] - c->h_prev[k]) / S;
+        double T = 0.0;
+        for (int32_t k = 0; k < c->m; ++k) T += c->Rc[k];
+        for (int32_t k = 0; k < c->m; ++k) c->w[k] = m * dmax(c->Rc[k] / T, c->p.w_floor / m);
+    }
+    memcpy(c->h_prev, c->h, sizeof(uint64_t) * (size_t)c->m);
+}
+
+/* Bootstrap (Sec. 3.2: b estimated by independent MC in a preprocess) and the
+ * initial states, drawn in proportion to pi by stratified inverse CDF.
+ * Reading: the paper does not say how initial paths are chosen. */
+int32_t or_init(or_ctx* c)
+{
+    const or_params* p = &c->p;
+    int64_t nb = p->n_bootstrap;
+    if (nb <= 0) return -1;
+    double* cum = (double*)malloc(sizeof(double) * (size_t)nb);
+    uint32_t q[OR_MAX_DIM];
+    double f[3], acc = 0.0;
+    for (int64_t s = 0; s < nb; ++s) {
+        for (int32_t j = 0; 4 * j < c->D; ++j) {
+            uint32_t r[4];
+            draw(p->seed, (uint64_t)s, 0xFFFFFFFFu, 0x8000u + (uint32_t)j, r);
+            for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) q[4 * j + a] = r[a];
+        }
+        if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
+        acc += luminance(f);
+        cum[s] = acc;
+        c->Bk[or_region_of(c, q)] += luminance(f);
+    }
+    c->st[7] = (uint64_t)nb;
+    c->nU = (uint64_t)nb;
+    c->bhat = acc / (double)nb;
+    for (int32_t ch = 0; ch < p->n_chains; ++ch) {
+        int64_t sel;
+        if (acc > 0) {
+            double target = ((double)ch + 0.5) / (double)p->n_chains * acc;
+            int64_t lo = 0, hi = nb - 1;
+            while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (cum[mid] > target) hi = mid; else lo = mid + 1; }
+            sel = lo;
+        } else {
+            sel = ch % nb;
+        }
+        c->boot[ch] = sel;
+        uint32_t* qc = &c->q[(size_t)ch * c->D];
+        for (int32_t j = 0; 4 * j < c->D; ++j) {
+            uint32_t r[4];
+            draw(p->seed, (uint64_t)sel, 0xFFFFFFFFu, 0x8000u + (uint32_t)j, r);
+            for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) qc[4 * j + a] = r[a];
+        }
+        or_path_eval(c->s, p->width, p->height, p->max_depth, qc, &c->f[3 * ch], NULL, NULL);
+        c->pi[ch] = luminance(&c->f[3 * ch]);
+        c->k[ch] = or_region_of(c, qc);
+    }
+    free(cum);
+    /* Alg. 1 lines 2-6: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
+    for (int32_t k = 0; k < c->m; ++k) {
+        c->lam[k] = p->lambda_init;
+        c->n[k] = 1;
+        c->i[k] = c->A[k] = c->h[k] = c->h_prev[k] = 0;
+        c->w[k] = 1.0;
+        c->Rc[k] = 0.0;
+        c->sig[k] = sigma_of_lambda(c->lam[k]);
+    }
+    c->mut = 0;
+    c->inited = 1;
+    return 0;
+}
+
+int32_t or_run_epochs(or_ctx* c, int64_t n_epochs)
+{
+    if (!c->inited) return -1;
+    for (int64_t e = 0; e < n_epochs; ++e) {
+        uint64_t mut0 = c->mut;
+        for (uint32_t ch = 0; ch < (uint32_t)c->p.n_chains; ++ch) {
+            c->mut = mut0;
+            for (int32_t j = 0; j < c->p.epoch_len; ++j) {
+                mutate(c, ch);
+                c->mut++;
+            }
+        }
+        region_update(c);
+        if (c->p.target_mode) weight_update(c);
+    }
+    return 0;
+}
+
+/* Plain target: I_j = (b / N) sum_i f(x_i) / pi(x_i) over the chain states
+ * at pixel j (Sec. 3.2), times W H for radiance units.
+ * Region-weighted target (extension): the target changes between epochs, so
+ * the chains' region occupancy lags behind it; within one region w is
+ * constant and the visits follow pi restricted to the region.  Each region is
+ * therefore normalised by its own mass, I_j = B_k sum_i f / pi / h_k, with
+ * B_k = int_{P_k} pi estimated from the uniform samples (bootstrap and large
+ * steps).  At equilibrium h_k / N = B_k / b and both forms agree. */
+void or_read_image(const or_ctx* c, double* out)
+{
+    const or_params* p = &c->p;
+    double N = (double)c->mut * (double)p->n_chains;
+    double WH = (double)p->width * (double)p->height;
+    for (int32_t y = 0; y < p->height; ++y)
+        for (int32_t x = 0; x < p->width; ++x) {
+            double s;
+            if (!p->target_mode) {
+                s = N > 0 ? c->bhat * WH / N : 0.0;
+            } else {
+                int32_t k = x / p->region_px + (y / p->region_px) * c->nx;
+                s = (c->h[k] > 0 && c->nU > 0) ? WH * (c->Bk[k] / (double)c->nU) / (double)c->h[k] : 0.0;
+            }
+            size_t o = ((size_t)y * p->width + x) * 3;
+            for (int a = 0; a < 3; ++a) out[o + a] = c->img[o + a] * s;
+        }
+}
+
+int32_t or_dims(const or_ctx* c) { return c->D; }
+int32_t or_regions(const or_ctx* c) { return c->m; }
+uint64_t or_mutations_done(const or_ctx* c) { return c->mut; }
+double or_bhat(const or_ctx* c) { return c->bhat; }
+uint32_t* or_state_q(or_ctx* c) { return c->q; }
+double* or_state_f(or_ctx* c) { return c->f; }
+double* or_state_pi(or_ctx* c) { return c->pi; }
+int32_t* or_state_k(or_ctx* c) { return c->k; }
+int64_t* or_boot_choice(or_ctx* c) { return c->boot; }
+double* or_lambda(or_ctx* c) { return c->lam; }
+int64_t* or_n_updates(or_ctx* c) { return c->n; }
+uint64_t* or_visits(or_ctx* c) { return c->i; }
+uint64_t* or_accsum(or_ctx* c) { return c->A; }
+uint64_t* or_hist(or_ctx* c) { return c->h; }
+double* or_weight(or_ctx* c) { return c->w; }
+float* or_sigma(or_ctx* c) { return c->sig; }
+double* or_image_acc(or_ctx* c) { return c->img; }
+void or_stats(const or_ctx* c, uint64_t out[8]) { memcpy(out, c->st, sizeof c->st); }

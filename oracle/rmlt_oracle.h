@@ -1,0 +1,131 @@
+/*
+ * CPU oracle for Regional Adaptive Metropolis Light Transport (Otsu, Herveau,
+ * Hanika, Nowrouzezahrai, Dachsbacher) restated in primary sample space.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The product path (the
+ * CUDA library) never includes, links or calls it, and this code includes
+ * nothing from the product.
+ *
+ * Plain, slow, single-threaded, binary64 everywhere except where a floating
+ * point value decides an integer that both sides must agree on bit for bit
+ * (the quantised small-step offset and the per-region step scale sigma_k):
+ * those are taken in binary32 with an explicitly ordered sequence of
+ * correctly rounded operations, the same precision the kernel decides them in.
+ *
+ * Section / equation references are to the paper:
+ *   Sec. 3.1  path integral, I_j = int h_j f dmu; target pi = l(f)
+ *   Sec. 3.2  MH acceptance, estimator I_j ~ (b/N) sum f/pi, strategy mixture
+ *   Sec. 3.3  perturbation kernels parameterised by a scale sigma
+ *   Sec. 5.2  state-dependent proposal T(.|x) = sum_k 1_{P_k}(x) T_k(.|x)
+ *   Sec. 5.3  est_exp_acc (acceptance estimate), update_lambda, step_size_n
+ *   Sec. 5.4  2-D screen-space partition
+ *   Alg. 1    regional adaptive sample generation
+ *   App. B    region independence, b_k = P(x in P_k)
+ */
+#ifndef RMLT_ORACLE_H
+#define RMLT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* 2^t in binary32 (own routine: rint range reduction + degree-7 Taylor). */
+float or_exp2_f32(float t);
+
+/* Magnitude (units of 2^-32) of one Kelemen small-step offset. */
+int64_t or_kelemen_delta(uint32_t xmag, float sigma_s2, float log2_ratio);
+
+typedef struct or_scene or_scene;
+typedef struct or_ctx or_ctx;
+
+typedef struct {
+    int32_t  n_chains;
+    int32_t  width, height, region_px;
+    int32_t  max_depth;        /* d: surface interactions; D = 2 + 5 d      */
+    int32_t  epoch_len;        /* E mutations per chain between updates      */
+    int32_t  L;                /* visits before a region update (Alg. 1)     */
+    int32_t  target_mode;      /* 0 plain pi, 1 region-weighted pi / w_k     */
+    int64_t  n_bootstrap;
+    uint64_t seed;
+    double   p_large, s1, s2;
+    double   alpha_star, gamma_max, gamma_scale;
+    double   lambda_init, lambda_min, lambda_max;
+    double   w_floor;
+    int32_t  debug_flags;      /* tests only: bit 0 drops the reverse-kernel factor */
+    int32_t  pad_;
+} or_params;
+
+/* Per-mutation hook (tests only): sees the proposal and may override the
+ * proposal's contribution, acceptance probability and decision. */
+typedef void (*or_mut_hook)(void* user, uint32_t chain, uint64_t mut,
+                            const uint32_t* qy, int32_t D, int32_t large,
+                            int32_t early_reject, double margin, double xi_accept,
+                            double* f_y, double* a, int32_t* accept);
+/* Region-update hook (tests only): may override sgn(alpha_hat - alpha*). */
+typedef void (*or_upd_hook)(void* user, int32_t k, uint64_t i_k, uint64_t A_k,
+                            double alpha_hat, int32_t* sign);
+
+or_scene* or_scene_create(int32_t nv, const float* verts, int32_t nt, const uint32_t* tris,
+                          const uint32_t* mat_id, int32_t nm, const int32_t* mat_type,
+                          const float* albedo, const float* emission, const float* roughness,
+                          const float* camera, int32_t use_bvh);
+or_scene* or_scene_create_toy(const double* params10);
+void      or_scene_destroy(or_scene* s);
+double    or_scene_scale(const or_scene* s);
+
+/* Closest hit along o + t d, t in (tmin, tmax).  Returns 1 on hit.
+ * margin (optional): distance of the decision from flipping, scene-relative. */
+int32_t or_closest_hit(const or_scene* s, const double o[3], const double d[3],
+                       double tmin, double tmax, int32_t brute,
+                       double* t_out, int32_t* tri_out, double* margin);
+/* Any hit in (tmin, tmax).  Returns 1 if occluded. */
+int32_t or_any_hit(const or_scene* s, const double o[3], const double d[3],
+                   double tmin, double tmax, int32_t brute, double* margin);
+
+/* Path contribution f(u) of a primary-sample vector q (D = 2 + 5 max_depth
+ * words).  counts (optional): counts[0] += rays cast; [1], [2] unused. */
+int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                     const uint32_t* q, double f[3], double* margin, uint64_t counts[3]);
+
+or_ctx*  or_ctx_create(const or_scene* s, const or_params* p);
+void     or_ctx_destroy(or_ctx* c);
+void     or_set_hooks(or_ctx* c, or_mut_hook mh, or_upd_hook uh, void* user);
+int32_t  or_init(or_ctx* c);                       /* bootstrap + initial states */
+int32_t  or_run_epochs(or_ctx* c, int64_t n_epochs);
+void     or_read_image(const or_ctx* c, double* out_rgb);   /* H*W*3 radiance */
+
+int32_t   or_dims(const or_ctx* c);
+int32_t   or_regions(const or_ctx* c);
+int32_t   or_region_of(const or_ctx* c, const uint32_t* q);
+uint64_t  or_mutations_done(const or_ctx* c);       /* per chain */
+double    or_bhat(const or_ctx* c);
+uint32_t* or_state_q(or_ctx* c);      /* [C][D] */
+double*   or_state_f(or_ctx* c);      /* [C][3] */
+double*   or_state_pi(or_ctx* c);     /* [C]    */
+int32_t*  or_state_k(or_ctx* c);      /* [C]    */
+int64_t*  or_boot_choice(or_ctx* c);  /* [C]    */
+double*   or_lambda(or_ctx* c);       /* [m]    */
+int64_t*  or_n_updates(or_ctx* c);    /* [m]    */
+uint64_t* or_visits(or_ctx* c);       /* i_k [m] */
+uint64_t* or_accsum(or_ctx* c);       /* A_k [m], fixed point 2^-32 */
+uint64_t* or_hist(or_ctx* c);         /* h_k [m] */
+double*   or_weight(or_ctx* c);       /* w_k [m] */
+float*    or_sigma(or_ctx* c);        /* sigma_k [m] binary32 */
+double*   or_image_acc(or_ctx* c);    /* [H][W][3] unnormalised */
+void      or_stats(const or_ctx* c, uint64_t out[8]);
+/* Acceptance probability of moving x -> y under the current region tables
+ * (regions taken from the states; large = 1 for the independent large step). */
+double    or_accept_prob(const or_ctx* c, const uint32_t* qx, const uint32_t* qy,
+                         double pi_x, double pi_y, int32_t large);
+/* out: mutations, accepted, large, small, early_reject, invalid, rays, boot */
+
+#ifdef __cplusplus
+}
+#endif
+#endif
