@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the regional adaptive PSS-MLT chain step on one or more GB300s.
+
+Workload (default): the two-rooms / 5 cm door-gap scene, 200k triangles
+(seeded tessellated spheres and tori, 50 % Lambert, 50 % GGX), 512 x 512
+image, 16-px regions (1024 regions), path depth <= 10 with next-event
+estimation (D = 52), 2^16 chains, large-step probability 0.3, Kelemen small
+steps s1 = 1/1024, s2 = 1/64, host-built SAH BVH, binary32 tracing.
+
+One step = rmlt_step(1024): 1024 mutations of every chain (64 epochs of 16,
+each epoch = one chain-kernel launch + one region-update launch).  The
+metric is mutations/s (and rays/s) of the whole job; the image is the
+regional adaptive estimate (plain target) and the L2 is flushed between
+timed steps by writing a 256 MiB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+# FP32 operations the traversal needs per BVH node visit (both child boxes:
+# 6 FMA + 6 min + 6 max per slab test, 2 compares) and per ray-triangle test
+# (Moller-Trumbore: 2 cross products, 3 dot products, a reciprocal, 3 scales,
+# 4 compares); an FMA counts as 2 floating-point operations.
+FLOPS_PER_NODE = 2 * (6 * 2 + 12) + 2          # 50
+FLOPS_PER_TRI = 2 * (6 * 2) + 3 * 5 + 3 + 1 + 3 + 4   # 50
+BYTES_PER_NODE = 64
+BYTES_PER_TRI = 48
+SM_COUNT = 152
+FP32_LANES = 128
+
+WORKLOADS = {
+    "two_rooms": dict(desc="two rooms joined by a 5 cm door gap, 200k triangles, 512x512, 16-px "
+                           "regions, depth 10, 2^16 chains x 1024 mutations",
+                      scene=("two_rooms", dict(n_tris=200_000, seed=0)),
+                      params=dict(n_chains=1 << 16, width=512, height=512, region_px=16,
+                                  max_depth=10, epoch_len=16, n_bootstrap=1 << 20, p_large=0.3,
+                                  seed=1),
+                      mutations=1024, cpu_chains=2048, cpu_epochs=4),
+    "cornell": dict(desc="Cornell box, 34+2 triangles (brute force), 64x64, 8-px regions, depth 5, "
+                         "64 chains x 1e4 mutations",
+                    scene=("cornell_box", {}),
+                    params=dict(n_chains=64, width=64, height=64, region_px=8, max_depth=5,
+                                epoch_len=16, n_bootstrap=1 << 16, p_large=0.3, seed=1),
+                    mutations=10000, cpu_chains=64, cpu_epochs=200),
+    "corridor": dict(desc="glossy corridor lit through a slit, 2M triangles, 1920x1080, 32-px "
+                          "regions, depth 12, 2^20 chains x 256 mutations",
+                     scene=("glossy_corridor", dict(n_tris=2_000_000, seed=0)),
+                     params=dict(n_chains=1 << 20, width=1920, height=1080, region_px=32,
+                                 max_depth=12, epoch_len=16, n_bootstrap=1 << 21, p_large=0.3,
+                                 seed=1),
+                     mutations=256, cpu_chains=1024, cpu_epochs=2),
+}
+
+
+def make_scene(w):
+    from paper_2402_08273_gb300 import scenes
+    name, kw = w["scene"]
+    return getattr(scenes, name)(**kw)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample(w, chains: int, epochs: int) -> dict:
+    """Time the CPU oracle (single thread, as it stands) on a bounded sample of
+    the workload: `chains` chains x `epochs` epochs, the bootstrap excluded."""
+    import oracle
+    scene = make_scene(w)
+    p = dict(w["params"])
+    p.update(n_chains=chains, n_bootstrap=chains)
+    osc = oracle.Scene(scene, use_bvh=True)
+    keys = ("n_chains", "width", "height", "region_px", "max_depth", "epoch_len", "n_bootstrap",
+            "p_large", "seed")
+    ch = oracle.Chains(osc, **{k: p[k] for k in keys})
+    ch.init()
+    t0 = time.perf_counter()
+    ch.run_epochs(epochs)
+    dt = time.perf_counter() - t0
+    st = ch.stats()
+    n_mut = chains * epochs * p["epoch_len"]
+    return {"value": n_mut / dt, "unit": "mutations/s", "rays_per_s": st["rays"] / dt, "cores": 1,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{chains} chains x {epochs * p['epoch_len']} mutations of the same scene and "
+                      f"parameters (bootstrap excluded), single-threaded binary64 oracle"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(w, max(64, w["cpu_chains"] // 8), 1)
+    cpu = None
+    for _ in range(args.steps):
+        cpu = oracle_sample(w, max(64, w["cpu_chains"] // 8), 1)
+        vals.append(cpu["value"])
+    v = statistics.median(vals)
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": "mutations/s", "value": v, "unit": "mutations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cpu["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "mutations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+    from paper_2402_08273_gb300 import rmlt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    scene = make_scene(w)
+    params = dict(w["params"])
+    params["seed"] = params["seed"] + rank      # independent chain population per GPU
+    M = w["mutations"]
+    stream = torch.cuda.Stream(device=dev)
+    R = rmlt.Renderer(device=local, stream=stream)
+    t0 = time.perf_counter()
+    R.load_scene(scene)
+    t_load = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    R.init_chains(**params)
+    R.synchronize()
+    t_init = time.perf_counter() - t0
+    C = params["n_chains"]
+    epochs_per_step = -(-M // params["epoch_len"])
+
+    for _ in range(args.warmup):
+        R.step(M)
+    R.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st0 = R.read_stats()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.step(M)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    t_dev = sum(step_ms) / 1e3
+    st1 = R.read_stats()
+    t_max = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_max = float(t_max.item())
+    mutations = C * M * args.steps * world
+    rays = (st1["rays"] - st0["rays"]) * world
+    value = mutations / t_max
+
+    # end to end through the public API: the step plus the image and region
+    # histogram read into pinned host memory every step
+    img_h = torch.empty((params["height"], params["width"], 3), dtype=torch.float64).pin_memory()
+    hist_h = torch.empty(R.m, dtype=torch.int64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        R.step(M)
+        R.read_image(out=img_h.numpy())
+        R.read_region_hist(out=hist_h.numpy().view("uint64"))
+    torch.cuda.synchronize()
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = mutations / float(t_e2e.item())
+    d2h = img_h.numel() * 8 + hist_h.numel() * 8
+
+    # work per ray from one instrumented step (same kernel with counters on)
+    R.set_work_counters(True)
+    sa = R.read_stats()
+    R.step(params["epoch_len"] * 4)
+    sb = R.read_stats()
+    R.set_work_counters(False)
+    dr = max(1, sb["rays"] - sa["rays"])
+    nodes_per_ray = (sb["node_visits"] - sa["node_visits"]) / dr
+    tris_per_ray = (sb["tri_tests"] - sa["tri_tests"]) / dr
+    flops_ray = nodes_per_ray * FLOPS_PER_NODE + tris_per_ray * FLOPS_PER_TRI
+    bytes_ray = nodes_per_ray * BYTES_PER_NODE + tris_per_ray * BYTES_PER_TRI
+    rays_per_s_gpu = rays / world / t_max
+    clk_mhz = clk["sm_mhz"] or 1965.0
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
+    achieved = flops_ray * rays_per_s_gpu / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "chain_epoch_kernel",
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock "
+                               f"{clk_mhz:.0f} MHz sampled during the timed region",
+                "per_ray": {"nodes": nodes_per_ray, "tris": tris_per_ray, "flops": flops_ray,
+                            "bytes": bytes_ray}}
+    try:
+        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+        hbm = float(peaks["hbm_gbs"])
+        roofline["node_fetch_gbs"] = bytes_ray * rays_per_s_gpu / 1e9
+        roofline["node_fetch_frac_of_measured_hbm"] = roofline["node_fetch_gbs"] / hbm
+    except Exception:
+        pass
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, w["cpu_chains"], w["cpu_epochs"])
+        cpu["rays_per_s"] = cpu["rays_per_s"]
+
+    if rank == 0:
+        line = {
+            "metric": "mutations/s", "value": value, "unit": "mutations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "chains_per_gpu": C,
+                       "mutations_per_step": M, "epochs_per_step": epochs_per_step,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"{world} independent chain populations (one per GPU)"},
+            "rays_per_s": rays / t_max,
+            "rays_per_mutation": rays / mutations,
+            "gpu_launches": 2 * epochs_per_step * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "mutations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h,
+                    "note": "rmlt_step + image and region histogram read to pinned host memory"},
+            "clocks": clk,
+            "setup_s": {"scene_load_and_bvh": t_load, "init_chains_bootstrap": t_init},
+            "stats": {k: st1[k] for k in ("accepted", "large", "small", "early_reject",
+                                          "invalid_paths", "stack_overflow")},
+        }
+        print(json.dumps(line), flush=True)
+    R.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default="two_rooms")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * rmlt — regional adaptive primary-sample-space Metropolis light transport on
+ * one GB300 (sm_103a).  C ABI of the CUDA library librmlt.so.
+ *
+ * The method is Regional Adaptive Metropolis Light Transport (Otsu, Herveau,
+ * Hanika, Nowrouzezahrai, Dachsbacher): many Metropolis chains whose small-step
+ * scale sigma_k = sqrt(exp(lambda_k)) is adapted per screen region k by the
+ * Robbins-Monro rule of Alg. 1 (eqs. est_exp_acc, update_lambda,
+ * step_size_n; Sec. 5.3) over the 2-D screen-space grid partition of
+ * Sec. 5.4 / 6.1, with the MLT estimator I_j = (b/N) sum f/pi of Sec. 3.2.
+ *
+ * Conventions
+ *  - Every function returns an rmlt_status; negative values are errors and
+ *    rmlt_last_error() gives a message for the calling thread.  No C++
+ *    exception or abort crosses this boundary.
+ *  - Call order: rmlt_create -> rmlt_load_scene | rmlt_load_toy_integrand ->
+ *    rmlt_init_chains -> rmlt_step* -> rmlt_read_* .  Out-of-order calls return
+ *    RMLT_E_STATE and change nothing.  Loading a new scene discards the chains.
+ *  - Input arrays are read during the call and copied; the caller keeps them.
+ *  - Output buffers are caller-owned and may be host or device pointers (the
+ *    library asks the CUDA driver which); device outputs are written on the
+ *    context's stream and the call synchronises that stream before returning.
+ *  - Device memory the library needs is obtained from the allocator installed
+ *    with rmlt_set_allocator (the Python binding installs PyTorch's caching
+ *    allocator), else from cudaMalloc.
+ *  - A failed rmlt_step marks the context failed: later steps and reads return
+ *    RMLT_E_STATE; rmlt_destroy is always safe.
+ */
+#ifndef RMLT_H
+#define RMLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RMLT_ABI_VERSION 1
+#define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
+
+typedef struct rmlt_ctx rmlt_ctx;
+
+typedef enum {
+    RMLT_OK = 0,
+    RMLT_E_INVALID_ARG = -1,
+    RMLT_E_INVALID_SCENE = -2,
+    RMLT_E_OOM = -3,
+    RMLT_E_CUDA = -4,
+    RMLT_E_STATE = -5,     /* wrong call order, or the context failed earlier */
+    RMLT_E_TIMEOUT = -6,   /* a bounded device-side wait expired */
+    RMLT_E_OVERFLOW = -7,  /* reserved */
+    RMLT_E_IO = -8
+} rmlt_status;
+
+typedef enum { RMLT_LAMBERT = 0, RMLT_GGX = 1 } rmlt_material_type;
+typedef enum { RMLT_TARGET_PLAIN = 0, RMLT_TARGET_REGION_WEIGHTED = 1 } rmlt_target_mode;
+
+typedef struct {
+    int32_t type;          /* rmlt_material_type */
+    float albedo[3];       /* Lambert albedo, or GGX Fresnel F0 (Schlick) */
+    float emission[3];     /* radiance emitted from the front face (counter-clockwise winding) */
+    float roughness;       /* GGX alpha */
+} rmlt_material;
+
+typedef struct {
+    float pos[3], look_at[3], up[3];
+    float vfov_deg;        /* vertical field of view of the pinhole camera */
+} rmlt_camera;
+
+typedef struct {
+    int32_t n_verts;
+    const float* verts;        /* [n_verts][3] host */
+    int32_t n_tris;
+    const uint32_t* tris;      /* [n_tris][3] vertex indices, host */
+    const uint32_t* mat_id;    /* [n_tris] host */
+    int32_t n_mats;
+    const rmlt_material* mats; /* [n_mats] host */
+    rmlt_camera camera;
+    int32_t brute_force_max;   /* scenes with n_tris <= this skip the BVH (0: default 64) */
+} rmlt_scene_desc;
+
+/* Chain parameters (Alg. 1 and Sec. 7.1 names).  D = 2 + 5 max_depth. */
+typedef struct {
+    int32_t n_chains;          /* C independent chains */
+    int32_t width, height;     /* image size W x H */
+    int32_t region_px;         /* grid partition: regions of region_px^2 pixels (Sec. 6.1) */
+    int32_t max_depth;         /* d surface interactions, NEE at each, 1..RMLT_MAX_DEPTH (0: toy) */
+    int32_t epoch_len;         /* E mutations per chain between region updates */
+    int32_t L;                 /* visits per region before an update (Alg. 1) */
+    int32_t target_mode;       /* rmlt_target_mode */
+    int64_t n_bootstrap;       /* uniform samples for b and the initial states (Sec. 3.2) */
+    uint64_t seed;             /* Philox4x32-10 key */
+    double p_large;            /* probability of the large (independent) step */
+    double s1, s2;             /* Kelemen small-step offset range [sigma s1, sigma s2] */
+    double alpha_star;         /* target acceptance (Sec. 5.3; 0.5 in Sec. 7.1) */
+    double gamma_max, gamma_scale;  /* eq. step_size_n */
+    double lambda_init, lambda_min, lambda_max;
+    double w_floor;            /* region-weighted target: lower bound of w_k as a share of 1/m */
+} rmlt_chain_params;
+
+typedef struct {
+    uint64_t mutations;        /* per chain, since rmlt_init_chains */
+    uint64_t accepted, large, small, early_reject, invalid_paths;
+    uint64_t rays;             /* closest-hit + shadow rays traced by rmlt_step */
+    uint64_t stack_overflow;   /* paths dropped because the traversal stack overflowed */
+    uint64_t epochs;
+    double bhat;               /* bootstrap normaliser b (Sec. 3.2) */
+    int32_t n_regions, dims;
+    uint64_t node_visits;      /* BVH internal nodes visited (only while work counters are on) */
+    uint64_t tri_tests;        /* ray-triangle tests in BVH leaves (only while work counters are on) */
+} rmlt_stats;
+
+/* One record per traced mutation (test instrument, see rmlt_set_trace). */
+typedef struct {
+    float f[3];                /* contribution of the proposal y (0 if rejected early) */
+    float a;                   /* acceptance probability */
+    uint32_t qhash;            /* FNV-1a of the proposal's D words */
+    uint32_t flags;            /* bit 0 accepted, 1 large step, 2 early reject, 3 invalid */
+} rmlt_trace_record;
+
+typedef void* (*rmlt_alloc_fn)(void* user, size_t bytes, void* stream);
+typedef void (*rmlt_free_fn)(void* user, void* ptr, void* stream);
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: RMLT_E_INVALID_ARG (out NULL), RMLT_E_CUDA (no device). */
+rmlt_status rmlt_create(rmlt_ctx** out, int device, void* cuda_stream);
+
+/* Route the context's device allocations through alloc/free (both non-NULL),
+ * or back to cudaMalloc/cudaFree (both NULL).  Only before rmlt_load_scene. */
+rmlt_status rmlt_set_allocator(rmlt_ctx* ctx, rmlt_alloc_fn alloc, rmlt_free_fn free_fn, void* user);
+
+/* Copy the scene, build a binned-SAH BVH on the host (or keep a flat list when
+ * n_tris <= brute_force_max) and upload nodes, triangles, materials and the
+ * light list (emitting triangles, sampled by area).  The paper's path integral
+ * (Sec. 3.1) is over this geometry.  Errors: RMLT_E_INVALID_SCENE (index out
+ * of range, non-finite vertex, unknown material type, no triangle),
+ * RMLT_E_OOM, RMLT_E_CUDA. */
+rmlt_status rmlt_load_scene(rmlt_ctx* ctx, const rmlt_scene_desc* scene);
+
+/* Test scene: D = 2, identity path map, f(u) = p0 + p1 1[u in box] +
+ * p6 exp(-|u - (p7, p8)|^2 / (2 p9^2)), box [p2,p3) x [p4,p5).  params: 10
+ * doubles, host.  Requires max_depth = 0 in rmlt_init_chains. */
+rmlt_status rmlt_load_toy_integrand(rmlt_ctx* ctx, const double* params);
+
+/* Allocate chain state and region tables, run the bootstrap (n_bootstrap
+ * uniform samples -> b, Sec. 3.2 "preprocess"), choose each chain's initial
+ * state by stratified inverse CDF of pi, and set lambda_k = lambda_init,
+ * i_k = A_k = 0, n_k = 1 (Alg. 1 lines 2-6).  Errors: RMLT_E_INVALID_ARG
+ * (non-positive sizes, max_depth out of range, s1 >= s2, p_large outside
+ * [0,1], lambda bounds outside [-150, 2 ln(1/(2 s2))] ...), RMLT_E_STATE (no
+ * scene), RMLT_E_OOM, RMLT_E_CUDA. */
+rmlt_status rmlt_init_chains(rmlt_ctx* ctx, const rmlt_chain_params* params);
+
+/* Advance every chain by n_mutations Metropolis-Hastings mutations (Alg. 1
+ * lines 8-19), rounded up to whole epochs of epoch_len, with the region
+ * update (Alg. 1 lines 13-18; at most one per region per epoch) at each epoch
+ * boundary.  Asynchronous on the context's stream (no host synchronisation);
+ * launch errors are returned here, execution errors at the next synchronising
+ * call.  A proposal whose ray overflows the traversal stack is given zero
+ * contribution and counted in rmlt_stats.stack_overflow. */
+rmlt_status rmlt_step(rmlt_ctx* ctx, uint64_t n_mutations);
+
+/* Image estimate, [height][width][3] doubles.  normalized = 1: radiance
+ * I_j * W * H with I_j = (b/N) sum_i f(x_i)/pi(x_i) (Sec. 3.2; region-weighted
+ * mode normalises each region by its own mass); normalized = 0: the raw sum
+ * of f/pi splats. */
+rmlt_status rmlt_read_image(rmlt_ctx* ctx, double* out_rgb, int normalized);
+
+/* Region visit histogram h_k (post-MH state of every mutation), [m] u64. */
+rmlt_status rmlt_read_region_hist(rmlt_ctx* ctx, uint64_t* out_h);
+
+/* Region parameters, each [m]; any pointer may be NULL.  lambda_k, n_k (update
+ * count, starts at 1), i_k and A_k (visits and 2^32-scaled acceptance sum since
+ * the region's last update), w_k (region weight; 1 in plain mode). */
+rmlt_status rmlt_read_region_params(rmlt_ctx* ctx, double* lambda, int64_t* n, uint64_t* i,
+                                    uint64_t* A, double* w);
+
+/* Chain states in the device's structure-of-arrays layout: q [D][n_chains]
+ * u32 primary-sample words (u = q 2^-32), f [3][n_chains] float contribution,
+ * k [n_chains] region.  Any may be NULL. */
+rmlt_status rmlt_read_chain_state(rmlt_ctx* ctx, uint32_t* q, float* f, int32_t* k);
+
+rmlt_status rmlt_read_stats(rmlt_ctx* ctx, rmlt_stats* out);
+
+/* Test instrument.  While set, rmlt_step writes one rmlt_trace_record per
+ * mutation of every chain c with c % chain_stride == 0, in the order
+ * [epoch][traced chain][mutation in epoch], to `records` (device memory, room
+ * for `capacity` records), and lambda after each epoch's update, [epoch][m]
+ * doubles, to `lambdas` (device, room for `lambda_capacity` doubles; may be
+ * NULL).  Tracing stops silently when a buffer is full.  records = NULL
+ * switches tracing off.  The traced kernel is the production kernel with the
+ * record stores enabled. */
+rmlt_status rmlt_set_trace(rmlt_ctx* ctx, rmlt_trace_record* records, uint64_t capacity,
+                           double* lambdas, uint64_t lambda_capacity, uint32_t chain_stride);
+
+/* Count BVH node visits and triangle tests in rmlt_stats (enable = 1), using
+ * an instrumented build of the same chain kernel; enable = 0 returns to the
+ * uninstrumented kernel.  The chain trajectory does not depend on it. */
+rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
+
+/* Bytes of device memory the context holds. */
+rmlt_status rmlt_memory_usage(rmlt_ctx* ctx, uint64_t* bytes);
+
+/* Checkpoint: chain state, region tables, image, counters, parameters and the
+ * mutation index (Philox counters make resume-then-run equal an uninterrupted
+ * run).  rmlt_restore needs the same scene loaded.  Errors: RMLT_E_IO,
+ * RMLT_E_INVALID_ARG (file from another scene or version). */
+rmlt_status rmlt_save(rmlt_ctx* ctx, const char* path);
+rmlt_status rmlt_restore(rmlt_ctx* ctx, const char* path);
+
+/* Wait for the context's stream; returns a pending execution error. */
+rmlt_status rmlt_synchronize(rmlt_ctx* ctx);
+
+void rmlt_destroy(rmlt_ctx* ctx);
+const char* rmlt_last_error(void);
+int rmlt_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

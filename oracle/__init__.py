@@ -80,6 +80,10 @@ def lib():
         "or_ctx_destroy": (None, [C.c_void_p]),
         "or_set_hooks": (None, [C.c_void_p, MUT_HOOK, UPD_HOOK, C.c_void_p]),
         "or_init": (C.c_int32, [C.c_void_p]),
+        "or_init_tables": (C.c_int32, [C.c_void_p]),
+        "or_refresh_sigma": (None, [C.c_void_p]),
+        "or_set_state": (C.c_int32, [C.c_void_p, C.c_uint32, u32p]),
+        "or_mutate_one": (C.c_int32, [C.c_void_p, C.c_uint32, C.c_uint64]),
         "or_run_epochs": (C.c_int32, [C.c_void_p, C.c_int64]),
         "or_read_image": (None, [C.c_void_p, f64p]),
         "or_dims": (C.c_int32, [C.c_void_p]),
@@ -234,6 +238,21 @@ class Chains:
     def init(self):
         if lib().or_init(self.h) != 0:
             raise RuntimeError("or_init failed")
+
+    def init_tables(self):
+        lib().or_init_tables(self.h)
+
+    def refresh_sigma(self):
+        lib().or_refresh_sigma(self.h)
+
+    def set_state(self, chain: int, q):
+        q = np.ascontiguousarray(q, np.uint32)
+        if lib().or_set_state(self.h, int(chain), _ptr(q, C.c_uint32)) != 0:
+            raise ValueError("bad chain index")
+
+    def mutate_one(self, chain: int, mut: int):
+        if lib().or_mutate_one(self.h, int(chain), int(mut)) != 0:
+            raise RuntimeError("or_mutate_one failed")
 
     def run_epochs(self, n: int):
         if lib().or_run_epochs(self.h, int(n)) != 0:

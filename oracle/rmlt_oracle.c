@@ -677,6 +677,8 @@ struct or_ctx {
     void* user;
 };
 
+int32_t or_init_tables(or_ctx* c);
+
 or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
 {
     if (!s || !p) return NULL;
@@ -926,56 +928,63 @@ static void weight_update(or_ctx* c)
     memcpy(c->h_prev, c->h, sizeof(uint64_t) * (size_t)c->m);
 }
 
-/* Bootstrap (Sec. 3.2: b estimated by independent MC in a preprocess) and the
- * initial states, drawn in proportion to pi by stratified inverse CDF.
- * Reading: the paper does not say how initial paths are chosen. */
+static void boot_sample(const or_ctx* c, uint64_t s, uint32_t* q)
+{
+    for (int32_t j = 0; 4 * j < c->D; ++j) {
+        uint32_t r[4];
+        draw(c->p.seed, s, 0xFFFFFFFFu, 0x8000u + (uint32_t)j, r);
+        for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) q[4 * j + a] = r[a];
+    }
+}
+
+/* Bootstrap (Sec. 3.2: b estimated by independent Monte Carlo in a
+ * preprocess) and the initial states.  Reading: the paper does not say how
+ * the initial paths are chosen.  Chain c owns the K = n_boot / C uniform
+ * samples s in [cK, (c+1)K) and picks one of them with probability
+ * pi_s / sum(pi) by weighted reservoir sampling (keep s when v_s cum_s < pi_s,
+ * v_s a uniform of its own).  b = sum of all pi / (K C). */
 int32_t or_init(or_ctx* c)
 {
     const or_params* p = &c->p;
-    int64_t nb = p->n_bootstrap;
-    if (nb <= 0) return -1;
-    double* cum = (double*)malloc(sizeof(double) * (size_t)nb);
+    int64_t K = p->n_bootstrap / p->n_chains;
+    if (K <= 0) return -1;
     uint32_t q[OR_MAX_DIM];
-    double f[3], acc = 0.0;
-    for (int64_t s = 0; s < nb; ++s) {
-        for (int32_t j = 0; 4 * j < c->D; ++j) {
-            uint32_t r[4];
-            draw(p->seed, (uint64_t)s, 0xFFFFFFFFu, 0x8000u + (uint32_t)j, r);
-            for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) q[4 * j + a] = r[a];
-        }
-        if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
-        acc += luminance(f);
-        cum[s] = acc;
-        c->Bk[or_region_of(c, q)] += luminance(f);
-    }
-    c->st[7] = (uint64_t)nb;
-    c->nU = (uint64_t)nb;
-    c->bhat = acc / (double)nb;
+    double f[3], total = 0.0;
+    memset(c->Bk, 0, sizeof(double) * (size_t)c->m);
     for (int32_t ch = 0; ch < p->n_chains; ++ch) {
-        int64_t sel;
-        if (acc > 0) {
-            double target = ((double)ch + 0.5) / (double)p->n_chains * acc;
-            int64_t lo = 0, hi = nb - 1;
-            while (lo < hi) { int64_t mid = lo + (hi - lo) / 2; if (cum[mid] > target) hi = mid; else lo = mid + 1; }
-            sel = lo;
-        } else {
-            sel = ch % nb;
+        double cum = 0.0;
+        int64_t sel = -1;
+        for (int64_t i = 0; i < K; ++i) {
+            uint64_t s = (uint64_t)ch * (uint64_t)K + (uint64_t)i;
+            boot_sample(c, s, q);
+            if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
+            double pis = luminance(f);
+            c->Bk[or_region_of(c, q)] += pis;
+            cum += pis;
+            uint32_t r[4];
+            draw(p->seed, s, 0xFFFFFFFFu, 0x7FFFu, r);
+            if (pis > 0 && u24(r[0]) * cum < pis) sel = (int64_t)s;
         }
+        if (sel < 0) sel = (int64_t)ch * K;
+        total += cum;
         c->boot[ch] = sel;
         uint32_t* qc = &c->q[(size_t)ch * c->D];
-        for (int32_t j = 0; 4 * j < c->D; ++j) {
-            uint32_t r[4];
-            draw(p->seed, (uint64_t)sel, 0xFFFFFFFFu, 0x8000u + (uint32_t)j, r);
-            for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) qc[4 * j + a] = r[a];
-        }
+        boot_sample(c, (uint64_t)sel, qc);
         or_path_eval(c->s, p->width, p->height, p->max_depth, qc, &c->f[3 * ch], NULL, NULL);
         c->pi[ch] = luminance(&c->f[3 * ch]);
         c->k[ch] = or_region_of(c, qc);
     }
-    free(cum);
-    /* Alg. 1 lines 2-6: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
+    c->st[7] = (uint64_t)(K * p->n_chains);
+    c->nU = (uint64_t)(K * p->n_chains);
+    c->bhat = total / (double)(K * p->n_chains);
+    return or_init_tables(c);
+}
+
+/* Alg. 1 lines 2-6: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
+int32_t or_init_tables(or_ctx* c)
+{
     for (int32_t k = 0; k < c->m; ++k) {
-        c->lam[k] = p->lambda_init;
+        c->lam[k] = c->p.lambda_init;
         c->n[k] = 1;
         c->i[k] = c->A[k] = c->h[k] = c->h_prev[k] = 0;
         c->w[k] = 1.0;
@@ -984,6 +993,32 @@ int32_t or_init(or_ctx* c)
     }
     c->mut = 0;
     c->inited = 1;
+    return 0;
+}
+
+void or_refresh_sigma(or_ctx* c)
+{
+    for (int32_t k = 0; k < c->m; ++k) c->sig[k] = sigma_of_lambda(c->lam[k]);
+}
+
+int32_t or_set_state(or_ctx* c, uint32_t chain, const uint32_t* q)
+{
+    if ((int64_t)chain >= c->p.n_chains) return -1;
+    uint32_t* qc = &c->q[(size_t)chain * c->D];
+    memcpy(qc, q, sizeof(uint32_t) * (size_t)c->D);
+    or_path_eval(c->s, c->p.width, c->p.height, c->p.max_depth, qc, &c->f[3 * chain], NULL, NULL);
+    c->pi[chain] = luminance(&c->f[3 * chain]);
+    c->k[chain] = or_region_of(c, qc);
+    return 0;
+}
+
+int32_t or_mutate_one(or_ctx* c, uint32_t chain, uint64_t mut)
+{
+    if (!c->inited || (int64_t)chain >= c->p.n_chains) return -1;
+    uint64_t keep = c->mut;
+    c->mut = mut;
+    mutate(c, chain);
+    c->mut = keep;
     return 0;
 }
 

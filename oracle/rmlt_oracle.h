@@ -97,6 +97,12 @@ or_ctx*  or_ctx_create(const or_scene* s, const or_params* p);
 void     or_ctx_destroy(or_ctx* c);
 void     or_set_hooks(or_ctx* c, or_mut_hook mh, or_upd_hook uh, void* user);
 int32_t  or_init(or_ctx* c);                       /* bootstrap + initial states */
+int32_t  or_init_tables(or_ctx* c);                /* region tables only (Alg. 1 lines 2-6) */
+void     or_refresh_sigma(or_ctx* c);              /* sigma_k from the current lambda_k */
+/* Set chain `chain` to state q; f, pi and k are recomputed by the oracle. */
+int32_t  or_set_state(or_ctx* c, uint32_t chain, const uint32_t* q);
+/* One mutation of one chain at mutation index `mut` (region tables updated). */
+int32_t  or_mutate_one(or_ctx* c, uint32_t chain, uint64_t mut);
 int32_t  or_run_epochs(or_ctx* c, int64_t n_epochs);
 void     or_read_image(const or_ctx* c, double* out_rgb);   /* H*W*3 radiance */
 

@@ -1,0 +1,776 @@
+// Host side of librmlt: the C ABI declared in include/rmlt.h.
+//
+// Owns the context (device, stream, allocator hooks, device buffers), checks
+// arguments, builds and uploads the scene, drives the epoch loop of the chain
+// kernel and the region update (Alg. 1), and copies results out.  Every
+// arithmetic step of the method runs in the CUDA kernels (rmlt_kernels.cu).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rmlt.h"
+#include "rmlt_internal.h"
+
+using namespace rmlt;
+
+namespace {
+
+thread_local std::string g_err;
+
+rmlt_status fail(rmlt_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+rmlt_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(RMLT_E_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(RMLT_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct Alloc {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+uint64_t fnv64(const void* data, size_t n, uint64_t h)
+{
+    const unsigned char* p = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+}  // namespace
+
+struct rmlt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    rmlt_alloc_fn af = nullptr;
+    rmlt_free_fn ff = nullptr;
+    void* au = nullptr;
+    std::vector<Alloc> scene_mem, chain_mem;
+    uint64_t held = 0;
+
+    bool have_scene = false, have_chains = false, failed = false;
+    DevScene S;
+    double tan_half = 1.0;
+    uint64_t scene_hash = 0;
+
+    rmlt_chain_params P{};
+    DevChains Ch;
+    uint64_t mut = 0, epochs = 0;
+    int64_t n_boot = 0;
+    double* d_total = nullptr;   // bootstrap sum of pi (device, binary64)
+    double* d_stage = nullptr;   // image read-out staging [H][W][3]
+
+    rmlt_trace_record* tr = nullptr;
+    uint64_t tr_cap = 0, tr_epoch = 0;
+    double* tr_lam = nullptr;
+    uint64_t tr_lam_cap = 0;
+    uint32_t tr_stride = 1;
+    bool count_work = false;
+
+    rmlt_status dalloc(std::vector<Alloc>& pool, size_t bytes, void** out)
+    {
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        if (af) {
+            p = af(au, bytes, (void*)stream);
+            if (!p) return fail(RMLT_E_OOM, "allocator returned NULL for %zu bytes", bytes);
+        } else {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(RMLT_E_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+            }
+        }
+        pool.push_back({p, bytes});
+        held += bytes;
+        *out = p;
+        return RMLT_OK;
+    }
+    void release(std::vector<Alloc>& pool)
+    {
+        if (!pool.empty()) cudaStreamSynchronize(stream);
+        for (auto& a : pool) {
+            if (ff) ff(au, a.p, (void*)stream);
+            else cudaFree(a.p);
+            held -= a.bytes;
+        }
+        pool.clear();
+    }
+    template <class T>
+    rmlt_status alloc_n(std::vector<Alloc>& pool, size_t n, T** out)
+    {
+        return dalloc(pool, n * sizeof(T), (void**)out);
+    }
+};
+
+namespace {
+
+rmlt_status enter(rmlt_ctx* c)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return RMLT_OK;
+}
+
+rmlt_status sync(rmlt_ctx* c, const char* what)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(e, what);
+    }
+    return RMLT_OK;
+}
+
+// copy `bytes` from device memory to a caller buffer (host or device)
+rmlt_status copy_out(rmlt_ctx* c, void* dst, const void* src, size_t bytes)
+{
+    if (!dst || bytes == 0) return RMLT_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream), "copy out");
+    return RMLT_OK;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+}  // namespace
+
+extern "C" {
+
+int rmlt_abi_version(void) { return RMLT_ABI_VERSION; }
+
+const char* rmlt_last_error(void) { return g_err.c_str(); }
+
+rmlt_status rmlt_create(rmlt_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(RMLT_E_CUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= n) return fail(RMLT_E_INVALID_ARG, "device %d out of range [0,%d)", device, n);
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    CK(cudaFree(nullptr), "context init");
+    rmlt_ctx* c = new (std::nothrow) rmlt_ctx();
+    if (!c) return fail(RMLT_E_OOM, "host allocation failed");
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_allocator(rmlt_ctx* c, rmlt_alloc_fn alloc, rmlt_free_fn free_fn, void* user)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(RMLT_E_INVALID_ARG, "alloc and free must both be set or both be NULL");
+    if (!c->scene_mem.empty() || !c->chain_mem.empty()) return fail(RMLT_E_STATE, "allocator must be set before any device memory is held");
+    c->af = alloc;
+    c->ff = free_fn;
+    c->au = user;
+    return RMLT_OK;
+}
+
+static void drop_chains(rmlt_ctx* c)
+{
+    c->release(c->chain_mem);
+    c->have_chains = false;
+    c->failed = false;
+    c->Ch = DevChains();
+    c->d_total = c->d_stage = nullptr;
+    c->tr = nullptr;
+    c->tr_lam = nullptr;
+}
+
+rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!s) return fail(RMLT_E_INVALID_ARG, "scene is NULL");
+    if (s->n_tris <= 0 || s->n_verts <= 0 || s->n_mats <= 0 || !s->verts || !s->tris || !s->mat_id || !s->mats)
+        return fail(RMLT_E_INVALID_SCENE, "scene needs vertices, triangles, material ids and materials");
+    if (s->n_tris >= (1 << 28)) return fail(RMLT_E_INVALID_SCENE, "at most 2^28 - 1 triangles");
+    const int brute_max = s->brute_force_max > 0 ? s->brute_force_max : 64;
+    if (brute_max > 4096) return fail(RMLT_E_INVALID_ARG, "brute_force_max above 4096");
+    for (int i = 0; i < s->n_verts; ++i)
+        if (!finite3(&s->verts[3 * (size_t)i])) return fail(RMLT_E_INVALID_SCENE, "vertex %d is not finite", i);
+    for (int m = 0; m < s->n_mats; ++m) {
+        const rmlt_material& M = s->mats[m];
+        if (M.type != RMLT_LAMBERT && M.type != RMLT_GGX) return fail(RMLT_E_INVALID_SCENE, "material %d: unknown type %d", m, M.type);
+        if (!finite3(M.albedo) || !finite3(M.emission)) return fail(RMLT_E_INVALID_SCENE, "material %d: non-finite colour", m);
+        for (int a = 0; a < 3; ++a)
+            if (M.albedo[a] < 0.f || M.albedo[a] > 1.f || M.emission[a] < 0.f)
+                return fail(RMLT_E_INVALID_SCENE, "material %d: albedo outside [0,1] or negative emission", m);
+        if (M.type == RMLT_GGX && !(M.roughness >= 1e-3f && M.roughness <= 1.f))
+            return fail(RMLT_E_INVALID_SCENE, "material %d: GGX roughness outside [1e-3, 1]", m);
+    }
+    const int nt = s->n_tris;
+    std::vector<float> tv((size_t)9 * nt);
+    for (int i = 0; i < nt; ++i) {
+        for (int v = 0; v < 3; ++v) {
+            const uint32_t vi = s->tris[3 * (size_t)i + v];
+            if ((int64_t)vi >= s->n_verts) return fail(RMLT_E_INVALID_SCENE, "triangle %d: vertex index %u out of range", i, vi);
+            for (int a = 0; a < 3; ++a) tv[(size_t)9 * i + 3 * v + a] = s->verts[3 * (size_t)vi + a];
+        }
+        if ((int64_t)s->mat_id[i] >= s->n_mats) return fail(RMLT_E_INVALID_SCENE, "triangle %d: material %u out of range", i, s->mat_id[i]);
+    }
+    const rmlt_camera& cam = s->camera;
+    if (!finite3(cam.pos) || !finite3(cam.look_at) || !finite3(cam.up) || !(cam.vfov_deg > 0.f && cam.vfov_deg < 180.f))
+        return fail(RMLT_E_INVALID_SCENE, "bad camera");
+
+    // scene scale, lights in original triangle order sampled in proportion to area
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < s->n_verts; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::fmin(lo[a], (double)s->verts[3 * (size_t)i + a]);
+            hi[a] = std::fmax(hi[a], (double)s->verts[3 * (size_t)i + a]);
+        }
+    const double scale = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) + (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    if (!(scale > 0.0)) return fail(RMLT_E_INVALID_SCENE, "degenerate scene bounds");
+    std::vector<int> lights;
+    std::vector<double> lcum;
+    double acc = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        const rmlt_material& M = s->mats[s->mat_id[i]];
+        if (!(M.emission[0] > 0.f || M.emission[1] > 0.f || M.emission[2] > 0.f)) continue;
+        const float* p = &tv[(size_t)9 * i];
+        const double e1[3] = {(double)p[3] - p[0], (double)p[4] - p[1], (double)p[5] - p[2]};
+        const double e2[3] = {(double)p[6] - p[0], (double)p[7] - p[1], (double)p[8] - p[2]};
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2], cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double area2 = std::sqrt(cx * cx + cy * cy + cz * cz);
+        if (!(area2 > 0.0)) continue;
+        acc += 0.5 * area2;
+        lights.push_back(i);
+        lcum.push_back(acc);
+    }
+    std::vector<float> lcdf(lights.size());
+    for (size_t j = 0; j < lights.size(); ++j) lcdf[j] = (float)(lcum[j] / acc);
+    if (!lcdf.empty()) lcdf.back() = 1.0f;
+
+    // triangle order: BVH build order, or input order for brute force
+    const bool brute = nt <= brute_max || nt <= 4;
+    HostBVH bvh;
+    if (!brute) build_bvh(tv, nt, (float)(1e-6 * scale), bvh);
+    std::vector<uint32_t> order((size_t)nt), inv((size_t)nt);
+    for (int i = 0; i < nt; ++i) order[(size_t)i] = brute ? (uint32_t)i : bvh.order[(size_t)i];
+    for (int i = 0; i < nt; ++i) inv[order[(size_t)i]] = (uint32_t)i;
+    std::vector<float4> tri4((size_t)3 * nt);
+    for (int j = 0; j < nt; ++j) {
+        const uint32_t i = order[(size_t)j];
+        const float* p = &tv[(size_t)9 * i];
+        int32_t mid = (int32_t)s->mat_id[i];
+        float midf, idf;
+        std::memcpy(&midf, &mid, 4);
+        std::memcpy(&idf, &i, 4);
+        tri4[3 * (size_t)j + 0] = make_float4(p[0], p[1], p[2], midf);
+        tri4[3 * (size_t)j + 1] = make_float4(p[3] - p[0], p[4] - p[1], p[5] - p[2], idf);
+        tri4[3 * (size_t)j + 2] = make_float4(p[6] - p[0], p[7] - p[1], p[8] - p[2], 0.f);
+    }
+    std::vector<int32_t> ltri(lights.size());
+    for (size_t j = 0; j < lights.size(); ++j) ltri[j] = (int32_t)inv[(size_t)lights[j]];
+    std::vector<float4> mat4((size_t)3 * s->n_mats);
+    for (int m = 0; m < s->n_mats; ++m) {
+        const rmlt_material& M = s->mats[m];
+        const bool emissive = M.emission[0] > 0.f || M.emission[1] > 0.f || M.emission[2] > 0.f;
+        const bool black = M.albedo[0] <= 0.f && M.albedo[1] <= 0.f && M.albedo[2] <= 0.f;
+        mat4[3 * (size_t)m + 0] = make_float4(M.albedo[0], M.albedo[1], M.albedo[2], (float)M.type);
+        mat4[3 * (size_t)m + 1] = make_float4(M.emission[0], M.emission[1], M.emission[2], M.roughness);
+        mat4[3 * (size_t)m + 2] = make_float4(emissive ? 1.f : 0.f, black ? 1.f : 0.f, 0.f, 0.f);
+    }
+
+    // replace the previous scene (and chains)
+    drop_chains(c);
+    c->release(c->scene_mem);
+    c->have_scene = false;
+    DevScene S;
+    float4 *d_tri = nullptr, *d_nodes = nullptr, *d_mat = nullptr;
+    int32_t* d_lt = nullptr;
+    float* d_lc = nullptr;
+    if ((st = c->alloc_n(c->scene_mem, tri4.size(), &d_tri))) return st;
+    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(4, bvh.nodes.size()), &d_nodes))) return st;
+    if ((st = c->alloc_n(c->scene_mem, mat4.size(), &d_mat))) return st;
+    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, ltri.size()), &d_lt))) return st;
+    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, lcdf.size()), &d_lc))) return st;
+    CK(cudaMemcpyAsync(d_tri, tri4.data(), tri4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload triangles");
+    if (!bvh.nodes.empty())
+        CK(cudaMemcpyAsync(d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload nodes");
+    CK(cudaMemcpyAsync(d_mat, mat4.data(), mat4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload materials");
+    if (!ltri.empty()) {
+        CK(cudaMemcpyAsync(d_lt, ltri.data(), ltri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "upload lights");
+        CK(cudaMemcpyAsync(d_lc, lcdf.data(), lcdf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream), "upload light cdf");
+    }
+    if ((st = sync(c, "scene upload"))) return st;
+    S.tris = d_tri;
+    S.nodes = d_nodes;
+    S.mats = d_mat;
+    S.light_tri = d_lt;
+    S.light_cdf = d_lc;
+    S.n_tris = nt;
+    S.n_nodes = (int32_t)(bvh.nodes.size() / 4);
+    S.n_mats = s->n_mats;
+    S.n_lights = (int32_t)ltri.size();
+    S.brute = brute ? 1 : 0;
+    S.light_area = (float)acc;
+    // pinhole camera basis in binary64, stored in binary32
+    double pos[3] = {cam.pos[0], cam.pos[1], cam.pos[2]};
+    double fw[3] = {(double)cam.look_at[0] - pos[0], (double)cam.look_at[1] - pos[1], (double)cam.look_at[2] - pos[2]};
+    double fl = std::sqrt(fw[0] * fw[0] + fw[1] * fw[1] + fw[2] * fw[2]);
+    if (!(fl > 0.0)) return fail(RMLT_E_INVALID_SCENE, "camera looks at its own position");
+    for (double& x : fw) x /= fl;
+    const double up[3] = {cam.up[0], cam.up[1], cam.up[2]};
+    double rt[3] = {fw[1] * up[2] - fw[2] * up[1], fw[2] * up[0] - fw[0] * up[2], fw[0] * up[1] - fw[1] * up[0]};
+    double rl = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+    if (!(rl > 0.0)) return fail(RMLT_E_INVALID_SCENE, "camera up is parallel to the view direction");
+    for (double& x : rt) x /= rl;
+    const double uo[3] = {rt[1] * fw[2] - rt[2] * fw[1], rt[2] * fw[0] - rt[0] * fw[2], rt[0] * fw[1] - rt[1] * fw[0]};
+    for (int a = 0; a < 3; ++a) {
+        S.cam_pos[a] = (float)pos[a];
+        S.cam_fwd[a] = (float)fw[a];
+        S.cam_right[a] = (float)rt[a];
+        S.cam_up[a] = (float)uo[a];
+    }
+    c->tan_half = std::tan((double)cam.vfov_deg * 3.14159265358979323846 / 360.0);
+    S.eps = (float)(1e-4 * scale);
+    S.toy = 0;
+    c->S = S;
+    uint64_t h = fnv64(tv.data(), tv.size() * sizeof(float), 1469598103934665603ull);
+    h = fnv64(s->mat_id, (size_t)nt * sizeof(uint32_t), h);
+    h = fnv64(mat4.data(), mat4.size() * sizeof(float4), h);
+    c->scene_hash = fnv64(&cam, sizeof cam, h);
+    c->have_scene = true;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_load_toy_integrand(rmlt_ctx* c, const double* params)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!params) return fail(RMLT_E_INVALID_ARG, "params is NULL");
+    for (int i = 0; i < 10; ++i)
+        if (!std::isfinite(params[i])) return fail(RMLT_E_INVALID_ARG, "toy parameter %d not finite", i);
+    if (!(params[9] > 0.0)) return fail(RMLT_E_INVALID_ARG, "toy Gaussian width must be positive");
+    drop_chains(c);
+    c->release(c->scene_mem);
+    DevScene S;
+    S.toy = 1;
+    for (int i = 0; i < 10; ++i) S.toy_p[i] = (float)params[i];
+    S.brute = 0;
+    c->S = S;
+    c->scene_hash = fnv64(params, 10 * sizeof(double), 77);
+    c->have_scene = true;
+    return RMLT_OK;
+}
+
+static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
+{
+    if (!p) return fail(RMLT_E_INVALID_ARG, "params is NULL");
+    if (p->n_chains <= 0 || p->n_chains >= 0x7FFFFFFF) return fail(RMLT_E_INVALID_ARG, "n_chains must be in [1, 2^31-1)");
+    if (p->width <= 0 || p->height <= 0 || p->width > (1 << 16) || p->height > (1 << 16))
+        return fail(RMLT_E_INVALID_ARG, "image size must be in [1, 65536]");
+    if (p->region_px <= 0) return fail(RMLT_E_INVALID_ARG, "region_px must be positive");
+    if (c->S.toy ? p->max_depth != 0 : (p->max_depth < 1 || p->max_depth > RMLT_MAX_DEPTH))
+        return fail(RMLT_E_INVALID_ARG, "max_depth must be 0 for the toy integrand and 1..%d for a scene", RMLT_MAX_DEPTH);
+    if (p->epoch_len <= 0 || p->L <= 0) return fail(RMLT_E_INVALID_ARG, "epoch_len and L must be positive");
+    if (p->target_mode != RMLT_TARGET_PLAIN && p->target_mode != RMLT_TARGET_REGION_WEIGHTED)
+        return fail(RMLT_E_INVALID_ARG, "unknown target_mode");
+    if (p->n_bootstrap < p->n_chains || p->n_bootstrap > (1ll << 34))
+        return fail(RMLT_E_INVALID_ARG, "n_bootstrap must be in [n_chains, 2^34]");
+    if (!(p->p_large >= 0.0 && p->p_large <= 1.0)) return fail(RMLT_E_INVALID_ARG, "p_large outside [0,1]");
+    if (!(p->s1 > 0.0 && p->s1 < p->s2 && p->s2 <= 0.5)) return fail(RMLT_E_INVALID_ARG, "need 0 < s1 < s2 <= 1/2");
+    if (!(p->alpha_star > 0.0 && p->alpha_star < 1.0)) return fail(RMLT_E_INVALID_ARG, "alpha_star outside (0,1)");
+    if (!(p->gamma_max >= 0.0 && p->gamma_scale >= 0.0)) return fail(RMLT_E_INVALID_ARG, "negative gamma");
+    const double lmax_ok = 2.0 * std::log(1.0 / (2.0 * p->s2));
+    if (!(p->lambda_min >= -150.0 && p->lambda_min <= p->lambda_init && p->lambda_init <= p->lambda_max &&
+          p->lambda_max <= lmax_ok + 1e-12))
+        return fail(RMLT_E_INVALID_ARG, "need -150 <= lambda_min <= lambda_init <= lambda_max <= 2 ln(1/(2 s2)) = %g", lmax_ok);
+    if (!(p->w_floor >= 0.0 && p->w_floor <= 1.0)) return fail(RMLT_E_INVALID_ARG, "w_floor outside [0,1]");
+    return RMLT_OK;
+}
+
+// allocate chain state and region tables for params P (no initial values)
+static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
+{
+    drop_chains(c);
+    DevChains Ch;
+    Ch.C = p->n_chains;
+    Ch.D = 2 + 5 * p->max_depth;
+    Ch.W = p->width;
+    Ch.H = p->height;
+    Ch.region_px = p->region_px;
+    Ch.nx = (p->width + p->region_px - 1) / p->region_px;
+    Ch.m = Ch.nx * ((p->height + p->region_px - 1) / p->region_px);
+    Ch.max_depth = p->max_depth;
+    Ch.E = p->epoch_len;
+    Ch.L = p->L;
+    Ch.weighted = p->target_mode == RMLT_TARGET_REGION_WEIGHTED;
+    const size_t C = (size_t)Ch.C, m = (size_t)Ch.m, npx = (size_t)Ch.W * Ch.H * 3;
+    rmlt_status st;
+    auto& pool = c->chain_mem;
+    if ((st = c->alloc_n(pool, C * Ch.D, &Ch.q))) return st;
+    if ((st = c->alloc_n(pool, 3 * C, &Ch.f))) return st;
+    if ((st = c->alloc_n(pool, C, &Ch.pi))) return st;
+    if ((st = c->alloc_n(pool, C, &Ch.k))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.lam))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.n))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.vis))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.acc))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.hist))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.hprev))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.w))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.Rc))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.sig))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.wf))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.Bk))) return st;
+    if ((st = c->alloc_n(pool, npx, &Ch.img))) return st;
+    if ((st = c->alloc_n(pool, (size_t)kStCount, &Ch.stats))) return st;
+    if ((st = c->alloc_n(pool, 1, &c->d_total))) return st;
+    if ((st = c->alloc_n(pool, npx, &c->d_stage))) return st;
+    Ch.seed_lo = (uint32_t)p->seed;
+    Ch.seed_hi = (uint32_t)(p->seed >> 32);
+    double tl = std::ceil(p->p_large * 16777216.0);
+    Ch.T_large = (uint32_t)(tl < 0 ? 0 : (tl > 16777216.0 ? 16777216.0 : tl));
+    Ch.S1 = (float)(p->s1 * 4294967296.0);
+    Ch.S2 = (float)(p->s2 * 4294967296.0);
+    Ch.log2_ratio = (float)std::log2(p->s2 / p->s1);
+    Ch.alpha_star = p->alpha_star;
+    Ch.gamma_max = p->gamma_max;
+    Ch.gamma_scale = p->gamma_scale;
+    Ch.lambda_min = p->lambda_min;
+    Ch.lambda_max = p->lambda_max;
+    Ch.w_floor = p->w_floor;
+    c->Ch = Ch;
+    c->P = *p;
+    c->S.tan_y = (float)c->tan_half;
+    c->S.tan_x = (float)(c->tan_half * (double)p->width / (double)p->height);
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* p)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_scene) return fail(RMLT_E_STATE, "load a scene before rmlt_init_chains");
+    if ((st = check_params(c, p))) return st;
+    if ((st = alloc_chains(c, p))) return st;
+    DevChains& Ch = c->Ch;
+    const size_t npx = (size_t)Ch.W * Ch.H * 3;
+    CK(cudaMemsetAsync(Ch.img, 0, npx * sizeof(double), c->stream), "clear image");
+    CK(cudaMemsetAsync(Ch.stats, 0, kStCount * sizeof(unsigned long long), c->stream), "clear stats");
+    CK(launch_fill_regions(Ch, p->lambda_init, c->stream), "region init");
+    // bootstrap with scratch buffers released afterwards
+    std::vector<Alloc> scratch;
+    BootScratch B;
+    const int64_t K = p->n_bootstrap / p->n_chains;
+    const int64_t nb = K * p->n_chains;
+    if ((st = c->alloc_n(scratch, (size_t)nb, &B.pi)) || (st = c->alloc_n(scratch, (size_t)nb * 3, &B.f)) ||
+        (st = c->alloc_n(scratch, (size_t)Ch.C, &B.partial))) {
+        c->release(scratch);
+        drop_chains(c);
+        return st;
+    }
+    B.total = c->d_total;
+    cudaError_t e = launch_bootstrap(c->S, Ch, nb, B, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->release(scratch);
+    if (e != cudaSuccess) {
+        drop_chains(c);
+        return cuda_fail(e, "bootstrap");
+    }
+    c->n_boot = nb;
+    c->mut = 0;
+    c->epochs = 0;
+    c->have_chains = true;
+    c->failed = false;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
+    if (c->failed) return fail(RMLT_E_STATE, "context failed earlier: %s", g_err.c_str());
+    const uint64_t E = (uint64_t)c->Ch.E;
+    const uint64_t n_ep = (n_mutations + E - 1) / E;
+    const uint32_t n_traced = (uint32_t)(((uint64_t)c->Ch.C + c->tr_stride - 1) / c->tr_stride);
+    for (uint64_t e = 0; e < n_ep; ++e) {
+        DevChains Ch = c->Ch;
+        const bool trace = c->tr != nullptr;
+        if (trace) {
+            Ch.trace = c->tr;
+            Ch.trace_cap = c->tr_cap;
+            Ch.trace_stride = c->tr_stride;
+            Ch.trace_base = c->tr_epoch * (unsigned long long)n_traced * E;
+        }
+        cudaError_t err = launch_chain_epoch(c->S, Ch, c->mut, trace, c->count_work, c->stream);
+        if (err == cudaSuccess) err = launch_region_update(c->Ch, false, c->stream);
+        if (err != cudaSuccess) {
+            c->failed = true;
+            return cuda_fail(err, "rmlt_step launch");
+        }
+        if (trace && c->tr_lam && (c->tr_epoch + 1) * (uint64_t)c->Ch.m <= c->tr_lam_cap) {
+            err = cudaMemcpyAsync(c->tr_lam + c->tr_epoch * (uint64_t)c->Ch.m, c->Ch.lam, sizeof(double) * c->Ch.m,
+                                  cudaMemcpyDeviceToDevice, c->stream);
+            if (err != cudaSuccess) return cuda_fail(err, "trace lambda copy");
+        }
+        if (trace) c->tr_epoch++;
+        c->mut += E;
+        c->epochs++;
+    }
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_trace(rmlt_ctx* c, rmlt_trace_record* records, uint64_t capacity, double* lambdas,
+                           uint64_t lambda_capacity, uint32_t chain_stride)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (records && chain_stride == 0) return fail(RMLT_E_INVALID_ARG, "chain_stride must be positive");
+    c->tr = records;
+    c->tr_cap = records ? capacity : 0;
+    c->tr_lam = records ? lambdas : nullptr;
+    c->tr_lam_cap = records ? lambda_capacity : 0;
+    c->tr_stride = records ? chain_stride : 1;
+    c->tr_epoch = 0;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_read_image(rmlt_ctx* c, double* out, int normalized)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    const double n_total = (double)c->mut * (double)c->Ch.C;
+    CK(launch_read_image(c->Ch, c->d_total, c->n_boot, n_total, normalized, c->d_stage, c->stream), "read image");
+    if ((st = copy_out(c, out, c->d_stage, sizeof(double) * 3 * (size_t)c->Ch.W * c->Ch.H))) return st;
+    return sync(c, "read image");
+}
+
+rmlt_status rmlt_read_region_hist(rmlt_ctx* c, uint64_t* out)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    if ((st = copy_out(c, out, c->Ch.hist, sizeof(uint64_t) * c->Ch.m))) return st;
+    return sync(c, "read hist");
+}
+
+rmlt_status rmlt_read_region_params(rmlt_ctx* c, double* lambda, int64_t* n, uint64_t* i, uint64_t* A, double* w)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    const size_t m = (size_t)c->Ch.m;
+    if ((st = copy_out(c, lambda, c->Ch.lam, m * 8)) || (st = copy_out(c, n, c->Ch.n, m * 8)) ||
+        (st = copy_out(c, i, c->Ch.vis, m * 8)) || (st = copy_out(c, A, c->Ch.acc, m * 8)) ||
+        (st = copy_out(c, w, c->Ch.w, m * 8)))
+        return st;
+    return sync(c, "read region params");
+}
+
+rmlt_status rmlt_read_chain_state(rmlt_ctx* c, uint32_t* q, float* f, int32_t* k)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    const size_t C = (size_t)c->Ch.C;
+    if ((st = copy_out(c, q, c->Ch.q, C * c->Ch.D * 4)) || (st = copy_out(c, f, c->Ch.f, C * 3 * 4)) ||
+        (st = copy_out(c, k, c->Ch.k, C * 4)))
+        return st;
+    return sync(c, "read chain state");
+}
+
+rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    unsigned long long s[kStCount];
+    double total = 0.0;
+    CK(cudaMemcpyAsync(s, c->Ch.stats, sizeof s, cudaMemcpyDeviceToHost, c->stream), "read stats");
+    CK(cudaMemcpyAsync(&total, c->d_total, sizeof total, cudaMemcpyDeviceToHost, c->stream), "read total");
+    if ((st = sync(c, "read stats"))) return st;
+    std::memset(out, 0, sizeof *out);
+    out->mutations = c->mut;
+    out->accepted = s[kStAccepted];
+    out->large = s[kStLarge];
+    out->small = s[kStSmall];
+    out->early_reject = s[kStEarly];
+    out->invalid_paths = s[kStInvalid];
+    out->rays = s[kStRays];
+    out->stack_overflow = s[kStOverflow];
+    out->epochs = c->epochs;
+    out->bhat = total / (double)c->n_boot;
+    out->n_regions = c->Ch.m;
+    out->dims = c->Ch.D;
+    out->node_visits = s[kStNodes];
+    out->tri_tests = s[kStTris];
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_work_counters(rmlt_ctx* c, int enable)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    c->count_work = enable != 0;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_memory_usage(rmlt_ctx* c, uint64_t* bytes)
+{
+    if (!c || !bytes) return fail(RMLT_E_INVALID_ARG, "null argument");
+    *bytes = c->held;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_synchronize(rmlt_ctx* c)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    return sync(c, "synchronize");
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t abi, pad;
+    uint64_t scene_hash;
+    rmlt_chain_params P;
+    uint64_t mut, epochs;
+    int64_t n_boot;
+};
+
+struct Field {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<Field> fields(rmlt_ctx* c)
+{
+    DevChains& Ch = c->Ch;
+    const size_t C = (size_t)Ch.C, m = (size_t)Ch.m, npx = (size_t)Ch.W * Ch.H * 3;
+    return {{Ch.q, C * Ch.D * 4}, {Ch.f, C * 12}, {Ch.pi, C * 4}, {Ch.k, C * 4},
+            {Ch.lam, m * 8}, {Ch.n, m * 8}, {Ch.vis, m * 8}, {Ch.acc, m * 8}, {Ch.hist, m * 8},
+            {Ch.hprev, m * 8}, {Ch.w, m * 8}, {Ch.Rc, m * 8}, {Ch.sig, m * 4}, {Ch.wf, m * 4},
+            {Ch.Bk, m * 8}, {Ch.img, npx * 8}, {Ch.stats, kStCount * 8}, {c->d_total, 8}};
+}
+}  // namespace
+
+rmlt_status rmlt_save(rmlt_ctx* c, const char* path)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!path) return fail(RMLT_E_INVALID_ARG, "path is NULL");
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    if ((st = sync(c, "save"))) return st;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(RMLT_E_IO, "cannot open %s for writing", path);
+    CkptHeader h{};
+    std::memcpy(h.magic, "RMLTCKP1", 8);
+    h.abi = RMLT_ABI_VERSION;
+    h.scene_hash = c->scene_hash;
+    h.P = c->P;
+    h.mut = c->mut;
+    h.epochs = c->epochs;
+    h.n_boot = c->n_boot;
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1;
+    std::vector<unsigned char> buf;
+    for (const Field& f : fields(c)) {
+        if (!ok) break;
+        buf.resize(f.bytes);
+        if (cudaMemcpy(buf.data(), f.dev, f.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(fp);
+            return cuda_fail(cudaGetLastError(), "save copy");
+        }
+        ok = std::fwrite(buf.data(), 1, f.bytes, fp) == f.bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(RMLT_E_IO, "write to %s failed", path);
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!path) return fail(RMLT_E_INVALID_ARG, "path is NULL");
+    if (!c->have_scene) return fail(RMLT_E_STATE, "load the checkpoint's scene first");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(RMLT_E_IO, "cannot open %s", path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "RMLTCKP1", 8) != 0 || h.abi != RMLT_ABI_VERSION) {
+        std::fclose(fp);
+        return fail(RMLT_E_INVALID_ARG, "%s is not a checkpoint of this library version", path);
+    }
+    if (h.scene_hash != c->scene_hash) {
+        std::fclose(fp);
+        return fail(RMLT_E_INVALID_ARG, "checkpoint was taken on another scene");
+    }
+    if ((st = check_params(c, &h.P))) {
+        std::fclose(fp);
+        return st;
+    }
+    if ((st = alloc_chains(c, &h.P))) {
+        std::fclose(fp);
+        return st;
+    }
+    std::vector<unsigned char> buf;
+    for (const Field& f : fields(c)) {
+        buf.resize(f.bytes);
+        if (std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
+            std::fclose(fp);
+            drop_chains(c);
+            return fail(RMLT_E_IO, "truncated checkpoint %s", path);
+        }
+        if (cudaMemcpy(f.dev, buf.data(), f.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(fp);
+            drop_chains(c);
+            return cuda_fail(cudaGetLastError(), "restore copy");
+        }
+    }
+    std::fclose(fp);
+    c->mut = h.mut;
+    c->epochs = h.epochs;
+    c->n_boot = h.n_boot;
+    c->have_chains = true;
+    c->failed = false;
+    return RMLT_OK;
+}
+
+void rmlt_destroy(rmlt_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    c->release(c->chain_mem);
+    c->release(c->scene_mem);
+    delete c;
+}
+
+}  // extern "C"

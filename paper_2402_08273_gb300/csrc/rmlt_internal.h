@@ -1,0 +1,102 @@
+// Internal interface between the host side of librmlt (C ABI, scene/BVH
+// upload, bookkeeping) and its CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "rmlt.h"
+
+namespace rmlt {
+
+constexpr int kMaxDim = 2 + 5 * RMLT_MAX_DEPTH;   // 62 primary-sample dimensions
+constexpr int kStackSize = 64;                      // traversal stack entries per ray
+constexpr int kChainBlock = 128;                    // threads per block of the chain kernel
+
+// statistic slots in DevChains::stats
+enum StatSlot {
+    kStAccepted = 0, kStLarge, kStSmall, kStEarly, kStInvalid, kStRays, kStOverflow,
+    kStNodes, kStTris, kStCount = 16
+};
+
+// Leaf references in the BVH: bit 31 set, bits 28..30 = count - 1, bits 0..27 = first triangle.
+constexpr uint32_t kLeafBit = 0x80000000u;
+
+// Device view of a loaded scene.  Triangles: 3 float4 each (v0 | mat id bits,
+// e1 | original index bits, e2 | 0); nodes: 4 float4 each (child 0 x/y
+// bounds, child 1 x/y bounds, both z bounds, child refs); materials: 3 float4
+// each (albedo | type, emission | roughness, emissive flag | black flag).
+struct DevScene {
+    const float4* tris = nullptr;
+    const float4* nodes = nullptr;
+    const float4* mats = nullptr;
+    const int32_t* light_tri = nullptr;
+    const float* light_cdf = nullptr;
+    int32_t n_tris = 0, n_nodes = 0, n_mats = 0, n_lights = 0, brute = 1;
+    float light_area = 0.f;
+    float cam_pos[3] = {0, 0, 0}, cam_fwd[3] = {0, 0, 1}, cam_right[3] = {1, 0, 0}, cam_up[3] = {0, 1, 0};
+    float tan_x = 1.f, tan_y = 1.f;   // tan(vfov / 2) * aspect, tan(vfov / 2)
+    float eps = 1e-4f;                // ray offset, 1e-4 of the scene diagonal
+    int32_t toy = 0;
+    float toy_p[10] = {0};
+};
+
+// Device view of the chains and region tables.
+struct DevChains {
+    int32_t C = 0, D = 0, W = 0, H = 0, region_px = 1, nx = 1, m = 1, max_depth = 0, E = 1, L = 10;
+    int32_t weighted = 0;
+    uint32_t* q = nullptr;        // [D][C]
+    float* f = nullptr;           // [3][C]
+    float* pi = nullptr;          // [C]
+    int32_t* k = nullptr;         // [C]
+    double* lam = nullptr;        // [m]
+    long long* n = nullptr;       // [m]
+    unsigned long long* vis = nullptr;    // i_k [m]
+    unsigned long long* acc = nullptr;    // A_k [m]
+    unsigned long long* hist = nullptr;   // h_k [m]
+    unsigned long long* hprev = nullptr;  // h_k at the previous weight update [m]
+    double* w = nullptr;          // [m]
+    double* Rc = nullptr;         // [m]
+    float* sig = nullptr;         // sigma_k [m]
+    float* wf = nullptr;          // w_k as float [m]
+    double* Bk = nullptr;         // sum of pi over uniform samples per region [m]
+    double* img = nullptr;        // [H][W][3]
+    unsigned long long* stats = nullptr;  // [kStCount]
+    uint32_t seed_lo = 0, seed_hi = 0, T_large = 0;
+    float S1 = 0.f, S2 = 0.f, log2_ratio = 0.f;
+    double alpha_star = 0.5, gamma_max = 1.0, gamma_scale = 5.0, lambda_min = -30.0, lambda_max = 7.0;
+    double w_floor = 1e-3;
+    // trace instrument
+    rmlt_trace_record* trace = nullptr;
+    unsigned long long trace_cap = 0, trace_base = 0;
+    uint32_t trace_stride = 1;
+};
+
+// Scratch of the bootstrap (n = K C samples, K = n_bootstrap / C per chain).
+struct BootScratch {
+    float* pi = nullptr;          // [n]
+    float* f = nullptr;           // [3][n]
+    double* partial = nullptr;    // [C] per-chain slice sums
+    double* total = nullptr;      // [1] sum of pi over all samples (kept)
+};
+
+cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace,
+                               bool count_work, cudaStream_t st);
+cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st);
+cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot,
+                             const BootScratch& b, cudaStream_t st);
+cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int64_t n_boot,
+                              double n_total, int normalized, double* out, cudaStream_t st);
+cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st);
+
+// host-side BVH build (bvh_build.cpp)
+struct HostBVH {
+    std::vector<float4> nodes;    // 4 per node
+    std::vector<uint32_t> order;  // triangle order after the build
+    int max_depth = 0;
+};
+void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, HostBVH& out);
+
+}  // namespace rmlt

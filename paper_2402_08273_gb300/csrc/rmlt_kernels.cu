@@ -1,0 +1,895 @@
+// CUDA kernels of librmlt (sm_103a): the regional adaptive PSS-MLT chain step.
+//
+// One thread owns one chain for an epoch of E mutations (Alg. 1 lines 8-19).
+// Each loop iteration traces exactly one ray (camera/extension closest hit,
+// or a next-event shadow any-hit), so the threads of a warp meet at the same
+// traversal code whatever mutation or bounce each one is at.  Chain state is
+// structure-of-arrays (coalesced per dimension), BVH nodes and triangles are
+// read as 16-byte float4, splats and region counts are flushed only when a
+// chain's state changes (a rejected mutation re-splats the same state, so a
+// per-thread visit count replaces one atomic per mutation).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rmlt_internal.h"
+
+namespace rmlt {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies; the key is bumped by the Weyl constants per round.
+// Counter layout: mutation draws {mut lo, mut hi, chain, call}; bootstrap
+// draws {sample lo, sample hi, 0xFFFFFFFF, 0x8000 + call}; key = seed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// uniform in [0,1) from the top 24 bits (exact in binary32)
+__device__ __forceinline__ float u24(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-08f; }
+
+// ---------------------------------------------------------------------------
+// binary32 arithmetic that decides integers (the quantised small-step offset
+// and sigma_k): a fixed sequence of correctly rounded operations, never
+// contracted, so every conforming implementation gets the same bits.
+// ---------------------------------------------------------------------------
+// 2^t: t = n + r with n = rint(t), |r| <= 1/2; 2^r by its Taylor polynomial
+// sum_{i<=7} (ln 2)^i r^i / i! in Horner form with fused multiply-adds.
+__device__ __forceinline__ float exp2_ordered(float t)
+{
+    const float n = rintf(t);
+    const float r = __fsub_rn(t, n);
+    float p = 1.525273365e-05f;
+    p = __fmaf_rn(p, r, 1.540352969e-04f);
+    p = __fmaf_rn(p, r, 1.333355787e-03f);
+    p = __fmaf_rn(p, r, 9.618128650e-03f);
+    p = __fmaf_rn(p, r, 5.550410971e-02f);
+    p = __fmaf_rn(p, r, 2.402265072e-01f);
+    p = __fmaf_rn(p, r, 6.931471825e-01f);
+    p = __fmaf_rn(p, r, 1.0f);
+    return __fmul_rn(p, __int_as_float(((int)n + 127) << 23));
+}
+
+// Kelemen small step: |offset| = sigma s2 (s1/s2)^xi in units of 2^-32.
+__device__ __forceinline__ uint32_t kelemen_offset(uint32_t xmag, float sigS2, float log2_ratio)
+{
+    const float xi = __fmul_rn(__uint2float_rn(xmag >> 8), 5.9604644775390625e-08f);
+    const float t = -__fmul_rn(xi, log2_ratio);
+    const float m = __fmul_rn(sigS2, exp2_ordered(t));
+    return (uint32_t)(unsigned long long)__float2ll_rn(m);
+}
+
+__device__ __forceinline__ int pixel_x(uint32_t q0, int W) { return (int)(((unsigned long long)(q0 >> 8) * (unsigned)W) >> 24); }
+
+__device__ __forceinline__ float lum(float r, float g, float b) { return 0.2126f * r + 0.7152f * g + 0.0722f * b; }
+
+// ---------------------------------------------------------------------------
+// small float3 helpers
+// ---------------------------------------------------------------------------
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ V3 normalize(V3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ V3 xyz(float4 a) { return {a.x, a.y, a.z}; }
+
+// ---------------------------------------------------------------------------
+// ray casting
+// ---------------------------------------------------------------------------
+// Moller-Trumbore; returns t in (tmin, tmax) of a hit inside the triangle.
+__device__ __forceinline__ bool hit_tri(V3 o, V3 d, float4 a, float4 b, float4 c, float tmax, float& t)
+{
+    const V3 v0 = xyz(a), e1 = xyz(b), e2 = xyz(c);
+    const V3 p = cross(d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const V3 s = o - v0;
+    const float u = dot(s, p) * inv;
+    if (!(u >= 0.0f && u <= 1.0f)) return false;
+    const V3 qv = cross(s, e1);
+    const float v = dot(d, qv) * inv;
+    if (!(v >= 0.0f && u + v <= 1.0f)) return false;
+    const float tt = dot(e2, qv) * inv;
+    if (!(tt > 0.0f && tt < tmax)) return false;
+    t = tt;
+    return true;
+}
+
+struct Hit {
+    float t;
+    int tri;
+};
+
+// Brute-force closest hit / any hit over triangles staged in shared memory.
+__device__ __forceinline__ Hit trace_brute(const float4* __restrict__ tr, int n, V3 o, V3 d, float tmax, bool any)
+{
+    Hit h{tmax, -1};
+    for (int i = 0; i < n; ++i) {
+        float t;
+        if (hit_tri(o, d, tr[3 * i], tr[3 * i + 1], tr[3 * i + 2], h.t, t)) {
+            h.t = t;
+            h.tri = i;
+            if (any) break;
+        }
+    }
+    return h;
+}
+
+// BVH2 traversal with a per-thread stack: both children's boxes come with the
+// parent (16-byte loads through the read-only path), the nearer child is
+// visited first.  The slab test widens tmax by 3 ulp (robust traversal).
+__device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                         V3 o, V3 d, float tmax, bool any, int& overflow,
+                                         unsigned& n_nodes, unsigned& n_tris)
+{
+    const V3 id = {1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+                   1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+                   1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z))};
+    const V3 ood = {o.x * id.x, o.y * id.y, o.z * id.z};
+    Hit h{tmax, -1};
+    uint32_t stack[kStackSize];
+    int sp = 0;
+    uint32_t ref = 0;
+    while (true) {
+        if (!(ref & kLeafBit)) {
+            ++n_nodes;
+            const float4 n0 = __ldg(&nodes[4 * ref + 0]);
+            const float4 n1 = __ldg(&nodes[4 * ref + 1]);
+            const float4 n2 = __ldg(&nodes[4 * ref + 2]);
+            const float4 n3 = __ldg(&nodes[4 * ref + 3]);
+            const float tcap = h.t * 1.00000036f;
+            // child 0
+            float a0 = fmaf(n0.x, id.x, -ood.x), b0 = fmaf(n0.y, id.x, -ood.x);
+            float a1 = fmaf(n0.z, id.y, -ood.y), b1 = fmaf(n0.w, id.y, -ood.y);
+            float a2 = fmaf(n2.x, id.z, -ood.z), b2 = fmaf(n2.y, id.z, -ood.z);
+            const float tn0 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            const float tf0 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+            // child 1
+            a0 = fmaf(n1.x, id.x, -ood.x); b0 = fmaf(n1.y, id.x, -ood.x);
+            a1 = fmaf(n1.z, id.y, -ood.y); b1 = fmaf(n1.w, id.y, -ood.y);
+            a2 = fmaf(n2.z, id.z, -ood.z); b2 = fmaf(n2.w, id.z, -ood.z);
+            const float tn1 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            const float tf1 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+            const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+            const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp >= kStackSize) { overflow = 1; break; }
+                stack[sp++] = first0 ? c1 : c0;
+                ref = first0 ? c0 : c1;
+                continue;
+            }
+            if (h0) { ref = c0; continue; }
+            if (h1) { ref = c1; continue; }
+        } else {
+            const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
+            for (uint32_t i = first; i < first + cnt; ++i) {
+                ++n_tris;
+                float t;
+                if (hit_tri(o, d, __ldg(&tris[3 * i]), __ldg(&tris[3 * i + 1]), __ldg(&tris[3 * i + 2]), h.t, t)) {
+                    h.t = t;
+                    h.tri = (int)i;
+                    if (any) return h;
+                }
+            }
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// path map u -> f(u): pinhole camera through (u0 W, u1 H); bounce b uses
+// dims 2+5b..6+5b = (light select, light u, light v, BSDF u, BSDF v);
+// emission on the camera ray's hit; NEE at every interaction (light triangle
+// in proportion to area, uniform point, one-sided emitters); Lambert cosine
+// or GGX half-vector sampling; no Russian roulette.  Written as a state
+// machine that asks for one ray at a time.
+// ---------------------------------------------------------------------------
+struct Path {
+    V3 o, d;
+    float tmax;
+    int any;          // 1: the pending ray is a shadow ray
+    V3 T, L, P;       // throughput, radiance, NEE contribution awaiting visibility
+    V3 x, ns, wo;     // interaction waiting for its BSDF continuation
+    int mat, b, done;
+};
+
+__device__ __forceinline__ void path_begin(Path& p, const DevScene& S, const uint32_t* y)
+{
+    const float sx = (2.0f * u24(y[0]) - 1.0f) * S.tan_x;
+    const float sy = (1.0f - 2.0f * u24(y[1])) * S.tan_y;
+    const V3 fw = {S.cam_fwd[0], S.cam_fwd[1], S.cam_fwd[2]};
+    const V3 rt = {S.cam_right[0], S.cam_right[1], S.cam_right[2]};
+    const V3 up = {S.cam_up[0], S.cam_up[1], S.cam_up[2]};
+    p.o = {S.cam_pos[0], S.cam_pos[1], S.cam_pos[2]};
+    p.d = normalize(fw + rt * sx + up * sy);
+    p.tmax = 3.0e38f;
+    p.any = 0;
+    p.T = {1.f, 1.f, 1.f};
+    p.L = {0.f, 0.f, 0.f};
+    p.b = 0;
+    p.done = 0;
+}
+
+__device__ __forceinline__ float ggx_g1(float c, float a2)
+{
+    if (c <= 0.0f) return 0.0f;
+    return 2.0f * c / (c + sqrtf(a2 + (1.0f - a2) * c * c));
+}
+
+__device__ __forceinline__ void frame(V3 n, V3& t, V3& b)
+{
+    if (fabsf(n.z) < 0.9f) t = v3(-n.y, n.x, 0.0f);
+    else t = v3(0.0f, -n.z, n.y);
+    t = normalize(t);
+    b = cross(n, t);
+}
+
+__device__ __forceinline__ V3 bsdf_eval(float4 m0, float4 m1, V3 wo, V3 wi, V3 n)
+{
+    if (m0.w == 0.0f) {
+        const float k = 0.318309886183790672f;   // 1 / pi
+        return {m0.x * k, m0.y * k, m0.z * k};
+    }
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f) return {0.f, 0.f, 0.f};
+    const V3 h = normalize(wo + wi);
+    const float ch = dot(n, h), a2 = m1.w * m1.w;
+    const float den = 1.0f + (a2 - 1.0f) * ch * ch;
+    const float D = a2 / (3.14159265358979f * den * den);
+    const float G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+    const float x = 1.0f - dot(wi, h), x2 = x * x, c5 = x2 * x2 * x;
+    const float s = D * G / (4.0f * co * ci);
+    return {(m0.x + (1.0f - m0.x) * c5) * s, (m0.y + (1.0f - m0.y) * c5) * s, (m0.z + (1.0f - m0.z) * c5) * s};
+}
+
+// after NEE at interaction b: sample the BSDF to continue, or finish
+__device__ __forceinline__ void path_continue(Path& p, const DevScene& S, const uint32_t* y, int max_depth)
+{
+    if (p.b == max_depth - 1) { p.done = 1; return; }
+    const float bu = u24(y[5 + 5 * p.b]), bv = u24(y[6 + 5 * p.b]);
+    const float4 m0 = __ldg(&S.mats[3 * p.mat]), m1 = __ldg(&S.mats[3 * p.mat + 1]);
+    V3 ft, fb;
+    frame(p.ns, ft, fb);
+    float sp, cp;
+    sincospif(2.0f * bv, &sp, &cp);
+    V3 wi;
+    if (m0.w == 0.0f) {
+        const float r = sqrtf(bu);
+        wi = ft * (r * cp) + fb * (r * sp) + p.ns * sqrtf(fmaxf(0.0f, 1.0f - bu));
+        p.T = {p.T.x * m0.x, p.T.y * m0.y, p.T.z * m0.z};
+    } else {
+        const float a2 = m1.w * m1.w;
+        const float tan2 = a2 * bu / (1.0f - bu);
+        const float cm = 1.0f / sqrtf(1.0f + tan2);
+        const float sm = sqrtf(fmaxf(0.0f, 1.0f - cm * cm));
+        const V3 mv = ft * (sm * cp) + fb * (sm * sp) + p.ns * cm;
+        const float dom = dot(p.wo, mv);
+        if (dom <= 0.0f) { p.done = 1; return; }
+        wi = mv * (2.0f * dom) - p.wo;
+        const float ci = dot(wi, p.ns), co = dot(p.wo, p.ns);
+        if (ci <= 0.0f) { p.done = 1; return; }
+        const float G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+        const float x = 1.0f - dom, x2 = x * x, c5 = x2 * x2 * x;
+        const float s = G * dom / (co * cm);
+        p.T = {p.T.x * (m0.x + (1.0f - m0.x) * c5) * s, p.T.y * (m0.y + (1.0f - m0.y) * c5) * s,
+               p.T.z * (m0.z + (1.0f - m0.z) * c5) * s};
+    }
+    p.o = p.x + p.ns * S.eps;
+    p.d = wi;
+    p.tmax = 3.0e38f;
+    p.any = 0;
+    p.b += 1;
+}
+
+template <bool BRUTE>
+__device__ __forceinline__ float4 tri_load(const DevScene& S, const float4* s_tris, int i, int j)
+{
+    return BRUTE ? s_tris[3 * i + j] : __ldg(&S.tris[3 * i + j]);
+}
+
+// consume the result of the pending ray
+template <bool BRUTE>
+__device__ __forceinline__ void path_on_hit(Path& p, const DevScene& S, const float4* s_tris, const uint32_t* y,
+                                            int max_depth, Hit h)
+{
+    if (p.any) {
+        if (h.tri < 0) p.L = p.L + p.P;
+        p.any = 0;
+        path_continue(p, S, y, max_depth);
+        return;
+    }
+    if (h.tri < 0) { p.done = 1; return; }
+    const float4 ta = tri_load<BRUTE>(S, s_tris, h.tri, 0), tb = tri_load<BRUTE>(S, s_tris, h.tri, 1),
+                 tc = tri_load<BRUTE>(S, s_tris, h.tri, 2);
+    const V3 n = normalize(cross(xyz(tb), xyz(tc)));
+    const int mat = __float_as_int(ta.w);
+    const V3 x = p.o + p.d * h.t;
+    const float cosi = -dot(n, p.d);
+    const V3 ns = cosi > 0.0f ? n : n * -1.0f;
+    const float4 m0 = __ldg(&S.mats[3 * mat]), m1 = __ldg(&S.mats[3 * mat + 1]), m2 = __ldg(&S.mats[3 * mat + 2]);
+    if (p.b == 0 && m2.x != 0.0f && cosi > 0.0f) p.L = p.L + v3(p.T.x * m1.x, p.T.y * m1.y, p.T.z * m1.z);
+    if (m2.y != 0.0f) { p.done = 1; return; }
+    p.x = x;
+    p.ns = ns;
+    p.wo = p.d * -1.0f;
+    p.mat = mat;
+    if (S.n_lights > 0) {
+        const float ls = u24(y[2 + 5 * p.b]), lu = u24(y[3 + 5 * p.b]), lv = u24(y[4 + 5 * p.b]);
+        int lo = 0, hi = S.n_lights - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&S.light_cdf[mid]) > ls) hi = mid; else lo = mid + 1;
+        }
+        const int lt = __ldg(&S.light_tri[lo]);
+        const float4 la = tri_load<BRUTE>(S, s_tris, lt, 0), lb = tri_load<BRUTE>(S, s_tris, lt, 1),
+                     lc = tri_load<BRUTE>(S, s_tris, lt, 2);
+        const float su = sqrtf(lu), b1 = su * (1.0f - lv), b2 = su * lv;
+        const V3 pl = xyz(la) + xyz(lb) * b1 + xyz(lc) * b2;
+        V3 wi = pl - x;
+        const float dist2 = dot(wi, wi), dist = sqrtf(dist2);
+        wi = wi * (1.0f / dist);
+        const V3 ln = normalize(cross(xyz(lb), xyz(lc)));
+        const float cx = dot(ns, wi), cl = -dot(ln, wi);
+        if (cx > 0.0f && cl > 0.0f) {
+            const V3 xo = x + ns * S.eps;
+            V3 sd = pl - xo;
+            const float sdist = sqrtf(dot(sd, sd));
+            if (sdist > 2.0f * S.eps) {
+                const V3 fr = bsdf_eval(m0, m1, p.wo, wi, ns);
+                const float4 lm1 = __ldg(&S.mats[3 * __float_as_int(la.w) + 1]);
+                const float g = cx * cl / dist2 * S.light_area;
+                p.P = {p.T.x * fr.x * lm1.x * g, p.T.y * fr.y * lm1.y * g, p.T.z * fr.z * lm1.z * g};
+                p.o = xo;
+                p.d = sd * (1.0f / sdist);
+                p.tmax = sdist - S.eps;
+                p.any = 1;
+                return;
+            }
+        }
+    }
+    path_continue(p, S, y, max_depth);
+}
+
+__device__ __forceinline__ float toy_eval(const DevScene& S, uint32_t q0, uint32_t q1)
+{
+    const float u0 = u24(q0), u1 = u24(q1);
+    float f = S.toy_p[0];
+    if (u0 >= S.toy_p[2] && u0 < S.toy_p[3] && u1 >= S.toy_p[4] && u1 < S.toy_p[5]) f += S.toy_p[1];
+    const float dx = u0 - S.toy_p[7], dy = u1 - S.toy_p[8];
+    f += S.toy_p[6] * expf(-(dx * dx + dy * dy) / (2.0f * S.toy_p[9] * S.toy_p[9]));
+    return f;
+}
+
+template <bool BRUTE>
+__device__ __forceinline__ Hit trace_one(const DevScene& S, const float4* s_tris, const Path& p, int& overflow,
+                                         unsigned& nn, unsigned& nt)
+{
+    if (BRUTE) return trace_brute(s_tris, S.n_tris, p.o, p.d, p.tmax, p.any != 0);
+    return trace_bvh(S.nodes, S.tris, p.o, p.d, p.tmax, p.any != 0, overflow, nn, nt);
+}
+
+__device__ __forceinline__ void stage_triangles(const DevScene& S, float4* s_tris)
+{
+    for (int i = threadIdx.x; i < 3 * S.n_tris; i += blockDim.x) s_tris[i] = __ldg(&S.tris[i]);
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// the chain step: E mutations per chain (Alg. 1 lines 8-19)
+// ---------------------------------------------------------------------------
+template <bool BRUTE, bool TRACE, bool COUNT>
+__global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0)
+{
+    extern __shared__ float4 s_tris[];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned st_acc = 0, st_large = 0, st_small = 0, st_early = 0, st_inv = 0, st_rays = 0, st_ovf = 0;
+    unsigned n_nodes = 0, n_tris = 0;
+    if (c < Ch.C) {
+        const int C = Ch.C, D = Ch.D;
+        int kx = Ch.k[c];
+        float pix = Ch.pi[c];
+        V3 fx = {Ch.f[c], Ch.f[C + c], Ch.f[2 * C + c]};
+        int px = pixel_x(Ch.q[c], Ch.W), py = pixel_x(Ch.q[C + c], Ch.H);
+        unsigned pend_n = 0;
+        unsigned long long pend_i = 0, pend_A = 0;
+        uint32_t y[kMaxDim];
+        Path p;
+        int j = 0, large = 0, ky = 0, early = 0, need_setup = 1;
+        float xi = 0.f;
+        const bool traced = TRACE && (uint32_t)c % Ch.trace_stride == 0u;
+        while (true) {
+            V3 fy = {0.f, 0.f, 0.f};
+            bool finish = false;
+            if (need_setup) {
+                if (j >= Ch.E) break;
+                const uint64_t mut = mut0 + (uint64_t)j;
+                const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
+                const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+                large = (r0.x >> 8) < Ch.T_large;
+                xi = u24(r0.y);
+                int R = 1;
+                if (large) {
+                    for (int jj = 0; 4 * jj < D; ++jj) {
+                        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+                        y[4 * jj] = r.x;
+                        if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
+                        if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
+                        if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
+                    }
+                    ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+                } else {
+                    // every dimension perturbed with sigma of the current state's region
+                    const float sx = Ch.sig[kx];
+                    const float sigS2 = __fmul_rn(sx, Ch.S2);
+                    float lo = 0.f, hi = 0.f;
+                    bool check = false;
+                    for (int jj = 0; 2 * jj < D; ++jj) {
+                        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+                        const int d0 = 2 * jj;
+                        const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
+                        const uint32_t x0 = Ch.q[(size_t)d0 * C + c];
+                        y[d0] = (r.y >> 31) ? x0 - o0 : x0 + o0;
+                        uint32_t o1 = 0;
+                        if (d0 + 1 < D) {
+                            o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
+                            const uint32_t x1 = Ch.q[(size_t)(d0 + 1) * C + c];
+                            y[d0 + 1] = (r.w >> 31) ? x1 - o1 : x1 + o1;
+                        }
+                        if (jj == 0) {
+                            ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+                            const float sy = Ch.sig[ky];
+                            if (sy != sx) {
+                                // reverse kernel T_{k(y)}(x|y): every offset inside [sigma_y s1, sigma_y s2]
+                                check = true;
+                                lo = __fmul_rn(sy, Ch.S1);
+                                hi = __fmul_rn(sy, Ch.S2);
+                            }
+                        }
+                        if (check) {
+                            const float m0 = __ull2float_rn((unsigned long long)abs((long long)(int32_t)o0));
+                            if (!(m0 >= lo && m0 <= hi)) R = 0;
+                            if (d0 + 1 < D) {
+                                const float m1 = __ull2float_rn((unsigned long long)abs((long long)(int32_t)o1));
+                                if (!(m1 >= lo && m1 <= hi)) R = 0;
+                            }
+                        }
+                    }
+                }
+                early = !R;
+                if (!R) {
+                    finish = true;
+                } else if (S.toy) {
+                    const float v = toy_eval(S, y[0], y[1]);
+                    fy = {v, v, v};
+                    finish = true;
+                } else {
+                    path_begin(p, S, y);
+                    need_setup = 0;
+                }
+            }
+            if (!finish) {
+                int ovf = 0;
+                const Hit h = trace_one<BRUTE>(S, s_tris, p, ovf, n_nodes, n_tris);
+                ++st_rays;
+                if (ovf) {
+                    ++st_ovf;
+                    p.done = 1;
+                    p.L = {0.f, 0.f, 0.f};
+                } else {
+                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, h);
+                }
+                if (!p.done) continue;
+                fy = p.L;
+                finish = true;
+            }
+            // ---- finish the mutation: acceptance, statistics, MH update, splat
+            float piy = lum(fy.x, fy.y, fy.z);
+            int invalid = 0;
+            if (!isfinite(piy)) {
+                fy = {0.f, 0.f, 0.f};
+                piy = 0.f;
+                invalid = 1;
+                ++st_inv;
+            }
+            float a;
+            if (early) {
+                a = 0.0f;
+            } else {
+                const float ptx = Ch.weighted ? pix / Ch.wf[kx] : pix;
+                const float pty = Ch.weighted ? piy / Ch.wf[ky] : piy;
+                a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
+            }
+            const int accept = xi < a;
+            if (large) {
+                ++st_large;
+                atomicAdd(&Ch.Bk[ky], (double)piy);
+            } else {
+                ++st_small;
+                pend_i += 1;
+                pend_A += (unsigned long long)__float2ull_rn(a * 4294967296.0f);
+            }
+            st_early += early;
+            if (traced) {
+                const unsigned long long idx = Ch.trace_base + (unsigned long long)(c / Ch.trace_stride) * Ch.E + j;
+                if (idx < Ch.trace_cap) {
+                    uint32_t hsh = 2166136261u;
+                    for (int d = 0; d < D; ++d) hsh = (hsh ^ y[d]) * 16777619u;
+                    rmlt_trace_record r;
+                    r.f[0] = fy.x; r.f[1] = fy.y; r.f[2] = fy.z;
+                    r.a = a;
+                    r.qhash = hsh;
+                    r.flags = (uint32_t)accept | ((uint32_t)large << 1) | ((uint32_t)early << 2) | ((uint32_t)invalid << 3);
+                    Ch.trace[idx] = r;
+                }
+            }
+            if (accept) {
+                // flush the visits, splats and statistics of the state being left
+                if (pend_n) {
+                    atomicAdd(&Ch.hist[kx], (unsigned long long)pend_n);
+                    if (pix > 0.0f) {
+                        double* dst = Ch.img + 3 * ((size_t)py * Ch.W + px);
+                        const double s = (double)pend_n / (double)pix;
+                        atomicAdd(dst + 0, s * fx.x);
+                        atomicAdd(dst + 1, s * fx.y);
+                        atomicAdd(dst + 2, s * fx.z);
+                    }
+                }
+                if (pend_i) {
+                    atomicAdd(&Ch.vis[kx], pend_i);
+                    atomicAdd(&Ch.acc[kx], pend_A);
+                }
+                pend_n = 0;
+                pend_i = pend_A = 0;
+                for (int d = 0; d < D; ++d) Ch.q[(size_t)d * C + c] = y[d];
+                fx = fy;
+                pix = piy;
+                kx = ky;
+                px = pixel_x(y[0], Ch.W);
+                py = pixel_x(y[1], Ch.H);
+                ++st_acc;
+            }
+            pend_n += 1;
+            ++j;
+            need_setup = 1;
+        }
+        // end of epoch: flush and write back the cached state
+        if (pend_n) {
+            atomicAdd(&Ch.hist[kx], (unsigned long long)pend_n);
+            if (pix > 0.0f) {
+                double* dst = Ch.img + 3 * ((size_t)py * Ch.W + px);
+                const double s = (double)pend_n / (double)pix;
+                atomicAdd(dst + 0, s * fx.x);
+                atomicAdd(dst + 1, s * fx.y);
+                atomicAdd(dst + 2, s * fx.z);
+            }
+        }
+        if (pend_i) {
+            atomicAdd(&Ch.vis[kx], pend_i);
+            atomicAdd(&Ch.acc[kx], pend_A);
+        }
+        Ch.k[c] = kx;
+        Ch.pi[c] = pix;
+        Ch.f[c] = fx.x;
+        Ch.f[C + c] = fx.y;
+        Ch.f[2 * C + c] = fx.z;
+    }
+    // warp-aggregated statistics
+    unsigned long long v[9] = {st_acc, st_large, st_small, st_early, st_inv, st_rays, st_ovf, n_nodes, n_tris};
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+        if (s >= 7 && !COUNT) break;
+        const unsigned long long t = warp_sum(v[s]);
+        if (lane == 0 && t) atomicAdd(&Ch.stats[s], t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// region update at the epoch boundary (Alg. 1 lines 13-18; eqs.
+// est_exp_acc, update_lambda, step_size_n), binary64 with explicit rounding
+// ---------------------------------------------------------------------------
+__global__ void region_update_kernel(const DevChains Ch, int init_only)
+{
+    for (int k = threadIdx.x; k < Ch.m; k += blockDim.x) {
+        double lam = Ch.lam[k];
+        if (!init_only && Ch.vis[k] >= (unsigned long long)Ch.L) {
+            const double ah = __ddiv_rn((double)Ch.acc[k], __dmul_rn(4294967296.0, (double)Ch.vis[k]));
+            const int sg = ah > Ch.alpha_star ? 1 : (ah < Ch.alpha_star ? -1 : 0);
+            const double gs = __ddiv_rn(Ch.gamma_scale, __dsqrt_rn((double)Ch.n[k]));
+            const double g = Ch.gamma_max < gs ? Ch.gamma_max : gs;
+            lam = __dadd_rn(lam, __dmul_rn(g, (double)sg));
+            if (lam < Ch.lambda_min) lam = Ch.lambda_min;
+            if (lam > Ch.lambda_max) lam = Ch.lambda_max;
+            Ch.lam[k] = lam;
+            Ch.n[k] += 1;
+            Ch.vis[k] = 0;
+            Ch.acc[k] = 0;
+        }
+        // sigma_k = sqrt(exp(lambda_k)) = 2^(lambda_k / (2 ln 2))
+        Ch.sig[k] = exp2_ordered(__double2float_rn(__dmul_rn(lam, 0.7213475204444817)));
+    }
+    if (!Ch.weighted || init_only) return;
+    __syncthreads();
+    // region-weighted target: cumulative share of w_k h_k per epoch, fixed order
+    if (threadIdx.x == 0) {
+        const double m = (double)Ch.m;
+        double S = 0.0;
+        for (int k = 0; k < Ch.m; ++k) S = __dadd_rn(S, __dmul_rn(Ch.w[k], (double)(Ch.hist[k] - Ch.hprev[k])));
+        if (S > 0.0) {
+            double T = 0.0;
+            for (int k = 0; k < Ch.m; ++k) {
+                Ch.Rc[k] = __dadd_rn(Ch.Rc[k], __ddiv_rn(__dmul_rn(Ch.w[k], (double)(Ch.hist[k] - Ch.hprev[k])), S));
+            }
+            for (int k = 0; k < Ch.m; ++k) T = __dadd_rn(T, Ch.Rc[k]);
+            const double fl = __ddiv_rn(Ch.w_floor, m);
+            for (int k = 0; k < Ch.m; ++k) {
+                const double s = __ddiv_rn(Ch.Rc[k], T);
+                Ch.w[k] = __dmul_rn(m, s > fl ? s : fl);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < Ch.m; k += blockDim.x) {
+        Ch.hprev[k] = Ch.hist[k];
+        Ch.wf[k] = __double2float_rn(Ch.w[k]);
+    }
+}
+
+__global__ void fill_regions_kernel(const DevChains Ch, double lambda_init)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ch.m; k += gridDim.x * blockDim.x) {
+        Ch.lam[k] = lambda_init;
+        Ch.n[k] = 1;
+        Ch.vis[k] = Ch.acc[k] = Ch.hist[k] = Ch.hprev[k] = 0;
+        Ch.w[k] = 1.0;
+        Ch.Rc[k] = 0.0;
+        Ch.wf[k] = 1.0f;
+        Ch.Bk[k] = 0.0;
+        Ch.sig[k] = exp2_ordered(__double2float_rn(__dmul_rn(lambda_init, 0.7213475204444817)));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bootstrap (Sec. 3.2: b by independent Monte Carlo in a preprocess) and the
+// initial states (stratified inverse CDF of pi)
+// ---------------------------------------------------------------------------
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevScene S, const DevChains Ch,
+                                                                     long long n_boot, const BootScratch B)
+{
+    extern __shared__ float4 s_tris[];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_boot) return;
+    uint32_t y[kMaxDim];
+    const int D = Ch.D;
+    for (int jj = 0; 4 * jj < D; ++jj) {
+        const uint4 r = philox((uint32_t)s, (uint32_t)((unsigned long long)s >> 32), 0xFFFFFFFFu,
+                               0x8000u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        y[4 * jj] = r.x;
+        if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
+        if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
+        if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
+    }
+    V3 f = {0.f, 0.f, 0.f};
+    unsigned nn = 0, nt = 0;
+    if (S.toy) {
+        const float v = toy_eval(S, y[0], y[1]);
+        f = {v, v, v};
+    } else {
+        Path p;
+        path_begin(p, S, y);
+        while (!p.done) {
+            int ovf = 0;
+            const Hit h = trace_one<BRUTE>(S, s_tris, p, ovf, nn, nt);
+            if (ovf) { p.L = {0.f, 0.f, 0.f}; break; }
+            path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, h);
+        }
+        f = p.L;
+    }
+    float pv = lum(f.x, f.y, f.z);
+    if (!isfinite(pv)) { f = {0.f, 0.f, 0.f}; pv = 0.f; }
+    B.pi[s] = pv;
+    B.f[s] = f.x;
+    B.f[n_boot + s] = f.y;
+    B.f[2 * n_boot + s] = f.z;
+    const int k = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+    if (pv != 0.f) atomicAdd(&Ch.Bk[k], (double)pv);
+}
+
+// Initial state of chain c: weighted reservoir sampling over its own K
+// uniform samples s in [cK, (c+1)K): keep s when v_s cum_s < pi_s, which picks
+// s with probability pi_s / sum(pi) (v_s a uniform of its own).  The slice sum
+// goes to `partial` for the normaliser b.
+__global__ void bootstrap_select_kernel(const DevChains Ch, long long K, const BootScratch B)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Ch.C) return;
+    const long long n_eff = K * Ch.C;
+    double cum = 0.0;
+    long long sel = -1;
+    for (long long i = 0; i < K; ++i) {
+        const long long s = (long long)c * K + i;
+        const double v = (double)B.pi[s];
+        cum += v;
+        const uint4 r = philox((uint32_t)s, (uint32_t)((unsigned long long)s >> 32), 0xFFFFFFFFu, 0x7FFFu,
+                               Ch.seed_lo, Ch.seed_hi);
+        if (v > 0.0 && (double)u24(r.x) * cum < v) sel = s;
+    }
+    if (sel < 0) sel = (long long)c * K;
+    B.partial[c] = cum;
+    const int D = Ch.D, C = Ch.C;
+    uint32_t q0 = 0, q1 = 0;
+    for (int jj = 0; 4 * jj < D; ++jj) {
+        const uint4 r = philox((uint32_t)sel, (uint32_t)((unsigned long long)sel >> 32), 0xFFFFFFFFu,
+                               0x8000u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        const uint32_t v[4] = {r.x, r.y, r.z, r.w};
+        for (int a = 0; a < 4 && 4 * jj + a < D; ++a) Ch.q[(size_t)(4 * jj + a) * C + c] = v[a];
+        if (jj == 0) { q0 = r.x; q1 = r.y; }
+    }
+    Ch.f[c] = B.f[sel];
+    Ch.f[C + c] = B.f[n_eff + sel];
+    Ch.f[2 * C + c] = B.f[2 * n_eff + sel];
+    Ch.pi[c] = B.pi[sel];
+    Ch.k[c] = pixel_x(q0, Ch.W) / Ch.region_px + (pixel_x(q1, Ch.H) / Ch.region_px) * Ch.nx;
+}
+
+// fixed-order binary64 sum of the per-chain slice sums (deterministic)
+__global__ void __launch_bounds__(256) bootstrap_total_kernel(int C, const BootScratch B)
+{
+    __shared__ double sh[256];
+    const int per = (C + 255) / 256;
+    double acc = 0.0;
+    for (int i = 0; i < per; ++i) {
+        const int c = threadIdx.x * per + i;
+        if (c < C) acc += B.partial[c];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) B.total[0] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// image read-out: plain target I_j W H = (b W H / N) sum f/pi; region-weighted
+// target normalised per region by its mass B_k over its visits h_k
+// ---------------------------------------------------------------------------
+__global__ void read_image_kernel(const DevChains Ch, const double* bhat_total, long long n_boot, double n_total,
+                                  int normalized, double* out)
+{
+    const long long n = (long long)Ch.W * Ch.H;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = 1.0;
+        if (normalized) {
+            const double WH = (double)Ch.W * (double)Ch.H;
+            if (!Ch.weighted) {
+                const double bhat = bhat_total[0] / (double)n_boot;
+                s = n_total > 0.0 ? bhat * WH / n_total : 0.0;
+            } else {
+                const int x = (int)(i % Ch.W), y = (int)(i / Ch.W);
+                const int k = x / Ch.region_px + (y / Ch.region_px) * Ch.nx;
+                // uniform samples: the bootstrap plus every large-step proposal
+                const double nU = (double)n_boot + (double)Ch.stats[kStLarge];
+                s = (Ch.hist[k] > 0 && nU > 0.0) ? WH * (Ch.Bk[k] / nU) / (double)Ch.hist[k] : 0.0;
+            }
+        }
+        out[3 * i + 0] = Ch.img[3 * i + 0] * s;
+        out[3 * i + 1] = Ch.img[3 * i + 1] * s;
+        out[3 * i + 2] = Ch.img[3 * i + 2] * s;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <bool B, bool T, bool K>
+static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
+{
+    const int blocks = (c.C + kChainBlock - 1) / kChainBlock;
+    const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
+    auto kern = chain_epoch_kernel<B, T, K>;
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace, bool count_work,
+                               cudaStream_t st)
+{
+    if (s.brute) {
+        if (trace) return count_work ? launch_epoch_t<true, true, true>(s, c, mut0, st)
+                                     : launch_epoch_t<true, true, false>(s, c, mut0, st);
+        return count_work ? launch_epoch_t<true, false, true>(s, c, mut0, st)
+                          : launch_epoch_t<true, false, false>(s, c, mut0, st);
+    }
+    if (trace) return count_work ? launch_epoch_t<false, true, true>(s, c, mut0, st)
+                                 : launch_epoch_t<false, true, false>(s, c, mut0, st);
+    return count_work ? launch_epoch_t<false, false, true>(s, c, mut0, st)
+                      : launch_epoch_t<false, false, false>(s, c, mut0, st);
+}
+
+cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st)
+{
+    region_update_kernel<<<1, 256, 0, st>>>(c, init_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st)
+{
+    fill_regions_kernel<<<(c.m + 255) / 256, 256, 0, st>>>(c, lambda_init);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot, const BootScratch& b,
+                             cudaStream_t st)
+{
+    const long long K = n_boot / c.C;
+    const long long n_eff = K * c.C;
+    const long long blocks = (n_eff + kChainBlock - 1) / kChainBlock;
+    const size_t shm = s.brute ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
+    cudaError_t e;
+    if (s.brute) {
+        if (shm > 48 * 1024) {
+            e = cudaFuncSetAttribute(bootstrap_eval_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e != cudaSuccess) return e;
+        }
+        bootstrap_eval_kernel<true><<<(unsigned)blocks, kChainBlock, shm, st>>>(s, c, n_eff, b);
+    } else {
+        bootstrap_eval_kernel<false><<<(unsigned)blocks, kChainBlock, 0, st>>>(s, c, n_eff, b);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bootstrap_select_kernel<<<(c.C + 127) / 128, 128, 0, st>>>(c, K, b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bootstrap_total_kernel<<<1, 256, 0, st>>>(c.C, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int64_t n_boot, double n_total,
+                              int normalized, double* out, cudaStream_t st)
+{
+    const long long n = (long long)c.W * c.H;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    read_image_kernel<<<blocks, 256, 0, st>>>(c, bhat_total, n_boot, n_total, normalized, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rmlt

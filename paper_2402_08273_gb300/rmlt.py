@@ -1,0 +1,319 @@
+"""Python binding of librmlt (the C ABI in include/rmlt.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch provides device memory (its caching allocator is installed as the
+library's allocator) and the CUDA stream.  There is no CPU fallback: if the
+library cannot be built or loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from pathlib import Path
+
+import numpy as np
+
+from . import _build
+
+RMLT_OK = 0
+STATUS = {0: "RMLT_OK", -1: "RMLT_E_INVALID_ARG", -2: "RMLT_E_INVALID_SCENE", -3: "RMLT_E_OOM",
+          -4: "RMLT_E_CUDA", -5: "RMLT_E_STATE", -6: "RMLT_E_TIMEOUT", -7: "RMLT_E_OVERFLOW",
+          -8: "RMLT_E_IO"}
+LAMBERT, GGX = 0, 1
+TARGET_PLAIN, TARGET_REGION_WEIGHTED = 0, 1
+MAX_DEPTH = 12
+
+
+class RmltError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Material(C.Structure):
+    _fields_ = [("type", C.c_int32), ("albedo", C.c_float * 3), ("emission", C.c_float * 3),
+                ("roughness", C.c_float)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("verts", C.POINTER(C.c_float)), ("n_tris", C.c_int32),
+                ("tris", C.POINTER(C.c_uint32)), ("mat_id", C.POINTER(C.c_uint32)),
+                ("n_mats", C.c_int32), ("mats", C.POINTER(Material)), ("camera", Camera),
+                ("brute_force_max", C.c_int32)]
+
+
+class ChainParams(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("region_px", C.c_int32), ("max_depth", C.c_int32), ("epoch_len", C.c_int32),
+                ("L", C.c_int32), ("target_mode", C.c_int32), ("n_bootstrap", C.c_int64),
+                ("seed", C.c_uint64), ("p_large", C.c_double), ("s1", C.c_double),
+                ("s2", C.c_double), ("alpha_star", C.c_double), ("gamma_max", C.c_double),
+                ("gamma_scale", C.c_double), ("lambda_init", C.c_double),
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("w_floor", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("mutations", C.c_uint64), ("accepted", C.c_uint64), ("large", C.c_uint64),
+                ("small", C.c_uint64), ("early_reject", C.c_uint64), ("invalid_paths", C.c_uint64),
+                ("rays", C.c_uint64), ("stack_overflow", C.c_uint64), ("epochs", C.c_uint64),
+                ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
+                ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64)]
+
+
+TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
+                        ("flags", np.uint32)])
+assert TRACE_DTYPE.itemsize == 24
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+# (name, restype, argtypes) of every function declared in include/rmlt.h
+_P = C.POINTER
+_SIGS = [
+    ("rmlt_abi_version", C.c_int, []),
+    ("rmlt_last_error", C.c_char_p, []),
+    ("rmlt_create", C.c_int, [_P(C.c_void_p), C.c_int, C.c_void_p]),
+    ("rmlt_set_allocator", C.c_int, [C.c_void_p, ALLOC_FN, FREE_FN, C.c_void_p]),
+    ("rmlt_load_scene", C.c_int, [C.c_void_p, _P(SceneDesc)]),
+    ("rmlt_load_toy_integrand", C.c_int, [C.c_void_p, _P(C.c_double)]),
+    ("rmlt_init_chains", C.c_int, [C.c_void_p, _P(ChainParams)]),
+    ("rmlt_step", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("rmlt_read_image", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("rmlt_read_region_hist", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("rmlt_read_region_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
+    ("rmlt_read_chain_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rmlt_read_stats", C.c_int, [C.c_void_p, _P(Stats)]),
+    ("rmlt_set_trace", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64,
+                                 C.c_uint32]),
+    ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
+    ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
+    ("rmlt_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("rmlt_restore", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("rmlt_synchronize", C.c_int, [C.c_void_p]),
+    ("rmlt_destroy", None, [C.c_void_p]),
+]
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib(build: bool = True):
+    """Load librmlt.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    L = C.CDLL(str(path))
+    for name, res, args in _SIGS:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != RMLT_OK:
+        raise RmltError(st, lib().rmlt_last_error().decode(errors="replace"))
+
+
+def default_params(**kw) -> dict:
+    """Chain parameters: Sec. 7.1 values (L = 10, gamma_max = 1, gamma_scale = 5,
+    lambda_min = -30, alpha* = 0.5) with Kelemen's s1 = 1/1024, s2 = 1/64."""
+    p = dict(n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
+             target_mode=TARGET_PLAIN, n_bootstrap=1 << 16, seed=1, p_large=0.3, s1=1 / 1024,
+             s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
+             lambda_min=-30.0, lambda_max=None, w_floor=1e-3)
+    p.update(kw)
+    if p["lambda_max"] is None:
+        p["lambda_max"] = 2.0 * math.log(1.0 / (2.0 * p["s2"]))
+    return p
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+class Renderer:
+    """One rmlt context: a scene, a population of chains and their region tables."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RmltError(-4, "no CUDA device: librmlt has no CPU fallback")
+        self._torch = torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        L = lib()
+        h = C.c_void_p()
+        _check(L.rmlt_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self._keep = []
+        if torch_allocator:
+            dev, strm = device, self.stream
+
+            def _alloc(user, nbytes, stream_ptr):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+                except Exception:   # out of memory: the library reports RMLT_E_OOM
+                    return None
+
+            def _free(user, ptr, stream_ptr):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+            _check(L.rmlt_set_allocator(self.h, self._alloc_cb, self._free_cb, None))
+        self.params = None
+        self.D = self.m = None
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rmlt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- scene ---------------------------------------------------------------
+    def load_scene(self, scene: dict, brute_force_max: int = 0):
+        v = np.ascontiguousarray(scene["verts"], np.float32)
+        t = np.ascontiguousarray(scene["tris"], np.uint32)
+        mid = np.ascontiguousarray(scene["mat_id"], np.uint32)
+        nm = len(scene["mat_type"])
+        mats = (Material * nm)()
+        for i in range(nm):
+            mats[i].type = int(scene["mat_type"][i])
+            for a in range(3):
+                mats[i].albedo[a] = float(scene["albedo"][i][a])
+                mats[i].emission[a] = float(scene["emission"][i][a])
+            mats[i].roughness = float(scene["roughness"][i])
+        cam = np.asarray(scene["camera"], np.float32)
+        camera = Camera((C.c_float * 3)(*cam[0:3]), (C.c_float * 3)(*cam[3:6]),
+                        (C.c_float * 3)(*cam[6:9]), float(cam[9]))
+        desc = SceneDesc(len(v), v.ctypes.data_as(_P(C.c_float)), len(t),
+                         t.ctypes.data_as(_P(C.c_uint32)), mid.ctypes.data_as(_P(C.c_uint32)), nm,
+                         mats, camera, int(brute_force_max))
+        _check(lib().rmlt_load_scene(self.h, C.byref(desc)))
+        self.params = None
+
+    def load_toy_integrand(self, params):
+        p = np.ascontiguousarray(params, np.float64)
+        _check(lib().rmlt_load_toy_integrand(self.h, p.ctypes.data_as(_P(C.c_double))))
+        self.params = None
+
+    # -- chains --------------------------------------------------------------
+    def init_chains(self, **kw):
+        p = default_params(**kw)
+        cp = ChainParams(**p)
+        _check(lib().rmlt_init_chains(self.h, C.byref(cp)))
+        self.params = p
+        self.D = 2 + 5 * p["max_depth"]
+        nx = -(-p["width"] // p["region_px"])
+        ny = -(-p["height"] // p["region_px"])
+        self.m = nx * ny
+
+    def step(self, n_mutations: int):
+        _check(lib().rmlt_step(self.h, int(n_mutations)))
+
+    def synchronize(self):
+        _check(lib().rmlt_synchronize(self.h))
+
+    # -- read-out ------------------------------------------------------------
+    def read_image(self, normalized: bool = True, out=None):
+        """[H, W, 3] float64: numpy (host) unless `out` is given (host array or CUDA tensor)."""
+        if out is None:
+            out = np.zeros((self.params["height"], self.params["width"], 3), np.float64)
+        _check(lib().rmlt_read_image(self.h, _ptr(out), int(normalized)))
+        return out
+
+    def read_region_hist(self, out=None):
+        if out is None:
+            out = np.zeros(self.m, np.uint64)
+        _check(lib().rmlt_read_region_hist(self.h, _ptr(out)))
+        return out
+
+    def read_region_params(self) -> dict:
+        lam = np.zeros(self.m)
+        n = np.zeros(self.m, np.int64)
+        i = np.zeros(self.m, np.uint64)
+        A = np.zeros(self.m, np.uint64)
+        w = np.zeros(self.m)
+        _check(lib().rmlt_read_region_params(self.h, _ptr(lam), _ptr(n), _ptr(i), _ptr(A), _ptr(w)))
+        return {"lambda": lam, "n": n, "i": i, "A": A, "w": w}
+
+    def read_chain_state(self) -> dict:
+        Cn = self.params["n_chains"]
+        q = np.zeros((self.D, Cn), np.uint32)
+        f = np.zeros((3, Cn), np.float32)
+        k = np.zeros(Cn, np.int32)
+        _check(lib().rmlt_read_chain_state(self.h, _ptr(q), _ptr(f), _ptr(k)))
+        return {"q": q, "f": f, "k": k}
+
+    def read_stats(self) -> dict:
+        s = Stats()
+        _check(lib().rmlt_read_stats(self.h, C.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def set_work_counters(self, enable: bool):
+        _check(lib().rmlt_set_work_counters(self.h, int(enable)))
+
+    def memory_usage(self) -> int:
+        b = C.c_uint64()
+        _check(lib().rmlt_memory_usage(self.h, C.byref(b)))
+        return int(b.value)
+
+    # -- test instrument -----------------------------------------------------
+    def set_trace(self, records=None, lambdas=None, chain_stride: int = 1):
+        """records: CUDA uint8 tensor of n * 24 bytes; lambdas: CUDA float64 tensor."""
+        if records is None:
+            _check(lib().rmlt_set_trace(self.h, None, 0, None, 0, 1))
+            return
+        cap = records.numel() * records.element_size() // TRACE_DTYPE.itemsize
+        lcap = lambdas.numel() if lambdas is not None else 0
+        _check(lib().rmlt_set_trace(self.h, _ptr(records), cap, _ptr(lambdas), lcap, chain_stride))
+
+    # -- checkpoint ----------------------------------------------------------
+    def save(self, path):
+        _check(lib().rmlt_save(self.h, str(path).encode()))
+
+    def restore(self, path):
+        _check(lib().rmlt_restore(self.h, str(path).encode()))
+        # the checkpoint header: magic[8], abi u32, pad u32, scene hash u64, params
+        raw = Path(path).read_bytes()[24:24 + C.sizeof(ChainParams)]
+        cp = ChainParams.from_buffer_copy(raw)
+        self.params = {name: getattr(cp, name) for name, _ in ChainParams._fields_}
+        self.D = 2 + 5 * self.params["max_depth"]
+        nx = -(-self.params["width"] // self.params["region_px"])
+        ny = -(-self.params["height"] // self.params["region_px"])
+        self.m = nx * ny
+
+
+def trace_to_numpy(records_tensor) -> np.ndarray:
+    """View a trace buffer (CUDA uint8 tensor) as structured records on the host."""
+    raw = records_tensor.cpu().numpy().view(np.uint8)
+    return raw[: (raw.size // TRACE_DTYPE.itemsize) * TRACE_DTYPE.itemsize].view(TRACE_DTYPE)
