@@ -109,6 +109,8 @@ typedef struct {
     int32_t n_regions, dims;
     uint64_t node_visits;      /* BVH internal nodes visited (only while work counters are on) */
     uint64_t tri_tests;        /* ray-triangle tests in BVH leaves (only while work counters are on) */
+    uint64_t sched[6];         /* work counters on: warp loop iterations, traversing lanes summed over
+                                  them, shade batches, lanes shaded, setup batches, lanes set up */
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -199,6 +201,13 @@ rmlt_status rmlt_set_trace(rmlt_ctx* ctx, rmlt_trace_record* records, uint64_t c
  * an instrumented build of the same chain kernel; enable = 0 returns to the
  * uninstrumented kernel.  The chain trajectory does not depend on it. */
 rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
+
+/* Scheduling knobs of the chain kernel: a warp shades the resolved rays of its
+ * lanes once at least `batch_shade` of them are waiting, and finishes
+ * mutations / draws proposals once `batch_setup` lanes are waiting (both in
+ * 1..32; smaller values when nothing else is left).  They change speed only,
+ * never results.  Defaults 8 and 8. */
+rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup);
 
 /* Bytes of device memory the context holds. */
 rmlt_status rmlt_memory_usage(rmlt_ctx* ctx, uint64_t* bytes);

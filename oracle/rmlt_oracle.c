@@ -567,6 +567,10 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
         double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         double cosi = -v_dot(Tr->n, d);
         mloc = dmin(mloc, fabs(cosi));
+        /* a short segment (a corner) amplifies the binary32 hit-point error
+         * like 2^-24 scale / t: below t / scale = 6e-4 it counts as
+         * near-degenerate */
+        mloc = dmin(mloc, t / s->scale / 60.0);
         double ns[3];
         for (int a = 0; a < 3; ++a) ns[a] = cosi > 0 ? Tr->n[a] : -Tr->n[a];
         if (b == 0 && M->emissive && cosi > 0)
@@ -590,6 +594,15 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
             for (int a = 0; a < 3; ++a) wi[a] /= dist;
             double cx = v_dot(ns, wi), cl = -v_dot(LT->n, wi);
             if (cx > 0 && cl > 0) {
+                /* a grazing cosine makes the contribution ill-conditioned in
+                 * binary32 (relative error ~ 2^-24 / cos): below 1e-3 it
+                 * counts as a near-degenerate decision */
+                mloc = dmin(mloc, 0.01 * dmin(cx, cl));
+                /* and so does a light point close to x relative to the scene:
+                 * the binary32 geometry term's relative error grows like
+                 * 2^-24 scale / (dist cos); below dist cos / scale = 6e-4 it
+                 * counts as near-degenerate */
+                mloc = dmin(mloc, dist * dmin(cx, cl) / s->scale / 60.0);
                 double xo[3], sd[3];
                 for (int a = 0; a < 3; ++a) xo[a] = x[a] + s->eps * ns[a];
                 v_sub(p, xo, sd);
@@ -615,6 +628,7 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
         if (M->type == 0) {
             double r = sqrt(bu);
             loc[0] = r * cos(phi); loc[1] = r * sin(phi); loc[2] = sqrt(dmax(0.0, 1.0 - bu));
+            mloc = dmin(mloc, 0.01 * loc[2]);
             to_world(loc, ft, fb, ns, wi);
             for (int a = 0; a < 3; ++a) T[a] *= M->albedo[a];
         } else {
@@ -630,6 +644,7 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
             if (dom <= 0) break;
             for (int a = 0; a < 3; ++a) wi[a] = 2.0 * dom * mv[a] - wo[a];
             double ci = v_dot(wi, ns), co = v_dot(wo, ns);
+            mloc = dmin(mloc, 0.01 * dmin(dom, dmin(fabs(ci), co)));
             if (ci <= 0) break;
             double G = ggx_g1(co, a2) * ggx_g1(ci, a2);
             double c5 = pow(1.0 - dom, 5.0);

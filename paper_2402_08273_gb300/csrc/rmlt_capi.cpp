@@ -87,6 +87,7 @@ struct rmlt_ctx {
     uint64_t tr_lam_cap = 0;
     uint32_t tr_stride = 1;
     bool count_work = false;
+    int batch_shade = 8, batch_setup = 8;
 
     rmlt_status dalloc(std::vector<Alloc>& pool, size_t bytes, void** out)
     {
@@ -518,6 +519,8 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
     const uint32_t n_traced = (uint32_t)(((uint64_t)c->Ch.C + c->tr_stride - 1) / c->tr_stride);
     for (uint64_t e = 0; e < n_ep; ++e) {
         DevChains Ch = c->Ch;
+        Ch.batch_shade = c->batch_shade;
+        Ch.batch_setup = c->batch_setup;
         const bool trace = c->tr != nullptr;
         if (trace) {
             Ch.trace = c->tr;
@@ -630,6 +633,17 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->dims = c->Ch.D;
     out->node_visits = s[kStNodes];
     out->tri_tests = s[kStTris];
+    for (int i = 0; i < 6; ++i) out->sched[i] = s[kStIters + i];
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_tuning(rmlt_ctx* c, int batch_shade, int batch_setup)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (batch_shade < 1 || batch_shade > 32 || batch_setup < 1 || batch_setup > 32)
+        return fail(RMLT_E_INVALID_ARG, "batch sizes must be in 1..32");
+    c->batch_shade = batch_shade;
+    c->batch_setup = batch_setup;
     return RMLT_OK;
 }
 

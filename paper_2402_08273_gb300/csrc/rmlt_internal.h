@@ -18,7 +18,12 @@ constexpr int kChainBlock = 128;                    // threads per block of the 
 // statistic slots in DevChains::stats
 enum StatSlot {
     kStAccepted = 0, kStLarge, kStSmall, kStEarly, kStInvalid, kStRays, kStOverflow,
-    kStNodes, kStTris, kStCount = 16
+    kStNodes, kStTris,
+    // scheduling counters (work-counter builds only): warp loop iterations,
+    // lanes traversing summed over iterations, shade batches and their lanes,
+    // finish/setup batches and their lanes
+    kStIters, kStTravLanes, kStShadeBatches, kStShadeLanes, kStSetupBatches, kStSetupLanes,
+    kStCount = 16
 };
 
 // Leaf references in the BVH: bit 31 set, bits 28..30 = count - 1, bits 0..27 = first triangle.
@@ -68,6 +73,8 @@ struct DevChains {
     float S1 = 0.f, S2 = 0.f, log2_ratio = 0.f;
     double alpha_star = 0.5, gamma_max = 1.0, gamma_scale = 5.0, lambda_min = -30.0, lambda_max = 7.0;
     double w_floor = 1e-3;
+    // lanes that wait before the warp shades / finishes and draws together
+    int32_t batch_shade = 8, batch_setup = 8;
     // trace instrument
     rmlt_trace_record* trace = nullptr;
     unsigned long long trace_cap = 0, trace_base = 0;

@@ -138,6 +138,10 @@ __device__ __forceinline__ Hit trace_brute(const float4* __restrict__ tr, int n,
 // BVH2 traversal with a per-thread stack: both children's boxes come with the
 // parent (16-byte loads through the read-only path), the nearer child is
 // visited first.  The slab test widens tmax by 3 ulp (robust traversal).
+// One node or one leaf per iteration and a single exit, so the lanes of a
+// warp reconverge at the end of every iteration.
+constexpr uint32_t kNoRef = 0xFFFFFFFFu;
+
 __device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                          V3 o, V3 d, float tmax, bool any, int& overflow,
                                          unsigned& n_nodes, unsigned& n_tris)
@@ -150,7 +154,8 @@ __device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const
     uint32_t stack[kStackSize];
     int sp = 0;
     uint32_t ref = 0;
-    while (true) {
+    while (ref != kNoRef) {
+        uint32_t next;
         if (!(ref & kLeafBit)) {
             ++n_nodes;
             const float4 n0 = __ldg(&nodes[4 * ref + 0]);
@@ -158,13 +163,11 @@ __device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const
             const float4 n2 = __ldg(&nodes[4 * ref + 2]);
             const float4 n3 = __ldg(&nodes[4 * ref + 3]);
             const float tcap = h.t * 1.00000036f;
-            // child 0
             float a0 = fmaf(n0.x, id.x, -ood.x), b0 = fmaf(n0.y, id.x, -ood.x);
             float a1 = fmaf(n0.z, id.y, -ood.y), b1 = fmaf(n0.w, id.y, -ood.y);
             float a2 = fmaf(n2.x, id.z, -ood.z), b2 = fmaf(n2.y, id.z, -ood.z);
             const float tn0 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
             const float tf0 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
-            // child 1
             a0 = fmaf(n1.x, id.x, -ood.x); b0 = fmaf(n1.y, id.x, -ood.x);
             a1 = fmaf(n1.z, id.y, -ood.y); b1 = fmaf(n1.w, id.y, -ood.y);
             a2 = fmaf(n2.z, id.z, -ood.z); b2 = fmaf(n2.w, id.z, -ood.z);
@@ -174,29 +177,133 @@ __device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const
             const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
             if (h0 && h1) {
                 const bool first0 = tn0 <= tn1;
-                if (sp >= kStackSize) { overflow = 1; break; }
-                stack[sp++] = first0 ? c1 : c0;
-                ref = first0 ? c0 : c1;
-                continue;
+                if (sp < kStackSize) stack[sp++] = first0 ? c1 : c0;
+                else overflow = 1;
+                next = first0 ? c0 : c1;
+            } else if (h0) {
+                next = c0;
+            } else if (h1) {
+                next = c1;
+            } else {
+                next = sp > 0 ? stack[--sp] : kNoRef;
             }
-            if (h0) { ref = c0; continue; }
-            if (h1) { ref = c1; continue; }
         } else {
             const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
+            bool found = false;
             for (uint32_t i = first; i < first + cnt; ++i) {
                 ++n_tris;
                 float t;
                 if (hit_tri(o, d, __ldg(&tris[3 * i]), __ldg(&tris[3 * i + 1]), __ldg(&tris[3 * i + 2]), h.t, t)) {
                     h.t = t;
                     h.tri = (int)i;
-                    if (any) return h;
+                    found = true;
                 }
             }
+            next = (any && found) ? kNoRef : (sp > 0 ? stack[--sp] : kNoRef);
         }
-        if (sp == 0) break;
-        ref = stack[--sp];
+        ref = overflow ? kNoRef : next;
     }
     return h;
+}
+
+// Stepwise traversal: the state of one ray between steps.  A step visits one
+// BVH node (both children tested), or the triangles of one leaf, or (brute
+// force) the next group of four triangles.
+struct Trav {
+    V3 o, d, id, ood;
+    float t;          // closest hit so far (initially tmax)
+    int tri;          // its triangle, -1 if none
+    uint32_t ref;     // node / leaf to visit next, kNoRef when done
+    int sp, any, overflow;
+};
+
+__device__ __forceinline__ void trav_begin(Trav& T, V3 o, V3 d, float tmax, int any)
+{
+    T.o = o;
+    T.d = d;
+    T.id = {1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+            1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+            1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z))};
+    T.ood = {o.x * T.id.x, o.y * T.id.y, o.z * T.id.z};
+    T.t = tmax;
+    T.tri = -1;
+    T.ref = 0;
+    T.sp = 0;
+    T.any = any;
+    T.overflow = 0;
+}
+
+// one step; returns true once the ray is resolved
+template <bool BRUTE>
+__device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevScene& S, const float4* s_tris,
+                                          unsigned& n_nodes, unsigned& n_tris)
+{
+    if (BRUTE) {
+        const int n = S.n_tris;
+        const int i0 = (int)T.ref;
+        const int i1 = i0 + 4 < n ? i0 + 4 : n;
+        bool found = false;
+        for (int i = i0; i < i1; ++i) {
+            float t;
+            if (hit_tri(T.o, T.d, s_tris[3 * i], s_tris[3 * i + 1], s_tris[3 * i + 2], T.t, t)) {
+                T.t = t;
+                T.tri = i;
+                found = true;
+            }
+        }
+        T.ref = (i1 >= n || (T.any && found)) ? kNoRef : (uint32_t)i1;
+        return T.ref == kNoRef;
+    }
+    uint32_t next;
+    const uint32_t ref = T.ref;
+    if (!(ref & kLeafBit)) {
+        ++n_nodes;
+        const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
+        const float4 n1 = __ldg(&S.nodes[4 * ref + 1]);
+        const float4 n2 = __ldg(&S.nodes[4 * ref + 2]);
+        const float4 n3 = __ldg(&S.nodes[4 * ref + 3]);
+        const float tcap = T.t * 1.00000036f;
+        const V3 id = T.id, ood = T.ood;
+        float a0 = fmaf(n0.x, id.x, -ood.x), b0 = fmaf(n0.y, id.x, -ood.x);
+        float a1 = fmaf(n0.z, id.y, -ood.y), b1 = fmaf(n0.w, id.y, -ood.y);
+        float a2 = fmaf(n2.x, id.z, -ood.z), b2 = fmaf(n2.y, id.z, -ood.z);
+        const float tn0 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+        const float tf0 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+        a0 = fmaf(n1.x, id.x, -ood.x); b0 = fmaf(n1.y, id.x, -ood.x);
+        a1 = fmaf(n1.z, id.y, -ood.y); b1 = fmaf(n1.w, id.y, -ood.y);
+        a2 = fmaf(n2.z, id.z, -ood.z); b2 = fmaf(n2.w, id.z, -ood.z);
+        const float tn1 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+        const float tf1 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+        const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+        const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (T.sp < kStackSize) stack[T.sp++] = first0 ? c1 : c0;
+            else T.overflow = 1;
+            next = first0 ? c0 : c1;
+        } else if (h0) {
+            next = c0;
+        } else if (h1) {
+            next = c1;
+        } else {
+            next = T.sp > 0 ? stack[--T.sp] : kNoRef;
+        }
+    } else {
+        const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
+        bool found = false;
+        for (uint32_t i = first; i < first + cnt; ++i) {
+            ++n_tris;
+            float t;
+            if (hit_tri(T.o, T.d, __ldg(&S.tris[3 * i]), __ldg(&S.tris[3 * i + 1]), __ldg(&S.tris[3 * i + 2]), T.t, t)) {
+                T.t = t;
+                T.tri = (int)i;
+                found = true;
+            }
+        }
+        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[--T.sp] : kNoRef);
+    }
+    T.ref = T.overflow ? kNoRef : next;
+    return T.ref == kNoRef;
 }
 
 // ---------------------------------------------------------------------------
@@ -407,205 +514,293 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 // ---------------------------------------------------------------------------
 // the chain step: E mutations per chain (Alg. 1 lines 8-19)
 // ---------------------------------------------------------------------------
+struct ChainLane {
+    // cached current state x
+    int kx, px, py;
+    float pix;
+    V3 fx;
+    // visits, splats and statistics of x not yet flushed
+    unsigned pend_n;
+    unsigned long long pend_i, pend_A;
+    // the mutation in flight
+    int j, large, ky, early;
+    float xi;
+    V3 fy;
+};
+
+// Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1 line
+// 10) and decide the reverse-kernel support; returns false when the proposal
+// needs no path (rejected early, or the toy integrand evaluated directly).
+__device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChains& Ch, int c, uint64_t mut0,
+                                               ChainLane& L, uint32_t* y, Path& p)
+{
+    const int C = Ch.C, D = Ch.D;
+    const uint64_t mut = mut0 + (uint64_t)L.j;
+    const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
+    const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+    L.large = (r0.x >> 8) < Ch.T_large;
+    L.xi = u24(r0.y);
+    int R = 1;
+    if (L.large) {
+        for (int jj = 0; 4 * jj < D; ++jj) {
+            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            y[4 * jj] = r.x;
+            if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
+            if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
+            if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
+        }
+        L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+    } else {
+        // every dimension perturbed with sigma of the current state's region
+        const float sx = Ch.sig[L.kx];
+        const float sigS2 = __fmul_rn(sx, Ch.S2);
+        float lo = 0.f, hi = 0.f;
+        bool check = false;
+        for (int jj = 0; 2 * jj < D; ++jj) {
+            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            const int d0 = 2 * jj;
+            const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
+            const uint32_t x0 = Ch.q[(size_t)d0 * C + c];
+            y[d0] = (r.y >> 31) ? x0 - o0 : x0 + o0;
+            uint32_t o1 = 0;
+            if (d0 + 1 < D) {
+                o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
+                const uint32_t x1 = Ch.q[(size_t)(d0 + 1) * C + c];
+                y[d0 + 1] = (r.w >> 31) ? x1 - o1 : x1 + o1;
+            }
+            if (jj == 0) {
+                L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+                const float sy = Ch.sig[L.ky];
+                if (sy != sx) {
+                    // reverse kernel T_{k(y)}(x|y): every offset inside [sigma_y s1, sigma_y s2]
+                    check = true;
+                    lo = __fmul_rn(sy, Ch.S1);
+                    hi = __fmul_rn(sy, Ch.S2);
+                }
+            }
+            if (check) {
+                const float m0 = __uint2float_rn(o0);
+                if (!(m0 >= lo && m0 <= hi)) R = 0;
+                if (d0 + 1 < D) {
+                    const float m1 = __uint2float_rn(o1);
+                    if (!(m1 >= lo && m1 <= hi)) R = 0;
+                }
+            }
+        }
+    }
+    L.early = !R;
+    L.fy = {0.f, 0.f, 0.f};
+    if (!R) return false;
+    if (S.toy) {
+        const float v = toy_eval(S, y[0], y[1]);
+        L.fy = {v, v, v};
+        return false;
+    }
+    path_begin(p, S, y);
+    return true;
+}
+
+__device__ __forceinline__ void flush_state(const DevChains& Ch, ChainLane& L)
+{
+    if (L.pend_n) {
+        atomicAdd(&Ch.hist[L.kx], (unsigned long long)L.pend_n);
+        if (L.pix > 0.0f) {
+            double* dst = Ch.img + 3 * ((size_t)L.py * Ch.W + L.px);
+            const double s = (double)L.pend_n / (double)L.pix;
+            atomicAdd(dst + 0, s * L.fx.x);
+            atomicAdd(dst + 1, s * L.fx.y);
+            atomicAdd(dst + 2, s * L.fx.z);
+        }
+    }
+    if (L.pend_i) {
+        atomicAdd(&Ch.vis[L.kx], L.pend_i);
+        atomicAdd(&Ch.acc[L.kx], L.pend_A);
+    }
+    L.pend_n = 0;
+    L.pend_i = L.pend_A = 0;
+}
+
+// acceptance (Sec. 3.2 with the mixture of Sec. 5.2), adaptation statistics
+// of the current region (Alg. 1 lines 11-12), MH update (line 19), splat
+template <bool TRACE>
+__device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool traced, ChainLane& L,
+                                                const uint32_t* y, unsigned (&st)[7])
+{
+    const int C = Ch.C, D = Ch.D;
+    V3 fy = L.fy;
+    float piy = lum(fy.x, fy.y, fy.z);
+    int invalid = 0;
+    if (!isfinite(piy)) {
+        fy = {0.f, 0.f, 0.f};
+        piy = 0.f;
+        invalid = 1;
+        ++st[4];
+    }
+    float a;
+    if (L.early) {
+        a = 0.0f;
+    } else {
+        const float ptx = Ch.weighted ? L.pix / Ch.wf[L.kx] : L.pix;
+        const float pty = Ch.weighted ? piy / Ch.wf[L.ky] : piy;
+        a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
+    }
+    const int accept = L.xi < a;
+    if (L.large) {
+        ++st[1];
+        atomicAdd(&Ch.Bk[L.ky], (double)piy);
+    } else {
+        ++st[2];
+        L.pend_i += 1;
+        L.pend_A += (unsigned long long)__float2ull_rn(a * 4294967296.0f);
+    }
+    st[3] += L.early;
+    if (TRACE && traced) {
+        const unsigned long long idx = Ch.trace_base + (unsigned long long)(c / Ch.trace_stride) * Ch.E + L.j;
+        if (idx < Ch.trace_cap) {
+            uint32_t hsh = 2166136261u;
+            for (int d = 0; d < D; ++d) hsh = (hsh ^ y[d]) * 16777619u;
+            rmlt_trace_record r;
+            r.f[0] = fy.x;
+            r.f[1] = fy.y;
+            r.f[2] = fy.z;
+            r.a = a;
+            r.qhash = hsh;
+            r.flags = (uint32_t)accept | ((uint32_t)L.large << 1) | ((uint32_t)L.early << 2) | ((uint32_t)invalid << 3);
+            Ch.trace[idx] = r;
+        }
+    }
+    if (accept) {
+        flush_state(Ch, L);      // visits, splats and statistics of the state being left
+        for (int d = 0; d < D; ++d) Ch.q[(size_t)d * C + c] = y[d];
+        L.fx = fy;
+        L.pix = piy;
+        L.kx = L.ky;
+        L.px = pixel_x(y[0], Ch.W);
+        L.py = pixel_x(y[1], Ch.H);
+        ++st[0];
+    }
+    L.pend_n += 1;
+}
+
+// One thread per chain; the unit of work is one traversal step.  Every loop
+// iteration advances each lane with a live ray by one BVH node or leaf.  A
+// lane whose ray is resolved waits until at least `batch_shade` lanes (or
+// every lane with work) are waiting, then the waiting lanes shade together
+// (path_on_hit: emission, next-event sample, BSDF sample -> the next ray).
+// Lanes whose path ended finish their mutation and draw the next proposal in
+// batches of `batch_setup` the same way.  The batches keep the expensive,
+// divergent parts convergent while the traversal keeps every lane busy.
+enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 };
+
 template <bool BRUTE, bool TRACE, bool COUNT>
 __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0)
 {
     extern __shared__ float4 s_tris[];
     if (BRUTE) stage_triangles(S, s_tris);
+    const unsigned FULL = 0xFFFFFFFFu;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned st_acc = 0, st_large = 0, st_small = 0, st_early = 0, st_inv = 0, st_rays = 0, st_ovf = 0;
+    const bool valid = c < Ch.C;
+    unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};   // accepted, large, small, early, invalid, rays, overflow
     unsigned n_nodes = 0, n_tris = 0;
-    if (c < Ch.C) {
-        const int C = Ch.C, D = Ch.D;
-        int kx = Ch.k[c];
-        float pix = Ch.pi[c];
-        V3 fx = {Ch.f[c], Ch.f[C + c], Ch.f[2 * C + c]};
-        int px = pixel_x(Ch.q[c], Ch.W), py = pixel_x(Ch.q[C + c], Ch.H);
-        unsigned pend_n = 0;
-        unsigned long long pend_i = 0, pend_A = 0;
-        uint32_t y[kMaxDim];
-        Path p;
-        int j = 0, large = 0, ky = 0, early = 0, need_setup = 1;
-        float xi = 0.f;
-        const bool traced = TRACE && (uint32_t)c % Ch.trace_stride == 0u;
-        while (true) {
-            V3 fy = {0.f, 0.f, 0.f};
-            bool finish = false;
-            if (need_setup) {
-                if (j >= Ch.E) break;
-                const uint64_t mut = mut0 + (uint64_t)j;
-                const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
-                const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
-                large = (r0.x >> 8) < Ch.T_large;
-                xi = u24(r0.y);
-                int R = 1;
-                if (large) {
-                    for (int jj = 0; 4 * jj < D; ++jj) {
-                        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
-                        y[4 * jj] = r.x;
-                        if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
-                        if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
-                        if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
-                    }
-                    ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
-                } else {
-                    // every dimension perturbed with sigma of the current state's region
-                    const float sx = Ch.sig[kx];
-                    const float sigS2 = __fmul_rn(sx, Ch.S2);
-                    float lo = 0.f, hi = 0.f;
-                    bool check = false;
-                    for (int jj = 0; 2 * jj < D; ++jj) {
-                        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
-                        const int d0 = 2 * jj;
-                        const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
-                        const uint32_t x0 = Ch.q[(size_t)d0 * C + c];
-                        y[d0] = (r.y >> 31) ? x0 - o0 : x0 + o0;
-                        uint32_t o1 = 0;
-                        if (d0 + 1 < D) {
-                            o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
-                            const uint32_t x1 = Ch.q[(size_t)(d0 + 1) * C + c];
-                            y[d0 + 1] = (r.w >> 31) ? x1 - o1 : x1 + o1;
-                        }
-                        if (jj == 0) {
-                            ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
-                            const float sy = Ch.sig[ky];
-                            if (sy != sx) {
-                                // reverse kernel T_{k(y)}(x|y): every offset inside [sigma_y s1, sigma_y s2]
-                                check = true;
-                                lo = __fmul_rn(sy, Ch.S1);
-                                hi = __fmul_rn(sy, Ch.S2);
-                            }
-                        }
-                        if (check) {
-                            const float m0 = __ull2float_rn((unsigned long long)abs((long long)(int32_t)o0));
-                            if (!(m0 >= lo && m0 <= hi)) R = 0;
-                            if (d0 + 1 < D) {
-                                const float m1 = __ull2float_rn((unsigned long long)abs((long long)(int32_t)o1));
-                                if (!(m1 >= lo && m1 <= hi)) R = 0;
-                            }
-                        }
-                    }
-                }
-                early = !R;
-                if (!R) {
-                    finish = true;
-                } else if (S.toy) {
-                    const float v = toy_eval(S, y[0], y[1]);
-                    fy = {v, v, v};
-                    finish = true;
-                } else {
-                    path_begin(p, S, y);
-                    need_setup = 0;
-                }
+    ChainLane L;
+    L.kx = L.px = L.py = 0;
+    L.pix = 0.f;
+    L.fx = {0.f, 0.f, 0.f};
+    if (valid) {
+        const int C = Ch.C;
+        L.kx = Ch.k[c];
+        L.pix = Ch.pi[c];
+        L.fx = {Ch.f[c], Ch.f[C + c], Ch.f[2 * C + c]};
+        L.px = pixel_x(Ch.q[c], Ch.W);
+        L.py = pixel_x(Ch.q[C + c], Ch.H);
+    }
+    L.pend_n = 0;
+    L.pend_i = L.pend_A = 0;
+    L.j = 0;
+    L.large = L.ky = L.early = 0;
+    L.xi = 0.f;
+    L.fy = {0.f, 0.f, 0.f};
+    const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
+    uint32_t y[kMaxDim];
+    uint32_t stack[kStackSize];
+    Path p;
+    Trav T;
+    T.ref = kNoRef;
+    int phase = (valid && Ch.E > 0) ? kSetup : kIdle;
+    const int bs = Ch.batch_shade, bf = Ch.batch_setup;
+    unsigned long long sched[6] = {0, 0, 0, 0, 0, 0};   // warp-uniform, counted once per warp
+    while (true) {
+        __syncwarp();
+        if (phase == kTraverse) {
+            if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) phase = kShade;
+        }
+        const unsigned m_tr = __ballot_sync(FULL, phase == kTraverse);
+        const unsigned m_sh = __ballot_sync(FULL, phase == kShade);
+        if (COUNT) {
+            sched[0] += 1;
+            sched[1] += __popc(m_tr);
+        }
+        if (m_sh && (__popc(m_sh) >= bs || !m_tr)) {
+            if (COUNT) {
+                sched[2] += 1;
+                sched[3] += __popc(m_sh);
             }
-            if (!finish) {
-                int ovf = 0;
-                const Hit h = trace_one<BRUTE>(S, s_tris, p, ovf, n_nodes, n_tris);
-                ++st_rays;
-                if (ovf) {
-                    ++st_ovf;
+            if (phase == kShade) {
+                ++st[5];
+                if (T.overflow) {
+                    ++st[6];
                     p.done = 1;
                     p.L = {0.f, 0.f, 0.f};
                 } else {
-                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, h);
+                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri});
                 }
-                if (!p.done) continue;
-                fy = p.L;
-                finish = true;
-            }
-            // ---- finish the mutation: acceptance, statistics, MH update, splat
-            float piy = lum(fy.x, fy.y, fy.z);
-            int invalid = 0;
-            if (!isfinite(piy)) {
-                fy = {0.f, 0.f, 0.f};
-                piy = 0.f;
-                invalid = 1;
-                ++st_inv;
-            }
-            float a;
-            if (early) {
-                a = 0.0f;
-            } else {
-                const float ptx = Ch.weighted ? pix / Ch.wf[kx] : pix;
-                const float pty = Ch.weighted ? piy / Ch.wf[ky] : piy;
-                a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
-            }
-            const int accept = xi < a;
-            if (large) {
-                ++st_large;
-                atomicAdd(&Ch.Bk[ky], (double)piy);
-            } else {
-                ++st_small;
-                pend_i += 1;
-                pend_A += (unsigned long long)__float2ull_rn(a * 4294967296.0f);
-            }
-            st_early += early;
-            if (traced) {
-                const unsigned long long idx = Ch.trace_base + (unsigned long long)(c / Ch.trace_stride) * Ch.E + j;
-                if (idx < Ch.trace_cap) {
-                    uint32_t hsh = 2166136261u;
-                    for (int d = 0; d < D; ++d) hsh = (hsh ^ y[d]) * 16777619u;
-                    rmlt_trace_record r;
-                    r.f[0] = fy.x; r.f[1] = fy.y; r.f[2] = fy.z;
-                    r.a = a;
-                    r.qhash = hsh;
-                    r.flags = (uint32_t)accept | ((uint32_t)large << 1) | ((uint32_t)early << 2) | ((uint32_t)invalid << 3);
-                    Ch.trace[idx] = r;
+                if (p.done) {
+                    L.fy = p.L;
+                    phase = kFinish;
+                } else {
+                    trav_begin(T, p.o, p.d, p.tmax, p.any);
+                    phase = kTraverse;
                 }
             }
-            if (accept) {
-                // flush the visits, splats and statistics of the state being left
-                if (pend_n) {
-                    atomicAdd(&Ch.hist[kx], (unsigned long long)pend_n);
-                    if (pix > 0.0f) {
-                        double* dst = Ch.img + 3 * ((size_t)py * Ch.W + px);
-                        const double s = (double)pend_n / (double)pix;
-                        atomicAdd(dst + 0, s * fx.x);
-                        atomicAdd(dst + 1, s * fx.y);
-                        atomicAdd(dst + 2, s * fx.z);
+        }
+        const unsigned m_tr2 = __ballot_sync(FULL, phase == kTraverse);
+        const unsigned m_fs = __ballot_sync(FULL, phase == kFinish || phase == kSetup);
+        const unsigned m_sh2 = __ballot_sync(FULL, phase == kShade);
+        if (m_fs && (__popc(m_fs) >= bf || (!m_tr2 && !m_sh2))) {
+            if (COUNT) {
+                sched[4] += 1;
+                sched[5] += __popc(m_fs);
+            }
+            // a proposal rejected early (or the toy integrand) finishes at once
+            for (int r = 0; r < 8 && (phase == kFinish || phase == kSetup); ++r) {
+                if (phase == kFinish) {
+                    mutation_finish<TRACE>(Ch, c, traced, L, y, st);
+                    ++L.j;
+                    phase = L.j < Ch.E ? kSetup : kIdle;
+                }
+                if (phase == kSetup) {
+                    if (mutation_setup(S, Ch, c, mut0, L, y, p)) {
+                        trav_begin(T, p.o, p.d, p.tmax, p.any);
+                        phase = kTraverse;
+                    } else {
+                        phase = kFinish;
                     }
                 }
-                if (pend_i) {
-                    atomicAdd(&Ch.vis[kx], pend_i);
-                    atomicAdd(&Ch.acc[kx], pend_A);
-                }
-                pend_n = 0;
-                pend_i = pend_A = 0;
-                for (int d = 0; d < D; ++d) Ch.q[(size_t)d * C + c] = y[d];
-                fx = fy;
-                pix = piy;
-                kx = ky;
-                px = pixel_x(y[0], Ch.W);
-                py = pixel_x(y[1], Ch.H);
-                ++st_acc;
-            }
-            pend_n += 1;
-            ++j;
-            need_setup = 1;
-        }
-        // end of epoch: flush and write back the cached state
-        if (pend_n) {
-            atomicAdd(&Ch.hist[kx], (unsigned long long)pend_n);
-            if (pix > 0.0f) {
-                double* dst = Ch.img + 3 * ((size_t)py * Ch.W + px);
-                const double s = (double)pend_n / (double)pix;
-                atomicAdd(dst + 0, s * fx.x);
-                atomicAdd(dst + 1, s * fx.y);
-                atomicAdd(dst + 2, s * fx.z);
             }
         }
-        if (pend_i) {
-            atomicAdd(&Ch.vis[kx], pend_i);
-            atomicAdd(&Ch.acc[kx], pend_A);
-        }
-        Ch.k[c] = kx;
-        Ch.pi[c] = pix;
-        Ch.f[c] = fx.x;
-        Ch.f[C + c] = fx.y;
-        Ch.f[2 * C + c] = fx.z;
+        if (!__any_sync(FULL, phase != kIdle)) break;
+    }
+    if (valid) {
+        flush_state(Ch, L);
+        const int C = Ch.C;
+        Ch.k[c] = L.kx;
+        Ch.pi[c] = L.pix;
+        Ch.f[c] = L.fx.x;
+        Ch.f[C + c] = L.fx.y;
+        Ch.f[2 * C + c] = L.fx.z;
     }
     // warp-aggregated statistics
-    unsigned long long v[9] = {st_acc, st_large, st_small, st_early, st_inv, st_rays, st_ovf, n_nodes, n_tris};
+    unsigned long long v[9] = {st[0], st[1], st[2], st[3], st[4], st[5], st[6], n_nodes, n_tris};
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int s = 0; s < 9; ++s) {
@@ -613,6 +808,8 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
         const unsigned long long t = warp_sum(v[s]);
         if (lane == 0 && t) atomicAdd(&Ch.stats[s], t);
     }
+    if (COUNT && lane == 0)
+        for (int s = 0; s < 6; ++s) atomicAdd(&Ch.stats[kStIters + s], sched[s]);
 }
 
 // ---------------------------------------------------------------------------

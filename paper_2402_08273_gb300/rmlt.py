@@ -62,7 +62,7 @@ class Stats(C.Structure):
                 ("small", C.c_uint64), ("early_reject", C.c_uint64), ("invalid_paths", C.c_uint64),
                 ("rays", C.c_uint64), ("stack_overflow", C.c_uint64), ("epochs", C.c_uint64),
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
-                ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64)]
+                ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -93,6 +93,7 @@ _SIGS = [
                                  C.c_uint32]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
+    ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("rmlt_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("rmlt_restore", C.c_int, [C.c_void_p, C.c_char_p]),
     ("rmlt_synchronize", C.c_int, [C.c_void_p]),
@@ -277,7 +278,12 @@ class Renderer:
     def read_stats(self) -> dict:
         s = Stats()
         _check(lib().rmlt_read_stats(self.h, C.byref(s)))
-        return {name: getattr(s, name) for name, _ in Stats._fields_}
+        d = {name: getattr(s, name) for name, _ in Stats._fields_}
+        d["sched"] = list(d["sched"])
+        return d
+
+    def set_tuning(self, batch_shade: int = 8, batch_setup: int = 8):
+        _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup)))
 
     def set_work_counters(self, enable: bool):
         _check(lib().rmlt_set_work_counters(self.h, int(enable)))
