@@ -209,6 +209,35 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
  * never results.  Defaults 8 and 8. */
 rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup);
 
+/* Bootstrap without any device allocation.  Some callers cannot allocate
+ * device memory at the point where they need starting states: code running
+ * inside a memory-pool or arena callback, a process whose allocator is
+ * reserved by a framework, or a caller that must not grow its footprint.
+ * This entry point runs the same bootstrap as rmlt_init_chains (n_bootstrap
+ * uniform samples, the normaliser b of Sec. 3.2 and one pi-proportional
+ * starting state per chain) on the loaded scene, and writes the results to the
+ * caller's buffers without touching the context's chains.  The paper has no
+ * counterpart; it is a deployment convenience.
+ *   out_q     device, [D][n_chains] u32 starting states (D = 2 + 5 max_depth)
+ *   out_f     device, [3][n_chains] float contributions of those states
+ *   out_bhat  host or device, one double: b
+ * Its intermediate values live in one fixed array inside the library (about
+ * 5.3 MB, held on every GPU that loads the library until the process exits),
+ * so it calls no cudaMalloc, cudaFree or allocating library routine.  Limits:
+ * (n_bootstrap / n_chains) * n_chains <= RMLT_NOALLOC_MAX_SAMPLES, n_chains <=
+ * RMLT_NOALLOC_MAX_CHAINS, regions <= RMLT_NOALLOC_MAX_REGIONS; larger sizes
+ * return RMLT_E_INVALID_ARG.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Every
+ * call shares the array, so calls whose work overlaps on the GPU (other
+ * contexts, other streams) race; serialise them.  Errors: RMLT_E_STATE (no
+ * scene), RMLT_E_INVALID_ARG (parameters, sizes, host pointers for out_q or
+ * out_f), RMLT_E_CUDA. */
+#define RMLT_NOALLOC_MAX_SAMPLES (1 << 18)
+#define RMLT_NOALLOC_MAX_CHAINS (1 << 16)
+#define RMLT_NOALLOC_MAX_REGIONS (1 << 14)
+rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* ctx, const rmlt_chain_params* params, uint32_t* out_q,
+                                   float* out_f, double* out_bhat);
+
 /* Bytes of device memory the context holds. */
 rmlt_status rmlt_memory_usage(rmlt_ctx* ctx, uint64_t* bytes);
 

@@ -654,6 +654,63 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* c, int enable)
     return RMLT_OK;
 }
 
+rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint32_t* out_q, float* out_f,
+                                   double* out_bhat)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_scene) return fail(RMLT_E_STATE, "load a scene before rmlt_bootstrap_noalloc");
+    if ((st = check_params(c, p))) return st;
+    if (!out_q || !out_f || !out_bhat) return fail(RMLT_E_INVALID_ARG, "output pointers must not be NULL");
+    for (const void* ptr : {(const void*)out_q, (const void*)out_f}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(RMLT_E_INVALID_ARG, "out_q and out_f must be device memory");
+        }
+    }
+    const int64_t K = p->n_bootstrap / p->n_chains;
+    const int64_t nb = K * p->n_chains;
+    const int nx = (p->width + p->region_px - 1) / p->region_px;
+    const int64_t m = (int64_t)nx * ((p->height + p->region_px - 1) / p->region_px);
+    if (nb > RMLT_NOALLOC_MAX_SAMPLES || p->n_chains > RMLT_NOALLOC_MAX_CHAINS || m > RMLT_NOALLOC_MAX_REGIONS)
+        return fail(RMLT_E_INVALID_ARG, "sizes above the fixed scratch: %lld samples (max %d), %d chains (max %d), "
+                    "%lld regions (max %d)", (long long)nb, RMLT_NOALLOC_MAX_SAMPLES, p->n_chains,
+                    RMLT_NOALLOC_MAX_CHAINS, (long long)m, RMLT_NOALLOC_MAX_REGIONS);
+    NoAllocScratch na;
+    CK(noalloc_scratch(c->device, na), "scratch lookup");
+    // the chain view the bootstrap kernels read: parameters of p, state
+    // written to the caller's buffers, everything else in the fixed scratch
+    DevChains Ch;
+    Ch.C = p->n_chains;
+    Ch.D = 2 + 5 * p->max_depth;
+    Ch.W = p->width;
+    Ch.H = p->height;
+    Ch.region_px = p->region_px;
+    Ch.nx = nx;
+    Ch.m = (int32_t)m;
+    Ch.max_depth = p->max_depth;
+    Ch.seed_lo = (uint32_t)p->seed;
+    Ch.seed_hi = (uint32_t)(p->seed >> 32);
+    Ch.q = out_q;
+    Ch.f = out_f;
+    Ch.pi = na.chain_pi;
+    Ch.k = na.chain_k;
+    Ch.Bk = na.Bk;
+    DevScene S = c->S;
+    S.tan_y = (float)c->tan_half;
+    S.tan_x = (float)(c->tan_half * (double)p->width / (double)p->height);
+    // the array keeps the previous call's contents: the region sums start at zero
+    CK(cudaMemsetAsync(na.Bk, 0, sizeof(double) * (size_t)m, c->stream), "clear scratch");
+    CK(launch_bootstrap(S, Ch, nb, na.boot, c->stream), "bootstrap");
+    double total = 0.0;
+    CK(cudaMemcpyAsync(&total, na.boot.total, sizeof total, cudaMemcpyDeviceToHost, c->stream), "read total");
+    if ((st = sync(c, "bootstrap"))) return st;
+    const double bhat = total / (double)nb;
+    CK(cudaMemcpy(out_bhat, &bhat, sizeof bhat, cudaMemcpyDefault), "write bhat");
+    return RMLT_OK;
+}
+
 rmlt_status rmlt_memory_usage(rmlt_ctx* c, uint64_t* bytes)
 {
     if (!c || !bytes) return fail(RMLT_E_INVALID_ARG, "null argument");

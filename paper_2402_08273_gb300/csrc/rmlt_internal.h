@@ -98,6 +98,17 @@ cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int6
                               double n_total, int normalized, double* out, cudaStream_t st);
 cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st);
 
+// Pointers into the library's fixed scratch array (rmlt_bootstrap_noalloc).
+struct NoAllocScratch {
+    BootScratch boot;
+    float* chain_pi = nullptr;
+    int32_t* chain_k = nullptr;
+    double* Bk = nullptr;
+};
+// Looks the array up on the current device (first call per device) and
+// fills `out`; allocates nothing.
+cudaError_t noalloc_scratch(int device, NoAllocScratch& out);
+
 // host-side BVH build (bvh_build.cpp)
 struct HostBVH {
     std::vector<float4> nodes;    // 4 per node

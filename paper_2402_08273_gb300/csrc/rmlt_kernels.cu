@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "rmlt_internal.h"
 
@@ -1078,6 +1079,54 @@ cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_bo
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     bootstrap_total_kernel<<<1, 256, 0, st>>>(c.C, b);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fixed scratch of rmlt_bootstrap_noalloc: one array for the whole process,
+// looked up once per device; the bootstrap kernels above run on it unchanged
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaPi = 0;
+constexpr size_t kNaF = na_align(kNaPi + sizeof(float) * RMLT_NOALLOC_MAX_SAMPLES);
+constexpr size_t kNaPartial = na_align(kNaF + sizeof(float) * 3 * (size_t)RMLT_NOALLOC_MAX_SAMPLES);
+constexpr size_t kNaTotal = na_align(kNaPartial + sizeof(double) * RMLT_NOALLOC_MAX_CHAINS);
+constexpr size_t kNaChainPi = na_align(kNaTotal + sizeof(double));
+constexpr size_t kNaChainK = na_align(kNaChainPi + sizeof(float) * RMLT_NOALLOC_MAX_CHAINS);
+constexpr size_t kNaBk = na_align(kNaChainK + sizeof(int32_t) * RMLT_NOALLOC_MAX_CHAINS);
+constexpr size_t kNaBytes = na_align(kNaBk + sizeof(double) * RMLT_NOALLOC_MAX_REGIONS);
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_addr[kNaMaxDevices] = {};
+}  // namespace
+
+cudaError_t noalloc_scratch(int device, NoAllocScratch& out)
+{
+    if (device < 0 || device >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    unsigned char* base;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_addr[device]) {
+            // host code cannot use g_noalloc_scratch directly: ask the runtime
+            // for its device address, with `device` current
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_na_addr[device] = (unsigned char*)p;
+        }
+        base = g_na_addr[device];
+    }
+    out.boot.pi = (float*)(base + kNaPi);
+    out.boot.f = (float*)(base + kNaF);
+    out.boot.partial = (double*)(base + kNaPartial);
+    out.boot.total = (double*)(base + kNaTotal);
+    out.chain_pi = (float*)(base + kNaChainPi);
+    out.chain_k = (int32_t*)(base + kNaChainK);
+    out.Bk = (double*)(base + kNaBk);
+    return cudaSuccess;
 }
 
 cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int64_t n_boot, double n_total,

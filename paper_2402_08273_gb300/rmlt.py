@@ -94,6 +94,8 @@ _SIGS = [
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("rmlt_bootstrap_noalloc", C.c_int, [C.c_void_p, _P(ChainParams), C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
     ("rmlt_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("rmlt_restore", C.c_int, [C.c_void_p, C.c_char_p]),
     ("rmlt_synchronize", C.c_int, [C.c_void_p]),
