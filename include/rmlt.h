@@ -78,6 +78,7 @@ typedef struct {
     const rmlt_material* mats; /* [n_mats] host */
     rmlt_camera camera;
     int32_t brute_force_max;   /* scenes with n_tris <= this skip the BVH (0: default 64) */
+    int32_t bvh_width;         /* 2 or 4 children per BVH node (0: default 4) */
 } rmlt_scene_desc;
 
 /* Chain parameters (Alg. 1 and Sec. 7.1 names).  D = 2 + 5 max_depth. */
@@ -111,6 +112,8 @@ typedef struct {
     uint64_t tri_tests;        /* ray-triangle tests in BVH leaves (only while work counters are on) */
     uint64_t sched[6];         /* work counters on: warp loop iterations, traversing lanes summed over
                                   them, shade batches, lanes shaded, setup batches, lanes set up */
+    uint64_t cycles[5];        /* work counters on: SM cycles warps spent in traversal steps, shade
+                                  batches, finish/setup batches; warp lifetimes (sum, max) */
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -205,9 +208,14 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
 /* Scheduling knobs of the chain kernel: a warp shades the resolved rays of its
  * lanes once at least `batch_shade` of them are waiting, and finishes
  * mutations / draws proposals once `batch_setup` lanes are waiting (both in
- * 1..32; smaller values when nothing else is left).  They change speed only,
- * never results.  Defaults 8 and 8. */
-rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup);
+ * 1..32; smaller values when nothing else is left).  flags:
+ * RMLT_TUNE_LARGE_AHEAD traces the epoch's large-step proposals (independent
+ * of the chain states) in a separate kernel before the chain kernel;
+ * RMLT_TUNE_ADAPTIVE_BATCH shrinks the batches as lanes finish the epoch.
+ * They change speed only, never results.  Defaults 8, 8, 0. */
+#define RMLT_TUNE_LARGE_AHEAD 1
+#define RMLT_TUNE_ADAPTIVE_BATCH 2
+rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup, int flags);
 
 /* Bootstrap without any device allocation.  Some callers cannot allocate
  * device memory at the point where they need starting states: code running

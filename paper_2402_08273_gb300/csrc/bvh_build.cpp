@@ -1,15 +1,21 @@
-// Host-side binned SAH builder for the BVH2 the chain kernel traverses.
+// Host-side binned SAH builder for the BVH the chain kernel traverses.
 //
-// Layout (4 float4 per internal node, children's boxes stored in the parent
-// so one node fetch tests both children):
+// A binary tree is built with binned SAH (16 bins per axis, leaves of at most
+// 4 triangles) and emitted either as BVH2 or, collapsed, as BVH4.  In both
+// layouts an internal node stores its children's boxes, so one node fetch
+// tests all children.
+//
+// BVH2 (4 float4 per node):
 //   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
 //   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   n3 = (ref c0, ref c1, 0, 0)   (uint bits)
-// A ref is an internal node index, or a leaf: kLeafBit | (count-1) << 28 |
-// first triangle (in build order).  Leaves hold at most 4 triangles.  Boxes
-// are widened by `pad` and rounded outward so that binary32 traversal never
-// culls a box a ray grazes.
+//   n3 = (ref c0, ref c1, 0, 0)                      (uint bits)
+// BVH4 (8 float4 per node, children in the four lanes of each float4):
+//   lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, refs (uint bits), unused
+// A ref is an internal node index, a leaf (kLeafBit | (count-1) << 28 |
+// first triangle in build order), or kEmptyRef for an unused BVH4 slot.
+// Boxes are widened by `pad` and rounded outward so that binary32 traversal
+// never culls a box a ray grazes.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,44 +50,40 @@ struct Prim {
     uint32_t id;
 };
 
+struct BNode {
+    Box box;
+    int left = -1, right = -1;   // internal iff left >= 0
+    int first = 0, count = 0;
+};
+
 constexpr int kBins = 16;
 constexpr int kLeafMax = 4;
 
+uint32_t fbits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+float bitsf(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 struct Builder {
     std::vector<Prim>& prims;
-    std::vector<float4>& nodes;
-    float pad;
+    std::vector<BNode> nodes;
     int max_depth = 0;
 
-    static uint32_t fbits(float f)
-    {
-        uint32_t u;
-        std::memcpy(&u, &f, 4);
-        return u;
-    }
-    static float bitsf(uint32_t u)
-    {
-        float f;
-        std::memcpy(&f, &u, 4);
-        return f;
-    }
-    Box padded(const Box& b) const
-    {
-        Box o;
-        for (int a = 0; a < 3; ++a) {
-            o.lo[a] = std::nextafter(b.lo[a] - pad, -INFINITY);
-            o.hi[a] = std::nextafter(b.hi[a] + pad, INFINITY);
-        }
-        return o;
-    }
-
-    uint32_t leaf(int b, int n) const { return kLeafBit | ((uint32_t)(n - 1) << 28) | (uint32_t)b; }
-
-    uint32_t build(int b, int e, int depth, Box& box)
+    int build(int b, int e, int depth)
     {
         max_depth = std::max(max_depth, depth);
+        const int id = (int)nodes.size();
+        nodes.emplace_back();
+        Box box, cb;
         box.reset();
-        Box cb;
         cb.reset();
         for (int i = b; i < e; ++i) {
             box.grow(prims[i].b);
@@ -90,9 +92,13 @@ struct Builder {
                 cb.hi[a] = std::max(cb.hi[a], prims[i].c[a]);
             }
         }
+        nodes[id].box = box;
         const int n = e - b;
-        if (n <= kLeafMax) return leaf(b, n);
-        // binned SAH over the three axes
+        if (n <= kLeafMax) {
+            nodes[id].first = b;
+            nodes[id].count = n;
+            return id;
+        }
         float best = INFINITY;
         int best_axis = -1, best_split = -1;
         for (int a = 0; a < 3; ++a) {
@@ -143,24 +149,94 @@ struct Builder {
             mid = (int)(it - prims.begin());
             if (mid == b || mid == e) mid = b + n / 2;
         }
-        const uint32_t id = (uint32_t)(nodes.size() / 4);
-        nodes.resize(nodes.size() + 4);
-        Box lb, rb;
-        const uint32_t l = build(b, mid, depth + 1, lb);
-        const uint32_t r = build(mid, e, depth + 1, rb);
-        const Box L = padded(lb), R = padded(rb);
-        float4* nd = &nodes[4 * (size_t)id];
+        const int l = build(b, mid, depth + 1);
+        const int r = build(mid, e, depth + 1);
+        nodes[id].left = l;
+        nodes[id].right = r;
+        return id;
+    }
+};
+
+struct Emitter {
+    const std::vector<BNode>& bn;
+    std::vector<float4>& out;
+    float pad;
+    int depth = 0, max_depth = 0;
+
+    Box padded(const Box& b) const
+    {
+        Box o;
+        for (int a = 0; a < 3; ++a) {
+            o.lo[a] = std::nextafter(b.lo[a] - pad, -INFINITY);
+            o.hi[a] = std::nextafter(b.hi[a] + pad, INFINITY);
+        }
+        return o;
+    }
+    uint32_t leaf_ref(const BNode& n) const { return kLeafBit | ((uint32_t)(n.count - 1) << 28) | (uint32_t)n.first; }
+
+    uint32_t emit2(int i)
+    {
+        const BNode& n = bn[(size_t)i];
+        if (n.left < 0) return leaf_ref(n);
+        const uint32_t id = (uint32_t)(out.size() / 4);
+        out.resize(out.size() + 4);
+        const uint32_t l = emit2(n.left);
+        const uint32_t r = emit2(n.right);
+        const Box L = padded(bn[(size_t)n.left].box), R = padded(bn[(size_t)n.right].box);
+        float4* nd = &out[4 * (size_t)id];
         nd[0] = make_float4(L.lo[0], L.hi[0], L.lo[1], L.hi[1]);
         nd[1] = make_float4(R.lo[0], R.hi[0], R.lo[1], R.hi[1]);
         nd[2] = make_float4(L.lo[2], L.hi[2], R.lo[2], R.hi[2]);
         nd[3] = make_float4(bitsf(l), bitsf(r), 0.f, 0.f);
         return id;
     }
+
+    // collapse: open the child with the largest surface until 4 children
+    uint32_t emit4(int i)
+    {
+        const BNode& n = bn[(size_t)i];
+        if (n.left < 0) return leaf_ref(n);
+        max_depth = std::max(max_depth, ++depth);
+        int ch[4] = {n.left, n.right, -1, -1};
+        int nc = 2;
+        while (nc < 4) {
+            int pick = -1;
+            float area = -1.f;
+            for (int k = 0; k < nc; ++k) {
+                const BNode& c = bn[(size_t)ch[k]];
+                if (c.left >= 0 && c.box.area() > area) { area = c.box.area(); pick = k; }
+            }
+            if (pick < 0) break;
+            const BNode& c = bn[(size_t)ch[pick]];
+            ch[pick] = c.left;
+            ch[nc++] = c.right;
+        }
+        const uint32_t id = (uint32_t)(out.size() / 8);
+        out.resize(out.size() + 8);
+        uint32_t refs[4] = {kEmptyRef, kEmptyRef, kEmptyRef, kEmptyRef};
+        Box boxes[4];
+        for (int k = 0; k < 4; ++k) {
+            for (int a = 0; a < 3; ++a) { boxes[k].lo[a] = 0.f; boxes[k].hi[a] = 0.f; }
+            if (k < nc) {
+                refs[k] = emit4(ch[k]);
+                boxes[k] = padded(bn[(size_t)ch[k]].box);
+            }
+        }
+        float4* nd = &out[8 * (size_t)id];
+        for (int a = 0; a < 3; ++a) {
+            nd[2 * a] = make_float4(boxes[0].lo[a], boxes[1].lo[a], boxes[2].lo[a], boxes[3].lo[a]);
+            nd[2 * a + 1] = make_float4(boxes[0].hi[a], boxes[1].hi[a], boxes[2].hi[a], boxes[3].hi[a]);
+        }
+        nd[6] = make_float4(bitsf(refs[0]), bitsf(refs[1]), bitsf(refs[2]), bitsf(refs[3]));
+        nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+        --depth;
+        return id;
+    }
 };
 
 }  // namespace
 
-void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, HostBVH& out)
+void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out)
 {
     std::vector<Prim> prims((size_t)n_tris);
     for (int i = 0; i < n_tris; ++i) {
@@ -175,12 +251,19 @@ void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, HostBVH& 
         for (int a = 0; a < 3; ++a) p.c[a] = 0.5f * (p.b.lo[a] + p.b.hi[a]);
         p.id = (uint32_t)i;
     }
+    Builder bld{prims, {}};
+    bld.nodes.reserve((size_t)2 * n_tris / kLeafMax + 16);
+    bld.build(0, n_tris, 0);
     out.nodes.clear();
-    out.nodes.reserve((size_t)4 * (size_t)std::max(1, n_tris / 2));
-    Builder bld{prims, out.nodes, pad};
-    Box root;
-    bld.build(0, n_tris, 0, root);
-    out.max_depth = bld.max_depth;
+    out.width = width;
+    Emitter em{bld.nodes, out.nodes, pad};
+    if (width == 4) {
+        em.emit4(0);
+        out.max_depth = em.max_depth;
+    } else {
+        em.emit2(0);
+        out.max_depth = bld.max_depth;
+    }
     out.order.resize((size_t)n_tris);
     for (int i = 0; i < n_tris; ++i) out.order[(size_t)i] = prims[(size_t)i].id;
 }

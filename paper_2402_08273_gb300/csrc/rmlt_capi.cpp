@@ -88,6 +88,7 @@ struct rmlt_ctx {
     uint32_t tr_stride = 1;
     bool count_work = false;
     int batch_shade = 8, batch_setup = 8;
+    int large_ahead = 0, adaptive_batch = 0;
 
     rmlt_status dalloc(std::vector<Alloc>& pool, size_t bytes, void** out)
     {
@@ -216,6 +217,8 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     if (s->n_tris >= (1 << 28)) return fail(RMLT_E_INVALID_SCENE, "at most 2^28 - 1 triangles");
     const int brute_max = s->brute_force_max > 0 ? s->brute_force_max : 64;
     if (brute_max > 4096) return fail(RMLT_E_INVALID_ARG, "brute_force_max above 4096");
+    const int width = s->bvh_width == 0 ? 4 : s->bvh_width;
+    if (width != 2 && width != 4) return fail(RMLT_E_INVALID_ARG, "bvh_width must be 0, 2 or 4");
     for (int i = 0; i < s->n_verts; ++i)
         if (!finite3(&s->verts[3 * (size_t)i])) return fail(RMLT_E_INVALID_SCENE, "vertex %d is not finite", i);
     for (int m = 0; m < s->n_mats; ++m) {
@@ -274,7 +277,7 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     // triangle order: BVH build order, or input order for brute force
     const bool brute = nt <= brute_max || nt <= 4;
     HostBVH bvh;
-    if (!brute) build_bvh(tv, nt, (float)(1e-6 * scale), bvh);
+    if (!brute) build_bvh(tv, nt, (float)(1e-6 * scale), width, bvh);
     std::vector<uint32_t> order((size_t)nt), inv((size_t)nt);
     for (int i = 0; i < nt; ++i) order[(size_t)i] = brute ? (uint32_t)i : bvh.order[(size_t)i];
     for (int i = 0; i < nt; ++i) inv[order[(size_t)i]] = (uint32_t)i;
@@ -311,7 +314,7 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     int32_t* d_lt = nullptr;
     float* d_lc = nullptr;
     if ((st = c->alloc_n(c->scene_mem, tri4.size(), &d_tri))) return st;
-    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(4, bvh.nodes.size()), &d_nodes))) return st;
+    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(8, bvh.nodes.size()), &d_nodes))) return st;
     if ((st = c->alloc_n(c->scene_mem, mat4.size(), &d_mat))) return st;
     if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, ltri.size()), &d_lt))) return st;
     if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, lcdf.size()), &d_lc))) return st;
@@ -330,7 +333,8 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     S.light_tri = d_lt;
     S.light_cdf = d_lc;
     S.n_tris = nt;
-    S.n_nodes = (int32_t)(bvh.nodes.size() / 4);
+    S.n_nodes = (int32_t)(bvh.nodes.size() / (width == 4 ? 8 : 4));
+    S.bvh4 = width == 4 ? 1 : 0;
     S.n_mats = s->n_mats;
     S.n_lights = (int32_t)ltri.size();
     S.brute = brute ? 1 : 0;
@@ -447,6 +451,12 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     if ((st = c->alloc_n(pool, m, &Ch.Bk))) return st;
     if ((st = c->alloc_n(pool, npx, &Ch.img))) return st;
     if ((st = c->alloc_n(pool, (size_t)kStCount, &Ch.stats))) return st;
+    if (!c->S.toy && (uint64_t)Ch.E * (uint64_t)Ch.C < (1ull << 32)) {
+        const size_t ec = (size_t)Ch.E * C;
+        if ((st = c->alloc_n(pool, 3 * ec, &Ch.lf))) return st;
+        if ((st = c->alloc_n(pool, ec, &Ch.llist))) return st;
+        if ((st = c->alloc_n(pool, 1, &Ch.lcount))) return st;
+    }
     if ((st = c->alloc_n(pool, 1, &c->d_total))) return st;
     if ((st = c->alloc_n(pool, npx, &c->d_stage))) return st;
     Ch.seed_lo = (uint32_t)p->seed;
@@ -521,6 +531,8 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
         DevChains Ch = c->Ch;
         Ch.batch_shade = c->batch_shade;
         Ch.batch_setup = c->batch_setup;
+        Ch.adaptive_batch = c->adaptive_batch;
+        if (!c->large_ahead) Ch.lf = nullptr;
         const bool trace = c->tr != nullptr;
         if (trace) {
             Ch.trace = c->tr;
@@ -528,7 +540,10 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
             Ch.trace_stride = c->tr_stride;
             Ch.trace_base = c->tr_epoch * (unsigned long long)n_traced * E;
         }
-        cudaError_t err = launch_chain_epoch(c->S, Ch, c->mut, trace, c->count_work, c->stream);
+        const DevScene& S = c->S;
+        cudaError_t err = cudaSuccess;
+        if (Ch.lf) err = launch_large_steps(S, Ch, c->mut, c->stream);
+        if (err == cudaSuccess) err = launch_chain_epoch(S, Ch, c->mut, trace, c->count_work, c->stream);
         if (err == cudaSuccess) err = launch_region_update(c->Ch, false, c->stream);
         if (err != cudaSuccess) {
             c->failed = true;
@@ -634,16 +649,21 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->node_visits = s[kStNodes];
     out->tri_tests = s[kStTris];
     for (int i = 0; i < 6; ++i) out->sched[i] = s[kStIters + i];
+    for (int i = 0; i < 5; ++i) out->cycles[i] = s[kStCycTrav + i];
     return RMLT_OK;
 }
 
-rmlt_status rmlt_set_tuning(rmlt_ctx* c, int batch_shade, int batch_setup)
+rmlt_status rmlt_set_tuning(rmlt_ctx* c, int batch_shade, int batch_setup, int flags)
 {
     if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
     if (batch_shade < 1 || batch_shade > 32 || batch_setup < 1 || batch_setup > 32)
         return fail(RMLT_E_INVALID_ARG, "batch sizes must be in 1..32");
+    if (flags & ~(RMLT_TUNE_LARGE_AHEAD | RMLT_TUNE_ADAPTIVE_BATCH))
+        return fail(RMLT_E_INVALID_ARG, "unknown tuning flag");
     c->batch_shade = batch_shade;
     c->batch_setup = batch_setup;
+    c->large_ahead = (flags & RMLT_TUNE_LARGE_AHEAD) != 0;
+    c->adaptive_batch = (flags & RMLT_TUNE_ADAPTIVE_BATCH) != 0;
     return RMLT_OK;
 }
 

@@ -12,7 +12,7 @@
 namespace rmlt {
 
 constexpr int kMaxDim = 2 + 5 * RMLT_MAX_DEPTH;   // 62 primary-sample dimensions
-constexpr int kStackSize = 64;                      // traversal stack entries per ray
+constexpr int kStackSize = 48;                      // traversal stack entries per ray (shared memory)
 constexpr int kChainBlock = 128;                    // threads per block of the chain kernel
 
 // statistic slots in DevChains::stats
@@ -23,11 +23,16 @@ enum StatSlot {
     // lanes traversing summed over iterations, shade batches and their lanes,
     // finish/setup batches and their lanes
     kStIters, kStTravLanes, kStShadeBatches, kStShadeLanes, kStSetupBatches, kStSetupLanes,
-    kStCount = 16
+    // warp cycle counters (work-counter builds only): traversal steps, shade
+    // batches, finish/setup batches, warp lifetime (sum and max)
+    kStCycTrav, kStCycShade, kStCycSetup, kStCycLife, kStCycLifeMax,
+    kStCount = 32
 };
 
 // Leaf references in the BVH: bit 31 set, bits 28..30 = count - 1, bits 0..27 = first triangle.
 constexpr uint32_t kLeafBit = 0x80000000u;
+// unused child slot of a BVH4 node
+constexpr uint32_t kEmptyRef = 0xFFFFFFFEu;
 
 // Device view of a loaded scene.  Triangles: 3 float4 each (v0 | mat id bits,
 // e1 | original index bits, e2 | 0); nodes: 4 float4 each (child 0 x/y
@@ -40,6 +45,7 @@ struct DevScene {
     const int32_t* light_tri = nullptr;
     const float* light_cdf = nullptr;
     int32_t n_tris = 0, n_nodes = 0, n_mats = 0, n_lights = 0, brute = 1;
+    int32_t bvh4 = 1;                 // node layout: 1 = BVH4 (8 float4), 0 = BVH2 (4 float4)
     float light_area = 0.f;
     float cam_pos[3] = {0, 0, 0}, cam_fwd[3] = {0, 0, 1}, cam_right[3] = {1, 0, 0}, cam_up[3] = {0, 1, 0};
     float tan_x = 1.f, tan_y = 1.f;   // tan(vfov / 2) * aspect, tan(vfov / 2)
@@ -67,6 +73,10 @@ struct DevChains {
     float* sig = nullptr;         // sigma_k [m]
     float* wf = nullptr;          // w_k as float [m]
     double* Bk = nullptr;         // sum of pi over uniform samples per region [m]
+    // large steps traced ahead of the epoch (nullptr: traced in the chain kernel)
+    float* lf = nullptr;          // [3][E][C] their contributions
+    uint32_t* llist = nullptr;    // [E C] work list of (j C + c)
+    unsigned* lcount = nullptr;   // [1]
     double* img = nullptr;        // [H][W][3]
     unsigned long long* stats = nullptr;  // [kStCount]
     uint32_t seed_lo = 0, seed_hi = 0, T_large = 0;
@@ -75,6 +85,7 @@ struct DevChains {
     double w_floor = 1e-3;
     // lanes that wait before the warp shades / finishes and draws together
     int32_t batch_shade = 8, batch_setup = 8;
+    int32_t adaptive_batch = 0;   // shrink the batches when few lanes are still working
     // trace instrument
     rmlt_trace_record* trace = nullptr;
     unsigned long long trace_cap = 0, trace_base = 0;
@@ -92,6 +103,7 @@ struct BootScratch {
 cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace,
                                bool count_work, cudaStream_t st);
 cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st);
+cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st);
 cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot,
                              const BootScratch& b, cudaStream_t st);
 cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int64_t n_boot,
@@ -111,10 +123,11 @@ cudaError_t noalloc_scratch(int device, NoAllocScratch& out);
 
 // host-side BVH build (bvh_build.cpp)
 struct HostBVH {
-    std::vector<float4> nodes;    // 4 per node
+    std::vector<float4> nodes;    // 4 (BVH2) or 8 (BVH4) per node
     std::vector<uint32_t> order;  // triangle order after the build
+    int width = 4;
     int max_depth = 0;
 };
-void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, HostBVH& out);
+void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out);
 
 }  // namespace rmlt

@@ -96,116 +96,33 @@ __device__ __forceinline__ V3 xyz(float4 a) { return {a.x, a.y, a.z}; }
 // ---------------------------------------------------------------------------
 // ray casting
 // ---------------------------------------------------------------------------
-// Moller-Trumbore; returns t in (tmin, tmax) of a hit inside the triangle.
+// Moller-Trumbore without a division on the rejection path: the barycentric
+// and distance tests are taken on u det, v det, t det against |det| (the
+// same inequalities scaled by |det|); t is divided out only for a hit.
 __device__ __forceinline__ bool hit_tri(V3 o, V3 d, float4 a, float4 b, float4 c, float tmax, float& t)
 {
     const V3 v0 = xyz(a), e1 = xyz(b), e2 = xyz(c);
     const V3 p = cross(d, e2);
     const float det = dot(e1, p);
     if (det == 0.0f) return false;
-    const float inv = 1.0f / det;
+    const float sg = det > 0.0f ? 1.0f : -1.0f, ad = fabsf(det);
     const V3 s = o - v0;
-    const float u = dot(s, p) * inv;
-    if (!(u >= 0.0f && u <= 1.0f)) return false;
+    const float u = dot(s, p) * sg;
     const V3 qv = cross(s, e1);
-    const float v = dot(d, qv) * inv;
-    if (!(v >= 0.0f && u + v <= 1.0f)) return false;
-    const float tt = dot(e2, qv) * inv;
-    if (!(tt > 0.0f && tt < tmax)) return false;
-    t = tt;
-    return true;
+    const float v = dot(d, qv) * sg;
+    const float tt = dot(e2, qv) * sg;
+    if (!(u >= 0.0f && v >= 0.0f && u + v <= ad && tt > 0.0f && tt < tmax * ad)) return false;
+    t = tt / ad;
+    return t < tmax;
 }
 
 struct Hit {
     float t;
     int tri;
+    float4 a, b, c;   // the hit triangle (v0 | material, e1, e2), kept from the leaf test
 };
 
-// Brute-force closest hit / any hit over triangles staged in shared memory.
-__device__ __forceinline__ Hit trace_brute(const float4* __restrict__ tr, int n, V3 o, V3 d, float tmax, bool any)
-{
-    Hit h{tmax, -1};
-    for (int i = 0; i < n; ++i) {
-        float t;
-        if (hit_tri(o, d, tr[3 * i], tr[3 * i + 1], tr[3 * i + 2], h.t, t)) {
-            h.t = t;
-            h.tri = i;
-            if (any) break;
-        }
-    }
-    return h;
-}
-
-// BVH2 traversal with a per-thread stack: both children's boxes come with the
-// parent (16-byte loads through the read-only path), the nearer child is
-// visited first.  The slab test widens tmax by 3 ulp (robust traversal).
-// One node or one leaf per iteration and a single exit, so the lanes of a
-// warp reconverge at the end of every iteration.
 constexpr uint32_t kNoRef = 0xFFFFFFFFu;
-
-__device__ __forceinline__ Hit trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                         V3 o, V3 d, float tmax, bool any, int& overflow,
-                                         unsigned& n_nodes, unsigned& n_tris)
-{
-    const V3 id = {1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
-                   1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
-                   1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z))};
-    const V3 ood = {o.x * id.x, o.y * id.y, o.z * id.z};
-    Hit h{tmax, -1};
-    uint32_t stack[kStackSize];
-    int sp = 0;
-    uint32_t ref = 0;
-    while (ref != kNoRef) {
-        uint32_t next;
-        if (!(ref & kLeafBit)) {
-            ++n_nodes;
-            const float4 n0 = __ldg(&nodes[4 * ref + 0]);
-            const float4 n1 = __ldg(&nodes[4 * ref + 1]);
-            const float4 n2 = __ldg(&nodes[4 * ref + 2]);
-            const float4 n3 = __ldg(&nodes[4 * ref + 3]);
-            const float tcap = h.t * 1.00000036f;
-            float a0 = fmaf(n0.x, id.x, -ood.x), b0 = fmaf(n0.y, id.x, -ood.x);
-            float a1 = fmaf(n0.z, id.y, -ood.y), b1 = fmaf(n0.w, id.y, -ood.y);
-            float a2 = fmaf(n2.x, id.z, -ood.z), b2 = fmaf(n2.y, id.z, -ood.z);
-            const float tn0 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
-            const float tf0 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
-            a0 = fmaf(n1.x, id.x, -ood.x); b0 = fmaf(n1.y, id.x, -ood.x);
-            a1 = fmaf(n1.z, id.y, -ood.y); b1 = fmaf(n1.w, id.y, -ood.y);
-            a2 = fmaf(n2.z, id.z, -ood.z); b2 = fmaf(n2.w, id.z, -ood.z);
-            const float tn1 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
-            const float tf1 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
-            const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
-            const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp < kStackSize) stack[sp++] = first0 ? c1 : c0;
-                else overflow = 1;
-                next = first0 ? c0 : c1;
-            } else if (h0) {
-                next = c0;
-            } else if (h1) {
-                next = c1;
-            } else {
-                next = sp > 0 ? stack[--sp] : kNoRef;
-            }
-        } else {
-            const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
-            bool found = false;
-            for (uint32_t i = first; i < first + cnt; ++i) {
-                ++n_tris;
-                float t;
-                if (hit_tri(o, d, __ldg(&tris[3 * i]), __ldg(&tris[3 * i + 1]), __ldg(&tris[3 * i + 2]), h.t, t)) {
-                    h.t = t;
-                    h.tri = (int)i;
-                    found = true;
-                }
-            }
-            next = (any && found) ? kNoRef : (sp > 0 ? stack[--sp] : kNoRef);
-        }
-        ref = overflow ? kNoRef : next;
-    }
-    return h;
-}
 
 // Stepwise traversal: the state of one ray between steps.  A step visits one
 // BVH node (both children tested), or the triangles of one leaf, or (brute
@@ -214,6 +131,7 @@ struct Trav {
     V3 o, d, id, ood;
     float t;          // closest hit so far (initially tmax)
     int tri;          // its triangle, -1 if none
+    float4 ta, tb, tc;  // its data
     uint32_t ref;     // node / leaf to visit next, kNoRef when done
     int sp, any, overflow;
 };
@@ -246,9 +164,13 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         bool found = false;
         for (int i = i0; i < i1; ++i) {
             float t;
-            if (hit_tri(T.o, T.d, s_tris[3 * i], s_tris[3 * i + 1], s_tris[3 * i + 2], T.t, t)) {
+            const float4 a = s_tris[3 * i], b = s_tris[3 * i + 1], c = s_tris[3 * i + 2];
+            if (hit_tri(T.o, T.d, a, b, c, T.t, t)) {
                 T.t = t;
                 T.tri = i;
+                T.ta = a;
+                T.tb = b;
+                T.tc = c;
                 found = true;
             }
         }
@@ -257,7 +179,51 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
     }
     uint32_t next;
     const uint32_t ref = T.ref;
-    if (!(ref & kLeafBit)) {
+    if (!(ref & kLeafBit) && S.bvh4) {
+        // four children: slab tests in the lanes of each float4, nearest hit
+        // child next, the others pushed far to near
+        ++n_nodes;
+        const float4* nd = &S.nodes[8 * (size_t)ref];
+        const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const float tcap = T.t * 1.00000036f;
+        const V3 id = T.id, ood = T.ood;
+        float key[4];
+        uint32_t cr[4];
+        const float lox[4] = {lx.x, lx.y, lx.z, lx.w}, hix[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float loy[4] = {ly.x, ly.y, ly.z, ly.w}, hiy[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float loz[4] = {lz.x, lz.y, lz.z, lz.w}, hiz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                                __float_as_uint(rf.w)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float a0 = fmaf(lox[k], id.x, -ood.x), b0 = fmaf(hix[k], id.x, -ood.x);
+            const float a1 = fmaf(loy[k], id.y, -ood.y), b1 = fmaf(hiy[k], id.y, -ood.y);
+            const float a2 = fmaf(loz[k], id.z, -ood.z), b2 = fmaf(hiz[k], id.z, -ood.z);
+            const float tn = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            const float tf = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+            const bool hit = tn <= tf && rr[k] != kEmptyRef;
+            key[k] = hit ? tn : INFINITY;
+            cr[k] = rr[k];
+        }
+        // sorting network on (key, ref): (0,1) (2,3) (0,2) (1,3) (1,2)
+#define RMLT_CSWAP(i, j)                                                    \
+        if (key[j] < key[i]) {                                              \
+            const float tk = key[i]; key[i] = key[j]; key[j] = tk;          \
+            const uint32_t tr = cr[i]; cr[i] = cr[j]; cr[j] = tr;           \
+        }
+        RMLT_CSWAP(0, 1) RMLT_CSWAP(2, 3) RMLT_CSWAP(0, 2) RMLT_CSWAP(1, 3) RMLT_CSWAP(1, 2)
+#undef RMLT_CSWAP
+#pragma unroll
+        for (int k = 3; k >= 1; --k) {
+            if (key[k] != INFINITY) {
+                if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = cr[k];
+                else T.overflow = 1;
+            }
+        }
+
+        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
+    } else if (!(ref & kLeafBit)) {
         ++n_nodes;
         const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
         const float4 n1 = __ldg(&S.nodes[4 * ref + 1]);
@@ -279,7 +245,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (T.sp < kStackSize) stack[T.sp++] = first0 ? c1 : c0;
+            if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = first0 ? c1 : c0;
             else T.overflow = 1;
             next = first0 ? c0 : c1;
         } else if (h0) {
@@ -287,7 +253,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         } else if (h1) {
             next = c1;
         } else {
-            next = T.sp > 0 ? stack[--T.sp] : kNoRef;
+            next = T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef;
         }
     } else {
         const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
@@ -295,13 +261,17 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         for (uint32_t i = first; i < first + cnt; ++i) {
             ++n_tris;
             float t;
-            if (hit_tri(T.o, T.d, __ldg(&S.tris[3 * i]), __ldg(&S.tris[3 * i + 1]), __ldg(&S.tris[3 * i + 2]), T.t, t)) {
+            const float4 a = __ldg(&S.tris[3 * i]), b = __ldg(&S.tris[3 * i + 1]), c = __ldg(&S.tris[3 * i + 2]);
+            if (hit_tri(T.o, T.d, a, b, c, T.t, t)) {
                 T.t = t;
                 T.tri = (int)i;
+                T.ta = a;
+                T.tb = b;
+                T.tc = c;
                 found = true;
             }
         }
-        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[--T.sp] : kNoRef);
+        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
     }
     T.ref = T.overflow ? kNoRef : next;
     return T.ref == kNoRef;
@@ -430,8 +400,7 @@ __device__ __forceinline__ void path_on_hit(Path& p, const DevScene& S, const fl
         return;
     }
     if (h.tri < 0) { p.done = 1; return; }
-    const float4 ta = tri_load<BRUTE>(S, s_tris, h.tri, 0), tb = tri_load<BRUTE>(S, s_tris, h.tri, 1),
-                 tc = tri_load<BRUTE>(S, s_tris, h.tri, 2);
+    const float4 ta = h.a, tb = h.b, tc = h.c;
     const V3 n = normalize(cross(xyz(tb), xyz(tc)));
     const int mat = __float_as_int(ta.w);
     const V3 x = p.o + p.d * h.t;
@@ -491,14 +460,6 @@ __device__ __forceinline__ float toy_eval(const DevScene& S, uint32_t q0, uint32
     return f;
 }
 
-template <bool BRUTE>
-__device__ __forceinline__ Hit trace_one(const DevScene& S, const float4* s_tris, const Path& p, int& overflow,
-                                         unsigned& nn, unsigned& nt)
-{
-    if (BRUTE) return trace_brute(s_tris, S.n_tris, p.o, p.d, p.tmax, p.any != 0);
-    return trace_bvh(S.nodes, S.tris, p.o, p.d, p.tmax, p.any != 0, overflow, nn, nt);
-}
-
 __device__ __forceinline__ void stage_triangles(const DevScene& S, float4* s_tris)
 {
     for (int i = threadIdx.x; i < 3 * S.n_tris; i += blockDim.x) s_tris[i] = __ldg(&S.tris[i]);
@@ -552,7 +513,10 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
         }
         L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
     } else {
-        // every dimension perturbed with sigma of the current state's region
+        // every dimension perturbed with sigma of the current state's region;
+        // the current state's words are fetched first with independent loads
+#pragma unroll 4
+        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
         const float sx = Ch.sig[L.kx];
         const float sigS2 = __fmul_rn(sx, Ch.S2);
         float lo = 0.f, hi = 0.f;
@@ -561,13 +525,11 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
             const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
             const int d0 = 2 * jj;
             const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
-            const uint32_t x0 = Ch.q[(size_t)d0 * C + c];
-            y[d0] = (r.y >> 31) ? x0 - o0 : x0 + o0;
+            y[d0] = (r.y >> 31) ? y[d0] - o0 : y[d0] + o0;
             uint32_t o1 = 0;
             if (d0 + 1 < D) {
                 o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
-                const uint32_t x1 = Ch.q[(size_t)(d0 + 1) * C + c];
-                y[d0 + 1] = (r.w >> 31) ? x1 - o1 : x1 + o1;
+                y[d0 + 1] = (r.w >> 31) ? y[d0 + 1] - o1 : y[d0 + 1] + o1;
             }
             if (jj == 0) {
                 L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
@@ -595,6 +557,12 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
     if (S.toy) {
         const float v = toy_eval(S, y[0], y[1]);
         L.fy = {v, v, v};
+        return false;
+    }
+    if (L.large && Ch.lf) {
+        // independent of the chain's state: traced ahead of the epoch
+        const size_t o = (size_t)L.j * C + c;
+        L.fy = {Ch.lf[o], Ch.lf[(size_t)Ch.E * C + o], Ch.lf[(size_t)2 * Ch.E * C + o]};
         return false;
     }
     path_begin(p, S, y);
@@ -648,7 +616,7 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
     const int accept = L.xi < a;
     if (L.large) {
         ++st[1];
-        atomicAdd(&Ch.Bk[L.ky], (double)piy);
+        if (!Ch.lf) atomicAdd(&Ch.Bk[L.ky], (double)piy);   // else added by the large-step kernel
     } else {
         ++st[2];
         L.pend_i += 1;
@@ -723,25 +691,43 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
     L.fy = {0.f, 0.f, 0.f};
     const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
     uint32_t y[kMaxDim];
-    uint32_t stack[kStackSize];
+    // traversal stack in shared memory, one column per thread (conflict-free)
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    uint32_t* stack = s_stack + threadIdx.x;
     Path p;
     Trav T;
     T.ref = kNoRef;
     int phase = (valid && Ch.E > 0) ? kSetup : kIdle;
     const int bs = Ch.batch_shade, bf = Ch.batch_setup;
     unsigned long long sched[6] = {0, 0, 0, 0, 0, 0};   // warp-uniform, counted once per warp
+    unsigned long long cyc[3] = {0, 0, 0};   // cycles in traversal steps, shade batches, finish/setup batches
+    long long t_start = 0, t_mark = 0;
+    if (COUNT) t_start = t_mark = clock64();
     while (true) {
         __syncwarp();
         if (phase == kTraverse) {
             if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) phase = kShade;
         }
+        if (COUNT) {
+            __syncwarp();
+            const long long t = clock64();
+            cyc[0] += t - t_mark;
+            t_mark = t;
+        }
         const unsigned m_tr = __ballot_sync(FULL, phase == kTraverse);
         const unsigned m_sh = __ballot_sync(FULL, phase == kShade);
+        // fewer lanes at work (the end of the epoch): optionally smaller batches
+        int bs_eff = bs, bf_eff = bf;
+        if (Ch.adaptive_batch) {
+            const int busy = __popc(__ballot_sync(FULL, phase != kIdle));
+            bs_eff = min(bs, (busy + 3) >> 2);
+            bf_eff = min(bf, (busy + 3) >> 2);
+        }
         if (COUNT) {
             sched[0] += 1;
             sched[1] += __popc(m_tr);
         }
-        if (m_sh && (__popc(m_sh) >= bs || !m_tr)) {
+        if (m_sh && (__popc(m_sh) >= bs_eff || !m_tr)) {
             if (COUNT) {
                 sched[2] += 1;
                 sched[3] += __popc(m_sh);
@@ -753,7 +739,7 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
                     p.done = 1;
                     p.L = {0.f, 0.f, 0.f};
                 } else {
-                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri});
+                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
                 }
                 if (p.done) {
                     L.fy = p.L;
@@ -763,11 +749,17 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
                     phase = kTraverse;
                 }
             }
+            if (COUNT) {
+                __syncwarp();
+                const long long t = clock64();
+                cyc[1] += t - t_mark;
+                t_mark = t;
+            }
         }
         const unsigned m_tr2 = __ballot_sync(FULL, phase == kTraverse);
         const unsigned m_fs = __ballot_sync(FULL, phase == kFinish || phase == kSetup);
         const unsigned m_sh2 = __ballot_sync(FULL, phase == kShade);
-        if (m_fs && (__popc(m_fs) >= bf || (!m_tr2 && !m_sh2))) {
+        if (m_fs && (__popc(m_fs) >= bf_eff || (!m_tr2 && !m_sh2))) {
             if (COUNT) {
                 sched[4] += 1;
                 sched[5] += __popc(m_fs);
@@ -787,6 +779,12 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
                         phase = kFinish;
                     }
                 }
+            }
+            if (COUNT) {
+                __syncwarp();
+                const long long t = clock64();
+                cyc[2] += t - t_mark;
+                t_mark = t;
             }
         }
         if (!__any_sync(FULL, phase != kIdle)) break;
@@ -809,8 +807,97 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
         const unsigned long long t = warp_sum(v[s]);
         if (lane == 0 && t) atomicAdd(&Ch.stats[s], t);
     }
-    if (COUNT && lane == 0)
+    if (COUNT && lane == 0) {
         for (int s = 0; s < 6; ++s) atomicAdd(&Ch.stats[kStIters + s], sched[s]);
+        for (int s = 0; s < 3; ++s) atomicAdd(&Ch.stats[kStCycTrav + s], cyc[s]);
+        const unsigned long long life = (unsigned long long)(clock64() - t_start);
+        atomicAdd(&Ch.stats[kStCycLife], life);
+        atomicMax(&Ch.stats[kStCycLifeMax], life);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// large steps traced ahead of the epoch.  A large step proposes an
+// independent uniform point (its draws do not depend on the chain's state),
+// so its path can be evaluated before the epoch by a kernel with one thread
+// per proposal and full occupancy; the chain kernel then reads f.  The values
+// are bit-identical to tracing them inside the chain kernel.
+// ---------------------------------------------------------------------------
+__global__ void large_collect_kernel(const DevChains Ch, uint64_t mut0)
+{
+    const long long n = (long long)Ch.E * Ch.C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool large = false;
+    int c = 0, j = 0;
+    if (i < n) {
+        j = (int)(i / Ch.C);
+        c = (int)(i % Ch.C);
+        const uint64_t mut = mut0 + (uint64_t)j;
+        const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+        large = (r0.x >> 8) < Ch.T_large;
+    }
+    // warp-aggregated append to the work list
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, large);
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0 && m) base = atomicAdd(Ch.lcount, (unsigned)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (large) Ch.llist[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene S, const DevChains Ch, uint64_t mut0)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *Ch.lcount) return;
+    const uint32_t item = Ch.llist[i];
+    const int j = (int)(item / (uint32_t)Ch.C), c = (int)(item % (uint32_t)Ch.C);
+    const uint64_t mut = mut0 + (uint64_t)j;
+    const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
+    const int D = Ch.D;
+    uint32_t y[kMaxDim];
+    for (int jj = 0; 4 * jj < D; ++jj) {
+        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        y[4 * jj] = r.x;
+        if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
+        if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
+        if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
+    }
+    Path p;
+    Trav T;
+    uint32_t* stack = s_stack + threadIdx.x;
+    unsigned nn = 0, nt = 0, rays = 0, ovf = 0;
+    path_begin(p, S, y);
+    while (!p.done) {
+        trav_begin(T, p.o, p.d, p.tmax, p.any);
+        while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        }
+        ++rays;
+        if (T.overflow) {
+            ++ovf;
+            p.L = {0.f, 0.f, 0.f};
+            break;
+        }
+        path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
+    }
+    const size_t o = (size_t)j * Ch.C + c, plane = (size_t)Ch.E * Ch.C;
+    Ch.lf[o] = p.L.x;
+    Ch.lf[plane + o] = p.L.y;
+    Ch.lf[2 * plane + o] = p.L.z;
+    float piy = lum(p.L.x, p.L.y, p.L.z);
+    if (!isfinite(piy)) piy = 0.f;   // the chain kernel counts and zeroes invalid contributions
+    const int ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+    atomicAdd(&Ch.Bk[ky], (double)piy);
+    // reduce over the lanes that arrive together (one atomic per group)
+    const unsigned m = __activemask();
+    const unsigned rs = __reduce_add_sync(m, rays), os = __reduce_add_sync(m, ovf);
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
+        if (rs) atomicAdd(&Ch.stats[kStRays], (unsigned long long)rs);
+        if (os) atomicAdd(&Ch.stats[kStOverflow], (unsigned long long)os);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -887,6 +974,7 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
                                                                      long long n_boot, const BootScratch B)
 {
     extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
     if (BRUTE) stage_triangles(S, s_tris);
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_boot) return;
@@ -907,12 +995,15 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
         f = {v, v, v};
     } else {
         Path p;
+        Trav T;
+        uint32_t* stack = s_stack + threadIdx.x;
         path_begin(p, S, y);
         while (!p.done) {
-            int ovf = 0;
-            const Hit h = trace_one<BRUTE>(S, s_tris, p, ovf, nn, nt);
-            if (ovf) { p.L = {0.f, 0.f, 0.f}; break; }
-            path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, h);
+            trav_begin(T, p.o, p.d, p.tmax, p.any);
+            while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+            }
+            if (T.overflow) { p.L = {0.f, 0.f, 0.f}; break; }
+            path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
         }
         f = p.L;
     }
@@ -1043,6 +1134,27 @@ cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t m
                                  : launch_epoch_t<false, true, false>(s, c, mut0, st);
     return count_work ? launch_epoch_t<false, false, true>(s, c, mut0, st)
                       : launch_epoch_t<false, false, false>(s, c, mut0, st);
+}
+
+cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(c.lcount, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)c.E * c.C;
+    large_collect_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, mut0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n + kChainBlock - 1) / kChainBlock);
+    const size_t shm = s.brute ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
+    if (s.brute) {
+        if (shm > 48 * 1024) {
+            e = cudaFuncSetAttribute(large_trace_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e != cudaSuccess) return e;
+        }
+        large_trace_kernel<true><<<blocks, kChainBlock, shm, st>>>(s, c, mut0);
+    } else {
+        large_trace_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c, mut0);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st)

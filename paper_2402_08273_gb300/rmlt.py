@@ -44,7 +44,7 @@ class SceneDesc(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("verts", C.POINTER(C.c_float)), ("n_tris", C.c_int32),
                 ("tris", C.POINTER(C.c_uint32)), ("mat_id", C.POINTER(C.c_uint32)),
                 ("n_mats", C.c_int32), ("mats", C.POINTER(Material)), ("camera", Camera),
-                ("brute_force_max", C.c_int32)]
+                ("brute_force_max", C.c_int32), ("bvh_width", C.c_int32)]
 
 
 class ChainParams(C.Structure):
@@ -62,7 +62,8 @@ class Stats(C.Structure):
                 ("small", C.c_uint64), ("early_reject", C.c_uint64), ("invalid_paths", C.c_uint64),
                 ("rays", C.c_uint64), ("stack_overflow", C.c_uint64), ("epochs", C.c_uint64),
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
-                ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6)]
+                ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6),
+                ("cycles", C.c_uint64 * 5)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -93,7 +94,7 @@ _SIGS = [
                                  C.c_uint32]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
-    ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     ("rmlt_bootstrap_noalloc", C.c_int, [C.c_void_p, _P(ChainParams), C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
     ("rmlt_save", C.c_int, [C.c_void_p, C.c_char_p]),
@@ -203,7 +204,7 @@ class Renderer:
         self.close()
 
     # -- scene ---------------------------------------------------------------
-    def load_scene(self, scene: dict, brute_force_max: int = 0):
+    def load_scene(self, scene: dict, brute_force_max: int = 0, bvh_width: int = 0):
         v = np.ascontiguousarray(scene["verts"], np.float32)
         t = np.ascontiguousarray(scene["tris"], np.uint32)
         mid = np.ascontiguousarray(scene["mat_id"], np.uint32)
@@ -220,7 +221,7 @@ class Renderer:
                         (C.c_float * 3)(*cam[6:9]), float(cam[9]))
         desc = SceneDesc(len(v), v.ctypes.data_as(_P(C.c_float)), len(t),
                          t.ctypes.data_as(_P(C.c_uint32)), mid.ctypes.data_as(_P(C.c_uint32)), nm,
-                         mats, camera, int(brute_force_max))
+                         mats, camera, int(brute_force_max), int(bvh_width))
         _check(lib().rmlt_load_scene(self.h, C.byref(desc)))
         self.params = None
 
@@ -282,10 +283,13 @@ class Renderer:
         _check(lib().rmlt_read_stats(self.h, C.byref(s)))
         d = {name: getattr(s, name) for name, _ in Stats._fields_}
         d["sched"] = list(d["sched"])
+        d["cycles"] = list(d["cycles"])
         return d
 
-    def set_tuning(self, batch_shade: int = 8, batch_setup: int = 8):
-        _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup)))
+    def set_tuning(self, batch_shade: int = 8, batch_setup: int = 8, large_ahead: bool = False,
+                   adaptive_batch: bool = False):
+        flags = (1 if large_ahead else 0) | (2 if adaptive_batch else 0)
+        _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup), flags))
 
     def set_work_counters(self, enable: bool):
         _check(lib().rmlt_set_work_counters(self.h, int(enable)))
