@@ -21,7 +21,7 @@
 #include <string.h>
 
 #define OR_MAX_DIM 256
-#define OR_WIN 1e-3            /* scene-relative window of the decision margin */
+#define OR_WIN 1e-4            /* scene-relative window of the decision margin (10x the exclusion threshold) */
 #define OR_INF (1.0 / 0.0)
 #define OR_PI 3.14159265358979323846
 

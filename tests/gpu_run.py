@@ -6,7 +6,7 @@ import numpy as np
 from paper_2402_08273_gb300 import rmlt
 
 
-def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, **params):
+def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bvh_width=0, **params):
     """Initialise, trace `n_epochs` epochs of every `stride`-th chain, and
     return the trace together with the initial and final state."""
     import torch
@@ -14,7 +14,7 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, **
     if toy is not None:
         R.load_toy_integrand(toy)
     else:
-        R.load_scene(scene, brute_force_max=brute_force_max)
+        R.load_scene(scene, brute_force_max=brute_force_max, bvh_width=bvh_width)
     R.init_chains(**params)
     p = R.params
     init = R.read_chain_state()
@@ -48,3 +48,33 @@ def oracle_params(p: dict) -> dict:
             "n_bootstrap", "seed", "p_large", "s1", "s2", "alpha_star", "gamma_max", "gamma_scale",
             "lambda_init", "lambda_min", "lambda_max", "w_floor")
     return {k: p[k] for k in keys}
+
+
+def replay_full(oracle_mod, gpu, scene_obj, max_adopt=2, **replay_kw):
+    """Replay every traced mutation with the oracle (full population)."""
+    from oracle.replay import Replay, adopt_initial_states
+    p = gpu["params"]
+    ch = oracle_mod.Chains(scene_obj, **oracle_params(p))
+    ch.init()
+    adopted = adopt_initial_states(ch, gpu["init"]["q"], max_adopt)
+    rp = Replay(ch, gpu["trace"], gpu["lambdas"], **replay_kw)
+    rp.run_full(gpu["trace"].shape[0])
+    return ch, rp, adopted
+
+
+def check_counters(ch, gpu, rp):
+    """Exact integer state and tolerance-bounded sums after a full replay."""
+    assert rp.ok(), rp.summary()
+    reg = gpu["region"]
+    assert np.array_equal(ch.hist, gpu["hist"]), "h_k differs"
+    assert np.array_equal(ch.visits, reg["i"]), "i_k differs"
+    assert np.array_equal(ch.n_updates, reg["n"]), "n_k differs"
+    assert np.array_equal(ch.lam, reg["lambda"]), "lambda_k differs"
+    assert np.array_equal(ch.q, gpu["final"]["q"].T), "final chain states differ"
+    A_o, A_g = ch.accsum.astype(np.float64), reg["A"].astype(np.float64)
+    np.testing.assert_allclose(A_g, A_o, rtol=1e-4, atol=2.0 ** 32 * 1e-4)
+    raw_o = ch.image_acc
+    np.testing.assert_allclose(gpu["image_raw"], raw_o, rtol=1e-5, atol=1e-7 * max(1.0, raw_o.max()))
+    n = rp.s["mutations"]
+    assert rp.s["f_excluded"] <= max(2, 2e-3 * n)
+    assert rp.s["f_soft"] <= max(2, 2e-4 * n) and rp.s["a_soft"] <= max(2, 2e-4 * n)

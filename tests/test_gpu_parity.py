@@ -20,30 +20,13 @@ TOY = S.TOY_DEFAULT
 
 
 def _replay_full(oracle_mod, gpu, scene_obj, max_adopt=2, **replay_kw):
-    from oracle.replay import Replay, adopt_initial_states
-    from gpu_run import oracle_params
-    p = gpu["params"]
-    ch = oracle_mod.Chains(scene_obj, **oracle_params(p))
-    ch.init()
-    adopted = adopt_initial_states(ch, gpu["init"]["q"], max_adopt)
-    rp = Replay(ch, gpu["trace"], gpu["lambdas"], **replay_kw)
-    rp.run_full(gpu["trace"].shape[0])
-    return ch, rp, adopted
+    from gpu_run import replay_full
+    return replay_full(oracle_mod, gpu, scene_obj, max_adopt, **replay_kw)
 
 
 def _check_counters(ch, gpu, rp):
-    assert rp.ok(), rp.summary()
-    reg = gpu["region"]
-    assert np.array_equal(ch.hist, gpu["hist"]), "h_k differs"
-    assert np.array_equal(ch.visits, reg["i"]), "i_k differs"
-    assert np.array_equal(ch.n_updates, reg["n"]), "n_k differs"
-    assert np.array_equal(ch.lam, reg["lambda"]), "lambda_k differs"
-    assert np.array_equal(ch.q, gpu["final"]["q"].T), "final chain states differ"
-    A_o, A_g = ch.accsum.astype(np.float64), reg["A"].astype(np.float64)
-    np.testing.assert_allclose(A_g, A_o, rtol=1e-4, atol=2.0 ** 32 * 1e-4)
-    # raw splat sums f/pi: same visits, binary32 vs binary64 contributions
-    raw_o = ch.image_acc
-    np.testing.assert_allclose(gpu["image_raw"], raw_o, rtol=1e-5, atol=1e-7 * max(1.0, raw_o.max()))
+    from gpu_run import check_counters
+    check_counters(ch, gpu, rp)
 
 
 @pytest.mark.parametrize("n_chains,target_mode", [(200, 0), (64, 1)])
