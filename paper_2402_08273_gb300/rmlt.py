@@ -248,20 +248,29 @@ class Renderer:
         _check(lib().rmlt_synchronize(self.h))
 
     # -- read-out ------------------------------------------------------------
+    def _require_chains(self):
+        # before rmlt_init_chains the sizes are unknown: let the library report the state error
+        if self.params is None:
+            dummy = np.zeros(1, np.uint64)
+            _check(lib().rmlt_read_region_hist(self.h, _ptr(dummy)))
+
     def read_image(self, normalized: bool = True, out=None):
         """[H, W, 3] float64: numpy (host) unless `out` is given (host array or CUDA tensor)."""
+        self._require_chains()
         if out is None:
             out = np.zeros((self.params["height"], self.params["width"], 3), np.float64)
         _check(lib().rmlt_read_image(self.h, _ptr(out), int(normalized)))
         return out
 
     def read_region_hist(self, out=None):
+        self._require_chains()
         if out is None:
             out = np.zeros(self.m, np.uint64)
         _check(lib().rmlt_read_region_hist(self.h, _ptr(out)))
         return out
 
     def read_region_params(self) -> dict:
+        self._require_chains()
         lam = np.zeros(self.m)
         n = np.zeros(self.m, np.int64)
         i = np.zeros(self.m, np.uint64)
@@ -271,6 +280,7 @@ class Renderer:
         return {"lambda": lam, "n": n, "i": i, "A": A, "w": w}
 
     def read_chain_state(self) -> dict:
+        self._require_chains()
         Cn = self.params["n_chains"]
         q = np.zeros((self.D, Cn), np.uint32)
         f = np.zeros((3, Cn), np.float32)
