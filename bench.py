@@ -81,6 +81,25 @@ def measured_traffic():
         return None
 
 
+def population_params(base: dict, rank: int) -> dict:
+    """One independent chain population per GPU: the same workload with the
+    Philox key offset by the rank (no data-path collective)."""
+    p = dict(base)
+    p["seed"] = base["seed"] + rank
+    return p
+
+
+def reduce_job(dist, world: int, t_local: float, counts: dict, device) -> tuple[float, dict]:
+    """Whole-job numbers: the time is the maximum over ranks, counts are summed."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    c = torch.tensor([float(v) for v in counts.values()], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), dict(zip(counts, c.tolist()))
+
+
 def make_scene(w):
     from paper_2402_08273_gb300 import scenes
     name, kw = w["scene"]
@@ -211,8 +230,7 @@ def run_ours(args, w):
             dist.barrier()
 
     scene = make_scene(w)
-    params = dict(w["params"])
-    params["seed"] = params["seed"] + rank      # independent chain population per GPU
+    params = population_params(w["params"], rank)
     M = w["mutations"]
     stream = torch.cuda.Stream(device=dev)
     R = rmlt.Renderer(device=local, stream=stream)
@@ -251,12 +269,9 @@ def run_ours(args, w):
     step_ms = [a.elapsed_time(b) for a, b in times]
     t_dev = sum(step_ms) / 1e3
     st1 = R.read_stats()
-    t_max = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_max = float(t_max.item())
-    mutations = C * M * args.steps * world
-    rays = (st1["rays"] - st0["rays"]) * world
+    t_max, tot = reduce_job(dist, world, t_dev, {"mutations": C * M * args.steps,
+                                                  "rays": st1["rays"] - st0["rays"]}, dev)
+    mutations, rays = tot["mutations"], tot["rays"]
     value = mutations / t_max
 
     # end to end through the public API: the step plus the image and region
@@ -271,10 +286,8 @@ def run_ours(args, w):
         R.read_image(out=img_h.numpy())
         R.read_region_hist(out=hist_h.numpy().view("uint64"))
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = mutations / float(t_e2e.item())
+    t_e2e, _ = reduce_job(dist, world, time.perf_counter() - t0, {"steps": args.steps}, dev)
+    e2e_value = mutations / t_e2e
     d2h = img_h.numel() * 8 + hist_h.numel() * 8
 
     # work per ray from one instrumented step (same kernel with counters on)
@@ -288,7 +301,7 @@ def run_ours(args, w):
     tris_per_ray = (sb["tri_tests"] - sa["tri_tests"]) / dr
     flops_ray = nodes_per_ray * FLOPS_PER_NODE + tris_per_ray * FLOPS_PER_TRI
     bytes_ray = nodes_per_ray * BYTES_PER_NODE + tris_per_ray * BYTES_PER_TRI
-    rays_per_s_gpu = rays / world / t_max
+    rays_per_s_gpu = rays / world / t_max   # per GPU, for the per-kernel roofline
     clk_mhz = clk["sm_mhz"] or 1965.0
     peak_tflops = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
     achieved = flops_ray * rays_per_s_gpu / 1e12
