@@ -67,10 +67,13 @@ WORKLOADS = {
 }
 
 
-def measured_traffic():
+def measured_traffic(workload: str = "two_rooms"):
     """DRAM bytes per chain-kernel launch from the committed ncu capture of the
-    two-rooms workload, or None when the kernel source changed since."""
+    two-rooms workload, or None for another workload or when the kernel
+    source changed since the capture."""
     import hashlib
+    if workload != "two_rooms":
+        return None
     try:
         rec = json.loads((ROOT / "profiles" / "chain_epoch_kernel_traffic.json").read_text())
         src = (ROOT / "paper_2402_08273_gb300" / "csrc" / "rmlt_kernels.cu").read_bytes()
@@ -306,7 +309,7 @@ def run_ours(args, w):
     peak_tflops = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
     achieved = flops_ray * rays_per_s_gpu / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": measured_traffic(),
+                "frac": achieved / peak_tflops, "traffic": measured_traffic(args.workload),
                 "kernel": "chain_epoch_kernel",
                 "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock "
                                f"{clk_mhz:.0f} MHz sampled during the timed region",
