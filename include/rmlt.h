@@ -55,6 +55,7 @@ typedef enum {
 
 typedef enum { RMLT_LAMBERT = 0, RMLT_GGX = 1 } rmlt_material_type;
 typedef enum { RMLT_TARGET_PLAIN = 0, RMLT_TARGET_REGION_WEIGHTED = 1 } rmlt_target_mode;
+typedef enum { RMLT_PARTITION_GRID = 0, RMLT_PARTITION_QUADTREE = 1 } rmlt_partition;
 
 typedef struct {
     int32_t type;          /* rmlt_material_type */
@@ -98,6 +99,12 @@ typedef struct {
     double gamma_max, gamma_scale;  /* eq. step_size_n */
     double lambda_init, lambda_min, lambda_max;
     double w_floor;            /* region-weighted target: lower bound of w_k as a share of 1/m */
+    int32_t partition;         /* RMLT_PARTITION_GRID (Sec. 6.1) or RMLT_PARTITION_QUADTREE (Sec. 6.2) */
+    int32_t qt_max_leaves;     /* quadtree: region capacity */
+    int32_t qt_max_depth;      /* quadtree: deepest level (the root is level 0) */
+    int32_t qt_pad_;
+    int64_t qt_split;          /* quadtree: M_split, visits since the last pass that split a leaf */
+    int64_t qt_refine;         /* quadtree: M_refine, mutations (all chains) between passes */
 } rmlt_chain_params;
 
 typedef struct {
@@ -173,7 +180,9 @@ rmlt_status rmlt_step(rmlt_ctx* ctx, uint64_t n_mutations);
  * of f/pi splats. */
 rmlt_status rmlt_read_image(rmlt_ctx* ctx, double* out_rgb, int normalized);
 
-/* Region visit histogram h_k (post-MH state of every mutation), [m] u64. */
+/* Region visit histogram h_k (post-MH state of every mutation), [m] u64, m
+ * the current number of regions (rmlt_stats.n_regions; it grows with a
+ * quadtree partition, and a split leaf's children start from 0). */
 rmlt_status rmlt_read_region_hist(rmlt_ctx* ctx, uint64_t* out_h);
 
 /* Region parameters, each [m]; any pointer may be NULL.  lambda_k, n_k (update
@@ -181,6 +190,19 @@ rmlt_status rmlt_read_region_hist(rmlt_ctx* ctx, uint64_t* out_h);
  * the region's last update), w_k (region weight; 1 in plain mode). */
 rmlt_status rmlt_read_region_params(rmlt_ctx* ctx, double* lambda, int64_t* n, uint64_t* i,
                                     uint64_t* A, double* w);
+
+/* Quadtree partition (Sec. 6.2): regions are the leaves of a quadtree over
+ * the screen [0,1)^2, starting from the root.  Once every qt_refine mutations
+ * (counted over all chains, at an epoch boundary) each leaf visited more than
+ * qt_split times since the previous pass splits into four children, which
+ * inherit lambda and n_k / 4 (at least 1) and are not split again in the same
+ * pass; the first child keeps the parent's region id.  This call copies the
+ * tree: child [nodes][4] (-1 for a leaf; child j covers the quadrant with
+ * x bit j & 1 and y bit j >> 1), leaf [nodes] (region id, -1 when internal),
+ * depth [nodes], at most cap_nodes nodes; *n_nodes receives the node count.
+ * RMLT_E_STATE for a grid partition. */
+rmlt_status rmlt_read_quadtree(rmlt_ctx* ctx, int32_t* child, int32_t* leaf, int32_t* depth, int32_t cap_nodes,
+                               int32_t* n_nodes);
 
 /* Chain states in the device's structure-of-arrays layout: q [D][n_chains]
  * u32 primary-sample words (u = q 2^-32), f [3][n_chains] float contribution,

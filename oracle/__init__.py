@@ -44,7 +44,9 @@ class OrParams(C.Structure):
         ("seed", C.c_uint64), ("p_large", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
         ("alpha_star", C.c_double), ("gamma_max", C.c_double), ("gamma_scale", C.c_double),
         ("lambda_init", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
-        ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("pad_", C.c_int32),
+        ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("partition", C.c_int32),
+        ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32), ("qt_split", C.c_int64),
+        ("qt_refine", C.c_int64),
     ]
 
 
@@ -93,14 +95,16 @@ def lib():
         "or_bhat": (C.c_double, [C.c_void_p]),
         "or_stats": (None, [C.c_void_p, P(C.c_uint64)]),
         "or_accept_prob": (C.c_double, [C.c_void_p, u32p, u32p, C.c_double, C.c_double, C.c_int32]),
+        "or_quadtree": (C.c_int32, [C.c_void_p, i32p, i32p, i32p, C.c_int32]),
+        "or_refine": (C.c_int32, [C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
     for name in ("or_state_q", "or_state_f", "or_state_pi", "or_state_k", "or_boot_choice",
-                 "or_lambda", "or_n_updates", "or_visits", "or_accsum", "or_hist", "or_weight",
-                 "or_sigma", "or_image_acc"):
+                 "or_lambda", "or_n_updates", "or_visits", "or_accsum", "or_hist", "or_hist_prev",
+                 "or_weight", "or_sigma", "or_image_acc"):
         fn = getattr(L, name)
         fn.restype = C.c_void_p
         fn.argtypes = [C.c_void_p]
@@ -193,7 +197,8 @@ DEFAULT_PARAMS = dict(
     n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
     target_mode=0, n_bootstrap=1 << 14, seed=1, p_large=0.3, s1=1.0 / 1024.0, s2=1.0 / 64.0,
     alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
-    lambda_max=None, w_floor=1e-3, debug_flags=0,
+    lambda_max=None, w_floor=1e-3, debug_flags=0, partition=0, qt_max_leaves=4096, qt_max_depth=10,
+    qt_split=5000, qt_refine=10_000_000,
 )
 
 
@@ -275,6 +280,23 @@ class Chains:
         return float(lib().or_accept_prob(self.h, _ptr(qx, C.c_uint32), _ptr(qy, C.c_uint32),
                                           float(pi_x), float(pi_y), int(large)))
 
+    def quadtree(self):
+        """(child [nodes,4], leaf [nodes], depth [nodes]) of the quadtree partition."""
+        cap = 4 * self.params.qt_max_leaves // 3 + 8
+        child = np.zeros((cap, 4), np.int32)
+        leaf = np.zeros(cap, np.int32)
+        depth = np.zeros(cap, np.int32)
+        n = lib().or_quadtree(self.h, _ptr(child, C.c_int32), _ptr(leaf, C.c_int32), _ptr(depth, C.c_int32), cap)
+        return child[:n], leaf[:n], depth[:n]
+
+    def refine(self):
+        if lib().or_refine(self.h) != 0:
+            raise RuntimeError("or_refine needs an initialised quadtree context")
+
+    @property
+    def n_regions(self) -> int:
+        return int(lib().or_regions(self.h))
+
     def region_of(self, q) -> int:
         q = np.ascontiguousarray(q, np.uint32)
         return lib().or_region_of(self.h, _ptr(q, C.c_uint32))
@@ -316,31 +338,38 @@ class Chains:
 
     @property
     def lam(self):
-        return self._arr("or_lambda", C.c_double, (self.m,))
+        return self._arr("or_lambda", C.c_double, (self.n_regions,))
 
     @property
     def n_updates(self):
-        return self._arr("or_n_updates", C.c_int64, (self.m,))
+        return self._arr("or_n_updates", C.c_int64, (self.n_regions,))
 
     @property
     def visits(self):
-        return self._arr("or_visits", C.c_uint64, (self.m,))
+        return self._arr("or_visits", C.c_uint64, (self.n_regions,))
 
     @property
     def accsum(self):
-        return self._arr("or_accsum", C.c_uint64, (self.m,))
+        return self._arr("or_accsum", C.c_uint64, (self.n_regions,))
 
     @property
     def hist(self):
-        return self._arr("or_hist", C.c_uint64, (self.m,))
+        return self._arr("or_hist", C.c_uint64, (self.n_regions,))
+
+    @property
+    def hist_since_pass(self):
+        """h_k minus its value at the last quadtree refinement pass."""
+        h = self._arr("or_hist", C.c_uint64, (self.n_regions,))
+        hp = self._arr("or_hist_prev", C.c_uint64, (self.n_regions,))
+        return h - hp
 
     @property
     def weight(self):
-        return self._arr("or_weight", C.c_double, (self.m,))
+        return self._arr("or_weight", C.c_double, (self.n_regions,))
 
     @property
     def sigma(self):
-        return self._arr("or_sigma", C.c_float, (self.m,))
+        return self._arr("or_sigma", C.c_float, (self.n_regions,))
 
     @property
     def image_acc(self):

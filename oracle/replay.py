@@ -170,11 +170,12 @@ class Replay:
             self.cur_epoch = e
             self.ch.run_epochs(1)
             if self.lambdas is not None:
-                bad = np.flatnonzero(self.ch.lam != self.lambdas[e])
+                lam = self.ch.lam                   # the current regions (a quadtree grows)
+                bad = np.flatnonzero(lam != self.lambdas[e][:len(lam)])
                 if len(bad):
                     self.s["lambda_mismatch"] += len(bad)
                     self._fail(f"epoch {e}: lambda differs in regions {bad[:8].tolist()}")
-                    self.ch.lam[:] = self.lambdas[e]
+                    lam[:] = self.lambdas[e][:len(lam)]
                     self.ch.refresh_sigma()
 
     def run_sampled(self, n_epochs: int, traced_chains):

@@ -683,6 +683,13 @@ struct or_ctx {
     double* img;
     double* Bk;                   /* sum of pi over uniform samples landing in region k */
     uint64_t nU;                  /* number of uniform samples (bootstrap + large steps) */
+    /* quadtree partition (Sec. 6.2): node children (-1 for a leaf), leaf region ids, depths */
+    int32_t cap;                  /* region capacity */
+    int32_t* qt_child;
+    int32_t* qt_leaf;
+    int32_t* qt_depth;
+    int32_t qt_nodes;
+    uint64_t since_refine;
     double bhat;
     uint64_t mut;
     uint64_t st[8];
@@ -707,12 +714,25 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     c->nx = (p->width + p->region_px - 1) / p->region_px;
     int32_t ny = (p->height + p->region_px - 1) / p->region_px;
     c->m = c->nx * ny;
+    c->cap = c->m;
+    if (p->partition == 1) {
+        if (p->qt_max_leaves < 1 || p->qt_max_depth < 0 || p->qt_max_depth > 24 || p->target_mode != 0) {
+            free(c);
+            return NULL;
+        }
+        c->m = 1;
+        c->cap = p->qt_max_leaves;
+        size_t nodes = (size_t)(4 * (size_t)c->cap / 3 + 8);
+        c->qt_child = (int32_t*)malloc(sizeof(int32_t) * 4 * nodes);
+        c->qt_leaf = (int32_t*)malloc(sizeof(int32_t) * nodes);
+        c->qt_depth = (int32_t*)malloc(sizeof(int32_t) * nodes);
+    }
     double tl = ceil(p->p_large * 16777216.0);
     c->T_large = (uint32_t)(tl < 0 ? 0 : (tl > 16777216.0 ? 16777216.0 : tl));
     c->S1 = (float)(p->s1 * 4294967296.0);
     c->S2 = (float)(p->s2 * 4294967296.0);
     c->log2_ratio = (float)log2(p->s2 / p->s1);
-    size_t C = (size_t)p->n_chains, m = (size_t)c->m;
+    size_t C = (size_t)p->n_chains, m = (size_t)c->cap;
     c->q = (uint32_t*)calloc(C * (size_t)D, sizeof(uint32_t));
     c->f = (double*)calloc(C * 3, sizeof(double));
     c->pi = (double*)calloc(C, sizeof(double));
@@ -738,6 +758,7 @@ void or_ctx_destroy(or_ctx* c)
     free(c->q); free(c->f); free(c->pi); free(c->k); free(c->boot); free(c->lam); free(c->n);
     free(c->i); free(c->A); free(c->h); free(c->h_prev); free(c->w); free(c->Rc); free(c->sig);
     free(c->img); free(c->Bk);
+    free(c->qt_child); free(c->qt_leaf); free(c->qt_depth);
     free(c);
 }
 
@@ -752,12 +773,65 @@ static void pixel_of(const or_ctx* c, const uint32_t* q, int32_t* px, int32_t* p
     *py = (int32_t)(((uint64_t)(q[1] >> 8) * (uint64_t)c->p.height) >> 24);
 }
 
-/* region of a state: the 2-D screen-space grid partition of Sec. 5.4 / 6.1 */
+/* Region of a state in the 2-D screen-space partition (Sec. 5.4): a cell of
+ * the uniform grid (Sec. 6.1), or the quadtree leaf containing (u0, u1)
+ * (Sec. 6.2).  The quadtree halves [0,1)^2 per level, so the quadrant at
+ * depth l is bit 31 - l of the state words u0, u1. */
 int32_t or_region_of(const or_ctx* c, const uint32_t* q)
 {
+    if (c->p.partition == 1) {
+        int32_t node = 0, depth = 0;
+        while (c->qt_child[4 * node] >= 0) {
+            int32_t bx = (int32_t)((q[0] >> (31 - depth)) & 1u), by = (int32_t)((q[1] >> (31 - depth)) & 1u);
+            node = c->qt_child[4 * node + bx + 2 * by];
+            depth++;
+        }
+        return c->qt_leaf[node];
+    }
     int32_t px, py;
     pixel_of(c, q, &px, &py);
     return px / c->p.region_px + (py / c->p.region_px) * c->nx;
+}
+
+/* Refinement of the quadtree partition (Sec. 6.2), run once every qt_refine
+ * mutations at an epoch boundary: every leaf visited more than qt_split times
+ * since the previous pass splits into four children.  Children inherit the
+ * scale parameter lambda, get n = n_parent / 4 updates (at least 1), and are
+ * not split again in the same pass.  Readings: a visit is a post-MH state of
+ * any mutation (the histogram h); i, A and the visit counts of the children
+ * start at 0; the first child keeps the parent's region id and the other
+ * three get the next free ids, leaves taken in node order; splitting stops at
+ * qt_max_depth and qt_max_leaves. */
+static void quadtree_refine(or_ctx* c)
+{
+    const or_params* p = &c->p;
+    const int32_t nodes0 = c->qt_nodes;
+    for (int32_t node = 0; node < nodes0; ++node) {
+        if (c->qt_child[4 * node] >= 0) continue;
+        const int32_t k = c->qt_leaf[node];
+        if (c->h[k] - c->h_prev[k] <= (uint64_t)p->qt_split) continue;
+        if (c->qt_depth[node] >= p->qt_max_depth || c->m + 3 > c->cap) continue;
+        const double lam = c->lam[k];
+        const int64_t nc = c->n[k] / 4 > 1 ? c->n[k] / 4 : 1;
+        for (int32_t q = 0; q < 4; ++q) {
+            const int32_t ch = c->qt_nodes++;
+            const int32_t id = q == 0 ? k : c->m++;
+            c->qt_child[4 * node + q] = ch;
+            for (int32_t j = 0; j < 4; ++j) c->qt_child[4 * ch + j] = -1;
+            c->qt_leaf[ch] = id;
+            c->qt_depth[ch] = c->qt_depth[node] + 1;
+            c->lam[id] = lam;
+            c->n[id] = nc;
+            c->i[id] = c->A[id] = c->h[id] = c->h_prev[id] = 0;
+            c->w[id] = 1.0;
+            c->Rc[id] = 0.0;
+            c->Bk[id] = 0.0;
+            c->sig[id] = sigma_of_lambda(lam);
+        }
+        c->qt_leaf[node] = -1;
+    }
+    for (int32_t k = 0; k < c->m; ++k) c->h_prev[k] = c->h[k];
+    for (int32_t ch = 0; ch < c->p.n_chains; ++ch) c->k[ch] = or_region_of(c, &c->q[(size_t)ch * c->D]);
 }
 
 static double weight_of(const or_ctx* c, int32_t k) { return c->p.target_mode ? c->w[k] : 1.0; }
@@ -963,6 +1037,7 @@ int32_t or_init(or_ctx* c)
     const or_params* p = &c->p;
     int64_t K = p->n_bootstrap / p->n_chains;
     if (K <= 0) return -1;
+    if (p->partition == 1) or_init_tables(c);   /* the region lookup needs the root */
     uint32_t q[OR_MAX_DIM];
     double f[3], total = 0.0;
     memset(c->Bk, 0, sizeof(double) * (size_t)c->m);
@@ -998,6 +1073,15 @@ int32_t or_init(or_ctx* c)
 /* Alg. 1 lines 2-6: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
 int32_t or_init_tables(or_ctx* c)
 {
+    if (c->p.partition == 1) {
+        c->m = 1;
+        c->qt_nodes = 1;
+        for (int32_t j = 0; j < 4; ++j) c->qt_child[j] = -1;
+        c->qt_leaf[0] = 0;
+        c->qt_depth[0] = 0;
+        c->since_refine = 0;
+        for (int32_t ch = 0; ch < c->p.n_chains; ++ch) c->k[ch] = 0;
+    }
     for (int32_t k = 0; k < c->m; ++k) {
         c->lam[k] = c->p.lambda_init;
         c->n[k] = 1;
@@ -1051,8 +1135,33 @@ int32_t or_run_epochs(or_ctx* c, int64_t n_epochs)
         }
         region_update(c);
         if (c->p.target_mode) weight_update(c);
+        if (c->p.partition == 1) {
+            c->since_refine += (uint64_t)c->p.n_chains * (uint64_t)c->p.epoch_len;
+            if (c->since_refine >= (uint64_t)c->p.qt_refine) {
+                c->since_refine = 0;
+                quadtree_refine(c);
+            }
+        }
     }
     return 0;
+}
+
+int32_t or_refine(or_ctx* c)
+{
+    if (c->p.partition != 1 || !c->inited) return -1;
+    quadtree_refine(c);
+    return 0;
+}
+
+int32_t or_quadtree(const or_ctx* c, int32_t* child, int32_t* leaf, int32_t* depth, int32_t cap_nodes)
+{
+    if (c->p.partition != 1) return 0;
+    for (int32_t n = 0; n < c->qt_nodes && n < cap_nodes; ++n) {
+        for (int32_t j = 0; j < 4; ++j) child[4 * n + j] = c->qt_child[4 * n + j];
+        leaf[n] = c->qt_leaf[n];
+        depth[n] = c->qt_depth[n];
+    }
+    return c->qt_nodes;
 }
 
 /* Plain target: I_j = (b / N) sum_i f(x_i) / pi(x_i) over the chain states
@@ -1096,6 +1205,7 @@ int64_t* or_n_updates(or_ctx* c) { return c->n; }
 uint64_t* or_visits(or_ctx* c) { return c->i; }
 uint64_t* or_accsum(or_ctx* c) { return c->A; }
 uint64_t* or_hist(or_ctx* c) { return c->h; }
+uint64_t* or_hist_prev(or_ctx* c) { return c->h_prev; }
 double* or_weight(or_ctx* c) { return c->w; }
 float* or_sigma(or_ctx* c) { return c->sig; }
 double* or_image_acc(or_ctx* c) { return c->img; }

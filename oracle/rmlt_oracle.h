@@ -58,7 +58,10 @@ typedef struct {
     double   lambda_init, lambda_min, lambda_max;
     double   w_floor;
     int32_t  debug_flags;      /* tests only: bit 0 drops the reverse-kernel factor */
-    int32_t  pad_;
+    int32_t  partition;        /* 0 uniform grid (Sec. 6.1), 1 quadtree (Sec. 6.2) */
+    int32_t  qt_max_leaves, qt_max_depth;
+    int64_t  qt_split;         /* M_split: visits since the last pass that split a leaf */
+    int64_t  qt_refine;        /* M_refine: mutations between refinement passes */
 } or_params;
 
 /* Per-mutation hook (tests only): sees the proposal and may override the
@@ -121,10 +124,17 @@ int64_t*  or_n_updates(or_ctx* c);    /* [m]    */
 uint64_t* or_visits(or_ctx* c);       /* i_k [m] */
 uint64_t* or_accsum(or_ctx* c);       /* A_k [m], fixed point 2^-32 */
 uint64_t* or_hist(or_ctx* c);         /* h_k [m] */
+uint64_t* or_hist_prev(or_ctx* c);    /* h_k at the last weight update or quadtree pass [m] */
 double*   or_weight(or_ctx* c);       /* w_k [m] */
 float*    or_sigma(or_ctx* c);        /* sigma_k [m] binary32 */
 double*   or_image_acc(or_ctx* c);    /* [H][W][3] unnormalised */
 void      or_stats(const or_ctx* c, uint64_t out[8]);
+/* Quadtree partition: copies child [nodes][4] (-1 leaf), leaf region id
+ * [nodes] (-1 internal) and depth [nodes]; returns the node count. */
+int32_t   or_quadtree(const or_ctx* c, int32_t* child, int32_t* leaf, int32_t* depth, int32_t cap_nodes);
+/* One refinement pass of the quadtree now (tests; the epoch loop runs it
+ * every qt_refine mutations). */
+int32_t   or_refine(or_ctx* c);
 /* Acceptance probability of moving x -> y under the current region tables
  * (regions taken from the states; large = 1 for the independent large step). */
 double    or_accept_prob(const or_ctx* c, const uint32_t* qx, const uint32_t* qy,

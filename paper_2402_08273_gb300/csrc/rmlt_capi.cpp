@@ -6,6 +6,7 @@
 // arithmetic step of the method runs in the CUDA kernels (rmlt_kernels.cu).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -87,6 +88,7 @@ struct rmlt_ctx {
     uint64_t tr_lam_cap = 0;
     uint32_t tr_stride = 1;
     bool count_work = false;
+    uint64_t since_refine = 0;   // mutations since the last quadtree pass
     int batch_shade = 8, batch_setup = 8;
     int large_ahead = 0, adaptive_batch = 0;
 
@@ -412,6 +414,14 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
           p->lambda_max <= lmax_ok + 1e-12))
         return fail(RMLT_E_INVALID_ARG, "need -150 <= lambda_min <= lambda_init <= lambda_max <= 2 ln(1/(2 s2)) = %g", lmax_ok);
     if (!(p->w_floor >= 0.0 && p->w_floor <= 1.0)) return fail(RMLT_E_INVALID_ARG, "w_floor outside [0,1]");
+    if (p->partition != RMLT_PARTITION_GRID && p->partition != RMLT_PARTITION_QUADTREE)
+        return fail(RMLT_E_INVALID_ARG, "unknown partition");
+    if (p->partition == RMLT_PARTITION_QUADTREE) {
+        if (p->target_mode != RMLT_TARGET_PLAIN) return fail(RMLT_E_INVALID_ARG, "the quadtree partition needs the plain target");
+        if (p->qt_max_leaves < 1 || p->qt_max_leaves > (1 << 20) || p->qt_max_depth < 0 || p->qt_max_depth > 24 ||
+            p->qt_split < 0 || p->qt_refine < 1)
+            return fail(RMLT_E_INVALID_ARG, "quadtree limits: leaves in [1, 2^20], depth in [0, 24], split >= 0, refine >= 1");
+    }
     return RMLT_OK;
 }
 
@@ -427,6 +437,13 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     Ch.region_px = p->region_px;
     Ch.nx = (p->width + p->region_px - 1) / p->region_px;
     Ch.m = Ch.nx * ((p->height + p->region_px - 1) / p->region_px);
+    if (p->partition == RMLT_PARTITION_QUADTREE) {
+        Ch.quadtree = 1;
+        Ch.m = p->qt_max_leaves;          // capacity; the current count lives on the device
+        Ch.qt_cap = p->qt_max_leaves;
+        Ch.qt_max_depth = p->qt_max_depth;
+        Ch.qt_split = p->qt_split;
+    }
     Ch.max_depth = p->max_depth;
     Ch.E = p->epoch_len;
     Ch.L = p->L;
@@ -459,6 +476,14 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     }
     if ((st = c->alloc_n(pool, 1, &c->d_total))) return st;
     if ((st = c->alloc_n(pool, npx, &c->d_stage))) return st;
+    if (Ch.quadtree) {
+        const size_t nodes = (size_t)4 * Ch.qt_cap / 3 + 8;
+        if ((st = c->alloc_n(pool, 4 * nodes, &Ch.qt_child))) return st;
+        if ((st = c->alloc_n(pool, nodes, &Ch.qt_leaf))) return st;
+        if ((st = c->alloc_n(pool, nodes, &Ch.qt_depth))) return st;
+        if ((st = c->alloc_n(pool, 2, &Ch.qt_state))) return st;
+    }
+    c->since_refine = 0;
     Ch.seed_lo = (uint32_t)p->seed;
     Ch.seed_hi = (uint32_t)(p->seed >> 32);
     double tl = std::ceil(p->p_large * 16777216.0);
@@ -549,6 +574,17 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
             c->failed = true;
             return cuda_fail(err, "rmlt_step launch");
         }
+        if (err == cudaSuccess && c->Ch.quadtree) {
+            c->since_refine += (uint64_t)c->Ch.C * E;
+            if (c->since_refine >= (uint64_t)c->P.qt_refine) {
+                c->since_refine = 0;
+                err = launch_quadtree_refine(c->Ch, c->stream);
+            }
+            if (err != cudaSuccess) {
+                c->failed = true;
+                return cuda_fail(err, "quadtree refinement");
+            }
+        }
         if (trace && c->tr_lam && (c->tr_epoch + 1) * (uint64_t)c->Ch.m <= c->tr_lam_cap) {
             err = cudaMemcpyAsync(c->tr_lam + c->tr_epoch * (uint64_t)c->Ch.m, c->Ch.lam, sizeof(double) * c->Ch.m,
                                   cudaMemcpyDeviceToDevice, c->stream);
@@ -587,13 +623,46 @@ rmlt_status rmlt_read_image(rmlt_ctx* c, double* out, int normalized)
     return sync(c, "read image");
 }
 
+// the current number of regions (grows with a quadtree partition)
+static rmlt_status current_regions(rmlt_ctx* c, int* m)
+{
+    *m = c->Ch.m;
+    if (!c->Ch.quadtree) return RMLT_OK;
+    int32_t s[2];
+    CK(cudaMemcpyAsync(s, c->Ch.qt_state, sizeof s, cudaMemcpyDeviceToHost, c->stream), "read leaf count");
+    rmlt_status st = sync(c, "read leaf count");
+    if (st) return st;
+    *m = s[0];
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_read_quadtree(rmlt_ctx* c, int32_t* child, int32_t* leaf, int32_t* depth, int32_t cap_nodes,
+                               int32_t* n_nodes)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    if (!c->Ch.quadtree) return fail(RMLT_E_STATE, "the partition is a grid");
+    int32_t s[2];
+    CK(cudaMemcpyAsync(s, c->Ch.qt_state, sizeof s, cudaMemcpyDeviceToHost, c->stream), "read tree size");
+    if ((st = sync(c, "read tree size"))) return st;
+    if (n_nodes) *n_nodes = s[1];
+    const size_t n = (size_t)std::min(s[1], cap_nodes);
+    if ((st = copy_out(c, child, c->Ch.qt_child, n * 16)) || (st = copy_out(c, leaf, c->Ch.qt_leaf, n * 4)) ||
+        (st = copy_out(c, depth, c->Ch.qt_depth, n * 4)))
+        return st;
+    return sync(c, "read tree");
+}
+
 rmlt_status rmlt_read_region_hist(rmlt_ctx* c, uint64_t* out)
 {
     rmlt_status st = enter(c);
     if (st) return st;
     if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
     if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
-    if ((st = copy_out(c, out, c->Ch.hist, sizeof(uint64_t) * c->Ch.m))) return st;
+    int m;
+    if ((st = current_regions(c, &m))) return st;
+    if ((st = copy_out(c, out, c->Ch.hist, sizeof(uint64_t) * m))) return st;
     return sync(c, "read hist");
 }
 
@@ -602,7 +671,9 @@ rmlt_status rmlt_read_region_params(rmlt_ctx* c, double* lambda, int64_t* n, uin
     rmlt_status st = enter(c);
     if (st) return st;
     if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
-    const size_t m = (size_t)c->Ch.m;
+    int mi;
+    if ((st = current_regions(c, &mi))) return st;
+    const size_t m = (size_t)mi;
     if ((st = copy_out(c, lambda, c->Ch.lam, m * 8)) || (st = copy_out(c, n, c->Ch.n, m * 8)) ||
         (st = copy_out(c, i, c->Ch.vis, m * 8)) || (st = copy_out(c, A, c->Ch.acc, m * 8)) ||
         (st = copy_out(c, w, c->Ch.w, m * 8)))
@@ -644,7 +715,9 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->stack_overflow = s[kStOverflow];
     out->epochs = c->epochs;
     out->bhat = total / (double)c->n_boot;
-    out->n_regions = c->Ch.m;
+    int mcur;
+    if ((st = current_regions(c, &mcur))) return st;
+    out->n_regions = mcur;
     out->dims = c->Ch.D;
     out->node_visits = s[kStNodes];
     out->tri_tests = s[kStTris];
@@ -756,6 +829,7 @@ struct CkptHeader {
     rmlt_chain_params P;
     uint64_t mut, epochs;
     int64_t n_boot;
+    uint64_t since_refine;
 };
 
 struct Field {
@@ -770,7 +844,11 @@ std::vector<Field> fields(rmlt_ctx* c)
     return {{Ch.q, C * Ch.D * 4}, {Ch.f, C * 12}, {Ch.pi, C * 4}, {Ch.k, C * 4},
             {Ch.lam, m * 8}, {Ch.n, m * 8}, {Ch.vis, m * 8}, {Ch.acc, m * 8}, {Ch.hist, m * 8},
             {Ch.hprev, m * 8}, {Ch.w, m * 8}, {Ch.Rc, m * 8}, {Ch.sig, m * 4}, {Ch.wf, m * 4},
-            {Ch.Bk, m * 8}, {Ch.img, npx * 8}, {Ch.stats, kStCount * 8}, {c->d_total, 8}};
+            {Ch.Bk, m * 8}, {Ch.img, npx * 8}, {Ch.stats, kStCount * 8}, {c->d_total, 8},
+            {Ch.qt_child, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 16 : 0},
+            {Ch.qt_leaf, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 4 : 0},
+            {Ch.qt_depth, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 4 : 0},
+            {Ch.qt_state, Ch.quadtree ? (size_t)8 : (size_t)0}};
 }
 }  // namespace
 
@@ -791,10 +869,12 @@ rmlt_status rmlt_save(rmlt_ctx* c, const char* path)
     h.mut = c->mut;
     h.epochs = c->epochs;
     h.n_boot = c->n_boot;
+    h.since_refine = c->since_refine;
     bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1;
     std::vector<unsigned char> buf;
     for (const Field& f : fields(c)) {
         if (!ok) break;
+        if (f.bytes == 0) continue;
         buf.resize(f.bytes);
         if (cudaMemcpy(buf.data(), f.dev, f.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
             std::fclose(fp);
@@ -834,6 +914,7 @@ rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
     }
     std::vector<unsigned char> buf;
     for (const Field& f : fields(c)) {
+        if (f.bytes == 0) continue;
         buf.resize(f.bytes);
         if (std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
             std::fclose(fp);
@@ -850,6 +931,7 @@ rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
     c->mut = h.mut;
     c->epochs = h.epochs;
     c->n_boot = h.n_boot;
+    c->since_refine = h.since_refine;
     c->have_chains = true;
     c->failed = false;
     return RMLT_OK;

@@ -73,6 +73,15 @@ struct DevChains {
     float* sig = nullptr;         // sigma_k [m]
     float* wf = nullptr;          // w_k as float [m]
     double* Bk = nullptr;         // sum of pi over uniform samples per region [m]
+    // quadtree partition (Sec. 6.2); m is then the region capacity and the
+    // current leaf count lives in qt_state[0] (nodes in qt_state[1])
+    int32_t quadtree = 0;
+    int32_t* qt_child = nullptr;  // [nodes][4], -1 for a leaf
+    int32_t* qt_leaf = nullptr;   // [nodes] region id of a leaf, -1 for an internal node
+    int32_t* qt_depth = nullptr;  // [nodes]
+    int32_t* qt_state = nullptr;  // [2] leaves, nodes
+    int32_t qt_cap = 0, qt_max_depth = 0;
+    long long qt_split = 0;
     // large steps traced ahead of the epoch (nullptr: traced in the chain kernel)
     float* lf = nullptr;          // [3][E][C] their contributions
     uint32_t* llist = nullptr;    // [E C] work list of (j C + c)
@@ -109,6 +118,7 @@ cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_bo
 cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int64_t n_boot,
                               double n_total, int normalized, double* out, cudaStream_t st);
 cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st);
+cudaError_t launch_quadtree_refine(const DevChains& c, cudaStream_t st);
 
 // Pointers into the library's fixed scratch array (rmlt_bootstrap_noalloc).
 struct NoAllocScratch {

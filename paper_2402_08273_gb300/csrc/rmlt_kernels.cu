@@ -80,6 +80,25 @@ __device__ __forceinline__ int pixel_x(uint32_t q0, int W) { return (int)(((unsi
 
 __device__ __forceinline__ float lum(float r, float g, float b) { return 0.2126f * r + 0.7152f * g + 0.0722f * b; }
 
+// Region of a state in the 2-D screen-space partition (Sec. 5.4): the grid
+// cell of its raster position (Sec. 6.1), or the quadtree leaf containing
+// (u0, u1) (Sec. 6.2), whose quadrant at depth l is bit 31 - l of u0 and u1.
+__device__ __forceinline__ int region_of(const DevChains& Ch, uint32_t q0, uint32_t q1)
+{
+    if (Ch.quadtree) {
+        int node = 0, depth = 0;
+        int ch0 = Ch.qt_child[0];
+        while (ch0 >= 0) {
+            const int bx = (int)((q0 >> (31 - depth)) & 1u), by = (int)((q1 >> (31 - depth)) & 1u);
+            node = Ch.qt_child[4 * node + bx + 2 * by];
+            ch0 = Ch.qt_child[4 * node];
+            ++depth;
+        }
+        return Ch.qt_leaf[node];
+    }
+    return pixel_x(q0, Ch.W) / Ch.region_px + (pixel_x(q1, Ch.H) / Ch.region_px) * Ch.nx;
+}
+
 // ---------------------------------------------------------------------------
 // small float3 helpers
 // ---------------------------------------------------------------------------
@@ -511,7 +530,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
             if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
             if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
         }
-        L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+        L.ky = region_of(Ch, y[0], y[1]);
     } else {
         // every dimension perturbed with sigma of the current state's region;
         // the current state's words are fetched first with independent loads
@@ -532,7 +551,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 y[d0 + 1] = (r.w >> 31) ? y[d0 + 1] - o1 : y[d0 + 1] + o1;
             }
             if (jj == 0) {
-                L.ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+                L.ky = region_of(Ch, y[0], y[1]);
                 const float sy = Ch.sig[L.ky];
                 if (sy != sx) {
                     // reverse kernel T_{k(y)}(x|y): every offset inside [sigma_y s1, sigma_y s2]
@@ -889,7 +908,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
     Ch.lf[2 * plane + o] = p.L.z;
     float piy = lum(p.L.x, p.L.y, p.L.z);
     if (!isfinite(piy)) piy = 0.f;   // the chain kernel counts and zeroes invalid contributions
-    const int ky = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+    const int ky = region_of(Ch, y[0], y[1]);
     atomicAdd(&Ch.Bk[ky], (double)piy);
     // reduce over the lanes that arrive together (one atomic per group)
     const unsigned m = __activemask();
@@ -906,7 +925,8 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
 // ---------------------------------------------------------------------------
 __global__ void region_update_kernel(const DevChains Ch, int init_only)
 {
-    for (int k = threadIdx.x; k < Ch.m; k += blockDim.x) {
+    const int m_now = Ch.quadtree ? Ch.qt_state[0] : Ch.m;
+    for (int k = threadIdx.x; k < m_now; k += blockDim.x) {
         double lam = Ch.lam[k];
         if (!init_only && Ch.vis[k] >= (unsigned long long)Ch.L) {
             const double ah = __ddiv_rn((double)Ch.acc[k], __dmul_rn(4294967296.0, (double)Ch.vis[k]));
@@ -949,6 +969,66 @@ __global__ void region_update_kernel(const DevChains Ch, int init_only)
         Ch.hprev[k] = Ch.hist[k];
         Ch.wf[k] = __double2float_rn(Ch.w[k]);
     }
+}
+
+// Refinement pass of the quadtree partition (Sec. 6.2): every leaf visited
+// more than qt_split times since the previous pass splits into four children
+// that inherit lambda and n / 4 (at least 1) and are not split again in this
+// pass; the first child keeps the parent's region id, the others take the
+// next free ids, leaves in node order.  Sequential in one thread (the table
+// has at most qt_cap leaves); binary64 lambda copied, sigma recomputed.
+__global__ void quadtree_refine_kernel(const DevChains Ch)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int m = Ch.qt_state[0], nodes = Ch.qt_state[1];
+    const int nodes0 = nodes;
+    for (int node = 0; node < nodes0; ++node) {
+        if (Ch.qt_child[4 * node] >= 0) continue;
+        const int k = Ch.qt_leaf[node];
+        if (Ch.hist[k] - Ch.hprev[k] <= (unsigned long long)Ch.qt_split) continue;
+        if (Ch.qt_depth[node] >= Ch.qt_max_depth || m + 3 > Ch.qt_cap) continue;
+        const double lam = Ch.lam[k];
+        const long long nc = Ch.n[k] / 4 > 1 ? Ch.n[k] / 4 : 1;
+        const float sg = exp2_ordered(__double2float_rn(__dmul_rn(lam, 0.7213475204444817)));
+        for (int q = 0; q < 4; ++q) {
+            const int chn = nodes++;
+            const int id = q == 0 ? k : m++;
+            Ch.qt_child[4 * node + q] = chn;
+            for (int j = 0; j < 4; ++j) Ch.qt_child[4 * chn + j] = -1;
+            Ch.qt_leaf[chn] = id;
+            Ch.qt_depth[chn] = Ch.qt_depth[node] + 1;
+            Ch.lam[id] = lam;
+            Ch.n[id] = nc;
+            Ch.vis[id] = Ch.acc[id] = Ch.hist[id] = Ch.hprev[id] = 0;
+            Ch.w[id] = 1.0;
+            Ch.Rc[id] = 0.0;
+            Ch.Bk[id] = 0.0;
+            Ch.wf[id] = 1.0f;
+            Ch.sig[id] = sg;
+        }
+        Ch.qt_leaf[node] = -1;
+    }
+    for (int k = 0; k < m; ++k) Ch.hprev[k] = Ch.hist[k];
+    Ch.qt_state[0] = m;
+    Ch.qt_state[1] = nodes;
+}
+
+// the chains' cached regions after the partition changed
+__global__ void chain_regions_kernel(const DevChains Ch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Ch.C) return;
+    Ch.k[c] = region_of(Ch, Ch.q[c], Ch.q[(size_t)Ch.C + c]);
+}
+
+__global__ void quadtree_init_kernel(const DevChains Ch)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int j = 0; j < 4; ++j) Ch.qt_child[j] = -1;
+    Ch.qt_leaf[0] = 0;
+    Ch.qt_depth[0] = 0;
+    Ch.qt_state[0] = 1;
+    Ch.qt_state[1] = 1;
 }
 
 __global__ void fill_regions_kernel(const DevChains Ch, double lambda_init)
@@ -1013,7 +1093,7 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     B.f[s] = f.x;
     B.f[n_boot + s] = f.y;
     B.f[2 * n_boot + s] = f.z;
-    const int k = pixel_x(y[0], Ch.W) / Ch.region_px + (pixel_x(y[1], Ch.H) / Ch.region_px) * Ch.nx;
+    const int k = region_of(Ch, y[0], y[1]);
     if (pv != 0.f) atomicAdd(&Ch.Bk[k], (double)pv);
 }
 
@@ -1051,7 +1131,7 @@ __global__ void bootstrap_select_kernel(const DevChains Ch, long long K, const B
     Ch.f[C + c] = B.f[n_eff + sel];
     Ch.f[2 * C + c] = B.f[2 * n_eff + sel];
     Ch.pi[c] = B.pi[sel];
-    Ch.k[c] = pixel_x(q0, Ch.W) / Ch.region_px + (pixel_x(q1, Ch.H) / Ch.region_px) * Ch.nx;
+    Ch.k[c] = region_of(Ch, q0, q1);
 }
 
 // fixed-order binary64 sum of the per-chain slice sums (deterministic)
@@ -1166,6 +1246,18 @@ cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_
 cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st)
 {
     fill_regions_kernel<<<(c.m + 255) / 256, 256, 0, st>>>(c, lambda_init);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !c.quadtree) return e;
+    quadtree_init_kernel<<<1, 1, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quadtree_refine(const DevChains& c, cudaStream_t st)
+{
+    quadtree_refine_kernel<<<1, 32, 0, st>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    chain_regions_kernel<<<(c.C + 255) / 256, 256, 0, st>>>(c);
     return cudaGetLastError();
 }
 

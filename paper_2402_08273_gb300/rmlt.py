@@ -54,7 +54,9 @@ class ChainParams(C.Structure):
                 ("seed", C.c_uint64), ("p_large", C.c_double), ("s1", C.c_double),
                 ("s2", C.c_double), ("alpha_star", C.c_double), ("gamma_max", C.c_double),
                 ("gamma_scale", C.c_double), ("lambda_init", C.c_double),
-                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("w_floor", C.c_double)]
+                ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("w_floor", C.c_double),
+                ("partition", C.c_int32), ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32),
+                ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -89,6 +91,8 @@ _SIGS = [
     ("rmlt_read_region_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
     ("rmlt_read_chain_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rmlt_read_quadtree", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                     _P(C.c_int32)]),
     ("rmlt_read_stats", C.c_int, [C.c_void_p, _P(Stats)]),
     ("rmlt_set_trace", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64,
                                  C.c_uint32]),
@@ -136,7 +140,8 @@ def default_params(**kw) -> dict:
     p = dict(n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
              target_mode=TARGET_PLAIN, n_bootstrap=1 << 16, seed=1, p_large=0.3, s1=1 / 1024,
              s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
-             lambda_min=-30.0, lambda_max=None, w_floor=1e-3)
+             lambda_min=-30.0, lambda_max=None, w_floor=1e-3, partition=0, qt_max_leaves=4096,
+             qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000)
     p.update(kw)
     if p["lambda_max"] is None:
         p["lambda_max"] = 2.0 * math.log(1.0 / (2.0 * p["s2"]))
@@ -239,7 +244,7 @@ class Renderer:
         self.D = 2 + 5 * p["max_depth"]
         nx = -(-p["width"] // p["region_px"])
         ny = -(-p["height"] // p["region_px"])
-        self.m = nx * ny
+        self.m = p["qt_max_leaves"] if p["partition"] == 1 else nx * ny   # region table capacity
 
     def step(self, n_mutations: int):
         _check(lib().rmlt_step(self.h, int(n_mutations)))
@@ -262,20 +267,35 @@ class Renderer:
         _check(lib().rmlt_read_image(self.h, _ptr(out), int(normalized)))
         return out
 
+    def n_regions(self) -> int:
+        """Current number of regions (grows with a quadtree partition)."""
+        return int(self.read_stats()["n_regions"])
+
+    def read_quadtree(self):
+        """(child [nodes,4], leaf [nodes], depth [nodes]) of the quadtree partition."""
+        cap = 4 * self.params["qt_max_leaves"] // 3 + 8
+        child = np.zeros((cap, 4), np.int32)
+        leaf = np.zeros(cap, np.int32)
+        depth = np.zeros(cap, np.int32)
+        n = C.c_int32()
+        _check(lib().rmlt_read_quadtree(self.h, _ptr(child), _ptr(leaf), _ptr(depth), cap, C.byref(n)))
+        return child[:n.value], leaf[:n.value], depth[:n.value]
+
     def read_region_hist(self, out=None):
         self._require_chains()
         if out is None:
-            out = np.zeros(self.m, np.uint64)
+            out = np.zeros(self.n_regions(), np.uint64)
         _check(lib().rmlt_read_region_hist(self.h, _ptr(out)))
         return out
 
     def read_region_params(self) -> dict:
         self._require_chains()
-        lam = np.zeros(self.m)
-        n = np.zeros(self.m, np.int64)
-        i = np.zeros(self.m, np.uint64)
-        A = np.zeros(self.m, np.uint64)
-        w = np.zeros(self.m)
+        m = self.n_regions()
+        lam = np.zeros(m)
+        n = np.zeros(m, np.int64)
+        i = np.zeros(m, np.uint64)
+        A = np.zeros(m, np.uint64)
+        w = np.zeros(m)
         _check(lib().rmlt_read_region_params(self.h, _ptr(lam), _ptr(n), _ptr(i), _ptr(A), _ptr(w)))
         return {"lambda": lam, "n": n, "i": i, "A": A, "w": w}
 

@@ -327,6 +327,19 @@ def toy_region_masses(params, width, height, region_px):
     return out
 
 
+def toy_rect_mass(params, x0, x1, y0, y1) -> float:
+    """Closed-form integral of the toy integrand over [x0,x1) x [y0,y1)."""
+    base, bh, bx0, bx1, by0, by1, amp, mx, my, s = [float(p) for p in params]
+    rt2s = math.sqrt(2.0) * s
+
+    def g1(a, c, mu):
+        return 0.5 * (math.erf((c - mu) / rt2s) - math.erf((a - mu) / rt2s)) * math.sqrt(2 * math.pi) * s
+
+    ox = max(0.0, min(x1, bx1) - max(x0, bx0))
+    oy = max(0.0, min(y1, by1) - max(y0, by0))
+    return base * (x1 - x0) * (y1 - y0) + bh * ox * oy + amp * g1(x0, x1, mx) * g1(y0, y1, my)
+
+
 def scene_stats(scene: dict) -> dict:
     return {"n_tris": int(len(scene["tris"])), "n_verts": int(len(scene["verts"])),
             "n_mats": int(len(scene["mat_type"]))}

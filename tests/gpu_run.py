@@ -40,13 +40,16 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
         "image_raw": R.read_image(normalized=False),
         "stats": R.read_stats(),
     }
+    if p.get("partition", 0) == 1:
+        out["quadtree"] = R.read_quadtree()
     return out
 
 
 def oracle_params(p: dict) -> dict:
     keys = ("n_chains", "width", "height", "region_px", "max_depth", "epoch_len", "L", "target_mode",
             "n_bootstrap", "seed", "p_large", "s1", "s2", "alpha_star", "gamma_max", "gamma_scale",
-            "lambda_init", "lambda_min", "lambda_max", "w_floor")
+            "lambda_init", "lambda_min", "lambda_max", "w_floor", "partition", "qt_max_leaves",
+            "qt_max_depth", "qt_split", "qt_refine")
     return {k: p[k] for k in keys}
 
 

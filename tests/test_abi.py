@@ -58,9 +58,28 @@ def test_create_without_gpu_reports_cuda_error():
         rmlt.Renderer()
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror has the C compiler's size and field offsets."""
+    import subprocess
     from paper_2402_08273_gb300 import rmlt
-    assert C.sizeof(rmlt.Material) == 32
-    assert C.sizeof(rmlt.Camera) == 40
-    assert C.sizeof(rmlt.ChainParams) == 32 + 16 + 10 * 8
-    assert rmlt.TRACE_DTYPE.itemsize == 24
+    structs = {"rmlt_material": rmlt.Material, "rmlt_camera": rmlt.Camera,
+               "rmlt_scene_desc": rmlt.SceneDesc, "rmlt_chain_params": rmlt.ChainParams,
+               "rmlt_stats": rmlt.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rmlt.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('printf("rmlt_trace_record %zu\\n", sizeof(rmlt_trace_record));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    out = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+    assert int(out["rmlt_trace_record"]) == rmlt.TRACE_DTYPE.itemsize
