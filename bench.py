@@ -357,6 +357,85 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------
+# matched relMSE: the variants of the paper's comparison (Sec. 7.1) on one GPU
+# ----------------------------------------------------------------------------
+def relmse(img, ref) -> float:
+    """mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2)"""
+    import numpy as np
+    return float(np.mean((img - ref) ** 2 / (ref ** 2 + 1e-2)))
+
+
+def run_relmse(args, w):
+    """Fixed / Global / RA-Grid / RA-Quadtree / region-weighted against one
+    long reference render (independent seed): relMSE after the same number of
+    mutations, and the device time each variant needs to reach a common
+    target (the Fixed variant's relMSE after `args.relmse_budget` mutations)."""
+    import numpy as np
+    import torch
+    from paper_2402_08273_gb300 import rmlt
+    scene = make_scene(w)
+    base = dict(w["params"])
+    W, H = base["width"], base["height"]
+    variants = {
+        "fixed": dict(gamma_max=0.0, gamma_scale=0.0),
+        "global": dict(region_px=max(W, H)),
+        "ra_grid": dict(),
+        "ra_quadtree": dict(partition=1, qt_max_leaves=4096, qt_max_depth=10, qt_split=5000,
+                            qt_refine=10_000_000),
+        "weighted": dict(target_mode=1),
+    }
+    R = rmlt.Renderer(stream=torch.cuda.Stream())
+    R.load_scene(scene)
+    R.init_chains(**dict(base, seed=base["seed"] + 1000))
+    R.step(args.relmse_budget * args.relmse_ref_factor)
+    ref = R.read_image()
+    R.close()
+    budget = args.relmse_budget
+    marks = [budget // 8, budget // 4, budget // 2, budget, 2 * budget]
+    out = {}
+    for name, kw in variants.items():
+        R = rmlt.Renderer(stream=torch.cuda.Stream())
+        R.load_scene(scene)
+        R.init_chains(**dict(base, **kw))
+        done, t = 0, 0.0
+        curve = []
+        for mk in marks:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(R.stream)
+            R.step(mk - done)
+            e1.record(R.stream)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+            done = mk
+            curve.append((done, t, relmse(R.read_image(), ref)))
+        st = R.read_stats()
+        out[name] = {"curve": curve, "accept_rate": st["accepted"] / max(1, st["mutations"] * base["n_chains"]),
+                     "regions": st["n_regions"]}
+        R.close()
+    target = [c for c in out["fixed"]["curve"] if c[0] == budget][0][2]
+    for name, o in out.items():
+        # device time to reach the target, log-log interpolation between marks
+        tt = None
+        cv = o["curve"]
+        for (m0, t0, e0), (m1, t1, e1) in zip(cv, cv[1:]):
+            if e0 >= target >= e1 and e0 > e1:
+                a = (math.log(e0) - math.log(target)) / (math.log(e0) - math.log(e1))
+                tt = math.exp(math.log(t0) + a * (math.log(t1) - math.log(t0)))
+                break
+        if tt is None and cv[0][2] <= target:
+            tt = cv[0][1] * cv[0][2] / target
+        o["seconds_to_target"] = tt
+        o["relmse_at_budget"] = [c for c in cv if c[0] == budget][0][2]
+    line = {"metric": "seconds to matched relMSE", "unit": "s", "higher_is_better": False,
+            "config": {"workload": args.workload, "desc": w["desc"], "budget_mutations_per_chain": budget,
+                       "reference_mutations_per_chain": budget * args.relmse_ref_factor,
+                       "target_relmse": target, "relmse": "mean (I - R)^2 / (R^2 + 1e-2)"},
+            "variants": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,9 +444,15 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="two_rooms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--relmse", action="store_true",
+                    help="compare the Fixed / Global / RA-Grid / RA-Quadtree / weighted variants at matched relMSE")
+    ap.add_argument("--relmse-budget", type=int, default=1024)
+    ap.add_argument("--relmse-ref-factor", type=int, default=32)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.relmse:
+        run_relmse(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)
