@@ -237,6 +237,8 @@ def run_ours(args, w):
     M = w["mutations"]
     stream = torch.cuda.Stream(device=dev)
     R = rmlt.Renderer(device=local, stream=stream)
+    if args.form == "wavefront":
+        R.set_tuning(wavefront=True)
     t0 = time.perf_counter()
     R.load_scene(scene)
     t_load = time.perf_counter() - t0
@@ -336,11 +338,12 @@ def run_ours(args, w):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "chains_per_gpu": C,
                        "mutations_per_step": M, "epochs_per_step": epochs_per_step,
-                       "l2": "flushed between timed steps (256 MiB write)",
+                       "l2": "flushed between timed steps (256 MiB write)", "form": args.form,
                        "parallelism": f"{world} independent chain populations (one per GPU)"},
             "rays_per_s": rays / t_max,
             "rays_per_mutation": rays / mutations,
-            "gpu_launches": 2 * epochs_per_step * args.steps,
+            "gpu_launches": (2 * epochs_per_step * args.steps if args.form == "chain" else
+                             3 * epochs_per_step * args.steps + 3 * (st1["waves"] - st0["waves"])),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "mutations/s", "h2d_bytes_per_step": 0,
@@ -444,6 +447,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="two_rooms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", choices=("chain", "wavefront"), default="chain",
+                    help="epoch execution form: one thread per chain, or waves of shade / setup / trace")
     ap.add_argument("--relmse", action="store_true",
                     help="compare the Fixed / Global / RA-Grid / RA-Quadtree / weighted variants at matched relMSE")
     ap.add_argument("--relmse-budget", type=int, default=1024)

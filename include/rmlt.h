@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 1
+#define RMLT_ABI_VERSION 2
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -121,6 +121,8 @@ typedef struct {
                                   them, shade batches, lanes shaded, setup batches, lanes set up */
     uint64_t cycles[5];        /* work counters on: SM cycles warps spent in traversal steps, shade
                                   batches, finish/setup batches; warp lifetimes (sum, max) */
+    uint64_t waves;            /* wavefront form: waves run (one trace pass each), summed over epochs */
+    uint64_t wave_limit_hits;  /* wavefront form: epochs stopped by the wave limit (0 unless a bug) */
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -237,7 +239,28 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
  * They change speed only, never results.  Defaults 8, 8, 0. */
 #define RMLT_TUNE_LARGE_AHEAD 1
 #define RMLT_TUNE_ADAPTIVE_BATCH 2
+/* RMLT_TUNE_WAVEFRONT runs each epoch in the wavefront form instead of the
+ * chain kernel: the epoch advances in waves; in each wave every chain with
+ * rays in flight shades its hits (the shadow ray of bounce b and the
+ * extension ray of bounce b + 1 are traced together), the chains whose path
+ * ended accept or reject and draw their next proposal, and a persistent trace
+ * kernel resolves all queued rays.  A CUDA graph repeats the wave on the
+ * device until no chain has a ray left.  The results are identical to the
+ * chain kernel's (same arithmetic per path, same Philox draws). */
+#define RMLT_TUNE_WAVEFRONT 4
 rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup, int flags);
+
+/* Launch shape of the wavefront form: resident blocks of 128 threads per SM
+ * for the persistent trace kernel and for the finish / setup kernel (0 = as
+ * many as fit), and how many lanes of a trace warp must be idle before they
+ * pull new rays together (1..32).  flags: RMLT_WAVEFRONT_HOST_LOOP launches
+ * the waves from the host (a fixed E (max_depth + 1) + 2 waves per epoch, the
+ * surplus ones empty) instead of the graph's device-side loop; profilers that
+ * cannot see into conditional graphs need it.  Speed only.  Defaults 0, 0, 16,
+ * 0. */
+#define RMLT_WAVEFRONT_HOST_LOOP 1
+rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_ctas_per_sm, int refill_lanes,
+                               int flags);
 
 /* Bootstrap without any device allocation.  Some callers cannot allocate
  * device memory at the point where they need starting states: code running

@@ -13,8 +13,11 @@ OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "librmlt.so"
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if Path("/usr/local/cuda/bin/nvcc").exists() else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["rmlt_kernels.cu", "rmlt_capi.cpp", "bvh_build.cpp"]
+# -fmad=false: no automatic multiply-add contraction in device code, so that
+# kernels inlining the same helpers round identically (fused operations are
+# written out as fmaf where wanted)
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O3", f"-I{INCLUDE}", f"-I{CSRC}"]
+SOURCES = ["rmlt_kernels.cu", "rmlt_wavefront.cu", "rmlt_capi.cpp", "bvh_build.cpp"]
 
 
 def _stale() -> bool:

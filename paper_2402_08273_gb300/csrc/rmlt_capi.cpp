@@ -91,6 +91,9 @@ struct rmlt_ctx {
     uint64_t since_refine = 0;   // mutations since the last quadtree pass
     int batch_shade = 8, batch_setup = 8;
     int large_ahead = 0, adaptive_batch = 0;
+    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0;
+    DevWave W;                   // wavefront state (allocated on first use)
+    WfGraph* wg = nullptr;       // its instantiated wave loop
 
     rmlt_status dalloc(std::vector<Alloc>& pool, size_t bytes, void** out)
     {
@@ -200,6 +203,10 @@ rmlt_status rmlt_set_allocator(rmlt_ctx* c, rmlt_alloc_fn alloc, rmlt_free_fn fr
 
 static void drop_chains(rmlt_ctx* c)
 {
+    if (c->wg) cudaStreamSynchronize(c->stream);
+    wf_graph_destroy(c->wg);
+    c->wg = nullptr;
+    c->W = DevWave();
     c->release(c->chain_mem);
     c->have_chains = false;
     c->failed = false;
@@ -567,8 +574,21 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
         }
         const DevScene& S = c->S;
         cudaError_t err = cudaSuccess;
+        if (c->wavefront && !c->W.s) {
+            void* mem = nullptr;
+            if ((st = c->dalloc(c->chain_mem, wf_bytes(Ch.C, Ch.D), &mem))) return st;
+            wf_carve(mem, Ch.C, Ch.D, c->W);
+        }
         if (Ch.lf) err = launch_large_steps(S, Ch, c->mut, c->stream);
-        if (err == cudaSuccess) err = launch_chain_epoch(S, Ch, c->mut, trace, c->count_work, c->stream);
+        if (err == cudaSuccess) {
+            if (c->wavefront) {
+                c->W.refill = c->wf_refill;
+                err = wf_epoch(&c->wg, S, Ch, c->W, c->mut, Ch.trace_base, trace, c->count_work, c->wf_trace_cps,
+                               c->wf_setup_cps, (c->wf_flags & RMLT_WAVEFRONT_HOST_LOOP) != 0, c->stream);
+            } else {
+                err = launch_chain_epoch(S, Ch, c->mut, trace, c->count_work, c->stream);
+            }
+        }
         if (err == cudaSuccess) err = launch_region_update(c->Ch, false, c->stream);
         if (err != cudaSuccess) {
             c->failed = true;
@@ -723,6 +743,8 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->tri_tests = s[kStTris];
     for (int i = 0; i < 6; ++i) out->sched[i] = s[kStIters + i];
     for (int i = 0; i < 5; ++i) out->cycles[i] = s[kStCycTrav + i];
+    out->waves = s[kStWaves];
+    out->wave_limit_hits = s[kStWaveLimit];
     return RMLT_OK;
 }
 
@@ -731,12 +753,28 @@ rmlt_status rmlt_set_tuning(rmlt_ctx* c, int batch_shade, int batch_setup, int f
     if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
     if (batch_shade < 1 || batch_shade > 32 || batch_setup < 1 || batch_setup > 32)
         return fail(RMLT_E_INVALID_ARG, "batch sizes must be in 1..32");
-    if (flags & ~(RMLT_TUNE_LARGE_AHEAD | RMLT_TUNE_ADAPTIVE_BATCH))
+    if (flags & ~(RMLT_TUNE_LARGE_AHEAD | RMLT_TUNE_ADAPTIVE_BATCH | RMLT_TUNE_WAVEFRONT))
         return fail(RMLT_E_INVALID_ARG, "unknown tuning flag");
     c->batch_shade = batch_shade;
     c->batch_setup = batch_setup;
     c->large_ahead = (flags & RMLT_TUNE_LARGE_AHEAD) != 0;
     c->adaptive_batch = (flags & RMLT_TUNE_ADAPTIVE_BATCH) != 0;
+    c->wavefront = (flags & RMLT_TUNE_WAVEFRONT) != 0;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_wavefront(rmlt_ctx* c, int trace_ctas_per_sm, int setup_ctas_per_sm, int refill_lanes,
+                               int flags)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (trace_ctas_per_sm < 0 || trace_ctas_per_sm > 32 || setup_ctas_per_sm < 0 || setup_ctas_per_sm > 32)
+        return fail(RMLT_E_INVALID_ARG, "blocks per SM must be in 0..32");
+    if (refill_lanes < 1 || refill_lanes > 32) return fail(RMLT_E_INVALID_ARG, "refill_lanes must be in 1..32");
+    if (flags & ~RMLT_WAVEFRONT_HOST_LOOP) return fail(RMLT_E_INVALID_ARG, "unknown wavefront flag");
+    c->wf_flags = flags;
+    c->wf_trace_cps = trace_ctas_per_sm;
+    c->wf_setup_cps = setup_ctas_per_sm;
+    c->wf_refill = refill_lanes;
     return RMLT_OK;
 }
 
@@ -941,7 +979,7 @@ void rmlt_destroy(rmlt_ctx* c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
-    c->release(c->chain_mem);
+    drop_chains(c);
     c->release(c->scene_mem);
     delete c;
 }

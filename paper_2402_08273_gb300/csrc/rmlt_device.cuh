@@ -1,0 +1,713 @@
+// Device building blocks shared by the chain kernels of librmlt (sm_103a):
+// Philox draws, the binary32 operations that decide integers, ray casting
+// against the BVH, the PT + NEE path map as a state machine that asks for one
+// ray at a time, and the per-mutation setup / finish of a chain.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rmlt_internal.h"
+
+namespace rmlt {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies; the key is bumped by the Weyl constants per round.
+// Counter layout: mutation draws {mut lo, mut hi, chain, call}; bootstrap
+// draws {sample lo, sample hi, 0xFFFFFFFF, 0x8000 + call}; key = seed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// uniform in [0,1) from the top 24 bits (exact in binary32)
+__device__ __forceinline__ float u24(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-08f; }
+
+// ---------------------------------------------------------------------------
+// binary32 arithmetic that decides integers (the quantised small-step offset
+// and sigma_k): a fixed sequence of correctly rounded operations, never
+// contracted, so every conforming implementation gets the same bits.
+// ---------------------------------------------------------------------------
+// 2^t: t = n + r with n = rint(t), |r| <= 1/2; 2^r by its Taylor polynomial
+// sum_{i<=7} (ln 2)^i r^i / i! in Horner form with fused multiply-adds.
+__device__ __forceinline__ float exp2_ordered(float t)
+{
+    const float n = rintf(t);
+    const float r = __fsub_rn(t, n);
+    float p = 1.525273365e-05f;
+    p = __fmaf_rn(p, r, 1.540352969e-04f);
+    p = __fmaf_rn(p, r, 1.333355787e-03f);
+    p = __fmaf_rn(p, r, 9.618128650e-03f);
+    p = __fmaf_rn(p, r, 5.550410971e-02f);
+    p = __fmaf_rn(p, r, 2.402265072e-01f);
+    p = __fmaf_rn(p, r, 6.931471825e-01f);
+    p = __fmaf_rn(p, r, 1.0f);
+    return __fmul_rn(p, __int_as_float(((int)n + 127) << 23));
+}
+
+// Kelemen small step: |offset| = sigma s2 (s1/s2)^xi in units of 2^-32.
+__device__ __forceinline__ uint32_t kelemen_offset(uint32_t xmag, float sigS2, float log2_ratio)
+{
+    const float xi = __fmul_rn(__uint2float_rn(xmag >> 8), 5.9604644775390625e-08f);
+    const float t = -__fmul_rn(xi, log2_ratio);
+    const float m = __fmul_rn(sigS2, exp2_ordered(t));
+    return (uint32_t)(unsigned long long)__float2ll_rn(m);
+}
+
+__device__ __forceinline__ int pixel_x(uint32_t q0, int W) { return (int)(((unsigned long long)(q0 >> 8) * (unsigned)W) >> 24); }
+
+// luminance, uncontracted so that every kernel that inlines it rounds alike
+__device__ __forceinline__ float lum(float r, float g, float b)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
+}
+
+// Region of a state in the 2-D screen-space partition (Sec. 5.4): the grid
+// cell of its raster position (Sec. 6.1), or the quadtree leaf containing
+// (u0, u1) (Sec. 6.2), whose quadrant at depth l is bit 31 - l of u0 and u1.
+__device__ __forceinline__ int region_of(const DevChains& Ch, uint32_t q0, uint32_t q1)
+{
+    if (Ch.quadtree) {
+        int node = 0, depth = 0;
+        int ch0 = Ch.qt_child[0];
+        while (ch0 >= 0) {
+            const int bx = (int)((q0 >> (31 - depth)) & 1u), by = (int)((q1 >> (31 - depth)) & 1u);
+            node = Ch.qt_child[4 * node + bx + 2 * by];
+            ch0 = Ch.qt_child[4 * node];
+            ++depth;
+        }
+        return Ch.qt_leaf[node];
+    }
+    return pixel_x(q0, Ch.W) / Ch.region_px + (pixel_x(q1, Ch.H) / Ch.region_px) * Ch.nx;
+}
+
+// ---------------------------------------------------------------------------
+// small float3 helpers
+// ---------------------------------------------------------------------------
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+// The library is compiled without automatic contraction (-fmad=false): a
+// multiply-add is fused only where it is written as fmaf, so every kernel
+// that inlines these helpers rounds the same way.
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b)
+{
+    return {fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x))};
+}
+__device__ __forceinline__ V3 normalize(V3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ V3 xyz(float4 a) { return {a.x, a.y, a.z}; }
+
+// ---------------------------------------------------------------------------
+// ray casting
+// ---------------------------------------------------------------------------
+// Moller-Trumbore without a division on the rejection path: the barycentric
+// and distance tests are taken on u det, v det, t det against |det| (the
+// same inequalities scaled by |det|); t is divided out only for a hit.
+__device__ __forceinline__ bool hit_tri(V3 o, V3 d, float4 a, float4 b, float4 c, float tmax, float& t)
+{
+    const V3 v0 = xyz(a), e1 = xyz(b), e2 = xyz(c);
+    const V3 p = cross(d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return false;
+    const float sg = det > 0.0f ? 1.0f : -1.0f, ad = fabsf(det);
+    const V3 s = o - v0;
+    const float u = dot(s, p) * sg;
+    const V3 qv = cross(s, e1);
+    const float v = dot(d, qv) * sg;
+    const float tt = dot(e2, qv) * sg;
+    if (!(u >= 0.0f && v >= 0.0f && u + v <= ad && tt > 0.0f && tt < tmax * ad)) return false;
+    t = tt / ad;
+    return t < tmax;
+}
+
+struct Hit {
+    float t;
+    int tri;
+    float4 a, b, c;   // the hit triangle (v0 | material, e1, e2), kept from the leaf test
+};
+
+constexpr uint32_t kNoRef = 0xFFFFFFFFu;
+
+// Stepwise traversal: the state of one ray between steps.  A step visits one
+// BVH node (both children tested), or the triangles of one leaf, or (brute
+// force) the next group of four triangles.
+struct Trav {
+    V3 o, d, id, ood;
+    float t;          // closest hit so far (initially tmax)
+    int tri;          // its triangle, -1 if none
+    float4 ta, tb, tc;  // its data
+    uint32_t ref;     // node / leaf to visit next, kNoRef when done
+    int sp, any, overflow;
+};
+
+__device__ __forceinline__ void trav_begin(Trav& T, V3 o, V3 d, float tmax, int any)
+{
+    T.o = o;
+    T.d = d;
+    T.id = {1.0f / (fabsf(d.x) > 1e-12f ? d.x : copysignf(1e-12f, d.x)),
+            1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
+            1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z))};
+    T.ood = {o.x * T.id.x, o.y * T.id.y, o.z * T.id.z};
+    T.t = tmax;
+    T.tri = -1;
+    T.ref = 0;
+    T.sp = 0;
+    T.any = any;
+    T.overflow = 0;
+}
+
+// one step; returns true once the ray is resolved
+template <bool BRUTE>
+__device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevScene& S, const float4* s_tris,
+                                          unsigned& n_nodes, unsigned& n_tris)
+{
+    if (BRUTE) {
+        const int n = S.n_tris;
+        const int i0 = (int)T.ref;
+        const int i1 = i0 + 4 < n ? i0 + 4 : n;
+        bool found = false;
+        for (int i = i0; i < i1; ++i) {
+            float t;
+            const float4 a = s_tris[3 * i], b = s_tris[3 * i + 1], c = s_tris[3 * i + 2];
+            if (hit_tri(T.o, T.d, a, b, c, T.t, t)) {
+                T.t = t;
+                T.tri = i;
+                T.ta = a;
+                T.tb = b;
+                T.tc = c;
+                found = true;
+            }
+        }
+        T.ref = (i1 >= n || (T.any && found)) ? kNoRef : (uint32_t)i1;
+        return T.ref == kNoRef;
+    }
+    uint32_t next;
+    const uint32_t ref = T.ref;
+    if (!(ref & kLeafBit) && S.bvh4) {
+        // four children: slab tests in the lanes of each float4, nearest hit
+        // child next, the others pushed far to near
+        ++n_nodes;
+        const float4* nd = &S.nodes[8 * (size_t)ref];
+        const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const float tcap = T.t * 1.00000036f;
+        const V3 id = T.id, ood = T.ood;
+        float key[4];
+        uint32_t cr[4];
+        const float lox[4] = {lx.x, lx.y, lx.z, lx.w}, hix[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float loy[4] = {ly.x, ly.y, ly.z, ly.w}, hiy[4] = {hy.x, hy.y, hy.z, hy.w};
+        const float loz[4] = {lz.x, lz.y, lz.z, lz.w}, hiz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                                __float_as_uint(rf.w)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float a0 = fmaf(lox[k], id.x, -ood.x), b0 = fmaf(hix[k], id.x, -ood.x);
+            const float a1 = fmaf(loy[k], id.y, -ood.y), b1 = fmaf(hiy[k], id.y, -ood.y);
+            const float a2 = fmaf(loz[k], id.z, -ood.z), b2 = fmaf(hiz[k], id.z, -ood.z);
+            const float tn = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+            const float tf = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+            const bool hit = tn <= tf && rr[k] != kEmptyRef;
+            key[k] = hit ? tn : INFINITY;
+            cr[k] = rr[k];
+        }
+        // sorting network on (key, ref): (0,1) (2,3) (0,2) (1,3) (1,2)
+#define RMLT_CSWAP(i, j)                                                    \
+        if (key[j] < key[i]) {                                              \
+            const float tk = key[i]; key[i] = key[j]; key[j] = tk;          \
+            const uint32_t tr = cr[i]; cr[i] = cr[j]; cr[j] = tr;           \
+        }
+        RMLT_CSWAP(0, 1) RMLT_CSWAP(2, 3) RMLT_CSWAP(0, 2) RMLT_CSWAP(1, 3) RMLT_CSWAP(1, 2)
+#undef RMLT_CSWAP
+#pragma unroll
+        for (int k = 3; k >= 1; --k) {
+            if (key[k] != INFINITY) {
+                if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = cr[k];
+                else T.overflow = 1;
+            }
+        }
+
+        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
+    } else if (!(ref & kLeafBit)) {
+        ++n_nodes;
+        const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
+        const float4 n1 = __ldg(&S.nodes[4 * ref + 1]);
+        const float4 n2 = __ldg(&S.nodes[4 * ref + 2]);
+        const float4 n3 = __ldg(&S.nodes[4 * ref + 3]);
+        const float tcap = T.t * 1.00000036f;
+        const V3 id = T.id, ood = T.ood;
+        float a0 = fmaf(n0.x, id.x, -ood.x), b0 = fmaf(n0.y, id.x, -ood.x);
+        float a1 = fmaf(n0.z, id.y, -ood.y), b1 = fmaf(n0.w, id.y, -ood.y);
+        float a2 = fmaf(n2.x, id.z, -ood.z), b2 = fmaf(n2.y, id.z, -ood.z);
+        const float tn0 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+        const float tf0 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+        a0 = fmaf(n1.x, id.x, -ood.x); b0 = fmaf(n1.y, id.x, -ood.x);
+        a1 = fmaf(n1.z, id.y, -ood.y); b1 = fmaf(n1.w, id.y, -ood.y);
+        a2 = fmaf(n2.z, id.z, -ood.z); b2 = fmaf(n2.w, id.z, -ood.z);
+        const float tn1 = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
+        const float tf1 = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+        const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+        const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = first0 ? c1 : c0;
+            else T.overflow = 1;
+            next = first0 ? c0 : c1;
+        } else if (h0) {
+            next = c0;
+        } else if (h1) {
+            next = c1;
+        } else {
+            next = T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef;
+        }
+    } else {
+        const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
+        bool found = false;
+        for (uint32_t i = first; i < first + cnt; ++i) {
+            ++n_tris;
+            float t;
+            const float4 a = __ldg(&S.tris[3 * i]), b = __ldg(&S.tris[3 * i + 1]), c = __ldg(&S.tris[3 * i + 2]);
+            if (hit_tri(T.o, T.d, a, b, c, T.t, t)) {
+                T.t = t;
+                T.tri = (int)i;
+                T.ta = a;
+                T.tb = b;
+                T.tc = c;
+                found = true;
+            }
+        }
+        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
+    }
+    T.ref = T.overflow ? kNoRef : next;
+    return T.ref == kNoRef;
+}
+
+// ---------------------------------------------------------------------------
+// path map u -> f(u): pinhole camera through (u0 W, u1 H); bounce b uses
+// dims 2+5b..6+5b = (light select, light u, light v, BSDF u, BSDF v);
+// emission on the camera ray's hit; NEE at every interaction (light triangle
+// in proportion to area, uniform point, one-sided emitters); Lambert cosine
+// or GGX half-vector sampling; no Russian roulette.  Written as a state
+// machine that asks for one ray at a time.
+// ---------------------------------------------------------------------------
+struct Path {
+    V3 o, d;
+    float tmax;
+    int any;          // 1: the pending ray is a shadow ray
+    V3 T, L, P;       // throughput, radiance, NEE contribution awaiting visibility
+    V3 x, ns, wo;     // interaction waiting for its BSDF continuation
+    int mat, b, done;
+};
+
+template <class Y>
+__device__ __forceinline__ void path_begin(Path& p, const DevScene& S, Y y)
+{
+    const float sx = (2.0f * u24(y[0]) - 1.0f) * S.tan_x;
+    const float sy = (1.0f - 2.0f * u24(y[1])) * S.tan_y;
+    const V3 fw = {S.cam_fwd[0], S.cam_fwd[1], S.cam_fwd[2]};
+    const V3 rt = {S.cam_right[0], S.cam_right[1], S.cam_right[2]};
+    const V3 up = {S.cam_up[0], S.cam_up[1], S.cam_up[2]};
+    p.o = {S.cam_pos[0], S.cam_pos[1], S.cam_pos[2]};
+    p.d = normalize(fw + rt * sx + up * sy);
+    p.tmax = 3.0e38f;
+    p.any = 0;
+    p.T = {1.f, 1.f, 1.f};
+    p.L = {0.f, 0.f, 0.f};
+    p.b = 0;
+    p.done = 0;
+}
+
+__device__ __forceinline__ float ggx_g1(float c, float a2)
+{
+    if (c <= 0.0f) return 0.0f;
+    return 2.0f * c / (c + sqrtf(a2 + (1.0f - a2) * c * c));
+}
+
+__device__ __forceinline__ void frame(V3 n, V3& t, V3& b)
+{
+    if (fabsf(n.z) < 0.9f) t = v3(-n.y, n.x, 0.0f);
+    else t = v3(0.0f, -n.z, n.y);
+    t = normalize(t);
+    b = cross(n, t);
+}
+
+__device__ __forceinline__ V3 bsdf_eval(float4 m0, float4 m1, V3 wo, V3 wi, V3 n)
+{
+    if (m0.w == 0.0f) {
+        const float k = 0.318309886183790672f;   // 1 / pi
+        return {m0.x * k, m0.y * k, m0.z * k};
+    }
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f) return {0.f, 0.f, 0.f};
+    const V3 h = normalize(wo + wi);
+    const float ch = dot(n, h), a2 = m1.w * m1.w;
+    const float den = 1.0f + (a2 - 1.0f) * ch * ch;
+    const float D = a2 / (3.14159265358979f * den * den);
+    const float G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+    const float x = 1.0f - dot(wi, h), x2 = x * x, c5 = x2 * x2 * x;
+    const float s = D * G / (4.0f * co * ci);
+    return {(m0.x + (1.0f - m0.x) * c5) * s, (m0.y + (1.0f - m0.y) * c5) * s, (m0.z + (1.0f - m0.z) * c5) * s};
+}
+
+// after NEE at interaction b: sample the BSDF to continue, or finish
+template <class Y>
+__device__ __forceinline__ void path_continue(Path& p, const DevScene& S, Y y, int max_depth)
+{
+    if (p.b == max_depth - 1) { p.done = 1; return; }
+    const float bu = u24(y[5 + 5 * p.b]), bv = u24(y[6 + 5 * p.b]);
+    const float4 m0 = __ldg(&S.mats[3 * p.mat]), m1 = __ldg(&S.mats[3 * p.mat + 1]);
+    V3 ft, fb;
+    frame(p.ns, ft, fb);
+    float sp, cp;
+    sincospif(2.0f * bv, &sp, &cp);
+    V3 wi;
+    if (m0.w == 0.0f) {
+        const float r = sqrtf(bu);
+        wi = ft * (r * cp) + fb * (r * sp) + p.ns * sqrtf(fmaxf(0.0f, 1.0f - bu));
+        p.T = {p.T.x * m0.x, p.T.y * m0.y, p.T.z * m0.z};
+    } else {
+        const float a2 = m1.w * m1.w;
+        const float tan2 = a2 * bu / (1.0f - bu);
+        const float cm = 1.0f / sqrtf(1.0f + tan2);
+        const float sm = sqrtf(fmaxf(0.0f, 1.0f - cm * cm));
+        const V3 mv = ft * (sm * cp) + fb * (sm * sp) + p.ns * cm;
+        const float dom = dot(p.wo, mv);
+        if (dom <= 0.0f) { p.done = 1; return; }
+        wi = mv * (2.0f * dom) - p.wo;
+        const float ci = dot(wi, p.ns), co = dot(p.wo, p.ns);
+        if (ci <= 0.0f) { p.done = 1; return; }
+        const float G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+        const float x = 1.0f - dom, x2 = x * x, c5 = x2 * x2 * x;
+        const float s = G * dom / (co * cm);
+        p.T = {p.T.x * (m0.x + (1.0f - m0.x) * c5) * s, p.T.y * (m0.y + (1.0f - m0.y) * c5) * s,
+               p.T.z * (m0.z + (1.0f - m0.z) * c5) * s};
+    }
+    p.o = p.x + p.ns * S.eps;
+    p.d = wi;
+    p.tmax = 3.0e38f;
+    p.any = 0;
+    p.b += 1;
+}
+
+template <bool BRUTE>
+__device__ __forceinline__ float4 tri_load(const DevScene& S, const float4* s_tris, int i, int j)
+{
+    return BRUTE ? s_tris[3 * i + j] : __ldg(&S.tris[3 * i + j]);
+}
+
+// Interaction at the closest hit h of the pending camera / extension ray:
+// emission seen by the camera ray, then the interaction kept for the
+// next-event sample and the BSDF continuation; false when the path ends here
+// (an emitter that absorbs).
+template <bool BRUTE>
+__device__ __forceinline__ bool shade_hit(Path& p, const DevScene& S, const Hit& h)
+{
+    const float4 ta = h.a, tb = h.b, tc = h.c;
+    const V3 n = normalize(cross(xyz(tb), xyz(tc)));
+    const int mat = __float_as_int(ta.w);
+    const V3 x = p.o + p.d * h.t;
+    const float cosi = -dot(n, p.d);
+    const V3 ns = cosi > 0.0f ? n : n * -1.0f;
+    const float4 m1 = __ldg(&S.mats[3 * mat + 1]), m2 = __ldg(&S.mats[3 * mat + 2]);
+    if (p.b == 0 && m2.x != 0.0f && cosi > 0.0f) p.L = p.L + v3(p.T.x * m1.x, p.T.y * m1.y, p.T.z * m1.z);
+    if (m2.y != 0.0f) return false;
+    p.x = x;
+    p.ns = ns;
+    p.wo = p.d * -1.0f;
+    p.mat = mat;
+    return true;
+}
+
+// Next-event sample at the interaction (light triangle in proportion to
+// area, uniform point): on a usable sample, P holds the unoccluded
+// contribution and (o, d, tmax) the shadow ray; false when there is none.
+template <bool BRUTE, class Y>
+__device__ __forceinline__ bool nee_sample(Path& p, const DevScene& S, const float4* s_tris, Y y)
+{
+    if (S.n_lights <= 0) return false;
+    const V3 x = p.x, ns = p.ns;
+    const float ls = u24(y[2 + 5 * p.b]), lu = u24(y[3 + 5 * p.b]), lv = u24(y[4 + 5 * p.b]);
+    int lo = 0, hi = S.n_lights - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&S.light_cdf[mid]) > ls) hi = mid; else lo = mid + 1;
+    }
+    const int lt = __ldg(&S.light_tri[lo]);
+    const float4 la = tri_load<BRUTE>(S, s_tris, lt, 0), lb = tri_load<BRUTE>(S, s_tris, lt, 1),
+                 lc = tri_load<BRUTE>(S, s_tris, lt, 2);
+    const float su = sqrtf(lu), b1 = su * (1.0f - lv), b2 = su * lv;
+    const V3 pl = xyz(la) + xyz(lb) * b1 + xyz(lc) * b2;
+    V3 wi = pl - x;
+    const float dist2 = dot(wi, wi), dist = sqrtf(dist2);
+    wi = wi * (1.0f / dist);
+    const V3 ln = normalize(cross(xyz(lb), xyz(lc)));
+    const float cx = dot(ns, wi), cl = -dot(ln, wi);
+    if (!(cx > 0.0f && cl > 0.0f)) return false;
+    const V3 xo = x + ns * S.eps;
+    V3 sd = pl - xo;
+    const float sdist = sqrtf(dot(sd, sd));
+    if (!(sdist > 2.0f * S.eps)) return false;
+    const float4 m0 = __ldg(&S.mats[3 * p.mat]), m1 = __ldg(&S.mats[3 * p.mat + 1]);
+    const V3 fr = bsdf_eval(m0, m1, p.wo, wi, ns);
+    const float4 lm1 = __ldg(&S.mats[3 * __float_as_int(la.w) + 1]);
+    const float g = cx * cl / dist2 * S.light_area;
+    p.P = {p.T.x * fr.x * lm1.x * g, p.T.y * fr.y * lm1.y * g, p.T.z * fr.z * lm1.z * g};
+    p.o = xo;
+    p.d = sd * (1.0f / sdist);
+    p.tmax = sdist - S.eps;
+    return true;
+}
+
+// consume the result of the pending ray (one ray at a time: the shadow ray
+// of bounce b is resolved before its BSDF continuation is drawn)
+template <bool BRUTE, class Y>
+__device__ __forceinline__ void path_on_hit(Path& p, const DevScene& S, const float4* s_tris, Y y,
+                                            int max_depth, Hit h)
+{
+    if (p.any) {
+        if (h.tri < 0) p.L = p.L + p.P;
+        p.any = 0;
+        path_continue(p, S, y, max_depth);
+        return;
+    }
+    if (h.tri < 0) { p.done = 1; return; }
+    if (!shade_hit<BRUTE>(p, S, h)) { p.done = 1; return; }
+    if (nee_sample<BRUTE>(p, S, s_tris, y)) {
+        p.any = 1;
+        return;
+    }
+    path_continue(p, S, y, max_depth);
+}
+
+__device__ __forceinline__ float toy_eval(const DevScene& S, uint32_t q0, uint32_t q1)
+{
+    const float u0 = u24(q0), u1 = u24(q1);
+    float f = S.toy_p[0];
+    if (u0 >= S.toy_p[2] && u0 < S.toy_p[3] && u1 >= S.toy_p[4] && u1 < S.toy_p[5]) f += S.toy_p[1];
+    const float dx = u0 - S.toy_p[7], dy = u1 - S.toy_p[8];
+    f += S.toy_p[6] * expf(-(dx * dx + dy * dy) / (2.0f * S.toy_p[9] * S.toy_p[9]));
+    return f;
+}
+
+__device__ __forceinline__ void stage_triangles(const DevScene& S, float4* s_tris)
+{
+    for (int i = threadIdx.x; i < 3 * S.n_tris; i += blockDim.x) s_tris[i] = __ldg(&S.tris[i]);
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// the chain step: E mutations per chain (Alg. 1 lines 8-19)
+// ---------------------------------------------------------------------------
+struct ChainLane {
+    // cached current state x
+    int kx, px, py;
+    float pix;
+    V3 fx;
+    // visits, splats and statistics of x not yet flushed
+    unsigned pend_n;
+    unsigned long long pend_i, pend_A;
+    // the mutation in flight
+    int j, large, ky, early;
+    float xi;
+    V3 fy;
+};
+
+// Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1 line
+// 10) and decide the reverse-kernel support; returns false when the proposal
+// needs no path (rejected early, or the toy integrand evaluated directly).
+template <class Y>
+__device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChains& Ch, int c, uint64_t mut0,
+                                               ChainLane& L, Y y, Path& p)
+{
+    const int C = Ch.C, D = Ch.D;
+    const uint64_t mut = mut0 + (uint64_t)L.j;
+    const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
+    const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+    L.large = (r0.x >> 8) < Ch.T_large;
+    L.xi = u24(r0.y);
+    int R = 1;
+    if (L.large) {
+        for (int jj = 0; 4 * jj < D; ++jj) {
+            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            y[4 * jj] = r.x;
+            if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
+            if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
+            if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
+        }
+        L.ky = region_of(Ch, y[0], y[1]);
+    } else {
+        // every dimension perturbed with sigma of the current state's region;
+        // the current state's words are fetched first with independent loads
+#pragma unroll 4
+        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
+        const float sx = Ch.sig[L.kx];
+        const float sigS2 = __fmul_rn(sx, Ch.S2);
+        float lo = 0.f, hi = 0.f;
+        bool check = false;
+        for (int jj = 0; 2 * jj < D; ++jj) {
+            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            const int d0 = 2 * jj;
+            const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
+            y[d0] = (r.y >> 31) ? y[d0] - o0 : y[d0] + o0;
+            uint32_t o1 = 0;
+            if (d0 + 1 < D) {
+                o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
+                y[d0 + 1] = (r.w >> 31) ? y[d0 + 1] - o1 : y[d0 + 1] + o1;
+            }
+            if (jj == 0) {
+                L.ky = region_of(Ch, y[0], y[1]);
+                const float sy = Ch.sig[L.ky];
+                if (sy != sx) {
+                    // reverse kernel T_{k(y)}(x|y): every offset inside [sigma_y s1, sigma_y s2]
+                    check = true;
+                    lo = __fmul_rn(sy, Ch.S1);
+                    hi = __fmul_rn(sy, Ch.S2);
+                }
+            }
+            if (check) {
+                const float m0 = __uint2float_rn(o0);
+                if (!(m0 >= lo && m0 <= hi)) R = 0;
+                if (d0 + 1 < D) {
+                    const float m1 = __uint2float_rn(o1);
+                    if (!(m1 >= lo && m1 <= hi)) R = 0;
+                }
+            }
+        }
+    }
+    L.early = !R;
+    L.fy = {0.f, 0.f, 0.f};
+    if (!R) return false;
+    if (S.toy) {
+        const float v = toy_eval(S, y[0], y[1]);
+        L.fy = {v, v, v};
+        return false;
+    }
+    if (L.large && Ch.lf) {
+        // independent of the chain's state: traced ahead of the epoch
+        const size_t o = (size_t)L.j * C + c;
+        L.fy = {Ch.lf[o], Ch.lf[(size_t)Ch.E * C + o], Ch.lf[(size_t)2 * Ch.E * C + o]};
+        return false;
+    }
+    path_begin(p, S, y);
+    return true;
+}
+
+__device__ __forceinline__ void flush_state(const DevChains& Ch, ChainLane& L)
+{
+    if (L.pend_n) {
+        atomicAdd(&Ch.hist[L.kx], (unsigned long long)L.pend_n);
+        if (L.pix > 0.0f) {
+            double* dst = Ch.img + 3 * ((size_t)L.py * Ch.W + L.px);
+            const double s = (double)L.pend_n / (double)L.pix;
+            atomicAdd(dst + 0, s * L.fx.x);
+            atomicAdd(dst + 1, s * L.fx.y);
+            atomicAdd(dst + 2, s * L.fx.z);
+        }
+    }
+    if (L.pend_i) {
+        atomicAdd(&Ch.vis[L.kx], L.pend_i);
+        atomicAdd(&Ch.acc[L.kx], L.pend_A);
+    }
+    L.pend_n = 0;
+    L.pend_i = L.pend_A = 0;
+}
+
+// acceptance (Sec. 3.2 with the mixture of Sec. 5.2), adaptation statistics
+// of the current region (Alg. 1 lines 11-12), MH update (line 19), splat
+template <bool TRACE, class Y>
+__device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool traced, ChainLane& L,
+                                                Y y, unsigned (&st)[7])
+{
+    const int C = Ch.C, D = Ch.D;
+    V3 fy = L.fy;
+    float piy = lum(fy.x, fy.y, fy.z);
+    int invalid = 0;
+    if (!isfinite(piy)) {
+        fy = {0.f, 0.f, 0.f};
+        piy = 0.f;
+        invalid = 1;
+        ++st[4];
+    }
+    float a;
+    if (L.early) {
+        a = 0.0f;
+    } else {
+        const float ptx = Ch.weighted ? L.pix / Ch.wf[L.kx] : L.pix;
+        const float pty = Ch.weighted ? piy / Ch.wf[L.ky] : piy;
+        a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
+    }
+    const int accept = L.xi < a;
+    if (L.large) {
+        ++st[1];
+        if (!Ch.lf) atomicAdd(&Ch.Bk[L.ky], (double)piy);   // else added by the large-step kernel
+    } else {
+        ++st[2];
+        L.pend_i += 1;
+        L.pend_A += (unsigned long long)__float2ull_rn(a * 4294967296.0f);
+    }
+    st[3] += L.early;
+    if (TRACE && traced) {
+        const unsigned long long idx = Ch.trace_base + (unsigned long long)(c / Ch.trace_stride) * Ch.E + L.j;
+        if (idx < Ch.trace_cap) {
+            uint32_t hsh = 2166136261u;
+            for (int d = 0; d < D; ++d) hsh = (hsh ^ y[d]) * 16777619u;
+            rmlt_trace_record r;
+            r.f[0] = fy.x;
+            r.f[1] = fy.y;
+            r.f[2] = fy.z;
+            r.a = a;
+            r.qhash = hsh;
+            r.flags = (uint32_t)accept | ((uint32_t)L.large << 1) | ((uint32_t)L.early << 2) | ((uint32_t)invalid << 3);
+            Ch.trace[idx] = r;
+        }
+    }
+    if (accept) {
+        flush_state(Ch, L);      // visits, splats and statistics of the state being left
+        // eight loads before their stores, so that the copy does not wait on
+        // one load at a time when y lives in global memory
+        for (int d0 = 0; d0 < D; d0 += 8) {
+            uint32_t t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t[k] = d0 + k < D ? y[d0 + k] : 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (d0 + k < D) Ch.q[(size_t)(d0 + k) * C + c] = t[k];
+        }
+        L.fx = fy;
+        L.pix = piy;
+        L.kx = L.ky;
+        L.px = pixel_x(y[0], Ch.W);
+        L.py = pixel_x(y[1], Ch.H);
+        ++st[0];
+    }
+    L.pend_n += 1;
+}
+
+}  // namespace
+}  // namespace rmlt

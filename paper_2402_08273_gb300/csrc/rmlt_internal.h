@@ -26,6 +26,8 @@ enum StatSlot {
     // warp cycle counters (work-counter builds only): traversal steps, shade
     // batches, finish/setup batches, warp lifetime (sum and max)
     kStCycTrav, kStCycShade, kStCycSetup, kStCycLife, kStCycLifeMax,
+    // wavefront form: waves run, epochs stopped by the wave limit
+    kStWaves, kStWaveLimit,
     kStCount = 32
 };
 
@@ -100,6 +102,50 @@ struct DevChains {
     unsigned long long trace_cap = 0, trace_base = 0;
     uint32_t trace_stride = 1;
 };
+
+// Wavefront form of the chain epoch (rmlt_wavefront.cu).  Per chain, a
+// column of kWfSlots 32-bit words holds the mutation in flight, the path
+// state between waves and the ray results; the proposal y lives in [D][C].
+// A wave is three kernels: shade (consume the ray results of the chains with
+// rays in flight, emit the next rays), finish / set up (the chains whose path
+// ended: accept or reject, the next proposal, its camera ray), and trace (a
+// persistent kernel that pulls rays from the queue).  A CUDA graph repeats
+// the wave under a device-side while condition until no chain has a ray.
+enum WfSlot {
+    kWKx = 0, kWPx, kWPy, kWPix, kWFx, kWPendN = kWFx + 3, kWPendI, kWPendA, kWJ = kWPendA + 2, kWFlags, kWKy,
+    kWXi, kWFy, kWT = kWFy + 3, kWL = kWT + 3, kWP = kWL + 3, kWB = kWP + 3, kWO, kWD = kWO + 3,
+    kWPfl = kWD + 3, kWSt, kWPhase = kWSt + 7, kWHitT, kWHitTri, kWShd, kWfSlots
+};
+
+struct WfCounters {
+    unsigned wave, ticket, fq_count, err;
+    unsigned cnt[2], fetch[2];      // rays appended / pulled, per queue
+    unsigned trace_n, trace_buf;    // the queue the next trace pass reads
+    unsigned long long mut0, trace_base;
+};
+
+struct DevWave {
+    uint32_t* s = nullptr;        // [kWfSlots][C]
+    uint32_t* y = nullptr;        // [D][C]
+    float4* rq[2] = {nullptr, nullptr};   // two queues of 2C rays, 2 float4 each
+    uint32_t* fq = nullptr;       // [C] chains to finish / set up
+    WfCounters* ctr = nullptr;
+    unsigned long long cond = 0;  // cudaGraphConditionalHandle of the wave loop
+    unsigned wave_cap = 0;        // E (max_depth + 1) + 2: more waves than any epoch needs
+    int refill = 16;              // idle lanes of a trace warp that pull new rays together
+};
+
+// device bytes of the wavefront state for C chains of D dimensions
+size_t wf_bytes(int C, int D);
+// carve the state out of one allocation of wf_bytes(C, D)
+void wf_carve(void* base, int C, int D, DevWave& w);
+
+struct WfGraph;   // the instantiated wave loop, rebuilt when its launch parameters change
+void wf_graph_destroy(WfGraph* g);
+// One epoch of E mutations per chain in the wavefront form.
+cudaError_t wf_epoch(WfGraph** g, const DevScene& s, const DevChains& c, DevWave& w, uint64_t mut0,
+                     unsigned long long trace_base, bool trace, bool count_work, int trace_ctas_per_sm,
+                     int setup_ctas_per_sm, bool host_loop, cudaStream_t st);
 
 // Scratch of the bootstrap (n = K C samples, K = n_bootstrap / C per chain).
 struct BootScratch {

@@ -1,0 +1,678 @@
+// Wavefront form of the chain epoch (sm_103a).
+//
+// The chain kernel of rmlt_kernels.cu keeps one chain per thread for a whole
+// epoch.  Its warps lose lanes to divergence (lanes at different phases and
+// traversal lengths), and a few tens of thousands of chains leave each SM too
+// few warps to hide the latency of node fetches.  Here the epoch advances in
+// waves, each made of three kernels over compacted work lists:
+//
+//   shade   one thread per chain with rays in flight: the shadow ray of bounce
+//           b-1 and the extension ray of bounce b were traced together; add
+//           the next-event contribution if unoccluded, shade the hit
+//           (emission, next-event sample, BSDF sample) and queue the next
+//           shadow and extension rays, or hand the chain to `setup` when its
+//           path has ended;
+//   setup   persistent, over the chains whose path ended (all chains in the
+//           first wave): accept or reject (Sec. 3.2, Alg. 1 lines 11-12, 19),
+//           then draw the next proposal (Alg. 1 line 10) and queue its camera
+//           ray; proposals that need no path finish at once;
+//   trace   persistent, one ray per lane: lanes whose ray is resolved pull
+//           new rays from the queue together, so warps stay full until the
+//           queue runs dry.
+//
+// A chain's shadow ray of bounce b and its extension ray of bounce b + 1 do
+// not depend on each other, so they are traced in the same wave; the
+// arithmetic of every path is that of the chain kernel (same functions, same
+// order of additions into the radiance), so both forms give identical
+// trajectories.  The wave loop is a CUDA graph with a while node whose
+// condition the last `setup` block sets from the number of rays queued.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "rmlt_device.cuh"
+
+namespace rmlt {
+namespace {
+
+enum WfPhase : uint32_t { kWfIdle = 0, kWfStart = 1, kWfRays = 2, kWfFinish = 3 };
+constexpr uint32_t kAnyBit = 0x80000000u;
+
+// word d of one chain's proposal in the [D][C] array
+struct YCol {
+    uint32_t* p;
+    int C;
+    __device__ __forceinline__ uint32_t& operator[](int d) const { return p[(size_t)d * C]; }
+};
+
+struct Slots {
+    uint32_t* s;
+    int C, c;
+    __device__ __forceinline__ uint32_t& operator[](int k) const { return s[(size_t)k * C + c]; }
+    __device__ __forceinline__ float f(int k) const { return __uint_as_float((*this)[k]); }
+    __device__ __forceinline__ void setf(int k, float v) const { (*this)[k] = __float_as_uint(v); }
+    __device__ __forceinline__ V3 v(int k) const { return {f(k), f(k + 1), f(k + 2)}; }
+    __device__ __forceinline__ void setv(int k, V3 v) const
+    {
+        setf(k, v.x);
+        setf(k + 1, v.y);
+        setf(k + 2, v.z);
+    }
+};
+
+__device__ __forceinline__ void load_lane(const Slots& s, ChainLane& L)
+{
+    L.kx = (int)s[kWKx];
+    L.px = (int)s[kWPx];
+    L.py = (int)s[kWPy];
+    L.pix = s.f(kWPix);
+    L.fx = s.v(kWFx);
+    L.pend_n = s[kWPendN];
+    L.pend_i = s[kWPendI];
+    L.pend_A = (unsigned long long)s[kWPendA] | ((unsigned long long)s[kWPendA + 1] << 32);
+    L.j = (int)s[kWJ];
+    const uint32_t fl = s[kWFlags];
+    L.large = (int)(fl & 1u);
+    L.early = (int)((fl >> 1) & 1u);
+    L.ky = (int)s[kWKy];
+    L.xi = s.f(kWXi);
+    L.fy = s.v(kWFy);
+}
+
+__device__ __forceinline__ void store_lane(const Slots& s, const ChainLane& L)
+{
+    s[kWKx] = (uint32_t)L.kx;
+    s[kWPx] = (uint32_t)L.px;
+    s[kWPy] = (uint32_t)L.py;
+    s.setf(kWPix, L.pix);
+    s.setv(kWFx, L.fx);
+    s[kWPendN] = L.pend_n;
+    s[kWPendI] = (uint32_t)L.pend_i;
+    s[kWPendA] = (uint32_t)L.pend_A;
+    s[kWPendA + 1] = (uint32_t)(L.pend_A >> 32);
+    s[kWJ] = (uint32_t)L.j;
+    s[kWFlags] = (uint32_t)L.large | ((uint32_t)L.early << 1);
+    s[kWKy] = (uint32_t)L.ky;
+    s.setf(kWXi, L.xi);
+    s.setv(kWFy, L.fy);
+}
+
+// Append n (0..2) rays per lane, 2 float4 each, to queue `buf`; every lane of
+// the warp calls it.  Lanes take consecutive slots, so the stores coalesce.
+__device__ __forceinline__ void append_rays(const DevWave& W, int C, unsigned buf, int n, const float4 (&r)[4])
+{
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(&W.ctr->cnt[buf], (unsigned)total);
+    base = __shfl_sync(FULL, base, 31);
+    const unsigned at = base + (unsigned)(incl - n), cap = 2u * (unsigned)C;
+    float4* q = W.rq[buf];
+    for (int i = 0; i < n; ++i) {
+        if (at + i < cap) {
+            q[2 * (size_t)(at + i)] = r[2 * i];
+            q[2 * (size_t)(at + i) + 1] = r[2 * i + 1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epoch start: chain state into the per-chain columns, every chain listed for
+// its first proposal, counters reset
+// ---------------------------------------------------------------------------
+__global__ void wf_begin_kernel(const DevChains Ch, const DevWave W, unsigned long long mut0,
+                                unsigned long long trace_base)
+{
+    const int C = Ch.C;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) {
+        WfCounters* k = W.ctr;
+        k->wave = k->ticket = k->err = 0u;
+        k->fq_count = Ch.E > 0 ? (unsigned)C : 0u;
+        k->cnt[0] = k->cnt[1] = k->fetch[0] = k->fetch[1] = 0u;
+        k->trace_n = k->trace_buf = 0u;
+        k->mut0 = mut0;
+        k->trace_base = trace_base;
+    }
+    if (c >= C) return;
+    const Slots s{W.s, C, c};
+    s[kWKx] = (uint32_t)Ch.k[c];
+    s[kWPx] = (uint32_t)pixel_x(Ch.q[c], Ch.W);
+    s[kWPy] = (uint32_t)pixel_x(Ch.q[(size_t)C + c], Ch.H);
+    s.setf(kWPix, Ch.pi[c]);
+    s.setv(kWFx, {Ch.f[c], Ch.f[(size_t)C + c], Ch.f[2 * (size_t)C + c]});
+    s[kWPendN] = s[kWPendI] = s[kWPendA] = s[kWPendA + 1] = 0u;
+    s[kWJ] = 0u;
+    for (int k = 0; k < 7; ++k) s[kWSt + k] = 0u;
+    s[kWPhase] = Ch.E > 0 ? kWfStart : kWfIdle;
+    W.fq[c] = (uint32_t)c;
+}
+
+// ---------------------------------------------------------------------------
+// shade: consume the rays traced in the previous wave
+// ---------------------------------------------------------------------------
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S, const DevChains Ch, const DevWave W)
+{
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int C = Ch.C;
+    WfCounters* ctr = W.ctr;
+    const unsigned wv = ctr->wave, buf = wv & 1u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->cnt[buf ^ 1u] = 0u;   // the queue the previous trace pass read
+        ctr->fetch[buf] = 0u;      // the pull counter of this wave's trace pass
+    }
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int nr = 0, fin = 0;
+    float4 r[4];
+    if (c < C) {
+        const Slots s{W.s, C, c};
+        if (s[kWPhase] == kWfRays) {
+            Path p;
+            p.T = s.v(kWT);
+            p.L = s.v(kWL);
+            p.P = s.v(kWP);
+            p.b = (int)s[kWB];
+            p.o = s.v(kWO);
+            p.d = s.v(kWD);
+            p.any = 0;
+            p.done = 0;
+            const uint32_t pfl = s[kWPfl];
+            unsigned rays = 0;
+            bool dropped = false;
+            if (pfl & 2u) {
+                ++rays;
+                const uint32_t res = s[kWShd];
+                if (res == 2u) dropped = true;
+                else if (res == 0u) p.L = p.L + p.P;
+            }
+            int emit = 0;
+            float4 sh0, sh1;
+            if (pfl & 1u) {
+                ++rays;
+                const int tri = (int)s[kWHitTri];
+                if (tri == -2) {
+                    dropped = true;
+                } else if (!dropped && tri >= 0) {
+                    Hit h;
+                    h.t = s.f(kWHitT);
+                    h.tri = tri;
+                    h.a = __ldg(&S.tris[3 * (size_t)tri]);
+                    h.b = __ldg(&S.tris[3 * (size_t)tri + 1]);
+                    h.c = __ldg(&S.tris[3 * (size_t)tri + 2]);
+                    if (shade_hit<BRUTE>(p, S, h)) {
+                        const YCol y{W.y + c, C};
+                        if (nee_sample<false>(p, S, nullptr, y)) {
+                            sh0 = make_float4(p.o.x, p.o.y, p.o.z, p.tmax);
+                            sh1 = make_float4(p.d.x, p.d.y, p.d.z, __uint_as_float((uint32_t)c | kAnyBit));
+                            emit |= 2;
+                        }
+                        path_continue(p, S, y, Ch.max_depth);
+                        if (!p.done) emit |= 1;
+                    }
+                }
+            }
+            if (dropped) {   // a traversal stack overflowed: the path contributes nothing
+                p.L = {0.f, 0.f, 0.f};
+                emit = 0;
+                s[kWSt + 6] += 1u;
+            }
+            s[kWSt + 5] += rays;
+            if (emit) {
+                s.setv(kWT, p.T);
+                s.setv(kWL, p.L);
+                s[kWPfl] = (uint32_t)emit;
+                if (emit & 1) {
+                    s[kWB] = (uint32_t)p.b;
+                    s.setv(kWO, p.o);
+                    s.setv(kWD, p.d);
+                    r[0] = make_float4(p.o.x, p.o.y, p.o.z, p.tmax);
+                    r[1] = make_float4(p.d.x, p.d.y, p.d.z, __uint_as_float((uint32_t)c));
+                    nr = 1;
+                }
+                if (emit & 2) {
+                    s.setv(kWP, p.P);
+                    r[2 * nr] = sh0;
+                    r[2 * nr + 1] = sh1;
+                    ++nr;
+                }
+            } else {
+                s.setv(kWFy, p.L);
+                s[kWPhase] = kWfFinish;
+                fin = 1;
+            }
+        }
+    }
+    append_rays(W, C, buf, nr, r);
+    const unsigned m = __ballot_sync(FULL, fin);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(&ctr->fq_count, (unsigned)__popc(m));
+        base = __shfl_sync(FULL, base, __ffs(m) - 1);
+        if (fin) W.fq[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// setup: finish the mutations whose path ended, draw the next proposals
+// ---------------------------------------------------------------------------
+template <bool TRACE>
+__global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S, DevChains Ch, const DevWave W)
+{
+    const int C = Ch.C;
+    WfCounters* ctr = W.ctr;
+    const unsigned wv = ctr->wave, buf = wv & 1u, n = ctr->fq_count;
+    const uint64_t mut0 = ctr->mut0;
+    if (TRACE) Ch.trace_base = ctr->trace_base;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = 0; base < n; base += stride) {
+        const unsigned i = base + blockIdx.x * blockDim.x + threadIdx.x;
+        int nr = 0;
+        float4 r[4];
+        if (i < n) {
+            const int c = (int)W.fq[i];
+            const Slots s{W.s, C, c};
+            const YCol y{W.y + c, C};
+            const bool traced = TRACE && (uint32_t)c % Ch.trace_stride == 0u;
+            ChainLane L;
+            load_lane(s, L);
+            unsigned st[7];
+            for (int k = 0; k < 7; ++k) st[k] = s[kWSt + k];
+            Path p;
+            if (s[kWPhase] != kWfStart) {
+                mutation_finish<TRACE>(Ch, c, traced, L, y, st);
+                ++L.j;
+            }
+            // the proposal is drawn into a local array (the chain kernel's
+            // code path) and stored to [D][C] only when a path needs it
+            uint32_t yl[kMaxDim];
+            bool ray = false;
+            while (L.j < Ch.E) {
+                if (mutation_setup(S, Ch, c, mut0, L, yl, p)) {
+                    ray = true;
+                    break;
+                }
+                mutation_finish<TRACE>(Ch, c, traced, L, yl, st);
+                ++L.j;
+            }
+            if (ray) {
+                for (int d = 0; d < Ch.D; ++d) y[d] = yl[d];
+                s.setv(kWT, p.T);
+                s.setv(kWL, p.L);
+                s[kWB] = (uint32_t)p.b;
+                s.setv(kWO, p.o);
+                s.setv(kWD, p.d);
+                s[kWPfl] = 1u;
+                s[kWPhase] = kWfRays;
+                r[0] = make_float4(p.o.x, p.o.y, p.o.z, p.tmax);
+                r[1] = make_float4(p.d.x, p.d.y, p.d.z, __uint_as_float((uint32_t)c));
+                nr = 1;
+            } else {
+                // epoch done for this chain: flush and write the state back
+                flush_state(Ch, L);
+                Ch.k[c] = L.kx;
+                Ch.pi[c] = L.pix;
+                Ch.f[c] = L.fx.x;
+                Ch.f[(size_t)C + c] = L.fx.y;
+                Ch.f[2 * (size_t)C + c] = L.fx.z;
+                s[kWPhase] = kWfIdle;
+            }
+            store_lane(s, L);
+            for (int k = 0; k < 7; ++k) s[kWSt + k] = st[k];
+        }
+        append_rays(W, C, buf, nr, r);
+    }
+    // the last block to finish decides whether another wave runs
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&ctr->ticket, 1u);
+        if (t == gridDim.x - 1u) {
+            __threadfence();
+            const unsigned nq = atomicAdd(&ctr->cnt[buf], 0u);
+            ctr->trace_n = nq;
+            ctr->trace_buf = buf;
+            ctr->fq_count = 0u;
+            ctr->ticket = 0u;
+            ctr->wave = wv + 1u;
+            unsigned go = nq > 0u ? 1u : 0u;
+            if (go && wv + 1u >= W.wave_cap) {
+                ctr->err = 1u;
+                go = 0u;
+            }
+            if (W.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)W.cond, go);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// trace: persistent; one ray per lane, idle lanes pull rays together
+// ---------------------------------------------------------------------------
+template <bool BRUTE, bool COUNT>
+__global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S, const DevWave W, int C,
+                                                               unsigned long long* stats)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const unsigned FULL = 0xFFFFFFFFu;
+    const unsigned cap = 2u * (unsigned)C, n = min(W.ctr->trace_n, cap), buf = W.ctr->trace_buf;
+    const float4* q = W.rq[buf];
+    unsigned* pull = &W.ctr->fetch[buf];
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int refill = W.refill;
+    uint32_t* stack = s_stack + threadIdx.x;
+    unsigned nn = 0, nt = 0;
+    Trav T;
+    T.ref = kNoRef;
+    int c = -1;
+    bool dry = n == 0u;
+    while (true) {
+        const unsigned idle = __ballot_sync(FULL, c < 0);
+        if (!dry && __popc(idle) >= refill) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(pull, (unsigned)__popc(idle));
+            base = __shfl_sync(FULL, base, 0);
+            if (base + (unsigned)__popc(idle) >= n) dry = true;
+            if (c < 0) {
+                const unsigned at = base + (unsigned)__popc(idle & below);
+                if (at < n) {
+                    const float4 r0 = q[2 * (size_t)at], r1 = q[2 * (size_t)at + 1];
+                    const uint32_t tag = __float_as_uint(r1.w);
+                    c = (int)(tag & ~kAnyBit);
+                    trav_begin(T, v3(r0.x, r0.y, r0.z), v3(r1.x, r1.y, r1.z), r0.w, (tag & kAnyBit) ? 1 : 0);
+                }
+            }
+        }
+        if (dry && __all_sync(FULL, c < 0)) break;
+        if (c >= 0 && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+            if (T.any) {
+                W.s[(size_t)kWShd * C + c] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
+            } else {
+                W.s[(size_t)kWHitTri * C + c] = T.overflow ? (uint32_t)-2 : (uint32_t)T.tri;
+                W.s[(size_t)kWHitT * C + c] = __float_as_uint(T.t);
+            }
+            c = -1;
+        }
+    }
+    if (COUNT) {
+        const unsigned long long a = warp_sum(nn), b = warp_sum(nt);
+        if (lane == 0) {
+            if (a) atomicAdd(&stats[kStNodes], a);
+            if (b) atomicAdd(&stats[kStTris], b);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epoch end: per-chain counters into the statistics
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) wf_end_kernel(const DevChains Ch, const DevWave W)
+{
+    __shared__ unsigned long long part[8][7];
+    const int C = Ch.C;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (c < C) {
+        const Slots s{W.s, C, c};
+        for (int k = 0; k < 7; ++k) v[k] = s[kWSt + k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 7; ++k) {
+        const unsigned long long t = warp_sum(v[k]);
+        if (lane == 0) part[wid][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
+        if (t) atomicAdd(&Ch.stats[threadIdx.x], t);
+    }
+    if (c == 0) {
+        atomicAdd(&Ch.stats[kStWaves], (unsigned long long)W.ctr->wave);
+        if (W.ctr->err) atomicAdd(&Ch.stats[kStWaveLimit], 1ull);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t wf_bytes(int C, int D)
+{
+    const size_t c = (size_t)C;
+    return align256(sizeof(uint32_t) * kWfSlots * c) + align256(sizeof(uint32_t) * (size_t)D * c) +
+           2 * align256(sizeof(float4) * 4 * c) + align256(sizeof(uint32_t) * c) + align256(sizeof(WfCounters));
+}
+
+void wf_carve(void* base, int C, int D, DevWave& w)
+{
+    const size_t c = (size_t)C;
+    char* p = (char*)base;
+    w.s = (uint32_t*)p;
+    p += align256(sizeof(uint32_t) * kWfSlots * c);
+    w.y = (uint32_t*)p;
+    p += align256(sizeof(uint32_t) * (size_t)D * c);
+    for (int b = 0; b < 2; ++b) {
+        w.rq[b] = (float4*)p;
+        p += align256(sizeof(float4) * 4 * c);
+    }
+    w.fq = (uint32_t*)p;
+    p += align256(sizeof(uint32_t) * c);
+    w.ctr = (WfCounters*)p;
+}
+
+struct WfGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    std::vector<unsigned char> key;
+};
+
+void wf_graph_destroy(WfGraph* g)
+{
+    if (!g) return;
+    if (g->x) cudaGraphExecDestroy(g->x);
+    if (g->g) cudaGraphDestroy(g->g);
+    delete g;
+}
+
+namespace {
+
+template <class T>
+void put(std::vector<unsigned char>& k, const T& v)
+{
+    const unsigned char* b = (const unsigned char*)&v;
+    k.insert(k.end(), b, b + sizeof v);
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+template <bool B, bool T, bool K>
+cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevWave W, int trace_ctas,
+                        int setup_ctas)
+{
+    cudaError_t e;
+    if ((e = cudaGraphCreate(&G.g, 0)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, G.g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    W.cond = (unsigned long long)h;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, G.g, nullptr, nullptr, 0, &cp)) != cudaSuccess) return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
+    auto kt = wf_trace_kernel<B, K>;
+    if (tshm > 48 * 1024) {
+        if ((e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm)) != cudaSuccess)
+            return e;
+    }
+    DevScene s = S;
+    DevChains ch = Ch;
+    int C = Ch.C;
+    unsigned long long* stats = Ch.stats;
+    void* a_shade[] = {&s, &ch, &W};
+    void* a_setup[] = {&s, &ch, &W};
+    void* a_trace[] = {&s, &W, &C, &stats};
+    cudaKernelNodeParams k1{}, k2{}, k3{};
+    k1.func = (void*)wf_shade_kernel<B>;
+    k1.gridDim = dim3((unsigned)((C + kChainBlock - 1) / kChainBlock));
+    k1.blockDim = dim3(kChainBlock);
+    k1.kernelParams = a_shade;
+    k2.func = (void*)wf_setup_kernel<T>;
+    k2.gridDim = dim3((unsigned)setup_ctas);
+    k2.blockDim = dim3(kChainBlock);
+    k2.kernelParams = a_setup;
+    k3.func = (void*)kt;
+    k3.gridDim = dim3((unsigned)trace_ctas);
+    k3.blockDim = dim3(kChainBlock);
+    k3.sharedMemBytes = (unsigned)tshm;
+    k3.kernelParams = a_trace;
+    cudaGraphNode_t n1, n2, n3;
+    if ((e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1)) != cudaSuccess) return e;
+    if ((e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2)) != cudaSuccess) return e;
+    if ((e = cudaGraphAddKernelNode(&n3, body, &n2, 1, &k3)) != cudaSuccess) return e;
+    return cudaGraphInstantiate(&G.x, G.g, 0);
+}
+
+template <bool B, bool T, bool K>
+int trace_occupancy(const DevScene& S)
+{
+    const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
+    int n = 0;
+    if (tshm > 48 * 1024)
+        cudaFuncSetAttribute(wf_trace_kernel<B, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wf_trace_kernel<B, K>, kChainBlock, tshm);
+    return n > 0 ? n : 1;
+}
+
+template <bool T>
+int setup_occupancy()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wf_setup_kernel<T>, kChainBlock, 0);
+    return n > 0 ? n : 1;
+}
+
+// the waves of one epoch launched from the host: wave_cap waves, those after
+// the last chain finished find nothing to do
+template <bool B, bool T, bool K>
+cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int trace_ctas, int setup_ctas,
+                       cudaStream_t st)
+{
+    W.cond = 0;
+    const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
+    if (tshm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(wf_trace_kernel<B, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tshm);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned g1 = (unsigned)((Ch.C + kChainBlock - 1) / kChainBlock);
+    for (unsigned w = 0; w < W.wave_cap; ++w) {
+        wf_shade_kernel<B><<<g1, kChainBlock, 0, st>>>(S, Ch, W);
+        wf_setup_kernel<T><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
+        wf_trace_kernel<B, K><<<(unsigned)trace_ctas, kChainBlock, tshm, st>>>(S, W, Ch.C, Ch.stats);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <bool B, bool T, bool K>
+cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWave& W, uint64_t mut0,
+                    unsigned long long trace_base, int trace_cps, int setup_cps, bool host_loop, cudaStream_t st)
+{
+    const int sms = sm_count();
+    const int tocc = trace_occupancy<B, T, K>(S), socc = setup_occupancy<T>();
+    const int tc = sms * (trace_cps > 0 && trace_cps < tocc ? trace_cps : tocc);
+    const int max_setup = (Ch.C + kChainBlock - 1) / kChainBlock;
+    int sc = sms * (setup_cps > 0 && setup_cps < socc ? setup_cps : socc);
+    if (sc > max_setup) sc = max_setup;
+    if (sc < 1) sc = 1;
+    W.wave_cap = (unsigned)Ch.E * (unsigned)(Ch.max_depth + 1) + 2u;
+    // the graph's kernels hold these values; rebuild when any of them changes
+    std::vector<unsigned char> key;
+    DevChains kc = Ch;
+    kc.trace_base = 0;
+    DevWave kw = W;
+    kw.cond = 0;
+    const int flags = (B ? 1 : 0) | (T ? 2 : 0) | (K ? 4 : 0);
+    put(key, flags);
+    put(key, S);
+    put(key, kc);
+    put(key, kw);
+    put(key, tc);
+    put(key, sc);
+    if (host_loop) {
+        wf_begin_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W, mut0, trace_base);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = host_waves<B, T, K>(S, Ch, W, tc, sc, st);
+        if (e != cudaSuccess) return e;
+        wf_end_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W);
+        return cudaGetLastError();
+    }
+    WfGraph* g = *gp;
+    if (!g || g->key != key) {
+        wf_graph_destroy(g);
+        *gp = nullptr;
+        g = new WfGraph();
+        cudaError_t e = build_graph<B, T, K>(*g, S, Ch, W, tc, sc);
+        if (e != cudaSuccess) {
+            wf_graph_destroy(g);
+            return e;
+        }
+        g->key = key;
+        *gp = g;
+    }
+    wf_begin_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W, mut0, trace_base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGraphLaunch(g->x, st)) != cudaSuccess) return e;
+    wf_end_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t wf_epoch(WfGraph** g, const DevScene& s, const DevChains& c, DevWave& w, uint64_t mut0,
+                     unsigned long long trace_base, bool trace, bool count_work, int trace_ctas_per_sm,
+                     int setup_ctas_per_sm, bool host_loop, cudaStream_t st)
+{
+    if (w.refill < 1) w.refill = 1;
+    if (w.refill > 32) w.refill = 32;
+#define RMLT_WF(B, T, K) \
+    epoch_t<B, T, K>(g, s, c, w, mut0, trace_base, trace_ctas_per_sm, setup_ctas_per_sm, host_loop, st)
+    if (s.brute) {
+        if (trace) return count_work ? RMLT_WF(true, true, true) : RMLT_WF(true, true, false);
+        return count_work ? RMLT_WF(true, false, true) : RMLT_WF(true, false, false);
+    }
+    if (trace) return count_work ? RMLT_WF(false, true, true) : RMLT_WF(false, true, false);
+    return count_work ? RMLT_WF(false, false, true) : RMLT_WF(false, false, false);
+#undef RMLT_WF
+}
+
+}  // namespace rmlt

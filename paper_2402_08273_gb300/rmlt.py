@@ -65,7 +65,7 @@ class Stats(C.Structure):
                 ("rays", C.c_uint64), ("stack_overflow", C.c_uint64), ("epochs", C.c_uint64),
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
                 ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6),
-                ("cycles", C.c_uint64 * 5)]
+                ("cycles", C.c_uint64 * 5), ("waves", C.c_uint64), ("wave_limit_hits", C.c_uint64)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -99,6 +99,7 @@ _SIGS = [
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    ("rmlt_set_wavefront", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     ("rmlt_bootstrap_noalloc", C.c_int, [C.c_void_p, _P(ChainParams), C.c_void_p, C.c_void_p,
                                          C.c_void_p]),
     ("rmlt_save", C.c_int, [C.c_void_p, C.c_char_p]),
@@ -317,9 +318,14 @@ class Renderer:
         return d
 
     def set_tuning(self, batch_shade: int = 8, batch_setup: int = 8, large_ahead: bool = False,
-                   adaptive_batch: bool = False):
-        flags = (1 if large_ahead else 0) | (2 if adaptive_batch else 0)
+                   adaptive_batch: bool = False, wavefront: bool = False):
+        flags = (1 if large_ahead else 0) | (2 if adaptive_batch else 0) | (4 if wavefront else 0)
         _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup), flags))
+
+    def set_wavefront(self, trace_ctas_per_sm: int = 0, setup_ctas_per_sm: int = 0, refill_lanes: int = 16,
+                      host_loop: bool = False):
+        _check(lib().rmlt_set_wavefront(self.h, int(trace_ctas_per_sm), int(setup_ctas_per_sm),
+                                        int(refill_lanes), 1 if host_loop else 0))
 
     def set_work_counters(self, enable: bool):
         _check(lib().rmlt_set_work_counters(self.h, int(enable)))

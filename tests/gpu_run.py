@@ -6,15 +6,22 @@ import numpy as np
 from paper_2402_08273_gb300 import rmlt
 
 
-def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bvh_width=0, **params):
+def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bvh_width=0, tuning=None,
+               wavefront=None, **params):
     """Initialise, trace `n_epochs` epochs of every `stride`-th chain, and
-    return the trace together with the initial and final state."""
+    return the trace together with the initial and final state.  `tuning`
+    (keyword arguments of Renderer.set_tuning) and `wavefront` (of
+    Renderer.set_wavefront) select the execution form."""
     import torch
     R = rmlt.Renderer()
     if toy is not None:
         R.load_toy_integrand(toy)
     else:
         R.load_scene(scene, brute_force_max=brute_force_max, bvh_width=bvh_width)
+    if tuning:
+        R.set_tuning(**tuning)
+    if wavefront:
+        R.set_wavefront(**wavefront)
     R.init_chains(**params)
     p = R.params
     init = R.read_chain_state()
