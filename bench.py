@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+from ctypes import byref, c_double as C_double, c_void_p as C_void_p
 import math
 import os
 import statistics
@@ -237,8 +238,6 @@ def run_ours(args, w):
     M = w["mutations"]
     stream = torch.cuda.Stream(device=dev)
     R = rmlt.Renderer(device=local, stream=stream)
-    if args.form == "wavefront":
-        R.set_tuning(wavefront=True)
     t0 = time.perf_counter()
     R.load_scene(scene)
     t_load = time.perf_counter() - t0
@@ -249,8 +248,24 @@ def run_ours(args, w):
     C = params["n_chains"]
     epochs_per_step = -(-M // params["epoch_len"])
 
+    # the traversal roofline's two ceilings, measured on this GPU
+    l2_gbs, fp32_tflops = C_double(), C_double()
+    rmlt._check(rmlt.lib().rmlt_probe_peaks(local, C_void_p(stream.cuda_stream), byref(l2_gbs), byref(fp32_tflops)))
+    l2_gbs, fp32_tflops = l2_gbs.value, fp32_tflops.value
+
     for _ in range(args.warmup):
         R.step(M)
+    R.synchronize()
+    # execution form: forced, or the fastest candidate timed on the live chains
+    from paper_2402_08273_gb300 import autotune
+    tuned = None
+    if args.form == "auto":
+        best, timings = autotune.autotune(R)
+        form = best["form"]
+        tuned = {"chosen": best, "ms_per_epoch": [[c, round(t, 3)] for c, t in timings]}
+    else:
+        form = args.form
+        autotune.apply(R, {"form": form})
     R.synchronize()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     st0 = R.read_stats()
@@ -307,21 +322,36 @@ def run_ours(args, w):
     flops_ray = nodes_per_ray * FLOPS_PER_NODE + tris_per_ray * FLOPS_PER_TRI
     bytes_ray = nodes_per_ray * BYTES_PER_NODE + tris_per_ray * BYTES_PER_TRI
     rays_per_s_gpu = rays / world / t_max   # per GPU, for the per-kernel roofline
-    clk_mhz = clk["sm_mhz"] or 1965.0
-    peak_tflops = SM_COUNT * FP32_LANES * 2 * clk_mhz * 1e6 / 1e12
-    achieved = flops_ray * rays_per_s_gpu / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": measured_traffic(args.workload),
-                "kernel": "chain_epoch_kernel",
-                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock "
-                               f"{clk_mhz:.0f} MHz sampled during the timed region",
+    # traversal roofline: rays/s_max = min(P_fp32 / flops_ray, BW_L2 / bytes_ray)
+    alu_max = fp32_tflops * 1e12 / flops_ray
+    l2_max = l2_gbs * 1e9 / bytes_ray
+    alu = {"achieved_tflops": flops_ray * rays_per_s_gpu / 1e12, "peak_tflops": fp32_tflops,
+           "rays_per_s_max": alu_max}
+    alu["frac"] = alu["achieved_tflops"] / fp32_tflops
+    l2 = {"achieved_gbs": bytes_ray * rays_per_s_gpu / 1e9, "peak_gbs": l2_gbs, "rays_per_s_max": l2_max}
+    l2["frac"] = l2["achieved_gbs"] / l2_gbs
+    if l2_max <= alu_max:
+        bound, achieved, peak, unit = "l2", l2["achieved_gbs"], l2_gbs, "GB/s"
+    else:
+        bound, achieved, peak, unit = "alu", alu["achieved_tflops"], fp32_tflops, "TFLOP/s"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": measured_traffic(args.workload) if form == "chain" else None,
+                "kernel": "chain_epoch_kernel" if form == "chain" else "wavefront waves (shade, setup, trace)",
+                "rays_per_s": rays_per_s_gpu, "rays_per_s_max": min(alu_max, l2_max),
+                "peak_source": "measured on this GPU by rmlt_probe_peaks before the timed region: L2 read "
+                               "bandwidth over a resident quarter-L2 buffer with L1-bypassing 16-byte loads, "
+                               "FP32 FMA rate with eight independent chains per thread",
+                "ceilings": {"l2": l2, "alu": alu,
+                             "alu_nominal_tflops": SM_COUNT * FP32_LANES * 2 * (clk["sm_mhz"] or 2070.0) / 1e6},
                 "per_ray": {"nodes": nodes_per_ray, "tris": tris_per_ray, "flops": flops_ray,
                             "bytes": bytes_ray}}
     try:
         peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
         hbm = float(peaks["hbm_gbs"])
-        roofline["node_fetch_gbs"] = bytes_ray * rays_per_s_gpu / 1e9
-        roofline["node_fetch_frac_of_measured_hbm"] = roofline["node_fetch_gbs"] / hbm
+        roofline["ceilings"]["hbm"] = {"achieved_gbs": l2["achieved_gbs"], "peak_gbs": hbm,
+                                       "frac": l2["achieved_gbs"] / hbm,
+                                       "note": "node and triangle bytes against the measured HBM copy rate; "
+                                               "the bench scenes' BVH fits in L2"}
     except Exception:
         pass
 
@@ -338,11 +368,12 @@ def run_ours(args, w):
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "chains_per_gpu": C,
                        "mutations_per_step": M, "epochs_per_step": epochs_per_step,
-                       "l2": "flushed between timed steps (256 MiB write)", "form": args.form,
+                       "l2": "flushed between timed steps (256 MiB write)", "form": form,
+                       "autotune": tuned,
                        "parallelism": f"{world} independent chain populations (one per GPU)"},
             "rays_per_s": rays / t_max,
             "rays_per_mutation": rays / mutations,
-            "gpu_launches": (2 * epochs_per_step * args.steps if args.form == "chain" else
+            "gpu_launches": (2 * epochs_per_step * args.steps if form == "chain" else
                              3 * epochs_per_step * args.steps + 3 * (st1["waves"] - st0["waves"])),
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -447,8 +478,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="two_rooms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", choices=("chain", "wavefront"), default="chain",
-                    help="epoch execution form: one thread per chain, or waves of shade / setup / trace")
+    ap.add_argument("--form", choices=("auto", "chain", "wavefront"), default="auto",
+                    help="epoch execution form: one thread per chain, waves of shade / setup / trace, "
+                         "or the faster of the autotuner's candidates (default)")
     ap.add_argument("--relmse", action="store_true",
                     help="compare the Fixed / Global / RA-Grid / RA-Quadtree / weighted variants at matched relMSE")
     ap.add_argument("--relmse-budget", type=int, default=1024)

@@ -291,6 +291,16 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_c
 rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* ctx, const rmlt_chain_params* params, uint32_t* out_q,
                                    float* out_f, double* out_bhat);
 
+/* Ceilings of the traversal roofline on `device`, measured by two
+ * microbenchmarks on `cuda_stream`: the aggregate L2 read bandwidth
+ * (16-byte loads that bypass L1, over a buffer of a quarter of the L2 that
+ * stays resident) in GB/s, and the FP32 fused multiply-add rate (eight
+ * independent chains per thread, 2 flops each) in TFLOP/s.  A ray's BVH node
+ * and triangle fetches draw on the first, its slab and triangle tests on the
+ * second.  Allocates and frees a scratch buffer of that size.  Errors:
+ * RMLT_E_INVALID_ARG (NULL output), RMLT_E_OOM, RMLT_E_CUDA. */
+rmlt_status rmlt_probe_peaks(int device, void* cuda_stream, double* l2_read_gbs, double* fp32_tflops);
+
 /* Bytes of device memory the context holds. */
 rmlt_status rmlt_memory_usage(rmlt_ctx* ctx, uint64_t* bytes);
 

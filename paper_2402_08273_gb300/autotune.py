@@ -1,0 +1,52 @@
+"""Launch-shape autotuner for rmlt_step.
+
+The execution form of an epoch (one thread per chain, or waves of shade /
+setup / trace kernels) and its knobs change speed only, never results: every
+form draws the same Philox numbers and evaluates each path with the same
+arithmetic.  So the tuner times each candidate on the live chains for a few
+epochs (CUDA events on the renderer's stream) and leaves the fastest one set.
+Which form wins depends on the population: a wave costs the latency of its
+slowest ray, so waves pay off once there are many more chains than lanes to
+run them on.
+"""
+from __future__ import annotations
+
+CANDIDATES = (
+    {"form": "chain", "batch_shade": 8, "batch_setup": 8},
+    {"form": "chain", "batch_shade": 4, "batch_setup": 8},
+    {"form": "chain", "batch_shade": 12, "batch_setup": 8},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
+    {"form": "wavefront", "trace_ctas_per_sm": 4, "refill_lanes": 8},
+)
+
+
+def apply(R, cand: dict) -> None:
+    """Set candidate `cand` on renderer R."""
+    if cand["form"] == "chain":
+        R.set_tuning(batch_shade=cand.get("batch_shade", 8), batch_setup=cand.get("batch_setup", 8))
+    else:
+        R.set_tuning(wavefront=True)
+        R.set_wavefront(trace_ctas_per_sm=cand.get("trace_ctas_per_sm", 0),
+                        setup_ctas_per_sm=cand.get("setup_ctas_per_sm", 0),
+                        refill_lanes=cand.get("refill_lanes", 16))
+
+
+def autotune(R, epochs: int = 2, candidates=CANDIDATES):
+    """Time each candidate for `epochs` epochs after one untimed epoch (graph
+    build, caches); set the fastest.  Returns (best, [(cand, ms_per_epoch)])."""
+    import torch
+    E = R.params["epoch_len"]
+    timings = []
+    for cand in candidates:
+        apply(R, cand)
+        R.step(E)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(R.stream)
+        R.step(epochs * E)
+        b.record(R.stream)
+        b.synchronize()
+        timings.append((dict(cand), a.elapsed_time(b) / epochs))
+    best = min(timings, key=lambda t: t[1])[0]
+    apply(R, best)
+    return best, timings

@@ -274,9 +274,12 @@ __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S,
     const unsigned wv = ctr->wave, buf = wv & 1u, n = ctr->fq_count;
     const uint64_t mut0 = ctr->mut0;
     if (TRACE) Ch.trace_base = ctr->trace_base;
+    // warp w of block b takes list slots of 32 at (w gridDim + b) 32, so a
+    // short list still spreads over every SM
+    const unsigned slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned base = 0; base < n; base += stride) {
-        const unsigned i = base + blockIdx.x * blockDim.x + threadIdx.x;
+        const unsigned i = base + 32u * slot + (threadIdx.x & 31u);
         int nr = 0;
         float4 r[4];
         if (i < n) {

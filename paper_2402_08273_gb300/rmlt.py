@@ -97,6 +97,7 @@ _SIGS = [
     ("rmlt_set_trace", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64,
                                  C.c_uint32]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
+    ("rmlt_probe_peaks", C.c_int, [C.c_int, C.c_void_p, _P(C.c_double), _P(C.c_double)]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     ("rmlt_set_wavefront", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
