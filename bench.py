@@ -470,6 +470,164 @@ def run_relmse(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """32 uneven problems (seeded procedural scenes of 1k-500k triangles,
+    128^2-1024^2 images, 4-32 px regions, 2^10-2^17 chains, depth 5-12):
+    rmlt_batch_step (one chain-kernel launch and one region-update launch per
+    epoch for all members, replayed as a CUDA graph) against the plain form,
+    every member stepping alone on its own stream.  Both forms give every
+    member the same trajectory (tests/test_gpu_batch.py), so their relMSE is
+    equal at equal mutations; the line reports throughput of both."""
+    import torch
+    from paper_2402_08273_gb300 import rmlt, scenes
+    torch.cuda.set_device(0)
+    work = scenes.batch_workload(args.batch_members, seed=0)
+    main_stream = torch.cuda.Stream()
+    Rs = []
+    t0 = time.perf_counter()
+    for scene, p in work:
+        R = rmlt.Renderer(stream=torch.cuda.Stream())
+        R.load_scene(scene)
+        R.init_chains(**p)
+        Rs.append(R)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n = len(Rs)
+    M = args.batch_mutations
+    E = work[0][1]["epoch_len"]
+    chains = sum(p["n_chains"] for _, p in work)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def plain_step(m):
+        ev = torch.cuda.Event()
+        ev.record(main_stream)
+        for R in Rs:
+            R.stream.wait_event(ev)
+            R.step(m)
+        for R in Rs:
+            e = torch.cuda.Event()
+            e.record(R.stream)
+            main_stream.wait_event(e)
+
+    B = rmlt.Batch(Rs)
+
+    def timed(step, steps):
+        spans = []
+        for _ in range(steps):
+            with torch.cuda.stream(main_stream):
+                flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(main_stream)
+            step()
+            b.record(main_stream)
+            spans.append((a, b))
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in spans) / 1e3
+
+    def batch_step(m):
+        ev = torch.cuda.Event()
+        ev.record(main_stream)
+        for R in Rs:
+            R.stream.wait_event(ev)
+        B.step(m)
+        for R in Rs:
+            e = torch.cuda.Event()
+            e.record(R.stream)
+            main_stream.wait_event(e)
+
+    def rays_total():
+        return sum(R.read_stats()["rays"] for R in Rs)
+
+    def sequential_step(m):
+        prev = torch.cuda.Event()
+        prev.record(main_stream)
+        for R in Rs:
+            R.stream.wait_event(prev)
+            R.step(m)
+            prev = torch.cuda.Event()
+            prev.record(R.stream)
+        main_stream.wait_event(prev)
+
+    for _ in range(args.warmup):
+        plain_step(M)
+    r0 = rays_total()
+    t_plain = timed(lambda: plain_step(M), args.steps)
+    rays_plain = rays_total() - r0
+    t_seq = timed(lambda: sequential_step(M), args.steps)
+    # launch order: autotuned over three candidates on the live chains
+    alone = []
+    for R in Rs:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(R.stream)
+        R.step(E)
+        b.record(R.stream)
+        b.synchronize()
+        alone.append(a.elapsed_time(b))
+    orders = {"given": list(range(n)),
+              "most_chains_first": sorted(range(n), key=lambda i: -work[i][1]["n_chains"]),
+              "slowest_alone_first": sorted(range(n), key=lambda i: -alone[i])}
+    # candidates: launch mode x launch order x resident blocks per SM, each
+    # timed on M mutations (the graph of the branch mode covers one call)
+    order_ms = {}
+    for mode in ("one_launch", "branches"):
+        for ctas in ((4, 3) if mode == "one_launch" else (4,)):
+            B.set_shape(ctas, mode == "branches")
+            for name, o in orders.items():
+                B.set_order(o)
+                batch_step(M)
+                order_ms[f"{mode}/{name}/{ctas}"] = timed(lambda: batch_step(M), 1) * 1e3 / (M // E)
+    best = min(order_ms, key=order_ms.get)
+    mode, name, ctas = best.split("/")
+    B.set_shape(int(ctas), mode == "branches")
+    B.set_order(orders[name])
+    for _ in range(args.warmup):
+        batch_step(M)
+    clocks = ClockSampler(0)
+    clocks.start()
+    r0 = rays_total()
+    t_batch = timed(lambda: batch_step(M), args.steps)
+    rays_batch = rays_total() - r0
+    clk = clocks.stop()
+    # end to end: the batched step plus every member's region histogram read
+    # into pinned host memory
+    hists = [torch.empty(R.m, dtype=torch.int64).pin_memory() for R in Rs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        batch_step(M)
+        for R, hh in zip(Rs, hists):
+            R.read_region_hist(out=hh.numpy().view("uint64"))
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    mut = chains * M * args.steps
+    value = mut / t_batch
+    line = {"metric": "mutations/s", "value": value, "unit": "mutations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_batch * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched_{n}", "desc": "uneven seeded problems (1k-500k triangles, "
+                       "128^2-1024^2 images, 4-32 px regions, 2^10-2^17 chains, depth 5-12), epoch_len 16",
+                       "members": n, "chains": chains, "mutations_per_step": M,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "launch_order": best, "order_ms_per_epoch": order_ms},
+            "rays_per_s": rays_batch / t_batch,
+            "plain_form": {"value": mut / t_plain, "rays_per_s": rays_plain / t_plain,
+                           "ms_per_step": t_plain * 1e3 / args.steps,
+                           "note": "every member stepping alone on its own stream"},
+            "sequential_form": {"value": mut / t_seq, "ms_per_step": t_seq * 1e3 / args.steps,
+                                "note": "members stepping alone one after the other"},
+            "batched_over_plain": t_plain / t_batch,
+            "batched_over_sequential": t_seq / t_batch,
+            "gpu_launches": (2 * n if mode == "branches" else 2) * (M // E) * args.steps,
+            "e2e": {"value": mut / t_e2e, "unit": "mutations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": sum(h.numel() * 8 for h in hists),
+                    "note": "rmlt_batch_step + every member's region histogram read to pinned host memory"},
+            "clocks": clk, "setup_s": t_setup}
+    print(json.dumps(line), flush=True)
+    B.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,11 +641,17 @@ def main():
                          "or the faster of the autotuner's candidates (default)")
     ap.add_argument("--relmse", action="store_true",
                     help="compare the Fixed / Global / RA-Grid / RA-Quadtree / weighted variants at matched relMSE")
+    ap.add_argument("--batched", action="store_true",
+                    help="uneven problems stepped by rmlt_batch_step against stepping each alone")
+    ap.add_argument("--batch-members", type=int, default=32)
+    ap.add_argument("--batch-mutations", type=int, default=64)
     ap.add_argument("--relmse-budget", type=int, default=1024)
     ap.add_argument("--relmse-ref-factor", type=int, default=32)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.relmse:
+    if args.batched and args.impl == "ours":
+        run_batched(args)
+    elif args.relmse:
         run_relmse(args, w)
     elif args.impl == "reference":
         run_reference(args, w)

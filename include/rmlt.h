@@ -291,6 +291,42 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_c
 rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* ctx, const rmlt_chain_params* params, uint32_t* out_q,
                                    float* out_f, double* out_bhat);
 
+/* Batched stepping.  A batch advances several contexts (their own scenes,
+ * resolutions, region grids and chain counts, of any size) together: per
+ * epoch, one launch of the chain kernel covers the chains of every member,
+ * block by block, and one launch runs every member's region update (Alg. 1
+ * lines 13-18); the two are a CUDA graph captured once and replayed per
+ * epoch.  Each member's trajectory is exactly the one rmlt_step gives it (the
+ * same kernel body, Philox streams and order of updates); only the launch is
+ * shared, so small populations fill the GPU together.  Members must be on
+ * one device, have chains, share epoch_len, use a BVH scene (more triangles
+ * than brute_force_max), and have neither the trace instrument nor the
+ * wavefront form set; large steps are traced in the chain kernel.  The batch
+ * holds the member handles, not their ownership: destroy the batch before its
+ * members.  rmlt_batch_step orders itself after and before each member's
+ * stream, so rmlt_read_* on a member sees its result.  Errors:
+ * RMLT_E_INVALID_ARG, RMLT_E_STATE (a member not ready or failed), RMLT_E_CUDA. */
+typedef struct rmlt_batch rmlt_batch;
+rmlt_status rmlt_batch_create(rmlt_batch** out, rmlt_ctx* const* members, int n_members);
+/* Launch order of the members' blocks (a permutation of 0..n-1); speed only.
+ * Blocks of earlier members start first, so putting the slowest members first
+ * shortens the launch's tail. */
+rmlt_status rmlt_batch_set_order(rmlt_batch* batch, const int* order);
+/* Launch shape of the batch; speed only.  ctas_per_sm: resident blocks of
+ * 128 chains per SM the batched chain kernel is compiled for, 4 (128
+ * registers, a few spilled) or 3 (none spilled).  mode: RMLT_BATCH_ONE_LAUNCH
+ * (one chain-kernel launch for all members per epoch, so every member waits
+ * at each epoch boundary for the slowest block) or RMLT_BATCH_BRANCHES (one
+ * graph per rmlt_batch_step call in which each member's epochs form their own
+ * chain of launches of the single-context chain kernel, so fast members run
+ * ahead; ctas_per_sm does not apply).  Defaults 4, RMLT_BATCH_ONE_LAUNCH. */
+#define RMLT_BATCH_ONE_LAUNCH 0
+#define RMLT_BATCH_BRANCHES 1
+rmlt_status rmlt_batch_set_shape(rmlt_batch* batch, int ctas_per_sm, int mode);
+/* n_mutations per chain of every member, rounded up to whole epochs. */
+rmlt_status rmlt_batch_step(rmlt_batch* batch, uint64_t n_mutations);
+void rmlt_batch_destroy(rmlt_batch* batch);
+
 /* Ceilings of the traversal roofline on `device`, measured by two
  * microbenchmarks on `cuda_stream`: the aggregate L2 read bandwidth
  * (16-byte loads that bypass L1, over a buffer of a quarter of the L2 that

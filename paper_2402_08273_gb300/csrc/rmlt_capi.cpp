@@ -975,6 +975,317 @@ rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
     return RMLT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batched stepping of several contexts
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct rmlt_batch {
+    std::vector<rmlt_ctx*> m;
+    std::vector<int> order;            // launch order of the members' blocks
+    int device = 0;
+    cudaStream_t stream = nullptr;     // the batch's own stream (capturable)
+    cudaEvent_t ev = nullptr;
+    std::vector<cudaStream_t> side;    // branch mode: one capture stream per member
+    std::vector<cudaEvent_t> join;
+    BatchMember* d_members = nullptr;
+    int* d_block_member = nullptr;
+    int n_blocks = 0;
+    std::vector<int> nblk;             // blocks of each member
+    bool table_dirty = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int mode = RMLT_BATCH_ONE_LAUNCH;
+    int ctas_per_sm = 4;
+    std::vector<unsigned char> graph_key;   // what the graph was captured with
+    std::vector<BatchMember> h;
+
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        graph_key.clear();
+    }
+};
+
+namespace {
+
+rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "member %d is NULL", i);
+    if (!c->have_chains) return fail(RMLT_E_STATE, "member %d: rmlt_init_chains first", i);
+    if (c->failed) return fail(RMLT_E_STATE, "member %d failed earlier", i);
+    if (c->device != b->device) return fail(RMLT_E_INVALID_ARG, "member %d is on another device", i);
+    if (c->S.brute || c->S.toy)
+        return fail(RMLT_E_INVALID_ARG, "member %d: batched members need a BVH scene (more than brute_force_max "
+                    "triangles)", i);
+    if (c->Ch.E != b->m[0]->Ch.E) return fail(RMLT_E_INVALID_ARG, "member %d: epoch_len differs from member 0", i);
+    if (c->tr) return fail(RMLT_E_STATE, "member %d: the trace instrument is set", i);
+    if (c->wavefront) return fail(RMLT_E_STATE, "member %d: the wavefront form is set", i);
+    return RMLT_OK;
+}
+
+// one launch of the chain kernel over every member's blocks, then one launch
+// of every member's region update; replayed once per epoch
+cudaError_t capture_one_launch(rmlt_batch* b, bool count)
+{
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t e1 = launch_chain_epoch_batch(b->d_members, b->d_block_member, 0, b->n_blocks, count,
+                                              b->ctas_per_sm, b->stream);
+    cudaError_t e2 = launch_region_update_batch(b->d_members, (int)b->m.size(), b->stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e);
+    }
+    b->graph = g;
+    return cudaGraphInstantiate(&b->exec, g, 0);
+}
+
+// every member's n_ep epochs as its own branch of one graph (chain kernel,
+// region update and, where due, the quadtree pass), so that members never
+// wait for each other between epochs
+cudaError_t capture_branches(rmlt_batch* b, bool count, uint64_t n_ep, const std::vector<unsigned char>& refine)
+{
+    const int n = (int)b->m.size();
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t err = cudaEventRecord(b->ev, b->stream);
+    for (int k = 0; k < n && err == cudaSuccess; ++k) {
+        const int i = b->order[(size_t)k];
+        cudaStream_t s = b->side[(size_t)i];
+        err = cudaStreamWaitEvent(s, b->ev, 0);
+        for (uint64_t ep = 0; ep < n_ep && err == cudaSuccess; ++ep) {
+            err = launch_chain_epoch_member(b->d_members + i, b->h[(size_t)i], count, s);
+            if (err == cudaSuccess) err = launch_region_update_batch(b->d_members + i, 1, s);
+            if (err == cudaSuccess && refine[(size_t)i * n_ep + ep]) err = launch_quadtree_refine(b->h[(size_t)i].Ch, s);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(b->join[(size_t)i], s);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(b->stream, b->join[(size_t)i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (err != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return err != cudaSuccess ? err : e;
+    }
+    b->graph = g;
+    return cudaGraphInstantiate(&b->exec, g, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+rmlt_status rmlt_batch_create(rmlt_batch** out, rmlt_ctx* const* ctxs, int n)
+{
+    if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return fail(RMLT_E_INVALID_ARG, "need at least one member");
+    rmlt_batch* b = new (std::nothrow) rmlt_batch();
+    if (!b) return fail(RMLT_E_OOM, "batch");
+    b->m.assign(ctxs, ctxs + n);
+    b->device = ctxs[0] ? ctxs[0]->device : 0;
+    for (int i = 0; i < n; ++i) {
+        rmlt_status st = batch_check_member(b, ctxs[i], i);
+        if (st) {
+            delete b;
+            return st;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) {
+                delete b;
+                return fail(RMLT_E_INVALID_ARG, "member %d repeats member %d", i, j);
+            }
+    }
+    b->side.assign((size_t)n, nullptr);
+    b->join.assign((size_t)n, nullptr);
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->side[(size_t)i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[(size_t)i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_members, sizeof(BatchMember) * (size_t)n);
+    if (e != cudaSuccess) {
+        rmlt_batch_destroy(b);
+        return cuda_fail(e, "rmlt_batch_create");
+    }
+    b->order.resize((size_t)n);
+    for (int i = 0; i < n; ++i) b->order[(size_t)i] = i;
+    *out = b;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_batch_set_order(rmlt_batch* b, const int* order)
+{
+    if (!b || !order) return fail(RMLT_E_INVALID_ARG, "NULL argument");
+    const int n = (int)b->m.size();
+    std::vector<int> seen((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (order[i] < 0 || order[i] >= n || seen[(size_t)order[i]]++)
+            return fail(RMLT_E_INVALID_ARG, "order must be a permutation of 0..%d", n - 1);
+    }
+    b->order.assign(order, order + n);
+    b->table_dirty = true;
+    b->drop_graph();
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_batch_set_shape(rmlt_batch* b, int ctas_per_sm, int mode)
+{
+    if (!b) return fail(RMLT_E_INVALID_ARG, "null batch");
+    if (ctas_per_sm != 3 && ctas_per_sm != 4) return fail(RMLT_E_INVALID_ARG, "ctas_per_sm must be 3 or 4");
+    if (mode != RMLT_BATCH_ONE_LAUNCH && mode != RMLT_BATCH_BRANCHES)
+        return fail(RMLT_E_INVALID_ARG, "unknown batch mode");
+    if (ctas_per_sm != b->ctas_per_sm || mode != b->mode) b->drop_graph();
+    b->ctas_per_sm = ctas_per_sm;
+    b->mode = mode;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
+{
+    if (!b) return fail(RMLT_E_INVALID_ARG, "null batch");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    const int n = (int)b->m.size();
+    for (int i = 0; i < n; ++i) {
+        rmlt_status st = batch_check_member(b, b->m[(size_t)i], i);
+        if (st) return st;
+    }
+    // block table: member order[0]'s blocks first, and so on
+    b->h.assign((size_t)n, BatchMember());
+    b->nblk.assign((size_t)n, 0);
+    int blocks = 0;
+    std::vector<int> table;
+    for (int k = 0; k < n; ++k) {
+        const int i = b->order[(size_t)k];
+        rmlt_ctx* c = b->m[(size_t)i];
+        BatchMember& bm = b->h[(size_t)i];
+        bm.S = c->S;
+        bm.Ch = c->Ch;
+        bm.Ch.batch_shade = c->batch_shade;
+        bm.Ch.batch_setup = c->batch_setup;
+        bm.Ch.adaptive_batch = c->adaptive_batch;
+        bm.Ch.lf = nullptr;
+        bm.mut0 = c->mut;
+        bm.block0 = blocks;
+        const int nb = (c->Ch.C + kChainBlock - 1) / kChainBlock;
+        b->nblk[(size_t)i] = nb;
+        table.insert(table.end(), (size_t)nb, i);
+        blocks += nb;
+    }
+    if (b->table_dirty || blocks != b->n_blocks) {
+        if (b->d_block_member) cudaFree(b->d_block_member);
+        b->d_block_member = nullptr;
+        CK(cudaMalloc(&b->d_block_member, sizeof(int) * (size_t)blocks), "batch block table");
+        CK(cudaMemcpy(b->d_block_member, table.data(), sizeof(int) * (size_t)blocks, cudaMemcpyHostToDevice),
+           "batch block table");
+        b->n_blocks = blocks;
+        b->table_dirty = false;
+        b->drop_graph();
+    }
+    bool count = false;
+    for (rmlt_ctx* c : b->m) count = count || c->count_work;
+    const uint64_t E = (uint64_t)b->m[0]->Ch.E;
+    const uint64_t n_ep = (n_mutations + E - 1) / E;
+    if (n_ep == 0) return RMLT_OK;
+    // quadtree passes due after each epoch (the same rule as rmlt_step)
+    std::vector<unsigned char> refine((size_t)n * n_ep, 0);
+    std::vector<uint64_t> since((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        rmlt_ctx* c = b->m[(size_t)i];
+        uint64_t s_ = c->since_refine;
+        for (uint64_t ep = 0; ep < n_ep && c->Ch.quadtree; ++ep) {
+            s_ += (uint64_t)c->Ch.C * E;
+            if (s_ >= (uint64_t)c->P.qt_refine) {
+                s_ = 0;
+                refine[(size_t)i * n_ep + ep] = 1;
+            }
+        }
+        since[(size_t)i] = s_;
+    }
+    // the graph holds device pointers, tuning and (branch mode) the epoch
+    // count and quadtree schedule; rebuild it when any of them changed
+    std::vector<unsigned char> key;
+    for (const BatchMember& bm : b->h) {
+        BatchMember k = bm;
+        k.mut0 = 0;
+        const unsigned char* p = (const unsigned char*)&k;
+        key.insert(key.end(), p, p + sizeof k);
+    }
+    key.push_back(count ? 1 : 0);
+    key.push_back((unsigned char)b->mode);
+    key.push_back((unsigned char)b->ctas_per_sm);
+    if (b->mode == RMLT_BATCH_BRANCHES) {
+        const unsigned char* p = (const unsigned char*)&n_ep;
+        key.insert(key.end(), p, p + sizeof n_ep);
+        key.insert(key.end(), refine.begin(), refine.end());
+    }
+    // the batch stream waits for every member's stream, and they for it afterwards
+    for (rmlt_ctx* c : b->m) {
+        CK(cudaEventRecord(b->ev, c->stream), "batch event");
+        CK(cudaStreamWaitEvent(b->stream, b->ev, 0), "batch wait");
+    }
+    CK(cudaMemcpyAsync(b->d_members, b->h.data(), sizeof(BatchMember) * (size_t)n, cudaMemcpyHostToDevice,
+                       b->stream), "batch member table");
+    if (!b->exec || key != b->graph_key) {
+        b->drop_graph();
+        cudaError_t e = b->mode == RMLT_BATCH_BRANCHES ? capture_branches(b, count, n_ep, refine)
+                                                       : capture_one_launch(b, count);
+        if (e != cudaSuccess) {
+            b->drop_graph();
+            return cuda_fail(e, "batch graph capture");
+        }
+        b->graph_key = key;
+    }
+    cudaError_t e = cudaSuccess;
+    if (b->mode == RMLT_BATCH_BRANCHES) {
+        e = cudaGraphLaunch(b->exec, b->stream);
+    } else {
+        for (uint64_t ep = 0; ep < n_ep && e == cudaSuccess; ++ep) {
+            e = cudaGraphLaunch(b->exec, b->stream);
+            for (int i = 0; i < n && e == cudaSuccess; ++i)
+                if (refine[(size_t)i * n_ep + ep]) e = launch_quadtree_refine(b->h[(size_t)i].Ch, b->stream);
+        }
+    }
+    if (e != cudaSuccess) {
+        for (rmlt_ctx* c : b->m) c->failed = true;
+        return cuda_fail(e, "rmlt_batch_step launch");
+    }
+    for (int i = 0; i < n; ++i) {
+        rmlt_ctx* c = b->m[(size_t)i];
+        c->mut += n_ep * E;
+        c->epochs += n_ep;
+        c->since_refine = since[(size_t)i];
+    }
+    CK(cudaEventRecord(b->ev, b->stream), "batch event");
+    for (rmlt_ctx* c : b->m) CK(cudaStreamWaitEvent(c->stream, b->ev, 0), "batch wait");
+    return RMLT_OK;
+}
+
+void rmlt_batch_destroy(rmlt_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->drop_graph();
+    if (b->d_block_member) cudaFree(b->d_block_member);
+    if (b->d_members) cudaFree(b->d_members);
+    if (b->ev) cudaEventDestroy(b->ev);
+    for (cudaEvent_t ev : b->join)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t st : b->side)
+        if (st) cudaStreamDestroy(st);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
 void rmlt_destroy(rmlt_ctx* c)
 {
     if (!c) return;

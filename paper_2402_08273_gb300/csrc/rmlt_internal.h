@@ -147,6 +147,24 @@ cudaError_t wf_epoch(WfGraph** g, const DevScene& s, const DevChains& c, DevWave
                      unsigned long long trace_base, bool trace, bool count_work, int trace_ctas_per_sm,
                      int setup_ctas_per_sm, bool host_loop, cudaStream_t st);
 
+// One member of a batched epoch (rmlt_batch_step): its scene, its chains,
+// the mutation index of its next epoch and its first block in the launch.
+struct BatchMember {
+    DevScene S;
+    DevChains Ch;
+    unsigned long long mut0 = 0;
+    int32_t block0 = 0, pad_ = 0;
+};
+// blocks [block_base, block_base + n_blocks) of the batch's block table
+cudaError_t launch_chain_epoch_batch(const BatchMember* members, const int* block_member, int block_base,
+                                     int n_blocks, bool count_work, int ctas_per_sm, cudaStream_t st);
+// the chain kernel of one member (its scene and chains as launch parameters),
+// reading the epoch's first mutation index from member_dev->mut0
+cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const BatchMember& member, bool count_work,
+                                      cudaStream_t st);
+// region update of every member and mut0 += E (one block per member)
+cudaError_t launch_region_update_batch(BatchMember* members, int n, cudaStream_t st);
+
 // Scratch of the bootstrap (n = K C samples, K = n_bootstrap / C per chain).
 struct BootScratch {
     float* pi = nullptr;          // [n]

@@ -30,13 +30,13 @@ namespace {
 // divergent parts convergent while the traversal keeps every lane busy.
 enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 };
 
+// The epoch of chain c (one thread); s_tris holds the staged triangles of a
+// brute-force scene, s_stack the block's traversal stacks.
 template <bool BRUTE, bool TRACE, bool COUNT>
-__global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0)
+__device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
+                                                 const float4* s_tris, uint32_t* s_stack)
 {
-    extern __shared__ float4 s_tris[];
-    if (BRUTE) stage_triangles(S, s_tris);
     const unsigned FULL = 0xFFFFFFFFu;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = c < Ch.C;
     unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};   // accepted, large, small, early, invalid, rays, overflow
     unsigned n_nodes = 0, n_tris = 0;
@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
     const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
     uint32_t y[kMaxDim];
     // traversal stack in shared memory, one column per thread (conflict-free)
-    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
     uint32_t* stack = s_stack + threadIdx.x;
     Path p;
     Trav T;
@@ -185,6 +184,44 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
     }
 }
 
+// mut0_dev, when set, holds the epoch's first mutation index on the device
+// (a graph replayed over several epochs advances it there)
+template <bool BRUTE, bool TRACE, bool COUNT>
+__global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0,
+                                                                  const unsigned long long* mut0_dev)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    if (mut0_dev) mut0 = *mut0_dev;
+    chain_epoch_body<BRUTE, TRACE, COUNT>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris, s_stack);
+}
+
+// ---------------------------------------------------------------------------
+// batched epoch: the chains of several contexts (scenes, resolutions, chain
+// counts of any size) in one launch.  Block b runs chains of member
+// block_member[b]; the member's scene and chain tables are copied to shared
+// memory once per block.
+// ---------------------------------------------------------------------------
+template <bool COUNT, int MIN_BLOCKS>
+__global__ void __launch_bounds__(kChainBlock, MIN_BLOCKS) chain_epoch_batch_kernel(const BatchMember* members,
+                                                                                 const int* block_member,
+                                                                                 int block_base)
+{
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    __shared__ BatchMember m;
+    const int bx = block_base + (int)blockIdx.x;
+    const int e = block_member[bx];
+    {
+        const uint32_t* src = (const uint32_t*)(members + e);
+        uint32_t* dst = (uint32_t*)&m;
+        for (int i = threadIdx.x; i < (int)(sizeof(BatchMember) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int c = (bx - m.block0) * kChainBlock + threadIdx.x;
+    chain_epoch_body<false, false, COUNT>(m.S, m.Ch, m.mut0, c, nullptr, s_stack);
+}
+
 // ---------------------------------------------------------------------------
 // large steps traced ahead of the epoch.  A large step proposes an
 // independent uniform point (its draws do not depend on the chain's state),
@@ -273,7 +310,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
 // region update at the epoch boundary (Alg. 1 lines 13-18; eqs.
 // est_exp_acc, update_lambda, step_size_n), binary64 with explicit rounding
 // ---------------------------------------------------------------------------
-__global__ void region_update_kernel(const DevChains Ch, int init_only)
+__device__ __forceinline__ void region_update_body(const DevChains& Ch, int init_only)
 {
     const int m_now = Ch.quadtree ? Ch.qt_state[0] : Ch.m;
     for (int k = threadIdx.x; k < m_now; k += blockDim.x) {
@@ -319,6 +356,18 @@ __global__ void region_update_kernel(const DevChains Ch, int init_only)
         Ch.hprev[k] = Ch.hist[k];
         Ch.wf[k] = __double2float_rn(Ch.w[k]);
     }
+}
+
+__global__ void region_update_kernel(const DevChains Ch, int init_only) { region_update_body(Ch, init_only); }
+
+// batched epoch boundary: member b's regions in block b, then its mutation
+// index advances by one epoch
+__global__ void region_update_batch_kernel(BatchMember* members)
+{
+    BatchMember* mb = members + blockIdx.x;
+    region_update_body(mb->Ch, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) mb->mut0 += (unsigned long long)mb->Ch.E;
 }
 
 // Refinement pass of the quadtree partition (Sec. 6.2): every leaf visited
@@ -547,7 +596,17 @@ static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
-    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0);
+    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const BatchMember& member, bool count_work,
+                                      cudaStream_t st)
+{
+    const int blocks = (member.Ch.C + kChainBlock - 1) / kChainBlock;
+    const unsigned long long* m0 = &member_dev->mut0;
+    if (count_work) chain_epoch_kernel<false, false, true><<<blocks, kChainBlock, 0, st>>>(member.S, member.Ch, 0, m0);
+    else chain_epoch_kernel<false, false, false><<<blocks, kChainBlock, 0, st>>>(member.S, member.Ch, 0, m0);
     return cudaGetLastError();
 }
 
@@ -584,6 +643,28 @@ cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t m
     } else {
         large_trace_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c, mut0);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_epoch_batch(const BatchMember* members, const int* block_member, int block_base,
+                                     int n_blocks, bool count_work, int ctas_per_sm, cudaStream_t st)
+{
+    // 4 resident blocks per SM caps the kernel at 128 registers (a few
+    // spills); 3 leaves it unspilled
+    const int bb = block_base;
+    if (ctas_per_sm == 3) {
+        if (count_work) chain_epoch_batch_kernel<true, 3><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
+        else chain_epoch_batch_kernel<false, 3><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
+    } else {
+        if (count_work) chain_epoch_batch_kernel<true, 4><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
+        else chain_epoch_batch_kernel<false, 4><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_update_batch(BatchMember* members, int n, cudaStream_t st)
+{
+    region_update_batch_kernel<<<n, 256, 0, st>>>(members);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,11 @@ _SIGS = [
                                  C.c_uint32]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_probe_peaks", C.c_int, [C.c_int, C.c_void_p, _P(C.c_double), _P(C.c_double)]),
+    ("rmlt_batch_create", C.c_int, [_P(C.c_void_p), _P(C.c_void_p), C.c_int]),
+    ("rmlt_batch_set_order", C.c_int, [C.c_void_p, _P(C.c_int)]),
+    ("rmlt_batch_set_shape", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("rmlt_batch_step", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("rmlt_batch_destroy", None, [C.c_void_p]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     ("rmlt_set_wavefront", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -360,6 +365,39 @@ class Renderer:
         nx = -(-self.params["width"] // self.params["region_px"])
         ny = -(-self.params["height"] // self.params["region_px"])
         self.m = nx * ny
+
+
+class Batch:
+    """Several renderers advanced together (rmlt_batch_*): one chain-kernel
+    launch and one region-update launch per epoch cover every member."""
+
+    def __init__(self, renderers):
+        self.members = list(renderers)
+        arr = (C.c_void_p * len(self.members))(*[r.h for r in self.members])
+        h = C.c_void_p()
+        _check(lib().rmlt_batch_create(C.byref(h), arr, len(self.members)))
+        self.h = h
+
+    def set_order(self, order):
+        arr = (C.c_int * len(self.members))(*[int(i) for i in order])
+        _check(lib().rmlt_batch_set_order(self.h, arr))
+
+    def set_shape(self, ctas_per_sm: int = 4, branches: bool = False):
+        _check(lib().rmlt_batch_set_shape(self.h, int(ctas_per_sm), 1 if branches else 0))
+
+    def step(self, n_mutations: int):
+        _check(lib().rmlt_batch_step(self.h, int(n_mutations)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rmlt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def trace_to_numpy(records_tensor) -> np.ndarray:

@@ -343,3 +343,26 @@ def toy_rect_mass(params, x0, x1, y0, y1) -> float:
 def scene_stats(scene: dict) -> dict:
     return {"n_tris": int(len(scene["tris"])), "n_verts": int(len(scene["verts"])),
             "n_mats": int(len(scene["mat_type"]))}
+
+
+def batch_workload(n_scenes: int = 32, seed: int = 0, tri_range=(1_000, 500_000), chain_range=(1 << 10, 1 << 17)):
+    """Seeded population of uneven problems for batched stepping: per member a
+    procedural scene (two rooms or glossy corridor, alternately) with a
+    triangle count log-uniform in tri_range, a square image of side 128, 256,
+    512 or 1024, regions of 4, 8, 16 or 32 px, a chain count log-uniform in
+    chain_range and a depth in 5..12.  Returns [(scene, chain params)]; every
+    member shares epoch_len 16."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        n_tris = int(round(math.exp(rng.uniform(math.log(tri_range[0]), math.log(tri_range[1])))))
+        side = int(rng.choice([128, 256, 512, 1024]))
+        r = int(rng.choice([4, 8, 16, 32]))
+        C = int(round(math.exp(rng.uniform(math.log(chain_range[0]), math.log(chain_range[1])))))
+        d = int(rng.integers(5, 13))
+        gen = two_rooms if i % 2 == 0 else glossy_corridor
+        scene = gen(n_tris=n_tris, seed=seed * 1000 + i)
+        params = dict(n_chains=C, width=side, height=side, region_px=r, max_depth=d, epoch_len=16,
+                      n_bootstrap=max(1 << 16, 8 * C), p_large=0.3, seed=seed * 1000 + i + 1)
+        out.append((scene, params))
+    return out
