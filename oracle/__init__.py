@@ -46,7 +46,8 @@ class OrParams(C.Structure):
         ("lambda_init", C.c_double), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
         ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("partition", C.c_int32),
         ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32), ("qt_split", C.c_int64),
-        ("qt_refine", C.c_int64),
+        ("qt_refine", C.c_int64), ("p_mala", C.c_double), ("mala_tau", C.c_double),
+        ("mala_drift_max", C.c_double),
     ]
 
 
@@ -97,6 +98,9 @@ def lib():
         "or_accept_prob": (C.c_double, [C.c_void_p, u32p, u32p, C.c_double, C.c_double, C.c_int32]),
         "or_quadtree": (C.c_int32, [C.c_void_p, i32p, i32p, i32p, C.c_int32]),
         "or_refine": (C.c_int32, [C.c_void_p]),
+        "or_path_grad": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, u32p, f64p, f64p]),
+        "or_mala_stats": (None, [C.c_void_p, P(C.c_uint64)]),
+        "or_state_grad": (C.c_void_p, [C.c_void_p, C.c_uint32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -137,6 +141,7 @@ class Scene:
 
     def __init__(self, scene: dict | None = None, use_bvh: bool = True, toy=None):
         L = lib()
+        self.toy = toy is not None
         if toy is not None:
             self._toy = np.ascontiguousarray(toy, np.float64)
             self.h = L.or_scene_create_toy(_ptr(self._toy, C.c_double))
@@ -192,13 +197,25 @@ class Scene:
                                 _ptr(f, C.c_double), C.byref(m), _ptr(cnt, C.c_uint64))
         return f, m.value, bool(ok), int(cnt[0])
 
+    def path_grad(self, q, width, height, max_depth):
+        """(f, grad log pi, status): forward-mode gradient in binary64 (status 1
+        ok, 0 not differentiable here: a non-Lambertian surface or a non-finite
+        path)."""
+        q = np.ascontiguousarray(q, np.uint32)
+        f = np.zeros(3)
+        D = 2 if self.toy else 2 + 5 * max_depth
+        g = np.zeros(max(D, 1))
+        st = lib().or_path_grad(self.h, width, height, max_depth, _ptr(q, C.c_uint32), _ptr(f, C.c_double),
+                                _ptr(g, C.c_double))
+        return f, g[:D], int(st)
+
 
 DEFAULT_PARAMS = dict(
     n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
     target_mode=0, n_bootstrap=1 << 14, seed=1, p_large=0.3, s1=1.0 / 1024.0, s2=1.0 / 64.0,
     alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
     lambda_max=None, w_floor=1e-3, debug_flags=0, partition=0, qt_max_leaves=4096, qt_max_depth=10,
-    qt_split=5000, qt_refine=10_000_000,
+    qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3, mala_drift_max=0.1,
 )
 
 
@@ -313,7 +330,17 @@ class Chains:
         o = np.zeros(8, np.uint64)
         lib().or_stats(self.h, _ptr(o, C.c_uint64))
         keys = ("mutations", "accepted", "large", "small", "early_reject", "invalid", "rays", "boot")
-        return {k: int(v) for k, v in zip(keys, o)}
+        out = {k: int(v) for k, v in zip(keys, o)}
+        m = np.zeros(2, np.uint64)
+        lib().or_mala_stats(self.h, _ptr(m, C.c_uint64))
+        out["mala"], out["mala_accepted"] = int(m[0]), int(m[1])
+        return out
+
+    def state_grad(self, chain: int):
+        p = lib().or_state_grad(self.h, chain)
+        if not p:
+            return None
+        return np.ctypeslib.as_array(C.cast(p, C.POINTER(C.c_double)), shape=(self.D,)).copy()
 
     # live views of the oracle's state arrays
     @property

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #define OR_MAX_DIM 256
+#define OR_MAX_GRAD 62          /* dimensions of the gradient (2 + 5 x 12) */
 #define OR_WIN 1e-4            /* scene-relative window of the decision margin (10x the exclusion threshold) */
 #define OR_INF (1.0 / 0.0)
 #define OR_PI 3.14159265358979323846
@@ -662,6 +663,189 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
 }
 
 /* ------------------------------------------------------------------------ */
+/* gradient of log pi(u) by forward-mode differentiation: every continuous  */
+/* quantity of the path map carries its derivative with respect to all D    */
+/* primary-sample coordinates (dual numbers); the discrete choices (hit      */
+/* triangle, light triangle, visibility, branch taken) come from the primal  */
+/* walk and are held fixed, so this is the gradient of the smooth piece of   */
+/* f that contains u.                                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double v;
+    double g[OR_MAX_GRAD];
+} dn;
+
+typedef struct {
+    dn c[3];
+} dv3;
+
+static int g_nd; /* dimensions carried by the dual numbers of the current call */
+
+static dn dn_c(double v)
+{
+    dn r;
+    r.v = v;
+    memset(r.g, 0, sizeof(double) * (size_t)g_nd);
+    return r;
+}
+static dn dn_var(double v, int j)
+{
+    dn r = dn_c(v);
+    r.g[j] = 1.0;
+    return r;
+}
+static dn dn_add(dn a, dn b) { for (int j = 0; j < g_nd; ++j) a.g[j] += b.g[j]; a.v += b.v; return a; }
+static dn dn_sub(dn a, dn b) { for (int j = 0; j < g_nd; ++j) a.g[j] -= b.g[j]; a.v -= b.v; return a; }
+static dn dn_scale(dn a, double s) { for (int j = 0; j < g_nd; ++j) a.g[j] *= s; a.v *= s; return a; }
+static dn dn_addc(dn a, double c) { a.v += c; return a; }
+static dn dn_mul(dn a, dn b)
+{
+    dn r;
+    r.v = a.v * b.v;
+    for (int j = 0; j < g_nd; ++j) r.g[j] = a.g[j] * b.v + a.v * b.g[j];
+    return r;
+}
+static dn dn_div(dn a, dn b)
+{
+    dn r;
+    r.v = a.v / b.v;
+    for (int j = 0; j < g_nd; ++j) r.g[j] = (a.g[j] * b.v - a.v * b.g[j]) / (b.v * b.v);
+    return r;
+}
+/* f(a) with f'(a.v) = df */
+static dn dn_apply(dn a, double fv, double df)
+{
+    a.v = fv;
+    for (int j = 0; j < g_nd; ++j) a.g[j] *= df;
+    return a;
+}
+static dn dn_sqrt(dn a) { double r = sqrt(a.v); return dn_apply(a, r, r > 0 ? 0.5 / r : 0.0); }
+static dn dn_cos(dn a) { return dn_apply(a, cos(a.v), -sin(a.v)); }
+static dn dn_sin(dn a) { return dn_apply(a, sin(a.v), cos(a.v)); }
+static dn dn_exp(dn a) { double e = exp(a.v); return dn_apply(a, e, e); }
+
+static dv3 dv_c(const double a[3]) { dv3 r; for (int k = 0; k < 3; ++k) r.c[k] = dn_c(a[k]); return r; }
+static dv3 dv_add(dv3 a, dv3 b) { for (int k = 0; k < 3; ++k) a.c[k] = dn_add(a.c[k], b.c[k]); return a; }
+static dv3 dv_sub(dv3 a, dv3 b) { for (int k = 0; k < 3; ++k) a.c[k] = dn_sub(a.c[k], b.c[k]); return a; }
+static dv3 dv_smul(dv3 a, dn s) { for (int k = 0; k < 3; ++k) a.c[k] = dn_mul(a.c[k], s); return a; }
+/* constant vector times a dual scalar */
+static dv3 dv_cs(const double a[3], dn s) { dv3 r; for (int k = 0; k < 3; ++k) r.c[k] = dn_scale(s, a[k]); return r; }
+static dn dv_dotc(dv3 a, const double b[3])
+{
+    dn r = dn_scale(a.c[0], b[0]);
+    r = dn_add(r, dn_scale(a.c[1], b[1]));
+    return dn_add(r, dn_scale(a.c[2], b[2]));
+}
+static dn dv_dot(dv3 a, dv3 b)
+{
+    dn r = dn_mul(a.c[0], b.c[0]);
+    r = dn_add(r, dn_mul(a.c[1], b.c[1]));
+    return dn_add(r, dn_mul(a.c[2], b.c[2]));
+}
+static void dv_val(dv3 a, double o[3]) { for (int k = 0; k < 3; ++k) o[k] = a.c[k].v; }
+
+int32_t or_path_grad(const or_scene* s, int32_t width, int32_t height, int32_t max_depth, const uint32_t* q,
+                     double f[3], double* grad)
+{
+    const int D = s->toy ? 2 : 2 + 5 * max_depth;
+    if (D > OR_MAX_GRAD) return -1;
+    g_nd = D;
+    memset(grad, 0, sizeof(double) * (size_t)D);
+    f[0] = f[1] = f[2] = 0.0;
+    dn u[OR_MAX_GRAD];
+    for (int j = 0; j < D; ++j) u[j] = dn_var(u24(q[j]), j);
+    if (s->toy) {
+        const double* p = s->toy_p;
+        double u0 = u[0].v, u1 = u[1].v;
+        dn fv = dn_c(p[0] + ((u0 >= p[2] && u0 < p[3] && u1 >= p[4] && u1 < p[5]) ? p[1] : 0.0));
+        dn dx = dn_addc(u[0], -p[7]), dy = dn_addc(u[1], -p[8]);
+        dn r2 = dn_add(dn_mul(dx, dx), dn_mul(dy, dy));
+        fv = dn_add(fv, dn_scale(dn_exp(dn_scale(r2, -1.0 / (2.0 * p[9] * p[9]))), p[6]));
+        f[0] = f[1] = f[2] = fv.v;
+        for (int j = 0; j < D; ++j) grad[j] = fv.g[j] / fv.v;
+        return 1;
+    }
+    dv3 L = dv_c((double[3]){0, 0, 0});
+    double T[3] = {1, 1, 1};
+    const double aspect = (double)width / (double)height;
+    dn sx = dn_scale(dn_addc(dn_scale(u[0], 2.0), -1.0), s->tan_half * aspect);
+    dn sy = dn_scale(dn_addc(dn_scale(u[1], -2.0), 1.0), s->tan_half);
+    dv3 o = dv_c(s->cam_pos);
+    dv3 d = dv_add(dv_add(dv_c(s->cam_fwd), dv_cs(s->cam_right, sx)), dv_cs(s->cam_up, sy));
+    dn dl = dn_sqrt(dv_dot(d, d));
+    for (int k = 0; k < 3; ++k) d.c[k] = dn_div(d.c[k], dl);
+    for (int b = 0; b < max_depth; ++b) {
+        double ov[3], dvv[3], t;
+        int32_t ti;
+        dv_val(o, ov);
+        dv_val(d, dvv);
+        if (!or_closest_hit(s, ov, dvv, 0.0, OR_INF, 0, &t, &ti, NULL)) break;
+        const or_tri* Tr = &s->tri[ti];
+        const or_mat* M = &s->mat[Tr->mat];
+        /* the hit on the triangle's plane: t = (v0 - o).n / d.n */
+        dn tn = dn_div(dv_dotc(dv_sub(dv_c(Tr->v0), o), Tr->n), dv_dotc(d, Tr->n));
+        dv3 x = dv_add(o, dv_smul(d, tn));
+        double cosi = -v_dot(Tr->n, dvv);
+        double ns[3];
+        for (int a = 0; a < 3; ++a) ns[a] = cosi > 0 ? Tr->n[a] : -Tr->n[a];
+        if (b == 0 && M->emissive && cosi > 0)
+            for (int a = 0; a < 3; ++a) L.c[a] = dn_addc(L.c[a], T[a] * M->emission[a]);
+        if (M->black) break;
+        if (s->nl > 0) {
+            dn lu = u[3 + 5 * b], lv = u[4 + 5 * b];
+            double ls = u[2 + 5 * b].v;
+            int32_t lo = 0, hi = s->nl - 1;
+            while (lo < hi) { int32_t mid = (lo + hi) / 2; if (s->light_cdf[mid] > ls) hi = mid; else lo = mid + 1; }
+            const or_tri* LT = &s->tri[s->light[lo]];
+            const or_mat* LM = &s->mat[LT->mat];
+            dn su = dn_sqrt(lu);
+            dn b1 = dn_mul(su, dn_addc(dn_scale(lv, -1.0), 1.0)), b2 = dn_mul(su, lv);
+            dv3 p = dv_add(dv_add(dv_c(LT->v0), dv_cs(LT->e1, b1)), dv_cs(LT->e2, b2));
+            dv3 wi = dv_sub(p, x);
+            dn dist2 = dv_dot(wi, wi), dist = dn_sqrt(dist2);
+            for (int k = 0; k < 3; ++k) wi.c[k] = dn_div(wi.c[k], dist);
+            dn cx = dv_dotc(wi, ns), cl = dn_scale(dv_dotc(wi, LT->n), -1.0);
+            if (cx.v > 0 && cl.v > 0) {
+                double xv[3], pv[3], xo[3], sd[3];
+                dv_val(x, xv);
+                dv_val(p, pv);
+                for (int a = 0; a < 3; ++a) xo[a] = xv[a] + s->eps * ns[a];
+                v_sub(pv, xo, sd);
+                double sdist = v_len(sd);
+                if (sdist > 2.0 * s->eps) {
+                    for (int a = 0; a < 3; ++a) sd[a] /= sdist;
+                    if (!or_any_hit(s, xo, sd, 0.0, sdist - s->eps, 0, NULL)) {
+                        if (M->type != 0) return 0;   /* the gradient covers Lambertian surfaces */
+                        dn g = dn_scale(dn_div(dn_mul(cx, cl), dist2), s->light_area);
+                        for (int a = 0; a < 3; ++a)
+                            L.c[a] = dn_add(L.c[a], dn_scale(g, T[a] * M->albedo[a] / OR_PI * LM->emission[a]));
+                    }
+                }
+            }
+        }
+        if (b == max_depth - 1) break;
+        if (M->type != 0) return 0;
+        dn bu = u[5 + 5 * b], bv = u[6 + 5 * b];
+        double ft[3], fb[3];
+        frame(ns, ft, fb, NULL);
+        dn phi = dn_scale(bv, 2.0 * OR_PI);
+        dn r = dn_sqrt(bu);
+        dn lz = dn_sqrt(dn_addc(dn_scale(bu, -1.0), 1.0));
+        dv3 wi = dv_add(dv_add(dv_cs(ft, dn_mul(r, dn_cos(phi))), dv_cs(fb, dn_mul(r, dn_sin(phi)))), dv_cs(ns, lz));
+        for (int a = 0; a < 3; ++a) T[a] *= M->albedo[a];
+        double epsn[3] = {s->eps * ns[0], s->eps * ns[1], s->eps * ns[2]};
+        o = dv_add(x, dv_c(epsn));
+        d = wi;
+    }
+    dn pi = dn_add(dn_add(dn_scale(L.c[0], 0.2126), dn_scale(L.c[1], 0.7152)), dn_scale(L.c[2], 0.0722));
+    for (int a = 0; a < 3; ++a) f[a] = L.c[a].v;
+    if (!isfinite(pi.v)) return 0;
+    if (pi.v > 0)
+        for (int j = 0; j < D; ++j) grad[j] = pi.g[j] / pi.v;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* chains                                                                    */
 /* ------------------------------------------------------------------------ */
 struct or_ctx {
@@ -693,6 +877,9 @@ struct or_ctx {
     double bhat;
     uint64_t mut;
     uint64_t st[8];
+    uint64_t mala_st[2];          /* Langevin moves proposed, accepted */
+    uint32_t T_mala;
+    double* g;                    /* [C][D] gradient of log pi at each chain's state (Langevin runs) */
     int inited;
     or_mut_hook mh;
     or_upd_hook uh;
@@ -729,6 +916,8 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     }
     double tl = ceil(p->p_large * 16777216.0);
     c->T_large = (uint32_t)(tl < 0 ? 0 : (tl > 16777216.0 ? 16777216.0 : tl));
+    double tm = ceil(p->p_mala * 16777216.0);
+    c->T_mala = (uint32_t)(tm < 0 ? 0 : (tm > 16777216.0 ? 16777216.0 : tm));
     c->S1 = (float)(p->s1 * 4294967296.0);
     c->S2 = (float)(p->s2 * 4294967296.0);
     c->log2_ratio = (float)log2(p->s2 / p->s1);
@@ -749,6 +938,17 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     c->sig = (float*)calloc(m, sizeof(float));
     c->img = (double*)calloc((size_t)p->width * (size_t)p->height * 3, sizeof(double));
     c->Bk = (double*)calloc(m, sizeof(double));
+    if (p->p_mala > 0) {
+        /* the Langevin strategy differentiates the path map: Lambertian scenes,
+         * D <= 62, a positive step and drift bound */
+        int ok = D <= OR_MAX_GRAD && p->mala_tau > 0 && p->mala_drift_max > 0 && p->p_large + p->p_mala <= 1.0;
+        for (int32_t mi = 0; mi < s->nm && ok && !s->toy; ++mi) ok = s->mat[mi].type == 0;
+        if (!ok) {
+            or_ctx_destroy(c);
+            return NULL;
+        }
+        c->g = (double*)calloc(C * (size_t)D, sizeof(double));
+    }
     return c;
 }
 
@@ -759,6 +959,7 @@ void or_ctx_destroy(or_ctx* c)
     free(c->i); free(c->A); free(c->h); free(c->h_prev); free(c->w); free(c->Rc); free(c->sig);
     free(c->img); free(c->Bk);
     free(c->qt_child); free(c->qt_leaf); free(c->qt_depth);
+    free(c->g);
     free(c);
 }
 
@@ -915,6 +1116,109 @@ static void splat(or_ctx* c, int32_t chain)
     for (int a = 0; a < 3; ++a) c->img[o + a] += c->f[3 * chain + a] / c->pi[chain];
 }
 
+/* ------------------------------------------------------------------------ */
+/* Langevin strategy (MALA, Roberts & Tweedie 1996, with the drift's norm    */
+/* bounded): y = x + m_x + sqrt(tau_x) xi, m_x = (tau_x / 2) grad log pi(x)  */
+/* scaled to norm <= drift_max, xi ~ N(0, I) by Box-Muller from the          */
+/* mutation's Philox draws (call 1 + j gives dims 4j..4j+3), on the torus    */
+/* with nearest-image displacements.  tau_x = tau sigma_{k(x)}^2: the step   */
+/* adapts with the region of the current state, so the reverse density uses */
+/* tau_{k(y)} and the ratio keeps its normalising factors.  Not in the      */
+/* paper (gradient methods appear only as related work); the region weight  */
+/* is constant inside a region, so grad log pi~ = grad log pi.              */
+/* ------------------------------------------------------------------------ */
+static void mala_drift(const or_ctx* c, const double* g, double tau, double* m)
+{
+    double n2 = 0.0;
+    for (int32_t d = 0; d < c->D; ++d) {
+        m[d] = 0.5 * tau * g[d];
+        n2 += m[d] * m[d];
+    }
+    double n = sqrt(n2);
+    if (n > c->p.mala_drift_max)
+        for (int32_t d = 0; d < c->D; ++d) m[d] *= c->p.mala_drift_max / n;
+}
+
+/* log N(delta; m, tau I) */
+static double mala_logq(int32_t D, double tau, const double* delta, const double* m)
+{
+    double s2 = 0.0;
+    for (int32_t d = 0; d < D; ++d) {
+        double e = delta[d] - m[d];
+        s2 += e * e;
+    }
+    return -0.5 * D * log(2.0 * OR_PI * tau) - s2 / (2.0 * tau);
+}
+
+static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
+{
+    const int32_t D = c->D;
+    uint32_t qy[OR_MAX_DIM];
+    uint32_t* qx = &c->q[(size_t)chain * D];
+    const double* gx = &c->g[(size_t)chain * D];
+    const int32_t kx = c->k[chain];
+    const double tx = c->p.mala_tau * (double)c->sig[kx] * (double)c->sig[kx];
+    double mx[OR_MAX_GRAD], my[OR_MAX_GRAD], delta[OR_MAX_GRAD], gy[OR_MAX_GRAD], z[OR_MAX_GRAD + 3];
+    mala_drift(c, gx, tx, mx);
+    for (int32_t j = 0; 4 * j < D; ++j) {
+        uint32_t r[4];
+        draw(c->p.seed, c->mut, chain, 1u + (uint32_t)j, r);
+        for (int a = 0; a < 2; ++a) {
+            double u1 = ((double)(r[2 * a] >> 8) + 0.5) * (1.0 / 16777216.0);
+            double u2 = u24(r[2 * a + 1]);
+            double rho = sqrt(-2.0 * log(u1));
+            z[4 * j + 2 * a] = rho * cos(2.0 * OR_PI * u2);
+            z[4 * j + 2 * a + 1] = rho * sin(2.0 * OR_PI * u2);
+        }
+    }
+    const double st = sqrt(tx);
+    for (int32_t d = 0; d < D; ++d) {
+        double step = mx[d] + st * z[d];
+        int64_t dq = (int64_t)llrint(step * 4294967296.0);
+        qy[d] = qx[d] + (uint32_t)(uint64_t)dq;
+        delta[d] = (double)(int32_t)(qy[d] - qx[d]) * (1.0 / 4294967296.0);
+    }
+    int32_t ky = or_region_of(c, qy);
+    double fy[3];
+    if (or_path_grad(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy, gy) != 1) {
+        fy[0] = fy[1] = fy[2] = 0.0;
+        for (int32_t d = 0; d < D; ++d) gy[d] = 0.0;
+        c->st[5]++;
+    }
+    const double ty = c->p.mala_tau * (double)c->sig[ky] * (double)c->sig[ky];
+    mala_drift(c, gy, ty, my);
+    double piy = luminance(fy);
+    double ptx = c->pi[chain] / weight_of(c, kx), pty = piy / weight_of(c, ky);
+    double a;
+    if (!(pty > 0)) {
+        a = 0.0;
+    } else if (!(ptx > 0)) {
+        a = 1.0;
+    } else {
+        double lr = log(pty) - log(ptx);
+        if (!(c->p.debug_flags & 2)) {   /* bit 1: planted mistake, proposal densities dropped */
+            double back[OR_MAX_GRAD];
+            for (int32_t d = 0; d < D; ++d) back[d] = -delta[d];
+            lr += mala_logq(D, ty, back, my) - mala_logq(D, tx, delta, mx);
+        }
+        a = lr >= 0 ? 1.0 : exp(lr);
+    }
+    int32_t acc = xi < a;
+    c->mala_st[0]++;
+    if (acc) {
+        memcpy(qx, qy, sizeof(uint32_t) * (size_t)D);
+        for (int x = 0; x < 3; ++x) c->f[3 * chain + x] = fy[x];
+        memcpy(&c->g[(size_t)chain * D], gy, sizeof(double) * (size_t)D);
+        c->pi[chain] = piy;
+        c->k[chain] = ky;
+        c->st[1]++;
+        c->mala_st[1]++;
+    }
+    c->h[c->k[chain]] += 1;
+    c->st[0]++;
+    splat(c, chain);
+}
+
 /* One Metropolis-Hastings mutation of chain `chain` (Alg. 1 lines 8-12, 19). */
 static void mutate(or_ctx* c, uint32_t chain)
 {
@@ -924,6 +1228,10 @@ static void mutate(or_ctx* c, uint32_t chain)
     draw(c->p.seed, c->mut, chain, 0u, r0);
     int32_t large = (r0[0] >> 8) < c->T_large;
     double xi = u24(r0[1]);
+    if (!large && c->g && (r0[0] >> 8) < c->T_large + c->T_mala) {
+        mala_mutate(c, chain, xi);
+        return;
+    }
     int32_t kx = c->k[chain];
     if (large) large_step(c, chain, c->mut, qy);
     else small_step(c, chain, c->mut, kx, qx, qy);
@@ -1063,6 +1371,10 @@ int32_t or_init(or_ctx* c)
         or_path_eval(c->s, p->width, p->height, p->max_depth, qc, &c->f[3 * ch], NULL, NULL);
         c->pi[ch] = luminance(&c->f[3 * ch]);
         c->k[ch] = or_region_of(c, qc);
+        if (c->g) {
+            double fg[3];
+            or_path_grad(c->s, p->width, p->height, p->max_depth, qc, fg, &c->g[(size_t)ch * c->D]);
+        }
     }
     c->st[7] = (uint64_t)(K * p->n_chains);
     c->nU = (uint64_t)(K * p->n_chains);
@@ -1108,6 +1420,10 @@ int32_t or_set_state(or_ctx* c, uint32_t chain, const uint32_t* q)
     or_path_eval(c->s, c->p.width, c->p.height, c->p.max_depth, qc, &c->f[3 * chain], NULL, NULL);
     c->pi[chain] = luminance(&c->f[3 * chain]);
     c->k[chain] = or_region_of(c, qc);
+    if (c->g) {
+        double fg[3];
+        or_path_grad(c->s, c->p.width, c->p.height, c->p.max_depth, qc, fg, &c->g[(size_t)chain * c->D]);
+    }
     return 0;
 }
 
@@ -1210,3 +1526,5 @@ double* or_weight(or_ctx* c) { return c->w; }
 float* or_sigma(or_ctx* c) { return c->sig; }
 double* or_image_acc(or_ctx* c) { return c->img; }
 void or_stats(const or_ctx* c, uint64_t out[8]) { memcpy(out, c->st, sizeof c->st); }
+void or_mala_stats(const or_ctx* c, uint64_t out[2]) { memcpy(out, c->mala_st, sizeof c->mala_st); }
+const double* or_state_grad(const or_ctx* c, uint32_t chain) { return c->g ? &c->g[(size_t)chain * c->D] : NULL; }

@@ -57,12 +57,25 @@ typedef struct {
     double   alpha_star, gamma_max, gamma_scale;
     double   lambda_init, lambda_min, lambda_max;
     double   w_floor;
-    int32_t  debug_flags;      /* tests only: bit 0 drops the reverse-kernel factor */
+    int32_t  debug_flags;      /* tests only: bit 0 drops the reverse-kernel factor,
+                                  bit 1 the Langevin proposal-density ratio */
     int32_t  partition;        /* 0 uniform grid (Sec. 6.1), 1 quadtree (Sec. 6.2) */
     int32_t  qt_max_leaves, qt_max_depth;
     int64_t  qt_split;         /* M_split: visits since the last pass that split a leaf */
     int64_t  qt_refine;        /* M_refine: mutations between refinement passes */
+    /* Langevin (MALA) strategy: probability, step tau (scaled by sigma_k^2 of
+     * the current state's region) and the bound on the drift's norm */
+    double   p_mala, mala_tau, mala_drift_max;
 } or_params;
+
+/* Gradient of log pi(u), pi = l(f(u)), over the D = 2 + 5 max_depth
+ * coordinates (2 for the toy integrand), by forward-mode differentiation in
+ * binary64 along the path the primal walk takes (hits, light choice and
+ * visibility fixed).  f receives f(u).  Returns 1 (grad = 0 where pi = 0),
+ * 0 when the path meets a non-Lambertian surface it would differentiate
+ * through or is not finite (grad = 0), -1 when D exceeds 62. */
+int32_t or_path_grad(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                     const uint32_t* q, double f[3], double* grad);
 
 /* Per-mutation hook (tests only): sees the proposal and may override the
  * proposal's contribution, acceptance probability and decision. */
@@ -129,6 +142,10 @@ double*   or_weight(or_ctx* c);       /* w_k [m] */
 float*    or_sigma(or_ctx* c);        /* sigma_k [m] binary32 */
 double*   or_image_acc(or_ctx* c);    /* [H][W][3] unnormalised */
 void      or_stats(const or_ctx* c, uint64_t out[8]);
+/* Langevin moves proposed and accepted. */
+void      or_mala_stats(const or_ctx* c, uint64_t out[2]);
+/* Gradient of log pi at chain's current state ([D] doubles; Langevin runs only). */
+const double* or_state_grad(const or_ctx* c, uint32_t chain);
 /* Quadtree partition: copies child [nodes][4] (-1 leaf), leaf region id
  * [nodes] (-1 internal) and depth [nodes]; returns the node count. */
 int32_t   or_quadtree(const or_ctx* c, int32_t* child, int32_t* leaf, int32_t* depth, int32_t cap_nodes);
