@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 2
+#define RMLT_ABI_VERSION 3
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -105,6 +105,14 @@ typedef struct {
     int32_t qt_pad_;
     int64_t qt_split;          /* quadtree: M_split, visits since the last pass that split a leaf */
     int64_t qt_refine;         /* quadtree: M_refine, mutations (all chains) between passes */
+    /* Langevin (MALA) strategy, an extension beyond the paper: with probability
+     * p_mala a mutation proposes y = x + m + sqrt(tau) xi, tau = mala_tau
+     * sigma_{k(x)}^2 (the region's adapted scale), m = (tau / 2) grad log pi(x)
+     * scaled to norm <= mala_drift_max, xi standard normal; the acceptance
+     * carries the ratio of the state-dependent proposal densities.  Its moves
+     * do not feed the adaptation statistics.  Needs a Lambertian scene (or the
+     * toy integrand), the chain kernel, and no trace instrument.  0 = off. */
+    double p_mala, mala_tau, mala_drift_max;
 } rmlt_chain_params;
 
 typedef struct {
@@ -123,6 +131,7 @@ typedef struct {
                                   batches, finish/setup batches; warp lifetimes (sum, max) */
     uint64_t waves;            /* wavefront form: waves run (one trace pass each), summed over epochs */
     uint64_t wave_limit_hits;  /* wavefront form: epochs stopped by the wave limit (0 unless a bug) */
+    uint64_t mala, mala_accepted;   /* Langevin moves proposed and accepted */
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -223,6 +232,26 @@ rmlt_status rmlt_read_stats(rmlt_ctx* ctx, rmlt_stats* out);
  * record stores enabled. */
 rmlt_status rmlt_set_trace(rmlt_ctx* ctx, rmlt_trace_record* records, uint64_t capacity,
                            double* lambdas, uint64_t lambda_capacity, uint32_t chain_stride);
+
+/* Gradient of log pi(u), pi = l(f(u)), at n points: q [D][n] u32 primary-
+ * sample words (u = q 2^-32, D = 2 + 5 max_depth of the chains, 2 for the toy
+ * integrand), all device memory.  Outputs (each may be NULL): f [3][n] float,
+ * logpi [n] float (-inf where pi = 0), grad [D][n] float, d log pi / d u.
+ * Evaluated by the chain kernel's path functions with a record of each
+ * bounce, then an adjoint sweep from the last bounce back to the camera
+ * (reverse-mode differentiation); hits, light choice and visibility are held
+ * fixed, so this is the gradient of the smooth piece of f containing u, and 0
+ * where pi = 0.  Lambertian and emitting surfaces only.  Needs
+ * rmlt_init_chains (depth, image size); asynchronous on the context stream.
+ * Errors: RMLT_E_STATE, RMLT_E_INVALID_ARG (host pointers, a GGX scene),
+ * RMLT_E_CUDA. */
+rmlt_status rmlt_path_grad(rmlt_ctx* ctx, const uint32_t* q, int64_t n, float* f, float* logpi, float* grad);
+
+/* grad log pi of the chains' current states, [D][n_chains] floats (host or
+ * device), for chains with the Langevin strategy.  A state reached by another
+ * strategy holds NaN in dimension 0 until a Langevin move needs its gradient.
+ * RMLT_E_STATE without the Langevin strategy. */
+rmlt_status rmlt_read_chain_grad(rmlt_ctx* ctx, float* g);
 
 /* Count BVH node visits and triangle tests in rmlt_stats (enable = 1), using
  * an instrumented build of the same chain kernel; enable = 0 returns to the

@@ -22,6 +22,7 @@
 
 #define OR_MAX_DIM 256
 #define OR_MAX_GRAD 62          /* dimensions of the gradient (2 + 5 x 12) */
+#define OR_MALA_TAU_MAX 0.01    /* Langevin step bound: std <= 0.1 keeps the nearest-image density exact */
 #define OR_WIN 1e-4            /* scene-relative window of the decision margin (10x the exclusion threshold) */
 #define OR_INF (1.0 / 0.0)
 #define OR_PI 3.14159265358979323846
@@ -1121,8 +1122,10 @@ static void splat(or_ctx* c, int32_t chain)
 /* bounded): y = x + m_x + sqrt(tau_x) xi, m_x = (tau_x / 2) grad log pi(x)  */
 /* scaled to norm <= drift_max, xi ~ N(0, I) by Box-Muller from the          */
 /* mutation's Philox draws (call 1 + j gives dims 4j..4j+3), on the torus    */
-/* with nearest-image displacements.  tau_x = tau sigma_{k(x)}^2: the step   */
-/* adapts with the region of the current state, so the reverse density uses */
+/* with nearest-image displacements.  tau_x = min(tau sigma_{k(x)}^2, 0.01): */
+/* the step adapts with the region of the current state (a standard        */
+/* deviation of at most 0.1 keeps the nearest-image density exact to       */
+/* e^-12), so the reverse density uses                                      */
 /* tau_{k(y)} and the ratio keeps its normalising factors.  Not in the      */
 /* paper (gradient methods appear only as related work); the region weight  */
 /* is constant inside a region, so grad log pi~ = grad log pi.              */
@@ -1157,7 +1160,7 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
     uint32_t* qx = &c->q[(size_t)chain * D];
     const double* gx = &c->g[(size_t)chain * D];
     const int32_t kx = c->k[chain];
-    const double tx = c->p.mala_tau * (double)c->sig[kx] * (double)c->sig[kx];
+    const double tx = dmin(c->p.mala_tau * (double)c->sig[kx] * (double)c->sig[kx], OR_MALA_TAU_MAX);
     double mx[OR_MAX_GRAD], my[OR_MAX_GRAD], delta[OR_MAX_GRAD], gy[OR_MAX_GRAD], z[OR_MAX_GRAD + 3];
     mala_drift(c, gx, tx, mx);
     for (int32_t j = 0; 4 * j < D; ++j) {
@@ -1185,7 +1188,7 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
         for (int32_t d = 0; d < D; ++d) gy[d] = 0.0;
         c->st[5]++;
     }
-    const double ty = c->p.mala_tau * (double)c->sig[ky] * (double)c->sig[ky];
+    const double ty = dmin(c->p.mala_tau * (double)c->sig[ky] * (double)c->sig[ky], OR_MALA_TAU_MAX);
     mala_drift(c, gy, ty, my);
     double piy = luminance(fy);
     double ptx = c->pi[chain] / weight_of(c, kx), pty = piy / weight_of(c, ky);
@@ -1273,6 +1276,10 @@ static void mutate(or_ctx* c, uint32_t chain)
         c->pi[chain] = piy;
         c->k[chain] = ky;
         c->st[1]++;
+        if (c->g) {   /* the Langevin strategy needs grad log pi of every state */
+            double fg[3];
+            or_path_grad(c->s, c->p.width, c->p.height, c->p.max_depth, qx, fg, &c->g[(size_t)chain * D]);
+        }
     }
     c->h[c->k[chain]] += 1;
     c->st[0]++;

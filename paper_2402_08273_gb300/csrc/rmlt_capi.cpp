@@ -71,6 +71,7 @@ struct rmlt_ctx {
     uint64_t held = 0;
 
     bool have_scene = false, have_chains = false, failed = false;
+    bool scene_lambert = true;   // every material Lambertian: the path map is differentiable (Langevin strategy)
     DevScene S;
     double tan_half = 1.0;
     uint64_t scene_hash = 0;
@@ -240,6 +241,8 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
         if (M.type == RMLT_GGX && !(M.roughness >= 1e-3f && M.roughness <= 1.f))
             return fail(RMLT_E_INVALID_SCENE, "material %d: GGX roughness outside [1e-3, 1]", m);
     }
+    bool lambert = true;
+    for (int m = 0; m < s->n_mats; ++m) lambert = lambert && s->mats[m].type == RMLT_LAMBERT;
     const int nt = s->n_tris;
     std::vector<float> tv((size_t)9 * nt);
     for (int i = 0; i < nt; ++i) {
@@ -375,6 +378,7 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     h = fnv64(mat4.data(), mat4.size() * sizeof(float4), h);
     c->scene_hash = fnv64(&cam, sizeof cam, h);
     c->have_scene = true;
+    c->scene_lambert = lambert;
     return RMLT_OK;
 }
 
@@ -395,6 +399,7 @@ rmlt_status rmlt_load_toy_integrand(rmlt_ctx* c, const double* params)
     c->S = S;
     c->scene_hash = fnv64(params, 10 * sizeof(double), 77);
     c->have_scene = true;
+    c->scene_lambert = true;
     return RMLT_OK;
 }
 
@@ -423,6 +428,14 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
     if (!(p->w_floor >= 0.0 && p->w_floor <= 1.0)) return fail(RMLT_E_INVALID_ARG, "w_floor outside [0,1]");
     if (p->partition != RMLT_PARTITION_GRID && p->partition != RMLT_PARTITION_QUADTREE)
         return fail(RMLT_E_INVALID_ARG, "unknown partition");
+    if (!(p->p_mala >= 0.0 && p->p_mala <= 1.0 && p->p_large + p->p_mala <= 1.0))
+        return fail(RMLT_E_INVALID_ARG, "p_mala outside [0, 1 - p_large]");
+    if (p->p_mala > 0.0) {
+        if (!(p->mala_tau > 0.0 && p->mala_tau <= 1.0 && p->mala_drift_max > 0.0 && p->mala_drift_max <= 0.5))
+            return fail(RMLT_E_INVALID_ARG, "Langevin strategy: need 0 < mala_tau <= 1, 0 < mala_drift_max <= 1/2");
+        if (!c->scene_lambert)
+            return fail(RMLT_E_INVALID_ARG, "the Langevin strategy differentiates the path map: Lambertian scenes only");
+    }
     if (p->partition == RMLT_PARTITION_QUADTREE) {
         if (p->target_mode != RMLT_TARGET_PLAIN) return fail(RMLT_E_INVALID_ARG, "the quadtree partition needs the plain target");
         if (p->qt_max_leaves < 1 || p->qt_max_leaves > (1 << 20) || p->qt_max_depth < 0 || p->qt_max_depth > 24 ||
@@ -490,6 +503,13 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
         if ((st = c->alloc_n(pool, nodes, &Ch.qt_depth))) return st;
         if ((st = c->alloc_n(pool, 2, &Ch.qt_state))) return st;
     }
+    if (p->p_mala > 0.0) {
+        if ((st = c->alloc_n(pool, C * Ch.D, &Ch.G))) return st;
+        double tm = std::ceil(p->p_mala * 16777216.0);
+        Ch.T_mala = (uint32_t)(tm < 1 ? 1 : (tm > 16777216.0 ? 16777216.0 : tm));
+        Ch.mala_tau = (float)p->mala_tau;
+        Ch.mala_drift_max = (float)p->mala_drift_max;
+    }
     c->since_refine = 0;
     Ch.seed_lo = (uint32_t)p->seed;
     Ch.seed_hi = (uint32_t)(p->seed >> 32);
@@ -536,6 +556,7 @@ rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     }
     B.total = c->d_total;
     cudaError_t e = launch_bootstrap(c->S, Ch, nb, B, c->stream);
+    if (e == cudaSuccess && Ch.G) e = launch_state_gradients(c->S, Ch, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->release(scratch);
     if (e != cudaSuccess) {
@@ -556,6 +577,8 @@ rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
     if (st) return st;
     if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
     if (c->failed) return fail(RMLT_E_STATE, "context failed earlier: %s", g_err.c_str());
+    if (c->Ch.T_mala && (c->wavefront || c->tr))
+        return fail(RMLT_E_STATE, "the Langevin strategy runs in the chain kernel without the trace instrument");
     const uint64_t E = (uint64_t)c->Ch.E;
     const uint64_t n_ep = (n_mutations + E - 1) / E;
     const uint32_t n_traced = (uint32_t)(((uint64_t)c->Ch.C + c->tr_stride - 1) / c->tr_stride);
@@ -745,6 +768,8 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     for (int i = 0; i < 5; ++i) out->cycles[i] = s[kStCycTrav + i];
     out->waves = s[kStWaves];
     out->wave_limit_hits = s[kStWaveLimit];
+    out->mala = s[kStMala];
+    out->mala_accepted = s[kStMalaAcc];
     return RMLT_OK;
 }
 
@@ -775,6 +800,37 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* c, int trace_ctas_per_sm, int setup_cta
     c->wf_trace_cps = trace_ctas_per_sm;
     c->wf_setup_cps = setup_ctas_per_sm;
     c->wf_refill = refill_lanes;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_read_chain_grad(rmlt_ctx* c, float* g)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!g) return fail(RMLT_E_INVALID_ARG, "g is NULL");
+    if (!c->have_chains || !c->Ch.G) return fail(RMLT_E_STATE, "no chains with the Langevin strategy");
+    CK(cudaMemcpyAsync(g, c->Ch.G, sizeof(float) * (size_t)c->Ch.D * c->Ch.C, cudaMemcpyDefault, c->stream),
+       "read gradients");
+    return sync(c, "read gradients");
+}
+
+rmlt_status rmlt_path_grad(rmlt_ctx* c, const uint32_t* q, int64_t n, float* f, float* logpi, float* grad)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first (it fixes depth and image size)");
+    if (!c->scene_lambert) return fail(RMLT_E_INVALID_ARG, "the gradient covers Lambertian scenes only");
+    if (n < 0 || n > (1ll << 31)) return fail(RMLT_E_INVALID_ARG, "n outside [0, 2^31]");
+    if (!q) return fail(RMLT_E_INVALID_ARG, "q is NULL");
+    for (const void* ptr : {(const void*)q, (const void*)f, (const void*)logpi, (const void*)grad}) {
+        if (!ptr) continue;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(RMLT_E_INVALID_ARG, "q and the outputs must be device pointers");
+        }
+    }
+    CK(launch_path_grad(c->S, c->Ch, q, n, f, logpi, grad, c->stream), "rmlt_path_grad");
     return RMLT_OK;
 }
 
@@ -966,6 +1022,14 @@ rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
         }
     }
     std::fclose(fp);
+    if (c->Ch.G) {   // gradients of the restored states (not stored: a function of q)
+        cudaError_t e = launch_state_gradients(c->S, c->Ch, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            drop_chains(c);
+            return cuda_fail(e, "restore gradients");
+        }
+    }
     c->mut = h.mut;
     c->epochs = h.epochs;
     c->n_boot = h.n_boot;
@@ -1024,6 +1088,7 @@ rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
     if (c->Ch.E != b->m[0]->Ch.E) return fail(RMLT_E_INVALID_ARG, "member %d: epoch_len differs from member 0", i);
     if (c->tr) return fail(RMLT_E_STATE, "member %d: the trace instrument is set", i);
     if (c->wavefront) return fail(RMLT_E_STATE, "member %d: the wavefront form is set", i);
+    if (c->Ch.T_mala) return fail(RMLT_E_STATE, "member %d: the Langevin strategy is set", i);
     return RMLT_OK;
 }
 

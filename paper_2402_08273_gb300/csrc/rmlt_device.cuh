@@ -508,6 +508,171 @@ __device__ __forceinline__ float toy_eval(const DevScene& S, uint32_t q0, uint32
     return f;
 }
 
+// ---------------------------------------------------------------------------
+// gradient of log pi(u) by reverse-mode differentiation (adjoint): the path
+// is evaluated once with the functions above while each bounce's ray, hit
+// distance, normal and throughput are recorded; the adjoint sweep then runs
+// from the last bounce back to the camera.  Discrete choices (hit triangle,
+// light triangle, visibility) are held fixed: this is the gradient of the
+// smooth piece of f containing u.  Covers Lambertian and emitting surfaces
+// (a Lambertian throughput is constant, so only the geometry carries
+// derivatives): dims 3 + 5b, 4 + 5b move the light point, 5 + 5b, 6 + 5b the
+// continuation direction, 0 and 1 the camera ray.
+// ---------------------------------------------------------------------------
+constexpr float kMalaTauMax = 0.01f;
+
+struct GradRec {
+    V3 o, d;          // the ray that found bounce b's hit
+    float t;
+    V3 ns;            // oriented normal at the hit
+    V3 T;             // throughput at the hit
+    int mat;
+    int nee;          // 1: the next-event sample was unoccluded and counted
+    int cont;         // 1: the BSDF continuation was drawn
+};
+
+// Forward evaluation with the record; returns the number of recorded bounces
+// (-1 after a traversal-stack overflow, -2 on a non-Lambertian surface).
+template <bool BRUTE, class Y>
+__device__ __forceinline__ int path_forward_rec(const DevScene& S, const float4* s_tris, uint32_t* stack, Y y,
+                                                int max_depth, GradRec* rec, V3& Lout, unsigned& rays)
+{
+    Path p;
+    Trav T;
+    unsigned nn = 0, nt = 0;
+    path_begin(p, S, y);
+    int nb = 0;
+    Lout = {0.f, 0.f, 0.f};
+    while (true) {
+        trav_begin(T, p.o, p.d, p.tmax, 0);
+        while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        }
+        ++rays;
+        if (T.overflow) return -1;
+        if (T.tri < 0) break;
+        const V3 o = p.o, d = p.d, Tb = p.T;
+        const Hit h{T.t, T.tri, T.ta, T.tb, T.tc};
+        // an emitter that ends the path adds only its constant emission: no record
+        if (!shade_hit<BRUTE>(p, S, h)) break;
+        if (__ldg(&S.mats[3 * p.mat]).w != 0.0f) return -2;
+        GradRec& r = rec[nb];
+        r.o = o;
+        r.d = d;
+        r.t = T.t;
+        r.T = Tb;
+        r.ns = p.ns;
+        r.mat = p.mat;
+        r.nee = 0;
+        r.cont = 0;
+        ++nb;
+        if (nee_sample<BRUTE>(p, S, s_tris, y)) {
+            trav_begin(T, p.o, p.d, p.tmax, 1);
+            while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+            }
+            ++rays;
+            if (T.overflow) return -1;
+            if (T.tri < 0) {
+                p.L = p.L + p.P;
+                r.nee = 1;
+            }
+        }
+        path_continue(p, S, y, max_depth);
+        if (p.done) break;
+        r.cont = 1;
+    }
+    Lout = p.L;
+    return nb;
+}
+
+// Adjoint sweep: g[d] = d log pi / d u_d for d < D (zero where pi <= 0).
+template <class Y, class G>
+__device__ __forceinline__ void path_adjoint(const DevScene& S, Y y, const GradRec* rec, int nb, V3 L, G g, int D)
+{
+    for (int d = 0; d < D; ++d) g[d] = 0.0f;
+    const float pi = lum(L.x, L.y, L.z);
+    if (!(pi > 0.0f)) return;
+    const float inv_pi = 1.0f / pi;
+    V3 ob = {0.f, 0.f, 0.f}, db = {0.f, 0.f, 0.f};   // adjoints of the next bounce's ray
+    for (int b = nb - 1; b >= 0; --b) {
+        const GradRec& r = rec[b];
+        const V3 ns = r.ns;
+        const V3 x = r.o + r.d * r.t;
+        V3 xb = ob;                                    // o_{b+1} = x + eps ns
+        if (r.cont) {                                  // d_{b+1}: Lambert cosine sample of (bu, bv)
+            const float bu = u24(y[5 + 5 * b]), bv = u24(y[6 + 5 * b]);
+            V3 ft, fb;
+            frame(ns, ft, fb);
+            float sp, cp;
+            sincospif(2.0f * bv, &sp, &cp);
+            const float rr = sqrtf(bu), lz = sqrtf(fmaxf(0.0f, 1.0f - bu));
+            const float ir = rr > 0.0f ? 0.5f / rr : 0.0f, il = lz > 0.0f ? 0.5f / lz : 0.0f;
+            const V3 d_bu = ft * (cp * ir) + fb * (sp * ir) - ns * il;
+            const V3 d_bv = (fb * (rr * cp) - ft * (rr * sp)) * 6.28318530717958648f;
+            g[5 + 5 * b] = dot(db, d_bu);
+            g[6 + 5 * b] = dot(db, d_bv);
+        }
+        if (r.nee) {                                   // P_b = T (rho / pi) Le cx cl / dist^2 A
+            const float ls = u24(y[2 + 5 * b]), lu = u24(y[3 + 5 * b]), lv = u24(y[4 + 5 * b]);
+            int lo = 0, hi = S.n_lights - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(&S.light_cdf[mid]) > ls) hi = mid; else lo = mid + 1;
+            }
+            const int lt = __ldg(&S.light_tri[lo]);
+            const float4 la = __ldg(&S.tris[3 * lt]), lb = __ldg(&S.tris[3 * lt + 1]), lc = __ldg(&S.tris[3 * lt + 2]);
+            const float su = sqrtf(lu), b1 = su * (1.0f - lv), b2 = su * lv;
+            const V3 pl = xyz(la) + xyz(lb) * b1 + xyz(lc) * b2;
+            const V3 wv = pl - x;
+            const float s2 = dot(wv, wv);
+            const V3 ln = normalize(cross(xyz(lb), xyz(lc)));
+            const float a = dot(ns, wv), c = -dot(ln, wv);
+            const float gg = a * c / (s2 * s2) * S.light_area;
+            const float4 m0 = __ldg(&S.mats[3 * r.mat]);
+            const float4 lm1 = __ldg(&S.mats[3 * __float_as_int(la.w) + 1]);
+            const float k1 = 0.318309886183790672f;
+            const float kappa = lum(r.T.x * m0.x * k1 * lm1.x, r.T.y * m0.y * k1 * lm1.y, r.T.z * m0.z * k1 * lm1.z) *
+                                inv_pi;
+            const V3 dg = (ns * c - ln * a) * (S.light_area / (s2 * s2)) - wv * (4.0f * gg / s2);
+            const V3 wvb = dg * kappa;
+            xb = xb - wvb;
+            const V3 d_lu = (xyz(lb) * (1.0f - lv) + xyz(lc) * lv) * (su > 0.0f ? 0.5f / su : 0.0f);
+            const V3 d_lv = (xyz(lc) - xyz(lb)) * su;
+            g[3 + 5 * b] = dot(wvb, d_lu);
+            g[4 + 5 * b] = dot(wvb, d_lv);
+        }
+        // hit on the triangle's plane: x = o + t d, t = (v0 - o).n / d.n
+        const float xd = dot(xb, r.d), dn = dot(r.d, ns);
+        ob = xb - ns * (xd / dn);
+        db = ob * r.t;
+    }
+    // camera: d_0 = dr / |dr|, dr = fwd + right sx + up sy
+    const float sx = (2.0f * u24(y[0]) - 1.0f) * S.tan_x;
+    const float sy = (1.0f - 2.0f * u24(y[1])) * S.tan_y;
+    const V3 fw = {S.cam_fwd[0], S.cam_fwd[1], S.cam_fwd[2]};
+    const V3 rt = {S.cam_right[0], S.cam_right[1], S.cam_right[2]};
+    const V3 up = {S.cam_up[0], S.cam_up[1], S.cam_up[2]};
+    const V3 dr = fw + rt * sx + up * sy;
+    const float il = 1.0f / sqrtf(dot(dr, dr));
+    const V3 d0 = dr * il;
+    const V3 drb = (db - d0 * dot(d0, db)) * il;
+    g[0] = dot(drb, rt) * (2.0f * S.tan_x);
+    g[1] = -dot(drb, up) * (2.0f * S.tan_y);
+}
+
+// toy integrand: f and grad log f in closed form (D = 2)
+template <class G>
+__device__ __forceinline__ float toy_grad(const DevScene& S, uint32_t q0, uint32_t q1, G g)
+{
+    const float u0 = u24(q0), u1 = u24(q1);
+    const float f = toy_eval(S, q0, q1);
+    const float dx = u0 - S.toy_p[7], dy = u1 - S.toy_p[8];
+    const float e = S.toy_p[6] * expf(-(dx * dx + dy * dy) / (2.0f * S.toy_p[9] * S.toy_p[9]));
+    const float k = -e / (S.toy_p[9] * S.toy_p[9] * f);
+    g[0] = f > 0.0f ? k * dx : 0.0f;
+    g[1] = f > 0.0f ? k * dy : 0.0f;
+    return f;
+}
+
 __device__ __forceinline__ void stage_triangles(const DevScene& S, float4* s_tris)
 {
     for (int i = threadIdx.x; i < 3 * S.n_tris; i += blockDim.x) s_tris[i] = __ldg(&S.tris[i]);
@@ -536,14 +701,143 @@ struct ChainLane {
     int j, large, ky, early;
     float xi;
     V3 fy;
+    // Langevin strategy: this mutation is one (its acceptance probability
+    // decided at the proposal), and moves proposed / accepted so far
+    int mala;
+    float amala;
+    unsigned n_mala, n_mala_acc;
 };
+
+// ---------------------------------------------------------------------------
+// Langevin strategy (MALA with a bounded drift): y = x + m_x + sqrt(tau_x) xi,
+// m_x = (tau_x / 2) grad log pi(x) scaled to norm <= drift_max, tau_x =
+// min(tau sigma_{k(x)}^2, 0.01) (a standard deviation of at most 0.1 keeps
+// the nearest-image density on the torus exact to e^-12); xi ~ N(0, I) by
+// Box-Muller from the mutation's Philox draws
+// (call 1 + j gives dims 4j..4j+3).  The acceptance carries the ratio of the
+// state-dependent proposal densities q(x|y) / q(y|x) with nearest-image
+// displacements on the torus; the region weight of the weighted target is
+// constant inside a region and drops out of the gradient.
+// ---------------------------------------------------------------------------
+template <bool BRUTE, class Y>
+__device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& Ch, int c, uint32_t mlo, uint32_t mhi,
+                                           ChainLane& L, Y y, uint32_t* stack, const float4* s_tris,
+                                           unsigned& rays)
+{
+    const int C = Ch.C, D = Ch.D;
+    if (isnan(Ch.G[c])) {
+        // the state was reached by another strategy: its gradient first
+        uint32_t yx[kMaxDim];
+        float gx[kMaxDim];
+        for (int d = 0; d < D; ++d) yx[d] = Ch.q[(size_t)d * C + c];
+        if (S.toy) {
+            toy_grad(S, yx[0], yx[1], gx);
+        } else {
+            GradRec rec[RMLT_MAX_DEPTH];
+            V3 fx;
+            const int nb = path_forward_rec<BRUTE>(S, s_tris, stack, yx, Ch.max_depth, rec, fx, rays);
+            if (nb < 0) {
+                for (int d = 0; d < D; ++d) gx[d] = 0.0f;
+            } else {
+                path_adjoint(S, yx, rec, nb, fx, gx, D);
+            }
+        }
+        for (int d = 0; d < D; ++d) Ch.G[(size_t)d * C + c] = gx[d];
+    }
+    const float sgx = Ch.sig[L.kx];
+    const float tx = fminf(Ch.mala_tau * sgx * sgx, kMalaTauMax);
+    const float dmax = Ch.mala_drift_max;
+    double n2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const float m = 0.5f * tx * Ch.G[(size_t)d * C + c];
+        n2 += (double)m * m;
+    }
+    const float scx = n2 > (double)dmax * dmax ? (float)(dmax / sqrt(n2)) : 1.0f;
+    const float stx = sqrtf(tx);
+    double sf = 0.0;   // |delta - m_x|^2
+    float delta[kMaxDim];
+    for (int jj = 0; 4 * jj < D; ++jj) {
+        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float u1 = ((float)(w[2 * a] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+            const float rho = sqrtf(-2.0f * logf(u1));
+            float sp, cp;
+            sincospif(2.0f * u24(w[2 * a + 1]), &sp, &cp);
+            const float z[2] = {rho * cp, rho * sp};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int d = 4 * jj + 2 * a + e;
+                if (d < D) {
+                    const uint32_t qx = Ch.q[(size_t)d * C + c];
+                    const float m = 0.5f * tx * Ch.G[(size_t)d * C + c] * scx;
+                    const float step = fmaf(stx, z[e], m);
+                    y[d] = qx + (uint32_t)(unsigned long long)__float2ll_rn(step * 4294967296.0f);
+                    const float dl = (float)(int32_t)(y[d] - qx) * 2.3283064365386963e-10f;
+                    delta[d] = dl;
+                    sf += (double)(dl - m) * (double)(dl - m);
+                }
+            }
+        }
+    }
+    L.mala = 1;
+    L.early = 0;
+    L.ky = region_of(Ch, y[0], y[1]);
+    float gy[kMaxDim];
+    V3 fy;
+    if (S.toy) {
+        const float v = toy_grad(S, y[0], y[1], gy);
+        fy = {v, v, v};
+    } else {
+        GradRec rec[RMLT_MAX_DEPTH];
+        const int nb = path_forward_rec<BRUTE>(S, s_tris, stack, y, Ch.max_depth, rec, fy, rays);
+        if (nb < 0) {
+            fy = {0.f, 0.f, 0.f};
+            for (int d = 0; d < D; ++d) gy[d] = 0.0f;
+        } else {
+            path_adjoint(S, y, rec, nb, fy, gy, D);
+        }
+    }
+    L.fy = fy;
+    const float sgy = Ch.sig[L.ky];
+    const float ty = fminf(Ch.mala_tau * sgy * sgy, kMalaTauMax);
+    n2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const float m = 0.5f * ty * gy[d];
+        n2 += (double)m * m;
+    }
+    const float scy = n2 > (double)dmax * dmax ? (float)(dmax / sqrt(n2)) : 1.0f;
+    double sb = 0.0;   // |-delta - m_y|^2
+    for (int d = 0; d < D; ++d) {
+        const double e = -(double)delta[d] - (double)(0.5f * ty * gy[d] * scy);
+        sb += e * e;
+    }
+    const float piy = lum(fy.x, fy.y, fy.z);
+    const float ptx = Ch.weighted ? L.pix / Ch.wf[L.kx] : L.pix;
+    const float pty = Ch.weighted ? piy / Ch.wf[L.ky] : piy;
+    float a;
+    if (!(pty > 0.0f) || !isfinite(piy)) {
+        a = 0.0f;
+    } else if (!(ptx > 0.0f)) {
+        a = 1.0f;
+    } else {
+        const double lr = log((double)pty) - log((double)ptx) - 0.5 * D * log((double)ty / (double)tx) -
+                          sb / (2.0 * (double)ty) + sf / (2.0 * (double)tx);
+        a = lr >= 0.0 ? 1.0f : (float)exp(lr);
+    }
+    L.amala = a;
+    if (L.xi < a)   // accepted (mutation_finish takes the same decision): keep grad log pi(y)
+        for (int d = 0; d < D; ++d) Ch.G[(size_t)d * C + c] = gy[d];
+}
 
 // Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1 line
 // 10) and decide the reverse-kernel support; returns false when the proposal
 // needs no path (rejected early, or the toy integrand evaluated directly).
-template <class Y>
+template <bool MALA = false, bool BRUTE = false, class Y>
 __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChains& Ch, int c, uint64_t mut0,
-                                               ChainLane& L, Y y, Path& p)
+                                               ChainLane& L, Y y, Path& p, uint32_t* stack = nullptr,
+                                               const float4* s_tris = nullptr, unsigned* rays = nullptr)
 {
     const int C = Ch.C, D = Ch.D;
     const uint64_t mut = mut0 + (uint64_t)L.j;
@@ -551,6 +845,13 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
     const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
     L.large = (r0.x >> 8) < Ch.T_large;
     L.xi = u24(r0.y);
+    if (MALA) {
+        L.mala = 0;
+        if (!L.large && (r0.x >> 8) < Ch.T_large + Ch.T_mala) {
+            mala_setup<BRUTE>(S, Ch, c, mlo, mhi, L, y, stack, s_tris, *rays);
+            return false;   // path and acceptance are done
+        }
+    }
     int R = 1;
     if (L.large) {
         for (int jj = 0; 4 * jj < D; ++jj) {
@@ -640,7 +941,7 @@ __device__ __forceinline__ void flush_state(const DevChains& Ch, ChainLane& L)
 
 // acceptance (Sec. 3.2 with the mixture of Sec. 5.2), adaptation statistics
 // of the current region (Alg. 1 lines 11-12), MH update (line 19), splat
-template <bool TRACE, class Y>
+template <bool TRACE, bool MALA = false, class Y>
 __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool traced, ChainLane& L,
                                                 Y y, unsigned (&st)[7])
 {
@@ -655,7 +956,9 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
         ++st[4];
     }
     float a;
-    if (L.early) {
+    if (MALA && L.mala) {
+        a = L.amala;   // decided with the proposal densities (mala_setup)
+    } else if (L.early) {
         a = 0.0f;
     } else {
         const float ptx = Ch.weighted ? L.pix / Ch.wf[L.kx] : L.pix;
@@ -663,7 +966,16 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
         a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
     }
     const int accept = L.xi < a;
-    if (L.large) {
+    if (MALA && L.mala) {
+        // Langevin moves do not feed the adaptation statistics of Alg. 1,
+        // which tune the small step
+        ++L.n_mala;
+        L.n_mala_acc += (unsigned)accept;
+    } else if (MALA && accept) {
+        Ch.G[c] = __int_as_float(0x7FC00000);   // the new state's gradient is computed when needed
+    }
+    if (MALA && L.mala) {
+    } else if (L.large) {
         ++st[1];
         if (!Ch.lf) atomicAdd(&Ch.Bk[L.ky], (double)piy);   // else added by the large-step kernel
     } else {

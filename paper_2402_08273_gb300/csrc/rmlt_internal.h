@@ -28,6 +28,8 @@ enum StatSlot {
     kStCycTrav, kStCycShade, kStCycSetup, kStCycLife, kStCycLifeMax,
     // wavefront form: waves run, epochs stopped by the wave limit
     kStWaves, kStWaveLimit,
+    // Langevin moves proposed and accepted
+    kStMala, kStMalaAcc,
     kStCount = 32
 };
 
@@ -97,6 +99,12 @@ struct DevChains {
     // lanes that wait before the warp shades / finishes and draws together
     int32_t batch_shade = 8, batch_setup = 8;
     int32_t adaptive_batch = 0;   // shrink the batches when few lanes are still working
+    // Langevin (MALA) strategy: gradients of the current states, the strategy
+    // threshold on the 24-bit strategy uniform (above T_large), step and
+    // drift bound
+    float* G = nullptr;           // [D][C] grad log pi at each chain's state
+    uint32_t T_mala = 0;
+    float mala_tau = 0.f, mala_drift_max = 0.f;
     // trace instrument
     rmlt_trace_record* trace = nullptr;
     unsigned long long trace_cap = 0, trace_base = 0;
@@ -175,6 +183,11 @@ struct BootScratch {
 
 cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace,
                                bool count_work, cudaStream_t st);
+// grad log pi of every chain's current state into c.G (Langevin strategy)
+cudaError_t launch_state_gradients(const DevScene& s, const DevChains& c, cudaStream_t st);
+// f, log pi and grad log pi at n points q [D][n] (D = c.D); any output may be NULL
+cudaError_t launch_path_grad(const DevScene& s, const DevChains& c, const uint32_t* q, long long n, float* f,
+                             float* logpi, float* grad, cudaStream_t st);
 cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st);
 cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st);
 cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot,

@@ -32,7 +32,7 @@ enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 }
 
 // The epoch of chain c (one thread); s_tris holds the staged triangles of a
 // brute-force scene, s_stack the block's traversal stacks.
-template <bool BRUTE, bool TRACE, bool COUNT>
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false>
 __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
                                                  const float4* s_tris, uint32_t* s_stack)
 {
@@ -58,6 +58,9 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     L.large = L.ky = L.early = 0;
     L.xi = 0.f;
     L.fy = {0.f, 0.f, 0.f};
+    L.mala = 0;
+    L.amala = 0.f;
+    L.n_mala = L.n_mala_acc = 0;
     const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
     uint32_t y[kMaxDim];
     // traversal stack in shared memory, one column per thread (conflict-free)
@@ -135,12 +138,12 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
             // a proposal rejected early (or the toy integrand) finishes at once
             for (int r = 0; r < 8 && (phase == kFinish || phase == kSetup); ++r) {
                 if (phase == kFinish) {
-                    mutation_finish<TRACE>(Ch, c, traced, L, y, st);
+                    mutation_finish<TRACE, MALA>(Ch, c, traced, L, y, st);
                     ++L.j;
                     phase = L.j < Ch.E ? kSetup : kIdle;
                 }
                 if (phase == kSetup) {
-                    if (mutation_setup(S, Ch, c, mut0, L, y, p)) {
+                    if (mutation_setup<MALA, BRUTE>(S, Ch, c, mut0, L, y, p, stack, s_tris, &st[5])) {
                         trav_begin(T, p.o, p.d, p.tmax, p.any);
                         phase = kTraverse;
                     } else {
@@ -175,6 +178,11 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
         const unsigned long long t = warp_sum(v[s]);
         if (lane == 0 && t) atomicAdd(&Ch.stats[s], t);
     }
+    if (MALA) {
+        const unsigned long long a = warp_sum(L.n_mala), b = warp_sum(L.n_mala_acc);
+        if (lane == 0 && a) atomicAdd(&Ch.stats[kStMala], a);
+        if (lane == 0 && b) atomicAdd(&Ch.stats[kStMalaAcc], b);
+    }
     if (COUNT && lane == 0) {
         for (int s = 0; s < 6; ++s) atomicAdd(&Ch.stats[kStIters + s], sched[s]);
         for (int s = 0; s < 3; ++s) atomicAdd(&Ch.stats[kStCycTrav + s], cyc[s]);
@@ -186,7 +194,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
 
 // mut0_dev, when set, holds the epoch's first mutation index on the device
 // (a graph replayed over several epochs advances it there)
-template <bool BRUTE, bool TRACE, bool COUNT>
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false>
 __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0,
                                                                   const unsigned long long* mut0_dev)
 {
@@ -194,7 +202,78 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
     __shared__ uint32_t s_stack[kStackSize * kChainBlock];
     if (BRUTE) stage_triangles(S, s_tris);
     if (mut0_dev) mut0 = *mut0_dev;
-    chain_epoch_body<BRUTE, TRACE, COUNT>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris, s_stack);
+    chain_epoch_body<BRUTE, TRACE, COUNT, MALA>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris,
+                                                 s_stack);
+}
+
+// grad log pi of the chains' current states (Langevin strategy: at
+// initialisation and after a restore)
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) state_grad_kernel(const DevScene S, const DevChains Ch)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Ch.C) return;
+    const int C = Ch.C, D = Ch.D;
+    uint32_t y[kMaxDim];
+    for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
+    float g[kMaxDim];
+    if (S.toy) {
+        toy_grad(S, y[0], y[1], g);
+    } else {
+        GradRec rec[RMLT_MAX_DEPTH];
+        V3 f;
+        unsigned rays = 0;
+        const int nb = path_forward_rec<BRUTE>(S, s_tris, s_stack + threadIdx.x, y, Ch.max_depth, rec, f, rays);
+        if (nb < 0) {
+            for (int d = 0; d < D; ++d) g[d] = 0.0f;
+        } else {
+            path_adjoint(S, y, rec, nb, f, g, D);
+        }
+    }
+    for (int d = 0; d < D; ++d) Ch.G[(size_t)d * C + c] = g[d];
+}
+
+// f, log pi and grad log pi at n given points q [D][n]
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) path_grad_kernel(const DevScene S, const DevChains Ch,
+                                                                const uint32_t* q, long long n, float* fo,
+                                                                float* logpi, float* grad)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int D = Ch.D;
+    uint32_t y[kMaxDim];
+    for (int d = 0; d < D; ++d) y[d] = q[(size_t)d * n + i];
+    float g[kMaxDim];
+    V3 f;
+    if (S.toy) {
+        const float v = toy_grad(S, y[0], y[1], g);
+        f = {v, v, v};
+    } else {
+        GradRec rec[RMLT_MAX_DEPTH];
+        unsigned rays = 0;
+        const int nb = path_forward_rec<BRUTE>(S, s_tris, s_stack + threadIdx.x, y, Ch.max_depth, rec, f, rays);
+        if (nb < 0) {
+            f = {0.f, 0.f, 0.f};
+            for (int d = 0; d < D; ++d) g[d] = 0.0f;
+        } else {
+            path_adjoint(S, y, rec, nb, f, g, D);
+        }
+    }
+    if (fo) {
+        fo[i] = f.x;
+        fo[n + i] = f.y;
+        fo[2 * n + i] = f.z;
+    }
+    if (logpi) logpi[i] = logf(lum(f.x, f.y, f.z));
+    if (grad)
+        for (int d = 0; d < D; ++d) grad[(size_t)d * n + i] = g[d];
 }
 
 // ---------------------------------------------------------------------------
@@ -610,9 +689,66 @@ cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const Batch
     return cudaGetLastError();
 }
 
+template <bool B>
+static cudaError_t launch_mala_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
+{
+    const int blocks = (c.C + kChainBlock - 1) / kChainBlock;
+    const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
+    auto kern = chain_epoch_kernel<B, false, false, true>;
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0, nullptr);
+    return cudaGetLastError();
+}
+
+template <class K>
+static cudaError_t launch_per_point(K kern, const DevScene& s, long long n, cudaStream_t st, size_t* shm_out)
+{
+    const size_t shm = s.brute ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
+    if (shm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    *shm_out = shm;
+    return cudaSuccess;
+}
+
+cudaError_t launch_state_gradients(const DevScene& s, const DevChains& c, cudaStream_t st)
+{
+    size_t shm = 0;
+    const unsigned blocks = (unsigned)((c.C + kChainBlock - 1) / kChainBlock);
+    cudaError_t e;
+    if (s.brute) {
+        if ((e = launch_per_point(state_grad_kernel<true>, s, c.C, st, &shm)) != cudaSuccess) return e;
+        state_grad_kernel<true><<<blocks, kChainBlock, shm, st>>>(s, c);
+    } else {
+        state_grad_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_path_grad(const DevScene& s, const DevChains& c, const uint32_t* q, long long n, float* f,
+                             float* logpi, float* grad, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    size_t shm = 0;
+    const unsigned blocks = (unsigned)((n + kChainBlock - 1) / kChainBlock);
+    cudaError_t e;
+    if (s.brute) {
+        if ((e = launch_per_point(path_grad_kernel<true>, s, n, st, &shm)) != cudaSuccess) return e;
+        path_grad_kernel<true><<<blocks, kChainBlock, shm, st>>>(s, c, q, n, f, logpi, grad);
+    } else {
+        path_grad_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c, q, n, f, logpi, grad);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace, bool count_work,
                                cudaStream_t st)
 {
+    if (c.T_mala) return s.brute ? launch_mala_epoch<true>(s, c, mut0, st) : launch_mala_epoch<false>(s, c, mut0, st);
     if (s.brute) {
         if (trace) return count_work ? launch_epoch_t<true, true, true>(s, c, mut0, st)
                                      : launch_epoch_t<true, true, false>(s, c, mut0, st);

@@ -56,7 +56,8 @@ class ChainParams(C.Structure):
                 ("gamma_scale", C.c_double), ("lambda_init", C.c_double),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("w_floor", C.c_double),
                 ("partition", C.c_int32), ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32),
-                ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64)]
+                ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64),
+                ("p_mala", C.c_double), ("mala_tau", C.c_double), ("mala_drift_max", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -65,7 +66,8 @@ class Stats(C.Structure):
                 ("rays", C.c_uint64), ("stack_overflow", C.c_uint64), ("epochs", C.c_uint64),
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
                 ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6),
-                ("cycles", C.c_uint64 * 5), ("waves", C.c_uint64), ("wave_limit_hits", C.c_uint64)]
+                ("cycles", C.c_uint64 * 5), ("waves", C.c_uint64), ("wave_limit_hits", C.c_uint64),
+                ("mala", C.c_uint64), ("mala_accepted", C.c_uint64)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -98,6 +100,8 @@ _SIGS = [
                                  C.c_uint32]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_probe_peaks", C.c_int, [C.c_int, C.c_void_p, _P(C.c_double), _P(C.c_double)]),
+    ("rmlt_path_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rmlt_read_chain_grad", C.c_int, [C.c_void_p, C.c_void_p]),
     ("rmlt_batch_create", C.c_int, [_P(C.c_void_p), _P(C.c_void_p), C.c_int]),
     ("rmlt_batch_set_order", C.c_int, [C.c_void_p, _P(C.c_int)]),
     ("rmlt_batch_set_shape", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -148,7 +152,8 @@ def default_params(**kw) -> dict:
              target_mode=TARGET_PLAIN, n_bootstrap=1 << 16, seed=1, p_large=0.3, s1=1 / 1024,
              s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
              lambda_min=-30.0, lambda_max=None, w_floor=1e-3, partition=0, qt_max_leaves=4096,
-             qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000)
+             qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3,
+             mala_drift_max=0.1)
     p.update(kw)
     if p["lambda_max"] is None:
         p["lambda_max"] = 2.0 * math.log(1.0 / (2.0 * p["s2"]))
@@ -333,6 +338,31 @@ class Renderer:
         _check(lib().rmlt_set_wavefront(self.h, int(trace_ctas_per_sm), int(setup_ctas_per_sm),
                                         int(refill_lanes), 1 if host_loop else 0))
 
+    def read_chain_grad(self) -> np.ndarray:
+        """grad log pi of the current states, [D, n_chains] (Langevin runs)."""
+        self._require_chains()
+        g = np.zeros((self.D, self.params["n_chains"]), np.float32)
+        _check(lib().rmlt_read_chain_grad(self.h, _ptr(g)))
+        return g
+
+    def path_grad(self, q, want_f: bool = False):
+        """(log pi [n], grad [D, n], f [3, n] or None) at primary-sample words
+        q [D, n] (a CUDA tensor of int32 / uint32 bits), by the adjoint kernel."""
+        torch = self._torch
+        if not (torch.is_tensor(q) and q.is_cuda and q.dim() == 2 and q.shape[0] == self.D):
+            raise RmltError(-1, f"q must be a CUDA tensor [D={self.D}, n]")
+        q = q.to(torch.int32).contiguous()
+        n = q.shape[1]
+        dev = q.device
+        logpi = torch.empty(n, dtype=torch.float32, device=dev)
+        grad = torch.empty((self.D, n), dtype=torch.float32, device=dev)
+        f = torch.empty((3, n), dtype=torch.float32, device=dev) if want_f else None
+        with torch.cuda.stream(self.stream):
+            _check(lib().rmlt_path_grad(self.h, C.c_void_p(q.data_ptr()), n,
+                                        C.c_void_p(f.data_ptr() if f is not None else 0),
+                                        C.c_void_p(logpi.data_ptr()), C.c_void_p(grad.data_ptr())))
+        return logpi, grad, f
+
     def set_work_counters(self, enable: bool):
         _check(lib().rmlt_set_work_counters(self.h, int(enable)))
 
@@ -365,6 +395,49 @@ class Renderer:
         nx = -(-self.params["width"] // self.params["region_px"])
         ny = -(-self.params["height"] // self.params["region_px"])
         self.m = nx * ny
+
+
+def u_to_words(u):
+    """Primary-sample coordinates u in [0, 1) (a tensor [..]) as the 32-bit
+    words the library takes (u = q 2^-32, floor), as int32 bits."""
+    import torch
+    q = torch.floor(u.detach().to(torch.float64) * 4294967296.0).clamp_(0, 4294967295.0).to(torch.int64)
+    return torch.where(q >= 2 ** 31, q - 2 ** 32, q).to(torch.int32)
+
+
+def _path_log_pi_function():
+    import torch
+
+    class PathLogPi(torch.autograd.Function):
+        """log pi(u) of the path map with its gradient from the adjoint kernel
+        (rmlt_path_grad): forward(u [n, D] in [0, 1), renderer) -> [n]."""
+
+        @staticmethod
+        def forward(ctx, u, renderer):
+            q = u_to_words(u).t().contiguous()
+            logpi, grad, _ = renderer.path_grad(q)
+            renderer.stream.synchronize()
+            ctx.save_for_backward(grad)
+            return logpi.to(u.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (grad,) = ctx.saved_tensors
+            return grad_out[:, None] * grad.t().to(grad_out.dtype), None
+
+    return PathLogPi
+
+
+_PLP = None
+
+
+def path_log_pi(u, renderer):
+    """Differentiable log pi(u): torch.autograd.Function around the adjoint
+    kernel.  u: CUDA tensor [n, D] of primary-sample coordinates in [0, 1)."""
+    global _PLP
+    if _PLP is None:
+        _PLP = _path_log_pi_function()
+    return _PLP.apply(u, renderer)
 
 
 class Batch:

@@ -107,3 +107,17 @@ def test_mala_needs_a_differentiable_scene(oracle_mod):
     sc = oracle_mod.Scene(S.two_rooms(2000, seed=0), use_bvh=True)   # GGX surfaces
     with pytest.raises(Exception):
         oracle_mod.Chains(sc, n_chains=16, width=32, height=32, region_px=8, max_depth=3, p_mala=0.5)
+
+
+def test_mala_with_adaptation_keeps_target(oracle_mod):
+    """Adaptation on (gamma as in Sec. 7.1): sigma_k, hence tau_k, keeps moving
+    per region while the histogram still converges to the region masses."""
+    ch = oracle_mod.Chains(oracle_mod.Scene(toy=TOY), n_chains=256, width=64, height=64, region_px=8,
+                           max_depth=0, epoch_len=16, n_bootstrap=1 << 14, p_large=0.1, p_mala=0.6,
+                           mala_tau=1e-3, mala_drift_max=0.1)
+    ch.init()
+    ch.run_epochs(300)
+    h = ch.hist.astype(float)
+    b = S.toy_region_masses(TOY, 64, 64, 8)
+    assert np.ptp(ch.lam) > 0.5
+    assert 0.5 * float(np.abs(h / h.sum() - b / b.sum()).sum()) < 0.025
