@@ -58,6 +58,12 @@ WORKLOADS = {
                     params=dict(n_chains=64, width=64, height=64, region_px=8, max_depth=5,
                                 epoch_len=16, n_bootstrap=1 << 16, p_large=0.3, seed=1),
                     mutations=10000, cpu_chains=64, cpu_epochs=200),
+    "cornell_d10": dict(desc="Cornell box (34+2 triangles, brute force), 64x64, 8-px regions, depth 10, "
+                             "2^16 chains x 256 mutations (the Langevin comparison's population)",
+                        scene=("cornell_box", {}),
+                        params=dict(n_chains=1 << 16, width=64, height=64, region_px=8, max_depth=10,
+                                    epoch_len=16, n_bootstrap=1 << 20, p_large=0.3, seed=1),
+                        mutations=256, cpu_chains=256, cpu_epochs=8),
     "corridor": dict(desc="glossy corridor lit through a slit, 2M triangles, 1920x1080, 32-px "
                           "regions, depth 12, 2^20 chains x 256 mutations",
                      scene=("glossy_corridor", dict(n_tris=2_000_000, seed=0)),
@@ -77,7 +83,8 @@ def measured_traffic(workload: str = "two_rooms"):
         return None
     try:
         rec = json.loads((ROOT / "profiles" / "chain_epoch_kernel_traffic.json").read_text())
-        src = (ROOT / "paper_2402_08273_gb300" / "csrc" / "rmlt_kernels.cu").read_bytes()
+        csrc = ROOT / "paper_2402_08273_gb300" / "csrc"
+        src = (csrc / "rmlt_kernels.cu").read_bytes() + (csrc / "rmlt_device.cuh").read_bytes()
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
             return None
         return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
@@ -419,6 +426,10 @@ def run_relmse(args, w):
                             qt_refine=10_000_000),
         "weighted": dict(target_mode=1),
     }
+    if all(int(t) == 0 for t in scene["mat_type"]):
+        # Langevin strategy (differentiable, Lambertian scenes): 30 % of the
+        # mutations, the rest as in the plain variants
+        variants["mala"] = dict(p_mala=0.3, mala_tau=1e-3, mala_drift_max=0.1)
     R = rmlt.Renderer(stream=torch.cuda.Stream())
     R.load_scene(scene)
     R.init_chains(**dict(base, seed=base["seed"] + 1000))
