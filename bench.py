@@ -639,6 +639,27 @@ def run_batched(args):
     B.close()
 
 
+def run_profile(args, w):
+    """The case a profiler captures: the workload's scene and chains (optionally
+    fewer chains), `--profile-epochs` epochs in the chosen form, nothing else
+    (no probes, no autotuning, no CPU leg)."""
+    import torch
+    from paper_2402_08273_gb300 import autotune, rmlt
+    params = dict(w["params"])
+    if args.chains:
+        params["n_chains"] = args.chains
+        params["n_bootstrap"] = max(params["n_chains"], min(params["n_bootstrap"], 16 * params["n_chains"]))
+    R = rmlt.Renderer(stream=torch.cuda.Stream())
+    R.load_scene(make_scene(w))
+    R.init_chains(**params)
+    autotune.apply(R, {"form": "chain" if args.form == "auto" else args.form})
+    R.step(params["epoch_len"] * args.profile_epochs)
+    R.synchronize()
+    st = R.read_stats()
+    print(json.dumps({"profile": args.workload, "form": args.form, "chains": params["n_chains"],
+                      "epochs": st["epochs"], "rays": st["rays"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -656,11 +677,17 @@ def main():
                     help="uneven problems stepped by rmlt_batch_step against stepping each alone")
     ap.add_argument("--batch-members", type=int, default=32)
     ap.add_argument("--batch-mutations", type=int, default=64)
+    ap.add_argument("--profile", action="store_true",
+                    help="run --profile-epochs epochs of the workload and exit (the case ncu captures)")
+    ap.add_argument("--profile-epochs", type=int, default=3)
+    ap.add_argument("--chains", type=int, default=0, help="--profile: chain count instead of the workload's")
     ap.add_argument("--relmse-budget", type=int, default=1024)
     ap.add_argument("--relmse-ref-factor", type=int, default=32)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.batched and args.impl == "ours":
+    if args.profile:
+        run_profile(args, w)
+    elif args.batched and args.impl == "ours":
         run_batched(args)
     elif args.relmse:
         run_relmse(args, w)

@@ -158,6 +158,7 @@ struct Trav {
     float4 ta, tb, tc;  // its data
     uint32_t ref;     // node / leaf to visit next, kNoRef when done
     int sp, any, overflow;
+    int oct;          // bit a set: the ray runs toward -a, so axis a's near plane is the upper bound
 };
 
 __device__ __forceinline__ void trav_begin(Trav& T, V3 o, V3 d, float tmax, int any)
@@ -168,6 +169,7 @@ __device__ __forceinline__ void trav_begin(Trav& T, V3 o, V3 d, float tmax, int 
             1.0f / (fabsf(d.y) > 1e-12f ? d.y : copysignf(1e-12f, d.y)),
             1.0f / (fabsf(d.z) > 1e-12f ? d.z : copysignf(1e-12f, d.z))};
     T.ood = {o.x * T.id.x, o.y * T.id.y, o.z * T.id.z};
+    T.oct = (T.id.x < 0.0f ? 1 : 0) | (T.id.y < 0.0f ? 2 : 0) | (T.id.z < 0.0f ? 4 : 0);
     T.t = tmax;
     T.tri = -1;
     T.ref = 0;
@@ -207,25 +209,30 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         // four children: slab tests in the lanes of each float4, nearest hit
         // child next, the others pushed far to near
         ++n_nodes;
+        // the near and far bounds of each axis are picked by the ray's octant
+        // when loading: (bound - o) / d is monotone in the bound, with the
+        // direction's sign, so min / max of the two planes is the near / far
+        // one and the slab test needs half the min / max operations
         const float4* nd = &S.nodes[8 * (size_t)ref];
-        const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
-        const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+        const int ox = T.oct & 1, oy = (T.oct >> 1) & 1, oz = (T.oct >> 2) & 1;
+        const float4 nx = __ldg(nd + ox), fx = __ldg(nd + 1 - ox), ny = __ldg(nd + 2 + oy), fy = __ldg(nd + 3 - oy);
+        const float4 nz = __ldg(nd + 4 + oz), fz = __ldg(nd + 5 - oz), rf = __ldg(nd + 6);
         const float tcap = T.t * 1.00000036f;
         const V3 id = T.id, ood = T.ood;
         float key[4];
         uint32_t cr[4];
-        const float lox[4] = {lx.x, lx.y, lx.z, lx.w}, hix[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float loy[4] = {ly.x, ly.y, ly.z, ly.w}, hiy[4] = {hy.x, hy.y, hy.z, hy.w};
-        const float loz[4] = {lz.x, lz.y, lz.z, lz.w}, hiz[4] = {hz.x, hz.y, hz.z, hz.w};
+        const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
         const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                                 __float_as_uint(rf.w)};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float a0 = fmaf(lox[k], id.x, -ood.x), b0 = fmaf(hix[k], id.x, -ood.x);
-            const float a1 = fmaf(loy[k], id.y, -ood.y), b1 = fmaf(hiy[k], id.y, -ood.y);
-            const float a2 = fmaf(loz[k], id.z, -ood.z), b2 = fmaf(hiz[k], id.z, -ood.z);
-            const float tn = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), 0.0f));
-            const float tf = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tcap));
+            const float a0 = fmaf(nxs[k], id.x, -ood.x), b0 = fmaf(fxs[k], id.x, -ood.x);
+            const float a1 = fmaf(nys[k], id.y, -ood.y), b1 = fmaf(fys[k], id.y, -ood.y);
+            const float a2 = fmaf(nzs[k], id.z, -ood.z), b2 = fmaf(fzs[k], id.z, -ood.z);
+            const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
+            const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
             const bool hit = tn <= tf && rr[k] != kEmptyRef;
             key[k] = hit ? tn : INFINITY;
             cr[k] = rr[k];
