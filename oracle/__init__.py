@@ -47,7 +47,7 @@ class OrParams(C.Structure):
         ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("partition", C.c_int32),
         ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32), ("qt_split", C.c_int64),
         ("qt_refine", C.c_int64), ("p_mala", C.c_double), ("mala_tau", C.c_double),
-        ("mala_drift_max", C.c_double),
+        ("mala_drift_max", C.c_double), ("kernel", C.c_int32), ("kernel_pad_", C.c_int32),
     ]
 
 
@@ -69,6 +69,7 @@ def lib():
         "or_philox4x32_10": (None, [u32p, u32p, u32p]),
         "or_exp2_f32": (C.c_float, [C.c_float]),
         "or_kelemen_delta": (C.c_int64, [C.c_uint32, C.c_float, C.c_float]),
+        "or_truncnorm_delta": (C.c_int64, [C.c_uint32, C.c_double]),
         "or_scene_create": (C.c_void_p, [C.c_int32, f32p, C.c_int32, u32p, u32p, C.c_int32, i32p,
                                          f32p, f32p, f32p, f32p, C.c_int32]),
         "or_scene_create_toy": (C.c_void_p, [f64p]),
@@ -134,6 +135,10 @@ def exp2_f32(t: float) -> np.float32:
 
 def kelemen_delta(xmag: int, sigma_s2: float, log2_ratio: float) -> int:
     return int(lib().or_kelemen_delta(xmag, C.c_float(sigma_s2), C.c_float(log2_ratio)))
+
+
+def truncnorm_delta(xmag: int, sigma: float) -> int:
+    return int(lib().or_truncnorm_delta(xmag, float(sigma)))
 
 
 class Scene:
@@ -215,7 +220,8 @@ DEFAULT_PARAMS = dict(
     target_mode=0, n_bootstrap=1 << 14, seed=1, p_large=0.3, s1=1.0 / 1024.0, s2=1.0 / 64.0,
     alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
     lambda_max=None, w_floor=1e-3, debug_flags=0, partition=0, qt_max_leaves=4096, qt_max_depth=10,
-    qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3, mala_drift_max=0.1,
+    qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3, mala_drift_max=0.1, kernel=0,
+    kernel_pad_=0,
 )
 
 
@@ -229,7 +235,8 @@ def make_params(**kw) -> OrParams:
     p = dict(DEFAULT_PARAMS)
     p.update(kw)
     if p["lambda_max"] is None:
-        p["lambda_max"] = lambda_max_default(p["s2"])
+        # Kelemen: sigma s2 <= 1/2; truncated normal: sigma <= 4
+        p["lambda_max"] = 2.0 * np.log(4.0) if p["kernel"] == 1 else lambda_max_default(p["s2"])
     return OrParams(**p)
 
 

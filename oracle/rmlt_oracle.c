@@ -98,6 +98,30 @@ int64_t or_kelemen_delta(uint32_t xmag, float sigma_s2, float log2_ratio)
     return (int64_t)llrintf(m);
 }
 
+/* erf^-1 by Newton's method on the library erf, from Winitzki's closed-form
+ * estimate (a = 0.147); four steps reach binary64 accuracy on |x| < 1 - 2^-24 */
+static double or_erfinv(double x)
+{
+    if (x <= -1.0) return -OR_INF;
+    if (x >= 1.0) return OR_INF;
+    if (x == 0.0) return 0.0;
+    const double ln = log((1.0 - x) * (1.0 + x)), a = 0.147, t = 2.0 / (OR_PI * a) + 0.5 * ln;
+    double y = copysign(sqrt(sqrt(t * t - ln / a) - t), x);
+    for (int i = 0; i < 4; ++i) y -= (erf(y) - x) / (2.0 / sqrt(OR_PI) * exp(-y * y));
+    return y;
+}
+
+/* Truncated-normal kernel (the paper's family, Sec. 5.2, with angles in
+ * [-pi, pi] mapped to torus offsets in (-1/2, 1/2)): inverse-CDF sample of a
+ * normal of standard deviation sigma truncated to (-1/2, 1/2). */
+int64_t or_truncnorm_delta(uint32_t xmag, double sigma)
+{
+    const double u = u24(xmag);
+    const double Z = erf(1.0 / (2.0 * sqrt(2.0) * sigma));
+    const double d = sigma * sqrt(2.0) * or_erfinv((2.0 * u - 1.0) * Z);
+    return (int64_t)llrint(d * 4294967296.0);
+}
+
 /* sigma_k = sqrt(exp(lambda_k)) = 2^(lambda_k / (2 ln 2))  (Alg. 1; Sec. 5.3) */
 static float sigma_of_lambda(double lambda)
 {
@@ -895,6 +919,9 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     int32_t D = 2 + 5 * p->max_depth;
     if (D > OR_MAX_DIM || p->n_chains <= 0 || p->width <= 0 || p->height <= 0 || p->region_px <= 0)
         return NULL;
+    /* the truncated normal's sigma stays below 4 (lambda_max = 2 ln 4): wider
+     * is uniform on the window for every purpose */
+    if (p->kernel != 0 && !(p->kernel == 1 && p->lambda_max <= 2.0 * log(4.0) + 1e-12)) return NULL;
     or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
     c->s = s;
     c->p = *p;
@@ -1058,12 +1085,32 @@ static void small_step(const or_ctx* c, uint32_t chain, uint64_t mut, int32_t kx
         uint32_t r[4];
         draw(c->p.seed, mut, chain, 1u + (uint32_t)j, r);
         for (int a = 0; a < 2 && 2 * j + a < c->D; ++a) {
+            int32_t dim = 2 * j + a;
+            if (c->p.kernel == 1) {   /* signed offset; the sign word is not used */
+                qy[dim] = qx[dim] + (uint32_t)(uint64_t)or_truncnorm_delta(r[2 * a], (double)c->sig[kx]);
+                continue;
+            }
             int64_t dq = or_kelemen_delta(r[2 * a], sigS2, c->log2_ratio);
             uint32_t off = (uint32_t)(uint64_t)dq;
-            int32_t dim = 2 * j + a;
             qy[dim] = (r[2 * a + 1] >> 31) ? qx[dim] - off : qx[dim] + off;
         }
     }
+}
+
+/* Ratio T_{k(y)}(x|y) / T_{k(x)}(y|x) of the truncated-normal kernel: per
+ * dimension phi(delta / s) / (s Z(s)) with the nearest-image displacement
+ * delta (|delta| < 1/2) and s = sigma of the state the move starts from. */
+static double truncnorm_ratio(const or_ctx* c, int32_t kx, int32_t ky, const uint32_t* qx, const uint32_t* qy)
+{
+    const double sx = (double)c->sig[kx], sy = (double)c->sig[ky];
+    if (sx == sy) return 1.0;
+    const double zx = erf(1.0 / (2.0 * sqrt(2.0) * sx)), zy = erf(1.0 / (2.0 * sqrt(2.0) * sy));
+    double s2 = 0.0;
+    for (int32_t d = 0; d < c->D; ++d) {
+        double dl = (double)(int32_t)(qy[d] - qx[d]) * (1.0 / 4294967296.0);
+        s2 += dl * dl;
+    }
+    return exp(c->D * log((sx * zx) / (sy * zy)) - 0.5 * s2 * (1.0 / (sy * sy) - 1.0 / (sx * sx)));
 }
 
 /* Ratio T_{k(y)}(x|y) / T_{k(x)}(y|x) of the state-dependent mixture
@@ -1091,20 +1138,29 @@ static int reverse_support(const or_ctx* c, int32_t kx, int32_t ky, const uint32
  * depend on the state and cancel; R is the kernel ratio (1 for the large step,
  * whose density is uniform).  A zero-contribution current state (possible only
  * at initialisation) accepts any proposal the reverse kernel can undo. */
-static double accept_prob(const or_ctx* c, int32_t kx, int32_t ky, double pix, double piy, int32_t R)
+static double accept_prob(const or_ctx* c, int32_t kx, int32_t ky, double pix, double piy, double R)
 {
-    if (!R) return 0.0;
+    if (!(R > 0)) return 0.0;
     double ptx = pix / weight_of(c, kx), pty = piy / weight_of(c, ky);
     if (!(ptx > 0)) return 1.0;
-    return dmin(1.0, pty / ptx);
+    return dmin(1.0, pty / ptx * R);
+}
+
+/* kernel ratio of a proposal: 1 for the large step, the reverse-support
+ * indicator for Kelemen, the density ratio for the truncated normal */
+static double kernel_ratio(const or_ctx* c, int32_t large, int32_t kx, int32_t ky, const uint32_t* qx,
+                           const uint32_t* qy)
+{
+    if (large) return 1.0;
+    if (c->p.kernel == 1) return truncnorm_ratio(c, kx, ky, qx, qy);
+    return (double)reverse_support(c, kx, ky, qx, qy);
 }
 
 double or_accept_prob(const or_ctx* c, const uint32_t* qx, const uint32_t* qy,
                       double pix, double piy, int32_t large)
 {
     int32_t kx = or_region_of(c, qx), ky = or_region_of(c, qy);
-    int32_t R = large ? 1 : reverse_support(c, kx, ky, qx, qy);
-    return accept_prob(c, kx, ky, pix, piy, R);
+    return accept_prob(c, kx, ky, pix, piy, kernel_ratio(c, large, kx, ky, qx, qy));
 }
 
 /* splat f(x) / pi(x) of the chain's current state at its pixel */
@@ -1239,10 +1295,10 @@ static void mutate(or_ctx* c, uint32_t chain)
     if (large) large_step(c, chain, c->mut, qy);
     else small_step(c, chain, c->mut, kx, qx, qy);
     int32_t ky = or_region_of(c, qy);
-    int32_t R = large ? 1 : reverse_support(c, kx, ky, qx, qy);
-    if (c->p.debug_flags & 1) R = 1;   /* planted mistake for negative-control tests */
+    double R = kernel_ratio(c, large, kx, ky, qx, qy);
+    if (c->p.debug_flags & 1) R = 1.0;   /* planted mistake for negative-control tests */
     double fy[3] = {0, 0, 0}, margin = OR_INF;
-    if (R) {
+    if (R > 0) {
         uint64_t cnt[3] = {0, 0, 0};
         if (!or_path_eval(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy,
                           c->mh ? &margin : NULL, cnt))
@@ -1256,7 +1312,7 @@ static void mutate(or_ctx* c, uint32_t chain)
     double a = accept_prob(c, kx, ky, c->pi[chain], piy, R);
     int32_t acc = xi < a;
     if (c->mh) {
-        c->mh(c->user, chain, c->mut, qy, D, large, !R, margin, xi, fy, &a, &acc);
+        c->mh(c->user, chain, c->mut, qy, D, large, !(R > 0), margin, xi, fy, &a, &acc);
         piy = luminance(fy);
         pty = piy / weight_of(c, ky);
     }

@@ -40,6 +40,9 @@ float or_exp2_f32(float t);
 
 /* Magnitude (units of 2^-32) of one Kelemen small-step offset. */
 int64_t or_kelemen_delta(uint32_t xmag, float sigma_s2, float log2_ratio);
+/* Truncated-normal small-step offset in units of 2^-32 for the 24-bit
+ * uniform of xmag: sigma sqrt(2) erfinv((2u - 1) Z), Z = erf(1 / (2 sqrt(2) sigma)). */
+int64_t or_truncnorm_delta(uint32_t xmag, double sigma);
 
 typedef struct or_scene or_scene;
 typedef struct or_ctx or_ctx;
@@ -66,6 +69,9 @@ typedef struct {
     /* Langevin (MALA) strategy: probability, step tau (scaled by sigma_k^2 of
      * the current state's region) and the bound on the drift's norm */
     double   p_mala, mala_tau, mala_drift_max;
+    /* small-step kernel: 0 Kelemen (log-uniform offsets), 1 truncated normal of
+     * standard deviation sigma_k on the torus window (-1/2, 1/2) */
+    int32_t  kernel, kernel_pad_;
 } or_params;
 
 /* Gradient of log pi(u), pi = l(f(u)), over the D = 2 + 5 max_depth
