@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 3
+#define RMLT_ABI_VERSION 4
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -113,7 +113,17 @@ typedef struct {
      * do not feed the adaptation statistics.  Needs a Lambertian scene (or the
      * toy integrand), the chain kernel, and no trace instrument.  0 = off. */
     double p_mala, mala_tau, mala_drift_max;
+    /* small-step kernel: RMLT_KERNEL_KELEMEN (log-uniform offsets on
+     * [sigma s1, sigma s2], random sign) or RMLT_KERNEL_TRUNCNORM (the
+     * paper's family, Sec. 5.2: a normal of standard deviation sigma_k
+     * truncated to the torus window (-1/2, 1/2); lambda_max <= 2 ln 4).  Both
+     * perturb every dimension with the sigma of the current state's region;
+     * the acceptance carries the reverse kernel of the proposal's region. */
+    int32_t kernel;
+    int32_t kernel_pad_;
 } rmlt_chain_params;
+#define RMLT_KERNEL_KELEMEN 0
+#define RMLT_KERNEL_TRUNCNORM 1
 
 typedef struct {
     uint64_t mutations;        /* per chain, since rmlt_init_chains */

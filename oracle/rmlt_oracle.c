@@ -118,7 +118,9 @@ int64_t or_truncnorm_delta(uint32_t xmag, double sigma)
 {
     const double u = u24(xmag);
     const double Z = erf(1.0 / (2.0 * sqrt(2.0) * sigma));
-    const double d = sigma * sqrt(2.0) * or_erfinv((2.0 * u - 1.0) * Z);
+    /* u = 0 with Z rounded to 1 (sigma below ~0.06) would ask for erfinv(-1) */
+    const double x = fmax(-1.0 + 0x1p-52, (2.0 * u - 1.0) * Z);
+    const double d = sigma * sqrt(2.0) * or_erfinv(x);
     return (int64_t)llrint(d * 4294967296.0);
 }
 

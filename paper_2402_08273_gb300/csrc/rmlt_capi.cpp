@@ -421,10 +421,13 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
     if (!(p->s1 > 0.0 && p->s1 < p->s2 && p->s2 <= 0.5)) return fail(RMLT_E_INVALID_ARG, "need 0 < s1 < s2 <= 1/2");
     if (!(p->alpha_star > 0.0 && p->alpha_star < 1.0)) return fail(RMLT_E_INVALID_ARG, "alpha_star outside (0,1)");
     if (!(p->gamma_max >= 0.0 && p->gamma_scale >= 0.0)) return fail(RMLT_E_INVALID_ARG, "negative gamma");
-    const double lmax_ok = 2.0 * std::log(1.0 / (2.0 * p->s2));
+    if (p->kernel != RMLT_KERNEL_KELEMEN && p->kernel != RMLT_KERNEL_TRUNCNORM)
+        return fail(RMLT_E_INVALID_ARG, "unknown small-step kernel");
+    // sigma s2 <= 1/2 for Kelemen; sigma <= 4 for the truncated normal
+    const double lmax_ok = p->kernel == RMLT_KERNEL_TRUNCNORM ? 2.0 * std::log(4.0) : 2.0 * std::log(1.0 / (2.0 * p->s2));
     if (!(p->lambda_min >= -150.0 && p->lambda_min <= p->lambda_init && p->lambda_init <= p->lambda_max &&
           p->lambda_max <= lmax_ok + 1e-12))
-        return fail(RMLT_E_INVALID_ARG, "need -150 <= lambda_min <= lambda_init <= lambda_max <= 2 ln(1/(2 s2)) = %g", lmax_ok);
+        return fail(RMLT_E_INVALID_ARG, "need -150 <= lambda_min <= lambda_init <= lambda_max <= %g", lmax_ok);
     if (!(p->w_floor >= 0.0 && p->w_floor <= 1.0)) return fail(RMLT_E_INVALID_ARG, "w_floor outside [0,1]");
     if (p->partition != RMLT_PARTITION_GRID && p->partition != RMLT_PARTITION_QUADTREE)
         return fail(RMLT_E_INVALID_ARG, "unknown partition");
@@ -468,6 +471,7 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     Ch.E = p->epoch_len;
     Ch.L = p->L;
     Ch.weighted = p->target_mode == RMLT_TARGET_REGION_WEIGHTED;
+    Ch.truncnorm = p->kernel == RMLT_KERNEL_TRUNCNORM ? 1 : 0;
     const size_t C = (size_t)Ch.C, m = (size_t)Ch.m, npx = (size_t)Ch.W * Ch.H * 3;
     rmlt_status st;
     auto& pool = c->chain_mem;

@@ -707,6 +707,7 @@ struct ChainLane {
     // the mutation in flight
     int j, large, ky, early;
     float xi;
+    float R;          // kernel ratio T_{k(y)}(x|y) / T_{k(x)}(y|x) of a truncated-normal small step (else 1)
     V3 fy;
     // Langevin strategy: this mutation is one (its acceptance probability
     // decided at the proposal), and moves proposed / accepted so far
@@ -852,6 +853,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
     const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
     L.large = (r0.x >> 8) < Ch.T_large;
     L.xi = u24(r0.y);
+    L.R = 1.0f;
     if (MALA) {
         L.mala = 0;
         if (!L.large && (r0.x >> 8) < Ch.T_large + Ch.T_mala) {
@@ -869,6 +871,39 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
             if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
         }
         L.ky = region_of(Ch, y[0], y[1]);
+    } else if (Ch.truncnorm) {
+        // truncated normal of standard deviation sigma_{k(x)} on (-1/2, 1/2)
+        // (the paper's kernel family, Sec. 5.2); the ratio of the reverse and
+        // forward densities enters the acceptance
+#pragma unroll 4
+        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
+        const float sx = Ch.sig[L.kx];
+        const float zx = erff(0.353553390593273762f / sx);
+        double s2 = 0.0;
+        for (int jj = 0; 2 * jj < D; ++jj) {
+            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int d = 2 * jj + e;
+                if (d < D) {
+                    const float u = u24(e ? r.z : r.x);
+                    const float x = fmaxf(-0.99999994f, fminf(0.99999994f, (2.0f * u - 1.0f) * zx));
+                    const float dl = sx * 1.41421356237309505f * erfinvf(x);
+                    const uint32_t off = (uint32_t)(unsigned long long)__float2ll_rn(dl * 4294967296.0f);
+                    y[d] += off;
+                    const double dr = (double)(int32_t)off * 2.3283064365386963e-10;
+                    s2 += dr * dr;
+                }
+            }
+        }
+        L.ky = region_of(Ch, y[0], y[1]);
+        const float sy = Ch.sig[L.ky];
+        if (sy != sx) {
+            const float zy = erff(0.353553390593273762f / sy);
+            const double lr = D * log(((double)sx * zx) / ((double)sy * zy)) -
+                              0.5 * s2 * (1.0 / ((double)sy * sy) - 1.0 / ((double)sx * sx));
+            L.R = (float)exp(lr);
+        }
     } else {
         // every dimension perturbed with sigma of the current state's region;
         // the current state's words are fetched first with independent loads
@@ -970,7 +1005,7 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
     } else {
         const float ptx = Ch.weighted ? L.pix / Ch.wf[L.kx] : L.pix;
         const float pty = Ch.weighted ? piy / Ch.wf[L.ky] : piy;
-        a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, pty / ptx);
+        a = !(ptx > 0.0f) ? 1.0f : fminf(1.0f, L.R == 1.0f ? pty / ptx : pty / ptx * L.R);
     }
     const int accept = L.xi < a;
     if (MALA && L.mala) {

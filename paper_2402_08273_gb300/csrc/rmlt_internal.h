@@ -62,6 +62,7 @@ struct DevScene {
 struct DevChains {
     int32_t C = 0, D = 0, W = 0, H = 0, region_px = 1, nx = 1, m = 1, max_depth = 0, E = 1, L = 10;
     int32_t weighted = 0;
+    int32_t truncnorm = 0;        // small-step kernel: 0 Kelemen, 1 truncated normal
     uint32_t* q = nullptr;        // [D][C]
     float* f = nullptr;           // [3][C]
     float* pi = nullptr;          // [C]
@@ -121,7 +122,7 @@ struct DevChains {
 // the wave under a device-side while condition until no chain has a ray.
 enum WfSlot {
     kWKx = 0, kWPx, kWPy, kWPix, kWFx, kWPendN = kWFx + 3, kWPendI, kWPendA, kWJ = kWPendA + 2, kWFlags, kWKy,
-    kWXi, kWFy, kWT = kWFy + 3, kWL = kWT + 3, kWP = kWL + 3, kWB = kWP + 3, kWO, kWD = kWO + 3,
+    kWXi, kWR, kWFy, kWT = kWFy + 3, kWL = kWT + 3, kWP = kWL + 3, kWB = kWP + 3, kWO, kWD = kWO + 3,
     kWPfl = kWD + 3, kWSt, kWPhase = kWSt + 7, kWHitT, kWHitTri, kWShd, kWfSlots
 };
 

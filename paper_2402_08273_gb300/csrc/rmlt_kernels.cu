@@ -57,6 +57,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     L.j = 0;
     L.large = L.ky = L.early = 0;
     L.xi = 0.f;
+    L.R = 1.0f;
     L.fy = {0.f, 0.f, 0.f};
     L.mala = 0;
     L.amala = 0.f;

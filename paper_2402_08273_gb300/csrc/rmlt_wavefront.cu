@@ -78,6 +78,7 @@ __device__ __forceinline__ void load_lane(const Slots& s, ChainLane& L)
     L.early = (int)((fl >> 1) & 1u);
     L.ky = (int)s[kWKy];
     L.xi = s.f(kWXi);
+    L.R = s.f(kWR);
     L.fy = s.v(kWFy);
 }
 
@@ -96,6 +97,7 @@ __device__ __forceinline__ void store_lane(const Slots& s, const ChainLane& L)
     s[kWFlags] = (uint32_t)L.large | ((uint32_t)L.early << 1);
     s[kWKy] = (uint32_t)L.ky;
     s.setf(kWXi, L.xi);
+    s.setf(kWR, L.R);
     s.setv(kWFy, L.fy);
 }
 

@@ -21,6 +21,7 @@ STATUS = {0: "RMLT_OK", -1: "RMLT_E_INVALID_ARG", -2: "RMLT_E_INVALID_SCENE", -3
           -8: "RMLT_E_IO"}
 LAMBERT, GGX = 0, 1
 TARGET_PLAIN, TARGET_REGION_WEIGHTED = 0, 1
+KERNEL_KELEMEN, KERNEL_TRUNCNORM = 0, 1
 MAX_DEPTH = 12
 
 
@@ -57,7 +58,8 @@ class ChainParams(C.Structure):
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("w_floor", C.c_double),
                 ("partition", C.c_int32), ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32),
                 ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64),
-                ("p_mala", C.c_double), ("mala_tau", C.c_double), ("mala_drift_max", C.c_double)]
+                ("p_mala", C.c_double), ("mala_tau", C.c_double), ("mala_drift_max", C.c_double),
+                ("kernel", C.c_int32), ("kernel_pad_", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -153,10 +155,12 @@ def default_params(**kw) -> dict:
              s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
              lambda_min=-30.0, lambda_max=None, w_floor=1e-3, partition=0, qt_max_leaves=4096,
              qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3,
-             mala_drift_max=0.1)
+             mala_drift_max=0.1, kernel=KERNEL_KELEMEN, kernel_pad_=0)
     p.update(kw)
     if p["lambda_max"] is None:
-        p["lambda_max"] = 2.0 * math.log(1.0 / (2.0 * p["s2"]))
+        # Kelemen: sigma s2 <= 1/2; truncated normal: sigma <= 4
+        p["lambda_max"] = (2.0 * math.log(4.0) if p["kernel"] == KERNEL_TRUNCNORM
+                           else 2.0 * math.log(1.0 / (2.0 * p["s2"])))
     return p
 
 
