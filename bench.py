@@ -708,6 +708,8 @@ def run_profile(args, w):
     R.load_scene(make_scene(w))
     R.init_chains(**params)
     autotune.apply(R, {"form": "chain" if args.form == "auto" else args.form})
+    if args.host_loop:
+        R.set_wavefront(host_loop=True)   # waves launched from the host: profilers see each kernel
     R.step(params["epoch_len"] * args.profile_epochs)
     R.synchronize()
     st = R.read_stats()
@@ -736,6 +738,7 @@ def main():
                     help="run --profile-epochs epochs of the workload and exit (the case ncu captures)")
     ap.add_argument("--profile-epochs", type=int, default=3)
     ap.add_argument("--chains", type=int, default=0, help="--profile: chain count instead of the workload's")
+    ap.add_argument("--host-loop", action="store_true", help="--profile, wavefront form: launch waves from the host")
     ap.add_argument("--relmse-budget", type=int, default=1024)
     ap.add_argument("--relmse-ref-factor", type=int, default=32)
     args = ap.parse_args()

@@ -476,6 +476,8 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     rmlt_status st;
     auto& pool = c->chain_mem;
     if ((st = c->alloc_n(pool, C * Ch.D, &Ch.q))) return st;
+    Ch.qd = (int64_t)C;
+    Ch.qc = 1;
     if ((st = c->alloc_n(pool, 3 * C, &Ch.f))) return st;
     if ((st = c->alloc_n(pool, C, &Ch.pi))) return st;
     if ((st = c->alloc_n(pool, C, &Ch.k))) return st;
@@ -884,6 +886,8 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint
     Ch.seed_lo = (uint32_t)p->seed;
     Ch.seed_hi = (uint32_t)(p->seed >> 32);
     Ch.q = out_q;
+    Ch.qd = (int64_t)p->n_chains;
+    Ch.qc = 1;
     Ch.f = out_f;
     Ch.pi = na.chain_pi;
     Ch.k = na.chain_k;

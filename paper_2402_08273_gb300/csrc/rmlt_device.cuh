@@ -737,7 +737,7 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
         // the state was reached by another strategy: its gradient first
         uint32_t yx[kMaxDim];
         float gx[kMaxDim];
-        for (int d = 0; d < D; ++d) yx[d] = Ch.q[(size_t)d * C + c];
+        for (int d = 0; d < D; ++d) yx[d] = Ch.q[(size_t)d * Ch.qd + (size_t)c * Ch.qc];
         if (S.toy) {
             toy_grad(S, yx[0], yx[1], gx);
         } else {
@@ -778,7 +778,7 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
             for (int e = 0; e < 2; ++e) {
                 const int d = 4 * jj + 2 * a + e;
                 if (d < D) {
-                    const uint32_t qx = Ch.q[(size_t)d * C + c];
+                    const uint32_t qx = Ch.q[(size_t)d * Ch.qd + (size_t)c * Ch.qc];
                     const float m = 0.5f * tx * Ch.G[(size_t)d * C + c] * scx;
                     const float step = fmaf(stx, z[e], m);
                     y[d] = qx + (uint32_t)(unsigned long long)__float2ll_rn(step * 4294967296.0f);
@@ -876,7 +876,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
         // (the paper's kernel family, Sec. 5.2); the ratio of the reverse and
         // forward densities enters the acceptance
 #pragma unroll 4
-        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
+        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * Ch.qd + (size_t)c * Ch.qc];
         const float sx = Ch.sig[L.kx];
         const float zx = erff(0.353553390593273762f / sx);
         double s2 = 0.0;
@@ -908,7 +908,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
         // every dimension perturbed with sigma of the current state's region;
         // the current state's words are fetched first with independent loads
 #pragma unroll 4
-        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * C + c];
+        for (int d = 0; d < D; ++d) y[d] = Ch.q[(size_t)d * Ch.qd + (size_t)c * Ch.qc];
         const float sx = Ch.sig[L.kx];
         const float sigS2 = __fmul_rn(sx, Ch.S2);
         float lo = 0.f, hi = 0.f;
@@ -1051,7 +1051,7 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
             for (int k = 0; k < 8; ++k) t[k] = d0 + k < D ? y[d0 + k] : 0u;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                if (d0 + k < D) Ch.q[(size_t)(d0 + k) * C + c] = t[k];
+                if (d0 + k < D) Ch.q[(size_t)(d0 + k) * Ch.qd + (size_t)c * Ch.qc] = t[k];
         }
         L.fx = fy;
         L.pix = piy;

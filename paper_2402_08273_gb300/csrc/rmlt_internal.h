@@ -63,7 +63,8 @@ struct DevChains {
     int32_t C = 0, D = 0, W = 0, H = 0, region_px = 1, nx = 1, m = 1, max_depth = 0, E = 1, L = 10;
     int32_t weighted = 0;
     int32_t truncnorm = 0;        // small-step kernel: 0 Kelemen, 1 truncated normal
-    uint32_t* q = nullptr;        // [D][C]
+    uint32_t* q = nullptr;        // word d of chain c at q[d qd + c qc]: [D][C] (qd = C, qc = 1)
+    int64_t qd = 0, qc = 1;       //   or, inside the wavefront form's epoch, a [C][D] copy (qd = 1, qc = D)
     float* f = nullptr;           // [3][C]
     float* pi = nullptr;          // [C]
     int32_t* k = nullptr;         // [C]
@@ -135,7 +136,8 @@ struct WfCounters {
 
 struct DevWave {
     uint32_t* s = nullptr;        // [kWfSlots][C]
-    uint32_t* y = nullptr;        // [D][C]
+    uint32_t* y = nullptr;        // [C][D] proposals, one chain's words contiguous
+    uint32_t* qa = nullptr;       // [C][D] the states during an epoch (transposed in and out)
     float4* rq[2] = {nullptr, nullptr};   // two queues of 2C rays, 2 float4 each
     uint32_t* fq = nullptr;       // [C] chains to finish / set up
     WfCounters* ctr = nullptr;

@@ -40,12 +40,35 @@ namespace {
 enum WfPhase : uint32_t { kWfIdle = 0, kWfStart = 1, kWfRays = 2, kWfFinish = 3 };
 constexpr uint32_t kAnyBit = 0x80000000u;
 
-// word d of one chain's proposal in the [D][C] array
+// word d of one chain's proposal (its row of the [C][D] array)
 struct YCol {
     uint32_t* p;
-    int C;
-    __device__ __forceinline__ uint32_t& operator[](int d) const { return p[(size_t)d * C]; }
+    __device__ __forceinline__ uint32_t& operator[](int d) const { return p[d]; }
 };
+
+// dst[c][r] = src[r][c] for a rows x cols matrix of words, in 32 x 32 tiles
+__global__ void __launch_bounds__(256) wf_transpose_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                                           int rows, int cols)
+{
+    __shared__ uint32_t tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = src[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(size_t)c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+cudaError_t transpose(const uint32_t* src, uint32_t* dst, int rows, int cols, cudaStream_t st)
+{
+    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    wf_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, dst, rows, cols);
+    return cudaGetLastError();
+}
 
 struct Slots {
     uint32_t* s;
@@ -212,7 +235,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S,
                     h.b = __ldg(&S.tris[3 * (size_t)tri + 1]);
                     h.c = __ldg(&S.tris[3 * (size_t)tri + 2]);
                     if (shade_hit<BRUTE>(p, S, h)) {
-                        const YCol y{W.y + c, C};
+                        const YCol y{W.y + (size_t)c * Ch.D};
                         if (nee_sample<false>(p, S, nullptr, y)) {
                             sh0 = make_float4(p.o.x, p.o.y, p.o.z, p.tmax);
                             sh1 = make_float4(p.d.x, p.d.y, p.d.z, __uint_as_float((uint32_t)c | kAnyBit));
@@ -287,7 +310,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S,
         if (i < n) {
             const int c = (int)W.fq[i];
             const Slots s{W.s, C, c};
-            const YCol y{W.y + c, C};
+            const YCol y{W.y + (size_t)c * Ch.D};
             const bool traced = TRACE && (uint32_t)c % Ch.trace_stride == 0u;
             ChainLane L;
             load_lane(s, L);
@@ -460,7 +483,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t wf_bytes(int C, int D)
 {
     const size_t c = (size_t)C;
-    return align256(sizeof(uint32_t) * kWfSlots * c) + align256(sizeof(uint32_t) * (size_t)D * c) +
+    return align256(sizeof(uint32_t) * kWfSlots * c) + 2 * align256(sizeof(uint32_t) * (size_t)D * c) +
            2 * align256(sizeof(float4) * 4 * c) + align256(sizeof(uint32_t) * c) + align256(sizeof(WfCounters));
 }
 
@@ -471,6 +494,8 @@ void wf_carve(void* base, int C, int D, DevWave& w)
     w.s = (uint32_t*)p;
     p += align256(sizeof(uint32_t) * kWfSlots * c);
     w.y = (uint32_t*)p;
+    p += align256(sizeof(uint32_t) * (size_t)D * c);
+    w.qa = (uint32_t*)p;
     p += align256(sizeof(uint32_t) * (size_t)D * c);
     for (int b = 0; b < 2; ++b) {
         w.rq[b] = (float4*)p;
@@ -619,9 +644,17 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
     if (sc > max_setup) sc = max_setup;
     if (sc < 1) sc = 1;
     W.wave_cap = (unsigned)Ch.E * (unsigned)(Ch.max_depth + 1) + 2u;
+    // during the epoch the waves address the states in the row-major copy: a
+    // wave's setup list is a sparse subset of the chains, and one chain's
+    // words in a row share cache lines where a column layout would give
+    // every word its own
+    DevChains Cw = Ch;
+    Cw.q = W.qa;
+    Cw.qd = 1;
+    Cw.qc = Ch.D;
     // the graph's kernels hold these values; rebuild when any of them changes
     std::vector<unsigned char> key;
-    DevChains kc = Ch;
+    DevChains kc = Cw;
     kc.trace_base = 0;
     DevWave kw = W;
     kw.cond = 0;
@@ -635,7 +668,9 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
     if (host_loop) {
         wf_begin_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W, mut0, trace_base);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = host_waves<B, T, K>(S, Ch, W, tc, sc, st);
+        if (e == cudaSuccess) e = transpose(Ch.q, W.qa, Ch.D, Ch.C, st);
+        if (e == cudaSuccess) e = host_waves<B, T, K>(S, Cw, W, tc, sc, st);
+        if (e == cudaSuccess) e = transpose(W.qa, Ch.q, Ch.C, Ch.D, st);
         if (e != cudaSuccess) return e;
         wf_end_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W);
         return cudaGetLastError();
@@ -645,7 +680,7 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
         wf_graph_destroy(g);
         *gp = nullptr;
         g = new WfGraph();
-        cudaError_t e = build_graph<B, T, K>(*g, S, Ch, W, tc, sc);
+        cudaError_t e = build_graph<B, T, K>(*g, S, Cw, W, tc, sc);
         if (e != cudaSuccess) {
             wf_graph_destroy(g);
             return e;
@@ -655,8 +690,10 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
     }
     wf_begin_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W, mut0, trace_base);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = transpose(Ch.q, W.qa, Ch.D, Ch.C, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaGraphLaunch(g->x, st)) != cudaSuccess) return e;
+    if ((e = transpose(W.qa, Ch.q, Ch.C, Ch.D, st)) != cudaSuccess) return e;
     wf_end_kernel<<<(Ch.C + 255) / 256, 256, 0, st>>>(Ch, W);
     return cudaGetLastError();
 }
