@@ -16,7 +16,7 @@ CANDIDATES = (
     {"form": "chain", "batch_shade": 4, "batch_setup": 8},
     {"form": "chain", "batch_shade": 12, "batch_setup": 8},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
-    {"form": "wavefront", "trace_ctas_per_sm": 4, "refill_lanes": 8},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
 )
 
 
