@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 4
+#define RMLT_ABI_VERSION 5
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -120,7 +120,12 @@ typedef struct {
      * perturb every dimension with the sigma of the current state's region;
      * the acceptance carries the reverse kernel of the proposal's region. */
     int32_t kernel;
-    int32_t kernel_pad_;
+    /* 4-D partition in primary sample space (the analogue of the paper's 4-D
+     * partition, Sec. 5.4): each screen region is crossed with a dir_cells x
+     * dir_cells grid over the first bounce's BSDF coordinates (u5, u6), so
+     * m = regions on screen x dir_cells^2.  0 or 1 = screen only.  Needs the
+     * grid partition, the plain target and max_depth >= 1. */
+    int32_t dir_cells;
 } rmlt_chain_params;
 #define RMLT_KERNEL_KELEMEN 0
 #define RMLT_KERNEL_TRUNCNORM 1

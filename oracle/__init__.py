@@ -47,7 +47,7 @@ class OrParams(C.Structure):
         ("w_floor", C.c_double), ("debug_flags", C.c_int32), ("partition", C.c_int32),
         ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32), ("qt_split", C.c_int64),
         ("qt_refine", C.c_int64), ("p_mala", C.c_double), ("mala_tau", C.c_double),
-        ("mala_drift_max", C.c_double), ("kernel", C.c_int32), ("kernel_pad_", C.c_int32),
+        ("mala_drift_max", C.c_double), ("kernel", C.c_int32), ("dir_cells", C.c_int32),
     ]
 
 
@@ -221,7 +221,7 @@ DEFAULT_PARAMS = dict(
     alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
     lambda_max=None, w_floor=1e-3, debug_flags=0, partition=0, qt_max_leaves=4096, qt_max_depth=10,
     qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3, mala_drift_max=0.1, kernel=0,
-    kernel_pad_=0,
+    dir_cells=0,
 )
 
 

@@ -931,6 +931,13 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     c->nx = (p->width + p->region_px - 1) / p->region_px;
     int32_t ny = (p->height + p->region_px - 1) / p->region_px;
     c->m = c->nx * ny;
+    if (p->dir_cells > 1) {
+        if (p->partition != 0 || p->target_mode != 0 || p->max_depth < 1 || s->toy || p->dir_cells > 64) {
+            free(c);
+            return NULL;
+        }
+        c->m *= p->dir_cells * p->dir_cells;
+    }
     c->cap = c->m;
     if (p->partition == 1) {
         if (p->qt_max_leaves < 1 || p->qt_max_depth < 0 || p->qt_max_depth > 24 || p->target_mode != 0) {
@@ -1021,7 +1028,17 @@ int32_t or_region_of(const or_ctx* c, const uint32_t* q)
     }
     int32_t px, py;
     pixel_of(c, q, &px, &py);
-    return px / c->p.region_px + (py / c->p.region_px) * c->nx;
+    int32_t k = px / c->p.region_px + (py / c->p.region_px) * c->nx;
+    if (c->p.dir_cells > 1) {
+        /* 4-D partition in PSS (analogue of Sec. 5.4): the screen region
+         * crossed with a dir_cells^2 grid over the first bounce's BSDF
+         * coordinates (u5, u6), cells taken like pixels */
+        const int32_t g = c->p.dir_cells;
+        const int32_t cu = (int32_t)(((uint64_t)(q[5] >> 8) * (uint64_t)g) >> 24);
+        const int32_t cv = (int32_t)(((uint64_t)(q[6] >> 8) * (uint64_t)g) >> 24);
+        k = k * g * g + cu + cv * g;
+    }
+    return k;
 }
 
 /* Refinement of the quadtree partition (Sec. 6.2), run once every qt_refine

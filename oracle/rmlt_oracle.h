@@ -71,7 +71,10 @@ typedef struct {
     double   p_mala, mala_tau, mala_drift_max;
     /* small-step kernel: 0 Kelemen (log-uniform offsets), 1 truncated normal of
      * standard deviation sigma_k on the torus window (-1/2, 1/2) */
-    int32_t  kernel, kernel_pad_;
+    int32_t  kernel;
+    /* 4-D partition: each screen region crossed with a dir_cells^2 grid over
+     * (u5, u6), the first bounce's BSDF coordinates; <= 1 screen only */
+    int32_t  dir_cells;
 } or_params;
 
 /* Gradient of log pi(u), pi = l(f(u)), over the D = 2 + 5 max_depth

@@ -431,6 +431,15 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
     if (!(p->w_floor >= 0.0 && p->w_floor <= 1.0)) return fail(RMLT_E_INVALID_ARG, "w_floor outside [0,1]");
     if (p->partition != RMLT_PARTITION_GRID && p->partition != RMLT_PARTITION_QUADTREE)
         return fail(RMLT_E_INVALID_ARG, "unknown partition");
+    if (p->dir_cells < 0 || p->dir_cells > 64) return fail(RMLT_E_INVALID_ARG, "dir_cells outside [0, 64]");
+    if (p->dir_cells > 1) {
+        if (p->partition != RMLT_PARTITION_GRID || p->target_mode != RMLT_TARGET_PLAIN || p->max_depth < 1 || c->S.toy)
+            return fail(RMLT_E_INVALID_ARG, "the 4-D partition needs the grid partition, the plain target and a scene "
+                        "with max_depth >= 1");
+        const int64_t m4 = (int64_t)((p->width + p->region_px - 1) / p->region_px) *
+                           ((p->height + p->region_px - 1) / p->region_px) * p->dir_cells * p->dir_cells;
+        if (m4 > (1 << 24)) return fail(RMLT_E_INVALID_ARG, "more than 2^24 regions");
+    }
     if (!(p->p_mala >= 0.0 && p->p_mala <= 1.0 && p->p_large + p->p_mala <= 1.0))
         return fail(RMLT_E_INVALID_ARG, "p_mala outside [0, 1 - p_large]");
     if (p->p_mala > 0.0) {
@@ -460,6 +469,10 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     Ch.region_px = p->region_px;
     Ch.nx = (p->width + p->region_px - 1) / p->region_px;
     Ch.m = Ch.nx * ((p->height + p->region_px - 1) / p->region_px);
+    if (p->dir_cells > 1) {
+        Ch.dcells = p->dir_cells;
+        Ch.m *= p->dir_cells * p->dir_cells;
+    }
     if (p->partition == RMLT_PARTITION_QUADTREE) {
         Ch.quadtree = 1;
         Ch.m = p->qt_max_leaves;          // capacity; the current count lives on the device

@@ -98,6 +98,17 @@ __device__ __forceinline__ int region_of(const DevChains& Ch, uint32_t q0, uint3
     return pixel_x(q0, Ch.W) / Ch.region_px + (pixel_x(q1, Ch.H) / Ch.region_px) * Ch.nx;
 }
 
+// Region of a state's words y: the screen region, crossed (4-D partition in
+// PSS, the analogue of the paper's 4-D partition of Sec. 5.4) with a
+// dcells x dcells grid over the first bounce's BSDF coordinates (u5, u6).
+template <class Y>
+__device__ __forceinline__ int region_y(const DevChains& Ch, Y y)
+{
+    int k = region_of(Ch, y[0], y[1]);
+    if (Ch.dcells > 1) k = k * Ch.dcells * Ch.dcells + pixel_x(y[5], Ch.dcells) + pixel_x(y[6], Ch.dcells) * Ch.dcells;
+    return k;
+}
+
 // ---------------------------------------------------------------------------
 // small float3 helpers
 // ---------------------------------------------------------------------------
@@ -791,7 +802,7 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
     }
     L.mala = 1;
     L.early = 0;
-    L.ky = region_of(Ch, y[0], y[1]);
+    L.ky = region_y(Ch, y);
     float gy[kMaxDim];
     V3 fy;
     if (S.toy) {
@@ -870,7 +881,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
             if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
             if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
         }
-        L.ky = region_of(Ch, y[0], y[1]);
+        L.ky = region_y(Ch, y);
     } else if (Ch.truncnorm) {
         // truncated normal of standard deviation sigma_{k(x)} on (-1/2, 1/2)
         // (the paper's kernel family, Sec. 5.2); the ratio of the reverse and
@@ -896,7 +907,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 }
             }
         }
-        L.ky = region_of(Ch, y[0], y[1]);
+        L.ky = region_y(Ch, y);
         const float sy = Ch.sig[L.ky];
         if (sy != sx) {
             const float zy = erff(0.353553390593273762f / sy);
@@ -923,7 +934,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
                 y[d0 + 1] = (r.w >> 31) ? y[d0 + 1] - o1 : y[d0 + 1] + o1;
             }
-            if (jj == 0) {
+            if (jj == 0 && Ch.dcells <= 1) {
                 L.ky = region_of(Ch, y[0], y[1]);
                 const float sy = Ch.sig[L.ky];
                 if (sy != sx) {
@@ -939,6 +950,21 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 if (d0 + 1 < D) {
                     const float m1 = __uint2float_rn(o1);
                     if (!(m1 >= lo && m1 <= hi)) R = 0;
+                }
+            }
+        }
+        if (Ch.dcells > 1) {
+            // the 4-D region needs dims 5 and 6: the reverse-kernel support is
+            // checked afterwards on the offset magnitudes y - x
+            L.ky = region_y(Ch, y);
+            const float sy = Ch.sig[L.ky];
+            if (sy != sx) {
+                lo = __fmul_rn(sy, Ch.S1);
+                hi = __fmul_rn(sy, Ch.S2);
+                for (int d = 0; d < D; ++d) {
+                    const uint32_t dd = y[d] - Ch.q[(size_t)d * Ch.qd + (size_t)c * Ch.qc];
+                    const float m = __uint2float_rn(dd < 0x80000000u ? dd : 0u - dd);
+                    if (!(m >= lo && m <= hi)) R = 0;
                 }
             }
         }

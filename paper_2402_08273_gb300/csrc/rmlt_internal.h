@@ -63,6 +63,7 @@ struct DevChains {
     int32_t C = 0, D = 0, W = 0, H = 0, region_px = 1, nx = 1, m = 1, max_depth = 0, E = 1, L = 10;
     int32_t weighted = 0;
     int32_t truncnorm = 0;        // small-step kernel: 0 Kelemen, 1 truncated normal
+    int32_t dcells = 0;           // 4-D partition: cells per axis over (u5, u6); <= 1 screen only
     uint32_t* q = nullptr;        // word d of chain c at q[d qd + c qc]: [D][C] (qd = C, qc = 1)
     int64_t qd = 0, qc = 1;       //   or, inside the wavefront form's epoch, a [C][D] copy (qd = 1, qc = D)
     float* f = nullptr;           // [3][C]

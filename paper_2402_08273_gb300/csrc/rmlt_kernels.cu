@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
     Ch.lf[2 * plane + o] = p.L.z;
     float piy = lum(p.L.x, p.L.y, p.L.z);
     if (!isfinite(piy)) piy = 0.f;   // the chain kernel counts and zeroes invalid contributions
-    const int ky = region_of(Ch, y[0], y[1]);
+    const int ky = region_y(Ch, y);
     atomicAdd(&Ch.Bk[ky], (double)piy);
     // reduce over the lanes that arrive together (one atomic per group)
     const unsigned m = __activemask();
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     B.f[s] = f.x;
     B.f[n_boot + s] = f.y;
     B.f[2 * n_boot + s] = f.z;
-    const int k = region_of(Ch, y[0], y[1]);
+    const int k = region_y(Ch, y);
     if (pv != 0.f) atomicAdd(&Ch.Bk[k], (double)pv);
 }
 
@@ -598,19 +598,21 @@ __global__ void bootstrap_select_kernel(const DevChains Ch, long long K, const B
     if (sel < 0) sel = (long long)c * K;
     B.partial[c] = cum;
     const int D = Ch.D, C = Ch.C;
-    uint32_t q0 = 0, q1 = 0;
+    uint32_t q0 = 0, q1 = 0, q5 = 0, q6 = 0;
     for (int jj = 0; 4 * jj < D; ++jj) {
         const uint4 r = philox((uint32_t)sel, (uint32_t)((unsigned long long)sel >> 32), 0xFFFFFFFFu,
                                0x8000u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
         const uint32_t v[4] = {r.x, r.y, r.z, r.w};
         for (int a = 0; a < 4 && 4 * jj + a < D; ++a) Ch.q[(size_t)(4 * jj + a) * C + c] = v[a];
         if (jj == 0) { q0 = r.x; q1 = r.y; }
+        if (jj == 1) { q5 = r.y; q6 = r.z; }
     }
     Ch.f[c] = B.f[sel];
     Ch.f[C + c] = B.f[n_eff + sel];
     Ch.f[2 * C + c] = B.f[2 * n_eff + sel];
     Ch.pi[c] = B.pi[sel];
-    Ch.k[c] = region_of(Ch, q0, q1);
+    const uint32_t qv[7] = {q0, q1, 0u, 0u, 0u, q5, q6};
+    Ch.k[c] = region_y(Ch, qv);
 }
 
 // fixed-order binary64 sum of the per-chain slice sums (deterministic)

@@ -59,7 +59,7 @@ class ChainParams(C.Structure):
                 ("partition", C.c_int32), ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32),
                 ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64),
                 ("p_mala", C.c_double), ("mala_tau", C.c_double), ("mala_drift_max", C.c_double),
-                ("kernel", C.c_int32), ("kernel_pad_", C.c_int32)]
+                ("kernel", C.c_int32), ("dir_cells", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -155,7 +155,7 @@ def default_params(**kw) -> dict:
              s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
              lambda_min=-30.0, lambda_max=None, w_floor=1e-3, partition=0, qt_max_leaves=4096,
              qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3,
-             mala_drift_max=0.1, kernel=KERNEL_KELEMEN, kernel_pad_=0)
+             mala_drift_max=0.1, kernel=KERNEL_KELEMEN, dir_cells=0)
     p.update(kw)
     if p["lambda_max"] is None:
         # Kelemen: sigma s2 <= 1/2; truncated normal: sigma <= 4
@@ -260,7 +260,8 @@ class Renderer:
         self.D = 2 + 5 * p["max_depth"]
         nx = -(-p["width"] // p["region_px"])
         ny = -(-p["height"] // p["region_px"])
-        self.m = p["qt_max_leaves"] if p["partition"] == 1 else nx * ny   # region table capacity
+        g = p["dir_cells"] if p["dir_cells"] > 1 else 1
+        self.m = p["qt_max_leaves"] if p["partition"] == 1 else nx * ny * g * g   # region table capacity
 
     def step(self, n_mutations: int):
         _check(lib().rmlt_step(self.h, int(n_mutations)))
@@ -398,7 +399,8 @@ class Renderer:
         self.D = 2 + 5 * self.params["max_depth"]
         nx = -(-self.params["width"] // self.params["region_px"])
         ny = -(-self.params["height"] // self.params["region_px"])
-        self.m = nx * ny
+        g = self.params["dir_cells"] if self.params["dir_cells"] > 1 else 1
+        self.m = self.params["qt_max_leaves"] if self.params["partition"] == 1 else nx * ny * g * g
 
 
 def u_to_words(u):

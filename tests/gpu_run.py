@@ -56,7 +56,7 @@ def oracle_params(p: dict) -> dict:
     keys = ("n_chains", "width", "height", "region_px", "max_depth", "epoch_len", "L", "target_mode",
             "n_bootstrap", "seed", "p_large", "s1", "s2", "alpha_star", "gamma_max", "gamma_scale",
             "lambda_init", "lambda_min", "lambda_max", "w_floor", "partition", "qt_max_leaves",
-            "qt_max_depth", "qt_split", "qt_refine")
+            "qt_max_depth", "qt_split", "qt_refine", "kernel", "dir_cells")
     return {k: p[k] for k in keys}
 
 

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 def test_host_side_errors_without_gpu():
     from paper_2402_08273_gb300 import rmlt
     L = rmlt.lib()
-    assert L.rmlt_abi_version() == 4
+    assert L.rmlt_abi_version() == 5
     # NULL context / NULL out: argument errors, no device needed
     assert L.rmlt_create(None, 0, None) == -1
     assert L.rmlt_step(None, 1) == -1
