@@ -481,6 +481,8 @@ def run_relmse(args, w):
                             qt_refine=10_000_000),
         "weighted": dict(target_mode=1),
     }
+    # 4-D partition in PSS: the grid's regions crossed with 2 x 2 cells over (u5, u6)
+    variants["ra_grid_4d"] = dict(dir_cells=2)
     if all(int(t) == 0 for t in scene["mat_type"]):
         # Langevin strategy (differentiable, Lambertian scenes): 30 % of the
         # mutations, the rest as in the plain variants

@@ -124,7 +124,8 @@ typedef struct {
      * partition, Sec. 5.4): each screen region is crossed with a dir_cells x
      * dir_cells grid over the first bounce's BSDF coordinates (u5, u6), so
      * m = regions on screen x dir_cells^2.  0 or 1 = screen only.  Needs the
-     * grid partition, the plain target and max_depth >= 1. */
+     * grid partition, the plain target, max_depth >= 1 and no Langevin
+     * strategy; not for batched members. */
     int32_t dir_cells;
 } rmlt_chain_params;
 #define RMLT_KERNEL_KELEMEN 0

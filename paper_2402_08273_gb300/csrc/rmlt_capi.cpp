@@ -433,9 +433,10 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
         return fail(RMLT_E_INVALID_ARG, "unknown partition");
     if (p->dir_cells < 0 || p->dir_cells > 64) return fail(RMLT_E_INVALID_ARG, "dir_cells outside [0, 64]");
     if (p->dir_cells > 1) {
-        if (p->partition != RMLT_PARTITION_GRID || p->target_mode != RMLT_TARGET_PLAIN || p->max_depth < 1 || c->S.toy)
-            return fail(RMLT_E_INVALID_ARG, "the 4-D partition needs the grid partition, the plain target and a scene "
-                        "with max_depth >= 1");
+        if (p->partition != RMLT_PARTITION_GRID || p->target_mode != RMLT_TARGET_PLAIN || p->max_depth < 1 || c->S.toy ||
+            p->p_mala > 0.0)
+            return fail(RMLT_E_INVALID_ARG, "the 4-D partition needs the grid partition, the plain target, a scene "
+                        "with max_depth >= 1 and no Langevin strategy");
         const int64_t m4 = (int64_t)((p->width + p->region_px - 1) / p->region_px) *
                            ((p->height + p->region_px - 1) / p->region_px) * p->dir_cells * p->dir_cells;
         if (m4 > (1 << 24)) return fail(RMLT_E_INVALID_ARG, "more than 2^24 regions");
@@ -1110,6 +1111,7 @@ rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
     if (c->tr) return fail(RMLT_E_STATE, "member %d: the trace instrument is set", i);
     if (c->wavefront) return fail(RMLT_E_STATE, "member %d: the wavefront form is set", i);
     if (c->Ch.T_mala) return fail(RMLT_E_STATE, "member %d: the Langevin strategy is set", i);
+    if (c->Ch.dcells > 1) return fail(RMLT_E_STATE, "member %d: the 4-D partition is set", i);
     return RMLT_OK;
 }
 

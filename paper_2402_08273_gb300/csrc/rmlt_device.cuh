@@ -101,11 +101,14 @@ __device__ __forceinline__ int region_of(const DevChains& Ch, uint32_t q0, uint3
 // Region of a state's words y: the screen region, crossed (4-D partition in
 // PSS, the analogue of the paper's 4-D partition of Sec. 5.4) with a
 // dcells x dcells grid over the first bounce's BSDF coordinates (u5, u6).
-template <class Y>
+// D4: the partition is known at compile time to be 4-D (1), screen only (0),
+// or read from the table (-1)
+template <int D4 = -1, class Y>
 __device__ __forceinline__ int region_y(const DevChains& Ch, Y y)
 {
     int k = region_of(Ch, y[0], y[1]);
-    if (Ch.dcells > 1) k = k * Ch.dcells * Ch.dcells + pixel_x(y[5], Ch.dcells) + pixel_x(y[6], Ch.dcells) * Ch.dcells;
+    if (D4 == 1 || (D4 < 0 && Ch.dcells > 1))
+        k = k * Ch.dcells * Ch.dcells + pixel_x(y[5], Ch.dcells) + pixel_x(y[6], Ch.dcells) * Ch.dcells;
     return k;
 }
 
@@ -853,7 +856,7 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
 // Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1 line
 // 10) and decide the reverse-kernel support; returns false when the proposal
 // needs no path (rejected early, or the toy integrand evaluated directly).
-template <bool MALA = false, bool BRUTE = false, class Y>
+template <bool MALA = false, bool BRUTE = false, bool D4 = false, class Y>
 __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChains& Ch, int c, uint64_t mut0,
                                                ChainLane& L, Y y, Path& p, uint32_t* stack = nullptr,
                                                const float4* s_tris = nullptr, unsigned* rays = nullptr)
@@ -881,7 +884,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
             if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
             if (4 * jj + 3 < D) y[4 * jj + 3] = r.w;
         }
-        L.ky = region_y(Ch, y);
+        L.ky = region_y<D4 ? 1 : 0>(Ch, y);
     } else if (Ch.truncnorm) {
         // truncated normal of standard deviation sigma_{k(x)} on (-1/2, 1/2)
         // (the paper's kernel family, Sec. 5.2); the ratio of the reverse and
@@ -907,7 +910,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 }
             }
         }
-        L.ky = region_y(Ch, y);
+        L.ky = region_y<D4 ? 1 : 0>(Ch, y);
         const float sy = Ch.sig[L.ky];
         if (sy != sx) {
             const float zy = erff(0.353553390593273762f / sy);
@@ -934,7 +937,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 o1 = kelemen_offset(r.z, sigS2, Ch.log2_ratio);
                 y[d0 + 1] = (r.w >> 31) ? y[d0 + 1] - o1 : y[d0 + 1] + o1;
             }
-            if (jj == 0 && Ch.dcells <= 1) {
+            if (jj == 0 && !D4) {
                 L.ky = region_of(Ch, y[0], y[1]);
                 const float sy = Ch.sig[L.ky];
                 if (sy != sx) {
@@ -953,10 +956,10 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
                 }
             }
         }
-        if (Ch.dcells > 1) {
+        if (D4) {
             // the 4-D region needs dims 5 and 6: the reverse-kernel support is
             // checked afterwards on the offset magnitudes y - x
-            L.ky = region_y(Ch, y);
+            L.ky = region_y<D4 ? 1 : 0>(Ch, y);
             const float sy = Ch.sig[L.ky];
             if (sy != sx) {
                 lo = __fmul_rn(sy, Ch.S1);

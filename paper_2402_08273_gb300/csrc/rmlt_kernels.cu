@@ -32,7 +32,7 @@ enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 }
 
 // The epoch of chain c (one thread); s_tris holds the staged triangles of a
 // brute-force scene, s_stack the block's traversal stacks.
-template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false>
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false>
 __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
                                                  const float4* s_tris, uint32_t* s_stack)
 {
@@ -144,7 +144,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
                     phase = L.j < Ch.E ? kSetup : kIdle;
                 }
                 if (phase == kSetup) {
-                    if (mutation_setup<MALA, BRUTE>(S, Ch, c, mut0, L, y, p, stack, s_tris, &st[5])) {
+                    if (mutation_setup<MALA, BRUTE, D4>(S, Ch, c, mut0, L, y, p, stack, s_tris, &st[5])) {
                         trav_begin(T, p.o, p.d, p.tmax, p.any);
                         phase = kTraverse;
                     } else {
@@ -195,7 +195,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
 
 // mut0_dev, when set, holds the epoch's first mutation index on the device
 // (a graph replayed over several epochs advances it there)
-template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false>
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false>
 __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0,
                                                                   const unsigned long long* mut0_dev)
 {
@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene
     __shared__ uint32_t s_stack[kStackSize * kChainBlock];
     if (BRUTE) stage_triangles(S, s_tris);
     if (mut0_dev) mut0 = *mut0_dev;
-    chain_epoch_body<BRUTE, TRACE, COUNT, MALA>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris,
-                                                 s_stack);
+    chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris,
+                                                     s_stack);
 }
 
 // grad log pi of the chains' current states (Langevin strategy: at
@@ -673,7 +673,8 @@ static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_
 {
     const int blocks = (c.C + kChainBlock - 1) / kChainBlock;
     const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
-    auto kern = chain_epoch_kernel<B, T, K>;
+    // the 4-D partition has its own instance, so the screen-only kernel carries none of its code
+    auto kern = c.dcells > 1 ? chain_epoch_kernel<B, T, K, false, true> : chain_epoch_kernel<B, T, K>;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;

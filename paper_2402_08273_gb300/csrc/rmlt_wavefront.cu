@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S,
 // ---------------------------------------------------------------------------
 // setup: finish the mutations whose path ended, draw the next proposals
 // ---------------------------------------------------------------------------
-template <bool TRACE>
+template <bool TRACE, bool D4 = false>
 __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S, DevChains Ch, const DevWave W)
 {
     const int C = Ch.C;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S,
             uint32_t yl[kMaxDim];
             bool ray = false;
             while (L.j < Ch.E) {
-                if (mutation_setup(S, Ch, c, mut0, L, yl, p)) {
+                if (mutation_setup<false, false, D4>(S, Ch, c, mut0, L, yl, p)) {
                     ray = true;
                     break;
                 }
@@ -573,7 +573,7 @@ cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevW
     k1.gridDim = dim3((unsigned)((C + kChainBlock - 1) / kChainBlock));
     k1.blockDim = dim3(kChainBlock);
     k1.kernelParams = a_shade;
-    k2.func = (void*)wf_setup_kernel<T>;
+    k2.func = Ch.dcells > 1 ? (void*)wf_setup_kernel<T, true> : (void*)wf_setup_kernel<T>;
     k2.gridDim = dim3((unsigned)setup_ctas);
     k2.blockDim = dim3(kChainBlock);
     k2.kernelParams = a_setup;
@@ -624,7 +624,8 @@ cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int tr
     const unsigned g1 = (unsigned)((Ch.C + kChainBlock - 1) / kChainBlock);
     for (unsigned w = 0; w < W.wave_cap; ++w) {
         wf_shade_kernel<B><<<g1, kChainBlock, 0, st>>>(S, Ch, W);
-        wf_setup_kernel<T><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
+        if (Ch.dcells > 1) wf_setup_kernel<T, true><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
+        else wf_setup_kernel<T><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
         wf_trace_kernel<B, K><<<(unsigned)trace_ctas, kChainBlock, tshm, st>>>(S, W, Ch.C, Ch.stats);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
