@@ -78,7 +78,29 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     while (true) {
         __syncwarp();
         if (phase == kTraverse) {
-            if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) phase = kShade;
+            if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) {
+                if (T.any) {
+                    // the shadow ray of the last interaction: its contribution
+                    // now, then straight on with the extension ray that the
+                    // interaction already drew (no shading batch needed)
+                    ++st[5];
+                    if (T.overflow) {
+                        ++st[6];
+                        p.L = {0.f, 0.f, 0.f};
+                        p.done = 1;
+                    } else if (T.tri < 0) {
+                        p.L = p.L + p.P;
+                    }
+                    if (p.done) {
+                        L.fy = p.L;
+                        phase = kFinish;
+                    } else {
+                        trav_begin(T, p.o, p.d, p.tmax, 0);
+                    }
+                } else {
+                    phase = kShade;
+                }
+            }
         }
         if (COUNT) {
             __syncwarp();
@@ -106,18 +128,29 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
             }
             if (phase == kShade) {
                 ++st[5];
+                bool shadow = false;
                 if (T.overflow) {
                     ++st[6];
                     p.done = 1;
                     p.L = {0.f, 0.f, 0.f};
+                } else if (T.tri < 0 || !shade_hit<BRUTE>(p, S, Hit{T.t, T.tri, T.ta, T.tb, T.tc})) {
+                    p.done = 1;
                 } else {
-                    path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
+                    // next-event sample and BSDF continuation together: the
+                    // shadow ray goes first, the extension ray waits in p
+                    if (nee_sample<BRUTE>(p, S, s_tris, y)) {
+                        trav_begin(T, p.o, p.d, p.tmax, 1);
+                        shadow = true;
+                    }
+                    path_continue(p, S, y, Ch.max_depth);
                 }
-                if (p.done) {
+                if (shadow) {
+                    phase = kTraverse;
+                } else if (p.done) {
                     L.fy = p.L;
                     phase = kFinish;
                 } else {
-                    trav_begin(T, p.o, p.d, p.tmax, p.any);
+                    trav_begin(T, p.o, p.d, p.tmax, 0);
                     phase = kTraverse;
                 }
             }
