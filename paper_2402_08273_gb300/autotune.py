@@ -13,8 +13,10 @@ from __future__ import annotations
 
 CANDIDATES = (
     {"form": "chain", "batch_shade": 8, "batch_setup": 8},
-    {"form": "chain", "batch_shade": 4, "batch_setup": 8},
     {"form": "chain", "batch_shade": 12, "batch_setup": 8},
+    {"form": "chain", "batch_shade": 12, "batch_setup": 4},
+    {"form": "chain", "batch_shade": 12, "batch_setup": 12},
+    {"form": "chain", "batch_shade": 16, "batch_setup": 8},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
 )
