@@ -192,6 +192,15 @@ __device__ __forceinline__ void trav_begin(Trav& T, V3 o, V3 d, float tmax, int 
     T.overflow = 0;
 }
 
+// This thread's traversal stack in a block's shared array of kStackSize
+// entries per thread: panels of kStackStride threads, one column per thread,
+// so the lanes of a warp touch consecutive words (no bank conflicts) whatever
+// the block size (a multiple of kStackStride).
+__device__ __forceinline__ uint32_t* thread_stack(uint32_t* s_stack)
+{
+    return s_stack + (threadIdx.x / kStackStride) * (kStackSize * kStackStride) + threadIdx.x % kStackStride;
+}
+
 // one step; returns true once the ray is resolved
 template <bool BRUTE>
 __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevScene& S, const float4* s_tris,
@@ -262,12 +271,12 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
 #pragma unroll
         for (int k = 3; k >= 1; --k) {
             if (key[k] != INFINITY) {
-                if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = cr[k];
+                if (T.sp < kStackSize) stack[kStackStride * T.sp++] = cr[k];
                 else T.overflow = 1;
             }
         }
 
-        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
+        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef);
     } else if (!(ref & kLeafBit)) {
         ++n_nodes;
         const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
@@ -290,7 +299,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (T.sp < kStackSize) stack[kChainBlock * T.sp++] = first0 ? c1 : c0;
+            if (T.sp < kStackSize) stack[kStackStride * T.sp++] = first0 ? c1 : c0;
             else T.overflow = 1;
             next = first0 ? c0 : c1;
         } else if (h0) {
@@ -298,7 +307,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         } else if (h1) {
             next = c1;
         } else {
-            next = T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef;
+            next = T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef;
         }
     } else {
         const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
@@ -316,7 +325,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
                 found = true;
             }
         }
-        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kChainBlock * --T.sp] : kNoRef);
+        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef);
     }
     T.ref = T.overflow ? kNoRef : next;
     return T.ref == kNoRef;

@@ -13,7 +13,10 @@ namespace rmlt {
 
 constexpr int kMaxDim = 2 + 5 * RMLT_MAX_DEPTH;   // 62 primary-sample dimensions
 constexpr int kStackSize = 48;                      // traversal stack entries per ray (shared memory)
-constexpr int kChainBlock = 128;                    // threads per block of the chain kernel
+constexpr int kChainBlock = 128;                    // threads per block of the per-chain / per-path kernels
+constexpr int kEpochBlock = 64;                     // threads per block of the chain epoch kernel (BVH scenes)
+constexpr int kStackStride = 64;                    // traversal stacks: panels of 64 threads, one column each
+static_assert(kChainBlock % kStackStride == 0 && kEpochBlock % kStackStride == 0, "stack panels");
 
 // statistic slots in DevChains::stats
 enum StatSlot {

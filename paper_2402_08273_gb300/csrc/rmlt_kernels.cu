@@ -20,14 +20,16 @@
 namespace rmlt {
 namespace {
 
-// One thread per chain; the unit of work is one traversal step.  Every loop
-// iteration advances each lane with a live ray by one BVH node or leaf.  A
-// lane whose ray is resolved waits until at least `batch_shade` lanes (or
+// One thread per chain; the unit of work is one traversal step.  Every step
+// advances each lane with a live ray by one BVH node or leaf.  A lane whose
+// extension ray is resolved waits until at least `batch_shade` lanes (or
 // every lane with work) are waiting, then the waiting lanes shade together
-// (path_on_hit: emission, next-event sample, BSDF sample -> the next ray).
-// Lanes whose path ended finish their mutation and draw the next proposal in
-// batches of `batch_setup` the same way.  The batches keep the expensive,
-// divergent parts convergent while the traversal keeps every lane busy.
+// (emission, next-event sample and BSDF sample at once: the shadow ray is
+// traversed next and resolved inside the traversal loop, then the extension
+// ray).  Lanes whose path ended finish their mutation and draw the next
+// proposal in batches of `batch_setup` the same way.  The batches keep the
+// expensive, divergent parts convergent while the traversal keeps every lane
+// busy.
 enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 };
 
 // The epoch of chain c (one thread); s_tris holds the staged triangles of a
@@ -65,7 +67,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
     uint32_t y[kMaxDim];
     // traversal stack in shared memory, one column per thread (conflict-free)
-    uint32_t* stack = s_stack + threadIdx.x;
+    uint32_t* stack = thread_stack(s_stack);
     Path p;
     Trav T;
     T.ref = kNoRef;
@@ -76,50 +78,58 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     long long t_start = 0, t_mark = 0;
     if (COUNT) t_start = t_mark = clock64();
     while (true) {
-        __syncwarp();
-        if (phase == kTraverse) {
-            if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) {
-                if (T.any) {
-                    // the shadow ray of the last interaction: its contribution
-                    // now, then straight on with the extension ray that the
-                    // interaction already drew (no shading batch needed)
-                    ++st[5];
-                    if (T.overflow) {
-                        ++st[6];
-                        p.L = {0.f, 0.f, 0.f};
-                        p.done = 1;
-                    } else if (T.tri < 0) {
-                        p.L = p.L + p.P;
-                    }
-                    if (p.done) {
-                        L.fy = p.L;
-                        phase = kFinish;
+        // traversal steps until a batch is due: enough lanes waiting to shade
+        // or to finish, or no lane left traversing (the votes of the batch
+        // conditions are paid once per step, the batch code only when due)
+        unsigned m_tr, m_sh;
+        int bs_eff = bs, bf_eff = bf;
+        while (true) {
+            __syncwarp();
+            if (phase == kTraverse) {
+                if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) {
+                    if (T.any) {
+                        // the shadow ray of the last interaction: its contribution
+                        // now, then straight on with the extension ray that the
+                        // interaction already drew (no shading batch needed)
+                        ++st[5];
+                        if (T.overflow) {
+                            ++st[6];
+                            p.L = {0.f, 0.f, 0.f};
+                            p.done = 1;
+                        } else if (T.tri < 0) {
+                            p.L = p.L + p.P;
+                        }
+                        if (p.done) {
+                            L.fy = p.L;
+                            phase = kFinish;
+                        } else {
+                            trav_begin(T, p.o, p.d, p.tmax, 0);
+                        }
                     } else {
-                        trav_begin(T, p.o, p.d, p.tmax, 0);
+                        phase = kShade;
                     }
-                } else {
-                    phase = kShade;
                 }
             }
+            m_tr = __ballot_sync(FULL, phase == kTraverse);
+            m_sh = __ballot_sync(FULL, phase == kShade);
+            const unsigned m_fs0 = __ballot_sync(FULL, phase == kFinish || phase == kSetup);
+            // fewer lanes at work (the end of the epoch): optionally smaller batches
+            if (Ch.adaptive_batch) {
+                const int busy = __popc(__ballot_sync(FULL, phase != kIdle));
+                bs_eff = min(bs, (busy + 3) >> 2);
+                bf_eff = min(bf, (busy + 3) >> 2);
+            }
+            if (COUNT) {
+                sched[0] += 1;
+                sched[1] += __popc(m_tr);
+            }
+            if (!m_tr || __popc(m_sh) >= bs_eff || __popc(m_fs0) >= bf_eff) break;
         }
         if (COUNT) {
             __syncwarp();
             const long long t = clock64();
             cyc[0] += t - t_mark;
             t_mark = t;
-        }
-        const unsigned m_tr = __ballot_sync(FULL, phase == kTraverse);
-        const unsigned m_sh = __ballot_sync(FULL, phase == kShade);
-        // fewer lanes at work (the end of the epoch): optionally smaller batches
-        int bs_eff = bs, bf_eff = bf;
-        if (Ch.adaptive_batch) {
-            const int busy = __popc(__ballot_sync(FULL, phase != kIdle));
-            bs_eff = min(bs, (busy + 3) >> 2);
-            bf_eff = min(bf, (busy + 3) >> 2);
-        }
-        if (COUNT) {
-            sched[0] += 1;
-            sched[1] += __popc(m_tr);
         }
         if (m_sh && (__popc(m_sh) >= bs_eff || !m_tr)) {
             if (COUNT) {
@@ -226,14 +236,23 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     }
 }
 
+// Threads per block of the chain epoch kernel.  BVH scenes: 64, so that the
+// 2^16 chains of a typical population spread over the SMs in steps of two
+// warps (at most 14 warps on an SM of a 152-SM GPU instead of 16 with
+// 128-thread blocks), with 8 blocks per SM keeping the register budget at
+// 128 per thread.  Brute-force scenes stage their triangles per block, so
+// they keep 128-thread blocks.
+template <bool BRUTE>
+__host__ __device__ constexpr int epoch_block() { return BRUTE ? kChainBlock : kEpochBlock; }
+
 // mut0_dev, when set, holds the epoch's first mutation index on the device
 // (a graph replayed over several epochs advances it there)
 template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false>
-__global__ void __launch_bounds__(kChainBlock) chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0,
-                                                                  const unsigned long long* mut0_dev)
+__global__ void __launch_bounds__(epoch_block<BRUTE>(), BRUTE ? 4 : 8)
+    chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0, const unsigned long long* mut0_dev)
 {
     extern __shared__ float4 s_tris[];
-    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    __shared__ uint32_t s_stack[kStackSize * epoch_block<BRUTE>()];
     if (BRUTE) stage_triangles(S, s_tris);
     if (mut0_dev) mut0 = *mut0_dev;
     chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris,
@@ -260,7 +279,7 @@ __global__ void __launch_bounds__(kChainBlock) state_grad_kernel(const DevScene 
         GradRec rec[RMLT_MAX_DEPTH];
         V3 f;
         unsigned rays = 0;
-        const int nb = path_forward_rec<BRUTE>(S, s_tris, s_stack + threadIdx.x, y, Ch.max_depth, rec, f, rays);
+        const int nb = path_forward_rec<BRUTE>(S, s_tris, thread_stack(s_stack), y, Ch.max_depth, rec, f, rays);
         if (nb < 0) {
             for (int d = 0; d < D; ++d) g[d] = 0.0f;
         } else {
@@ -292,7 +311,7 @@ __global__ void __launch_bounds__(kChainBlock) path_grad_kernel(const DevScene S
     } else {
         GradRec rec[RMLT_MAX_DEPTH];
         unsigned rays = 0;
-        const int nb = path_forward_rec<BRUTE>(S, s_tris, s_stack + threadIdx.x, y, Ch.max_depth, rec, f, rays);
+        const int nb = path_forward_rec<BRUTE>(S, s_tris, thread_stack(s_stack), y, Ch.max_depth, rec, f, rays);
         if (nb < 0) {
             f = {0.f, 0.f, 0.f};
             for (int d = 0; d < D; ++d) g[d] = 0.0f;
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
     }
     Path p;
     Trav T;
-    uint32_t* stack = s_stack + threadIdx.x;
+    uint32_t* stack = thread_stack(s_stack);
     unsigned nn = 0, nt = 0, rays = 0, ovf = 0;
     path_begin(p, S, y);
     while (!p.done) {
@@ -588,7 +607,7 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     } else {
         Path p;
         Trav T;
-        uint32_t* stack = s_stack + threadIdx.x;
+        uint32_t* stack = thread_stack(s_stack);
         path_begin(p, S, y);
         while (!p.done) {
             trav_begin(T, p.o, p.d, p.tmax, p.any);
@@ -704,7 +723,8 @@ __global__ void read_image_kernel(const DevChains Ch, const double* bhat_total, 
 template <bool B, bool T, bool K>
 static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
 {
-    const int blocks = (c.C + kChainBlock - 1) / kChainBlock;
+    constexpr int nt = epoch_block<B>();
+    const int blocks = (c.C + nt - 1) / nt;
     const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
     // the 4-D partition has its own instance, so the screen-only kernel carries none of its code
     auto kern = c.dcells > 1 ? chain_epoch_kernel<B, T, K, false, true> : chain_epoch_kernel<B, T, K>;
@@ -712,31 +732,33 @@ static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
-    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0, nullptr);
+    kern<<<blocks, nt, shm, st>>>(s, c, mut0, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const BatchMember& member, bool count_work,
                                       cudaStream_t st)
 {
-    const int blocks = (member.Ch.C + kChainBlock - 1) / kChainBlock;
+    constexpr int nt = epoch_block<false>();
+    const int blocks = (member.Ch.C + nt - 1) / nt;
     const unsigned long long* m0 = &member_dev->mut0;
-    if (count_work) chain_epoch_kernel<false, false, true><<<blocks, kChainBlock, 0, st>>>(member.S, member.Ch, 0, m0);
-    else chain_epoch_kernel<false, false, false><<<blocks, kChainBlock, 0, st>>>(member.S, member.Ch, 0, m0);
+    if (count_work) chain_epoch_kernel<false, false, true><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
+    else chain_epoch_kernel<false, false, false><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
     return cudaGetLastError();
 }
 
 template <bool B>
 static cudaError_t launch_mala_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
 {
-    const int blocks = (c.C + kChainBlock - 1) / kChainBlock;
+    constexpr int nt = epoch_block<B>();
+    const int blocks = (c.C + nt - 1) / nt;
     const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
     auto kern = chain_epoch_kernel<B, false, false, true>;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
     }
-    kern<<<blocks, kChainBlock, shm, st>>>(s, c, mut0, nullptr);
+    kern<<<blocks, nt, shm, st>>>(s, c, mut0, nullptr);
     return cudaGetLastError();
 }
 

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const int refill = W.refill;
-    uint32_t* stack = s_stack + threadIdx.x;
+    uint32_t* stack = thread_stack(s_stack);
     unsigned nn = 0, nt = 0;
     Trav T;
     T.ref = kNoRef;
