@@ -85,7 +85,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
         int bs_eff = bs, bf_eff = bf;
         while (true) {
             __syncwarp();
-            if (phase == kTraverse) {
+            if (step_turn<BRUTE>(phase == kTraverse, T)) {
                 if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) {
                     if (T.any) {
                         // the shadow ray of the last interaction: its contribution

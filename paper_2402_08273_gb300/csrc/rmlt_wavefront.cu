@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
             }
         }
         if (dry && __all_sync(FULL, c < 0)) break;
-        if (c >= 0 && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        if (step_turn<BRUTE>(c >= 0, T) && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
             if (T.any) {
                 W.s[(size_t)kWShd * C + c] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
             } else {
