@@ -330,10 +330,14 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
     } else {
         const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
         bool found = false;
-        for (uint32_t i = first; i < first + cnt; ++i) {
-            ++n_tris;
-            float t;
+        // two triangles per pass: both loads in flight before either test
+        for (uint32_t i = first; i < first + cnt; i += 2) {
+            const bool two = i + 1 < first + cnt;
+            const uint32_t i1 = two ? i + 1 : i;
             const float4 a = __ldg(&S.tris[3 * i]), b = __ldg(&S.tris[3 * i + 1]), c = __ldg(&S.tris[3 * i + 2]);
+            const float4 a1 = __ldg(&S.tris[3 * i1]), b1 = __ldg(&S.tris[3 * i1 + 1]), c1 = __ldg(&S.tris[3 * i1 + 2]);
+            float t;
+            ++n_tris;
             if (hit_tri(T.o, T.d, a, b, c, T.t, t)) {
                 T.t = t;
                 T.tri = (int)i;
@@ -341,6 +345,17 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
                 T.tb = b;
                 T.tc = c;
                 found = true;
+            }
+            if (two) {
+                ++n_tris;
+                if (hit_tri(T.o, T.d, a1, b1, c1, T.t, t)) {
+                    T.t = t;
+                    T.tri = (int)i1;
+                    T.ta = a1;
+                    T.tb = b1;
+                    T.tc = c1;
+                    found = true;
+                }
             }
         }
         next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef);
