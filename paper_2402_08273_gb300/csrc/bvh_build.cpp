@@ -1,7 +1,9 @@
 // Host-side binned SAH builder for the BVH the chain kernel traverses.
 //
-// A binary tree is built with binned SAH (16 bins per axis, leaves of at most
-// 4 triangles) and emitted either as BVH2 or, collapsed, as BVH4.  In both
+// A binary tree is built with binned SAH (32 bins per axis, leaves of at most
+// 2 triangles: with leaf turns and two triangle loads per pass, a leaf costs
+// about what a node does, and smaller leaves measured faster than 4 or 8) and
+// emitted either as BVH2 or, collapsed, as BVH4.  In both
 // layouts an internal node stores its children's boxes, so one node fetch
 // tests all children.
 //
@@ -56,8 +58,8 @@ struct BNode {
     int first = 0, count = 0;
 };
 
-constexpr int kBins = 16;
-constexpr int kLeafMax = 4;
+constexpr int kBins = 32;
+constexpr int kLeafMax = 2;
 
 uint32_t fbits(float f)
 {
