@@ -201,6 +201,19 @@ __device__ __forceinline__ uint32_t* thread_stack(uint32_t* s_stack)
     return s_stack + (threadIdx.x / kStackStride) * (kStackSize * kStackStride) + threadIdx.x % kStackStride;
 }
 
+// A thread's proposal words in a block's shared array of kMaxDim words per
+// thread, in panels of kStackStride columns like the stacks (conflict-free).
+// The epoch kernel keeps them there instead of in local memory: at 448
+// threads per SM, local copies would take ~110 KB of L1 from the BVH.
+struct YPanel {
+    uint32_t* p;
+    __device__ __forceinline__ uint32_t& operator[](int d) const { return p[d * kStackStride]; }
+};
+__device__ __forceinline__ YPanel thread_words(uint32_t* s_y)
+{
+    return YPanel{s_y + (threadIdx.x / kStackStride) * (kMaxDim * kStackStride) + threadIdx.x % kStackStride};
+}
+
 // Leaf turns.  A warp's lanes whose ray waits at a leaf test its triangles
 // together, once at least kLeafBatch of them (or every lane with a ray) are
 // there; until then only the lanes at inner nodes step.  The leaf loop is the

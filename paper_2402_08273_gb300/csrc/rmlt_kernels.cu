@@ -34,10 +34,25 @@ enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 }
 
 // The epoch of chain c (one thread); s_tris holds the staged triangles of a
 // brute-force scene, s_stack the block's traversal stacks.
-template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false>
+// The proposal words: in shared memory (YSM, blocks of NT threads), else in
+// local memory.
+template <bool YSM>
+struct ProposalWords;
+template <>
+struct ProposalWords<true> {
+    static __device__ __forceinline__ YPanel get(uint32_t* s_y, uint32_t*) { return thread_words(s_y); }
+};
+template <>
+struct ProposalWords<false> {
+    static __device__ __forceinline__ uint32_t* get(uint32_t*, uint32_t* y_local) { return y_local; }
+};
+
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false, bool YSM = false,
+          int NT = kChainBlock>
 __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
                                                  const float4* s_tris, uint32_t* s_stack)
 {
+    __shared__ uint32_t s_y[YSM ? kMaxDim * NT : 1];
     const unsigned FULL = 0xFFFFFFFFu;
     const bool valid = c < Ch.C;
     unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};   // accepted, large, small, early, invalid, rays, overflow
@@ -65,7 +80,8 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
     L.amala = 0.f;
     L.n_mala = L.n_mala_acc = 0;
     const bool traced = TRACE && valid && (uint32_t)c % Ch.trace_stride == 0u;
-    uint32_t y[kMaxDim];
+    uint32_t y_local[YSM ? 1 : kMaxDim];
+    const auto y = ProposalWords<YSM>::get(s_y, y_local);
     // traversal stack in shared memory, one column per thread (conflict-free)
     uint32_t* stack = thread_stack(s_stack);
     Path p;
@@ -255,8 +271,10 @@ __global__ void __launch_bounds__(epoch_block<BRUTE>(), BRUTE ? 4 : 8)
     __shared__ uint32_t s_stack[kStackSize * epoch_block<BRUTE>()];
     if (BRUTE) stage_triangles(S, s_tris);
     if (mut0_dev) mut0 = *mut0_dev;
-    chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4>(S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris,
-                                                     s_stack);
+    // proposal words in shared memory on BVH scenes; a brute-force scene's
+    // staged triangles may fill shared memory, so it keeps them local
+    chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4, !BRUTE, epoch_block<BRUTE>()>(
+        S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris, s_stack);
 }
 
 // grad log pi of the chains' current states (Langevin strategy: at
