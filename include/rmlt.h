@@ -281,7 +281,7 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* ctx, int enable);
  * RMLT_TUNE_LARGE_AHEAD traces the epoch's large-step proposals (independent
  * of the chain states) in a separate kernel before the chain kernel;
  * RMLT_TUNE_ADAPTIVE_BATCH shrinks the batches as lanes finish the epoch.
- * They change speed only, never results.  Defaults 12, 8, 0. */
+ * They change speed only, never results.  Defaults 12, 10, 0. */
 #define RMLT_TUNE_LARGE_AHEAD 1
 #define RMLT_TUNE_ADAPTIVE_BATCH 2
 /* RMLT_TUNE_WAVEFRONT runs each epoch in the wavefront form instead of the

@@ -12,11 +12,11 @@ run them on.
 from __future__ import annotations
 
 CANDIDATES = (
-    {"form": "chain", "batch_shade": 8, "batch_setup": 8},
+    {"form": "chain", "batch_shade": 12, "batch_setup": 10},
     {"form": "chain", "batch_shade": 12, "batch_setup": 8},
-    {"form": "chain", "batch_shade": 12, "batch_setup": 4},
     {"form": "chain", "batch_shade": 12, "batch_setup": 12},
-    {"form": "chain", "batch_shade": 16, "batch_setup": 8},
+    {"form": "chain", "batch_shade": 8, "batch_setup": 10},
+    {"form": "chain", "batch_shade": 16, "batch_setup": 10},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
 )
@@ -25,7 +25,7 @@ CANDIDATES = (
 def apply(R, cand: dict) -> None:
     """Set candidate `cand` on renderer R."""
     if cand["form"] == "chain":
-        R.set_tuning(batch_shade=cand.get("batch_shade", 8), batch_setup=cand.get("batch_setup", 8))
+        R.set_tuning(batch_shade=cand.get("batch_shade", 12), batch_setup=cand.get("batch_setup", 10))
     else:
         R.set_tuning(wavefront=True)
         R.set_wavefront(trace_ctas_per_sm=cand.get("trace_ctas_per_sm", 0),

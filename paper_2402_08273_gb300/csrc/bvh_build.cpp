@@ -218,7 +218,9 @@ struct Emitter {
         uint32_t refs[4] = {kEmptyRef, kEmptyRef, kEmptyRef, kEmptyRef};
         Box boxes[4];
         for (int k = 0; k < 4; ++k) {
-            for (int a = 0; a < 3; ++a) { boxes[k].lo[a] = 0.f; boxes[k].hi[a] = 0.f; }
+            // an unused slot gets an inverted infinite box, which every slab
+            // test rejects whatever the ray's direction
+            for (int a = 0; a < 3; ++a) { boxes[k].lo[a] = INFINITY; boxes[k].hi[a] = -INFINITY; }
             if (k < nc) {
                 refs[k] = emit4(ch[k]);
                 boxes[k] = padded(bn[(size_t)ch[k]].box);

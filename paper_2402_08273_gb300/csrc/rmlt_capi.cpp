@@ -90,7 +90,7 @@ struct rmlt_ctx {
     uint32_t tr_stride = 1;
     bool count_work = false;
     uint64_t since_refine = 0;   // mutations since the last quadtree pass
-    int batch_shade = 12, batch_setup = 8;
+    int batch_shade = 12, batch_setup = 10;
     int large_ahead = 0, adaptive_batch = 0;
     int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0;
     DevWave W;                   // wavefront state (allocated on first use)

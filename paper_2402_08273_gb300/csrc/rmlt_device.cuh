@@ -287,7 +287,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
             const float a2 = fmaf(nzs[k], id.z, -ood.z), b2 = fmaf(fzs[k], id.z, -ood.z);
             const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
             const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
-            const bool hit = tn <= tf && rr[k] != kEmptyRef;
+            const bool hit = tn <= tf;   // an unused slot's inverted infinite box never passes
             key[k] = hit ? tn : INFINITY;
             cr[k] = rr[k];
         }

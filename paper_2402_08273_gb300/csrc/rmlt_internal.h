@@ -17,7 +17,7 @@ constexpr int kChainBlock = 128;                    // threads per block of the 
 constexpr int kEpochBlock = 64;                     // threads per block of the chain epoch kernel (BVH scenes)
 constexpr int kStackStride = 64;                    // traversal stacks: panels of 64 threads, one column each
 static_assert(kChainBlock % kStackStride == 0 && kEpochBlock % kStackStride == 0, "stack panels");
-constexpr int kLeafBatch = 10;                      // lanes of a warp at leaves before they test them together
+constexpr int kLeafBatch = 8;                       // lanes of a warp at leaves before they test them together
 
 // statistic slots in DevChains::stats
 enum StatSlot {

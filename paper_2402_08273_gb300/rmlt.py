@@ -333,7 +333,7 @@ class Renderer:
         d["cycles"] = list(d["cycles"])
         return d
 
-    def set_tuning(self, batch_shade: int = 12, batch_setup: int = 8, large_ahead: bool = False,
+    def set_tuning(self, batch_shade: int = 12, batch_setup: int = 10, large_ahead: bool = False,
                    adaptive_batch: bool = False, wavefront: bool = False):
         flags = (1 if large_ahead else 0) | (2 if adaptive_batch else 0) | (4 if wavefront else 0)
         _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup), flags))
