@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S,
 template <bool TRACE, bool D4 = false>
 __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S, DevChains Ch, const DevWave W)
 {
+    __shared__ uint32_t s_y[kMaxDim * kChainBlock];
     const int C = Ch.C;
     WfCounters* ctr = W.ctr;
     const unsigned wv = ctr->wave, buf = wv & 1u, n = ctr->fq_count;
@@ -321,9 +322,9 @@ __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S,
                 mutation_finish<TRACE>(Ch, c, traced, L, y, st);
                 ++L.j;
             }
-            // the proposal is drawn into a local array (the chain kernel's
+            // the proposal is drawn into shared memory (the chain kernel's
             // code path) and stored to [D][C] only when a path needs it
-            uint32_t yl[kMaxDim];
+            const YPanel yl = thread_words(s_y);
             bool ray = false;
             while (L.j < Ch.E) {
                 if (mutation_setup<false, false, D4>(S, Ch, c, mut0, L, yl, p)) {
