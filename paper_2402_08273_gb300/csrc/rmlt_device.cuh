@@ -216,19 +216,19 @@ __device__ __forceinline__ YPanel thread_words(uint32_t* s_y)
 
 // Leaf turns.  A warp's lanes whose ray waits at a leaf test its triangles
 // together, once at least kLeafBatch of them (or every lane with a ray) are
-// there; until then only the lanes at inner nodes step.  The leaf loop is the
-// divergent part of a step (one to four triangles), and without the turns
-// nearly every step of a warp ran both the node and the leaf code.  A ray's
-// own sequence of steps, and so its result, does not change.  Called by all
-// lanes of the warp; `live`: this lane has a ray in traversal.
-template <bool BRUTE, int LB = kLeafBatch>
+// there; until then only the lanes at inner nodes step.  The leaf code is
+// the other half of a step (its own loads and triangle tests), and without
+// the turns nearly every step of a warp ran both the node and the leaf code.
+// A ray's own sequence of steps, and so its result, does not change.  Called
+// by all lanes of the warp; `live`: this lane has a ray in traversal.
+template <bool BRUTE>
 __device__ __forceinline__ bool step_turn(bool live, const Trav& T)
 {
     if (BRUTE) return live;
     const bool at_leaf = live && (T.ref & kLeafBit);
     const unsigned m_leaf = __ballot_sync(0xFFFFFFFFu, at_leaf);
     const unsigned m_node = __ballot_sync(0xFFFFFFFFu, live && !at_leaf);
-    const bool leaf_turn = m_leaf && (!m_node || __popc(m_leaf) >= LB);
+    const bool leaf_turn = m_leaf && (!m_node || __popc(m_leaf) >= kLeafBatch);
     return live && (at_leaf == leaf_turn);
 }
 

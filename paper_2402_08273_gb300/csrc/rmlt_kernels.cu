@@ -32,8 +32,6 @@ namespace {
 // busy.
 enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 };
 
-// The epoch of chain c (one thread); s_tris holds the staged triangles of a
-// brute-force scene, s_stack the block's traversal stacks.
 // The proposal words: in shared memory (YSM, blocks of NT threads), else in
 // local memory.
 template <bool YSM>
@@ -47,6 +45,8 @@ struct ProposalWords<false> {
     static __device__ __forceinline__ uint32_t* get(uint32_t*, uint32_t* y_local) { return y_local; }
 };
 
+// The epoch of chain c (one thread); s_tris holds the staged triangles of a
+// brute-force scene, s_stack the block's traversal stacks.
 template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false, bool YSM = false,
           int NT = kChainBlock>
 __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
