@@ -1,0 +1,43 @@
+"""The BVH builder's output, checked on the host (no GPU).
+
+`tests/bvh_check.cpp` is compiled with the host compiler against the
+library's builder (`csrc/bvh_build.cpp`) and walks the emitted node array:
+the triangle order is a permutation, leaves cover it exactly once with at
+most two triangles each, every vertex lies inside every box above its leaf,
+and unused BVH4 slots hold the empty reference with an inverted infinite box
+(which the traversal relies on to skip them without a test).  Cases: random
+small triangles, triangles with one shared centroid (the builder splits by
+count), long slivers, and a tiny scene; both node widths.
+"""
+import os
+import shutil
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+CSRC = ROOT / "paper_2402_08273_gb300" / "csrc"
+CUDA_INC = Path(os.environ.get("CUDA_HOME", "/usr/local/cuda")) / "include"
+LEAF_MAX = 2
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None or not (CUDA_INC / "cuda_runtime.h").exists():
+        pytest.skip("needs a host C++ compiler and the CUDA headers")
+    exe = tmp_path_factory.mktemp("bvh") / "bvh_check"
+    subprocess.run([cxx, "-O2", "-std=c++17", f"-I{CUDA_INC}", f"-I{ROOT / 'include'}", f"-I{CSRC}",
+                    str(ROOT / "tests" / "bvh_check.cpp"), str(CSRC / "bvh_build.cpp"), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+@pytest.mark.parametrize("width", [4, 2])
+@pytest.mark.parametrize("n_tris,mode,seed", [(20_000, 0, 1), (300, 1, 2), (5_000, 2, 3), (5, 0, 4), (777, 0, 5)])
+def test_bvh_structure(checker, width, n_tris, mode, seed):
+    r = subprocess.run([str(checker), str(width), str(n_tris), str(mode), str(seed), str(LEAF_MAX)],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok ")
