@@ -30,7 +30,22 @@ namespace {
 // proposal in batches of `batch_setup` the same way.  The batches keep the
 // expensive, divergent parts convergent while the traversal keeps every lane
 // busy.
-enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4 };
+// With the Langevin strategy, a lane whose next mutation is a Langevin move
+// waits in kMala: those moves trace their paths one lane at a time, so they
+// run in their own batches of at least kMalaBatch lanes instead of holding
+// up every setup batch.
+enum LanePhase { kIdle = 0, kTraverse = 1, kShade = 2, kFinish = 3, kSetup = 4, kMala = 5 };
+constexpr int kMalaBatch = 8;
+
+// whether mutation L.j of chain c is a Langevin move (the test mutation_setup
+// makes on the mutation's first Philox call)
+__device__ __forceinline__ bool next_is_mala(const DevChains& Ch, int c, uint64_t mut0, const ChainLane& L)
+{
+    const uint64_t mut = mut0 + (uint64_t)L.j;
+    const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+    const uint32_t h = r0.x >> 8;
+    return h >= Ch.T_large && h < Ch.T_large + Ch.T_mala;
+}
 
 // The proposal words: in shared memory (YSM, blocks of NT threads), else in
 // local memory.
@@ -140,6 +155,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
                 sched[1] += __popc(m_tr);
             }
             if (!m_tr || __popc(m_sh) >= bs_eff || __popc(m_fs0) >= bf_eff) break;
+            if (MALA && __popc(__ballot_sync(FULL, phase == kMala)) >= kMalaBatch) break;
         }
         if (COUNT) {
             __syncwarp();
@@ -203,11 +219,16 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
                     phase = L.j < Ch.E ? kSetup : kIdle;
                 }
                 if (phase == kSetup) {
-                    if (mutation_setup<MALA, BRUTE, D4>(S, Ch, c, mut0, L, y, p, stack, s_tris, &st[5])) {
-                        trav_begin(T, p.o, p.d, p.tmax, p.any);
-                        phase = kTraverse;
+                    if (MALA && next_is_mala(Ch, c, mut0, L)) {
+                        phase = kMala;   // made in the next Langevin batch
                     } else {
-                        phase = kFinish;
+                        if (MALA) L.mala = 0;
+                        if (mutation_setup<false, BRUTE, D4>(S, Ch, c, mut0, L, y, p, stack, s_tris, &st[5])) {
+                            trav_begin(T, p.o, p.d, p.tmax, p.any);
+                            phase = kTraverse;
+                        } else {
+                            phase = kFinish;
+                        }
                     }
                 }
             }
@@ -216,6 +237,26 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
                 const long long t = clock64();
                 cyc[2] += t - t_mark;
                 t_mark = t;
+            }
+        }
+        if (MALA) {
+            // Langevin batch: each waiting lane makes its move (proposal,
+            // path with gradient, acceptance probability); the mutation is
+            // finished in the next setup batch
+            const unsigned m_ml = __ballot_sync(FULL, phase == kMala);
+            const bool others = __any_sync(FULL, phase != kMala && phase != kIdle);
+            if (m_ml && (__popc(m_ml) >= kMalaBatch || !others)) {
+                if (phase == kMala) {
+                    // the fields mutation_setup sets before it hands over
+                    const uint64_t mut = mut0 + (uint64_t)L.j;
+                    const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
+                    const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+                    L.large = 0;
+                    L.xi = u24(r0.y);
+                    L.R = 1.0f;
+                    mala_setup<BRUTE>(S, Ch, c, mlo, mhi, L, y, stack, s_tris, st[5]);
+                    phase = kFinish;
+                }
             }
         }
         if (!__any_sync(FULL, phase != kIdle)) break;

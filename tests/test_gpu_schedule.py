@@ -63,3 +63,38 @@ def test_batch_sizes_change_nothing_4d_partition():
     assert ref["R"].n_regions() == 4 * (96 // 8) * (64 // 8)
     for tuning in SCHEDULES:
         _assert_identical(ref, traced_run(bvh_width=4, tuning=tuning, **_kw(dir_cells=2)))
+
+
+def _mala_run(tuning, brute_force_max):
+    from paper_2402_08273_gb300 import rmlt
+    R = rmlt.Renderer()
+    R.load_scene(S.cornell_box(), brute_force_max=brute_force_max)
+    if tuning:
+        R.set_tuning(**tuning)
+    R.init_chains(n_chains=1000, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, n_bootstrap=1 << 14,
+                  p_large=0.3, p_mala=0.3, mala_tau=1e-3, mala_drift_max=0.1, seed=3)
+    R.step(48)
+    R.synchronize()
+    out = {"final": R.read_chain_state(), "hist": R.read_region_hist(), "region": R.read_region_params(),
+           "stats": R.read_stats(), "image_raw": R.read_image(normalized=False)}
+    R.close()
+    return out
+
+
+@pytest.mark.parametrize("brute_force_max", [0, 1])   # 0: brute force (36 triangles), 1: BVH4
+def test_batch_sizes_change_nothing_langevin(brute_force_max):
+    """Langevin moves run in their own batches; the batch sizes around them
+    must not change the chains either (the trace instrument is not available
+    with the Langevin strategy, so states, counts and statistics are compared)."""
+    ref = _mala_run(None, brute_force_max)
+    assert ref["stats"]["mala"] > 0
+    for tuning in SCHEDULES:
+        other = _mala_run(tuning, brute_force_max)
+        for name in ("q", "f", "k"):
+            assert np.array_equal(ref["final"][name], other["final"][name]), f"final {name} differs"
+        assert np.array_equal(ref["hist"], other["hist"])
+        for name, v in ref["region"].items():
+            assert np.array_equal(v, other["region"][name]), f"region {name} differs"
+        for name in STAT_KEYS + ("mala", "mala_accepted"):
+            assert ref["stats"][name] == other["stats"][name], name
+        np.testing.assert_allclose(other["image_raw"], ref["image_raw"], rtol=1e-12, atol=1e-300)
