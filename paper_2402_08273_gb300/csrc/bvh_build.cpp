@@ -15,7 +15,8 @@
 // BVH4 (8 float4 per node, children in the four lanes of each float4):
 //   lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, refs (uint bits), unused
 // A ref is an internal node index, a leaf (kLeafBit | (count-1) << 28 |
-// first triangle in build order), or kEmptyRef for an unused BVH4 slot.
+// first triangle in build order), or kEmptyRef for an unused BVH4 slot, whose
+// box is inverted (lo = +inf, hi = -inf) so that no slab test accepts it.
 // Boxes are widened by `pad` and rounded outward so that binary32 traversal
 // never culls a box a ray grazes.
 #include <algorithm>
