@@ -92,12 +92,32 @@ def measured_traffic(workload: str = "two_rooms"):
         return None
 
 
-def population_params(base: dict, rank: int) -> dict:
-    """One independent chain population per GPU: the same workload with the
-    Philox key offset by the rank (no data-path collective)."""
+def shard_params(base: dict, rank: int, world: int) -> dict:
+    """Rank `rank`'s share of the population of base["n_chains"] chains
+    (global ids rank * C / world ..., the same seed on every rank).  One rank
+    is the unsharded population."""
     p = dict(base)
-    p["seed"] = base["seed"] + rank
+    C = base["n_chains"]
+    if world == 1:
+        return p
+    if C % world:
+        raise ValueError(f"{C} chains do not split over {world} ranks")
+    per = C // world
+    p.update(n_chains=per, chain_first=rank * per, chains_total=C)
     return p
+
+
+def step_sharded(chains, n_epochs: int, counts, sums, all_reduce):
+    """n_epochs epochs of a sharded population: each epoch this rank's chains
+    mutate, the region statistics they added are summed over the ranks (the
+    only data-path exchange: 3 m + 1 integers and m doubles), and every rank
+    runs the same region update on the summed tables.  `chains` is a CUDA
+    Renderer or an oracle population (the same two calls)."""
+    for _ in range(n_epochs):
+        chains.epoch_mutate(counts, sums)
+        all_reduce(counts)
+        all_reduce(sums)
+        chains.epoch_update(counts, sums)
 
 
 def reduce_job(dist, world: int, t_local: float, counts: dict, device) -> tuple[float, dict]:
@@ -294,7 +314,11 @@ def run_ours(args, w):
             dist.barrier()
 
     scene = make_scene(w)
-    params = population_params(w["params"], rank)
+    # weak scaling: each GPU holds the workload's chain count; the population
+    # of world x that many chains is split by global chain id
+    base = dict(w["params"])
+    base.update(n_chains=base["n_chains"] * world, n_bootstrap=base["n_bootstrap"] * world)
+    params = shard_params(base, rank, world)
     M = w["mutations"]
     stream = torch.cuda.Stream(device=dev)
     R = rmlt.Renderer(device=local, stream=stream)
@@ -306,7 +330,19 @@ def run_ours(args, w):
     R.synchronize()
     t_init = time.perf_counter() - t0
     C = params["n_chains"]
-    epochs_per_step = -(-M // params["epoch_len"])
+    E = params["epoch_len"]
+    epochs_per_step = -(-M // E)
+    if world > 1:
+        counts, sums = R.exchange_buffers()
+
+        def all_reduce(t):
+            with torch.cuda.stream(stream):
+                dist.all_reduce(t)
+
+        def step(n):
+            step_sharded(R, -(-n // E), counts, sums, all_reduce)
+    else:
+        step = R.step
 
     # the traversal roofline's two ceilings, measured on this GPU
     l2_gbs, fp32_tflops = C_double(), C_double()
@@ -314,13 +350,13 @@ def run_ours(args, w):
     l2_gbs, fp32_tflops = l2_gbs.value, fp32_tflops.value
 
     for _ in range(args.warmup):
-        R.step(M)
+        step(M)
     R.synchronize()
     # execution form: forced, or the fastest candidate timed on the live chains
     from paper_2402_08273_gb300 import autotune
     tuned = None
     if args.form == "auto":
-        best, timings = autotune.autotune(R)
+        best, timings = autotune.autotune(R, step=step)
         form = best["form"]
         tuned = {"chosen": best, "ms_per_epoch": [[c, round(t, 3)] for c, t in timings]}
     else:
@@ -340,7 +376,7 @@ def run_ours(args, w):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        R.step(M)
+        step(M)
         e1.record(stream)
         times.append((e0, e1))
     torch.cuda.synchronize()
@@ -362,7 +398,7 @@ def run_ours(args, w):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        R.step(M)
+        step(M)
         R.read_image(out=img_h.numpy())
         R.read_region_hist(out=hist_h.numpy().view("uint64"))
     torch.cuda.synchronize()
@@ -373,7 +409,7 @@ def run_ours(args, w):
     # work per ray from one instrumented step (same kernel with counters on)
     R.set_work_counters(True)
     sa = R.read_stats()
-    R.step(params["epoch_len"] * 4)
+    step(params["epoch_len"] * 4)
     sb = R.read_stats()
     R.set_work_counters(False)
     dr = max(1, sb["rays"] - sa["rays"])
@@ -432,7 +468,9 @@ def run_ours(args, w):
                        "mutations_per_step": M, "epochs_per_step": epochs_per_step,
                        "l2": "flushed between timed steps (256 MiB write)", "form": form,
                        "autotune": tuned,
-                       "parallelism": f"{world} independent chain populations (one per GPU)"},
+                       "parallelism": (f"dp{world}: one population of {world} x {C} chains split by global "
+                                       "chain id; per epoch one all-reduce of the region statistics"
+                                       if world > 1 else "one GPU")},
             "rays_per_s": rays / t_max,
             "rays_per_mutation": rays / mutations,
             "gpu_launches": (2 * epochs_per_step * args.steps if form == "chain" else

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 5
+#define RMLT_ABI_VERSION 6
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -48,8 +48,9 @@ typedef enum {
     RMLT_E_OOM = -3,
     RMLT_E_CUDA = -4,
     RMLT_E_STATE = -5,     /* wrong call order, or the context failed earlier */
-    RMLT_E_TIMEOUT = -6,   /* a bounded device-side wait expired */
-    RMLT_E_OVERFLOW = -7,  /* reserved */
+    /* -6 is not used: no kernel of this library waits on another */
+    RMLT_E_OVERFLOW = -7,  /* a device-side bound was exceeded (see rmlt_set_wave_limit and
+                              rmlt_bootstrap_noalloc) */
     RMLT_E_IO = -8
 } rmlt_status;
 
@@ -97,7 +98,13 @@ typedef struct {
     double s1, s2;             /* Kelemen small-step offset range [sigma s1, sigma s2] */
     double alpha_star;         /* target acceptance (Sec. 5.3; 0.5 in Sec. 7.1) */
     double gamma_max, gamma_scale;  /* eq. step_size_n */
-    double lambda_init, lambda_min, lambda_max;
+    double lambda_init, lambda_min;
+    /* upper clamp of lambda_k.  0 or NaN selects the largest value the
+     * kernel allows: 2 ln(1 / (2 s2)) for Kelemen's kernel (sigma s2 <= 1/2,
+     * the largest offset on the torus) and 2 ln 4 for the truncated normal
+     * (sigma <= 4, beyond which it is uniform on the window).  The paper
+     * (Sec. 7.1) bounds lambda only from below. */
+    double lambda_max;
     double w_floor;            /* region-weighted target: lower bound of w_k as a share of 1/m */
     int32_t partition;         /* RMLT_PARTITION_GRID (Sec. 6.1) or RMLT_PARTITION_QUADTREE (Sec. 6.2) */
     int32_t qt_max_leaves;     /* quadtree: region capacity */
@@ -127,6 +134,16 @@ typedef struct {
      * grid partition, the plain target, max_depth >= 1 and no Langevin
      * strategy; not for batched members. */
     int32_t dir_cells;
+    /* Sharding over several GPUs (one context per GPU): this context owns the
+     * chains with global ids chain_first .. chain_first + n_chains - 1 of a
+     * population of chains_total (0 = n_chains: not sharded).  Philox streams
+     * are keyed by the global id, and every context evaluates all
+     * n_bootstrap samples (so b and the starting states do not depend on the
+     * split).  A sharded context advances with rmlt_epoch_mutate /
+     * rmlt_epoch_update around a sum of the region statistics over all
+     * contexts (Sec. 6: the paper's threads share i_k and A_k the same
+     * way); rmlt_step refuses it. */
+    int32_t chain_first, chains_total;
 } rmlt_chain_params;
 #define RMLT_KERNEL_KELEMEN 0
 #define RMLT_KERNEL_TRUNCNORM 1
@@ -148,6 +165,7 @@ typedef struct {
     uint64_t waves;            /* wavefront form: waves run (one trace pass each), summed over epochs */
     uint64_t wave_limit_hits;  /* wavefront form: epochs stopped by the wave limit (0 unless a bug) */
     uint64_t mala, mala_accepted;   /* Langevin moves proposed and accepted */
+    uint64_t boot_overflow;    /* bootstrap paths dropped because the traversal stack overflowed */
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -167,7 +185,10 @@ typedef void (*rmlt_free_fn)(void* user, void* ptr, void* stream);
 rmlt_status rmlt_create(rmlt_ctx** out, int device, void* cuda_stream);
 
 /* Route the context's device allocations through alloc/free (both non-NULL),
- * or back to cudaMalloc/cudaFree (both NULL).  Only before rmlt_load_scene. */
+ * or back to cudaMalloc/cudaFree (both NULL).  Only before rmlt_load_scene.
+ * An allocation that returns NULL fails the call with RMLT_E_OOM; a failed
+ * rmlt_load_scene, rmlt_init_chains or rmlt_restore leaves the context as it
+ * was (its previous scene and chains stay usable). */
 rmlt_status rmlt_set_allocator(rmlt_ctx* ctx, rmlt_alloc_fn alloc, rmlt_free_fn free_fn, void* user);
 
 /* Copy the scene, build a binned-SAH BVH on the host (or keep a flat list when
@@ -198,13 +219,41 @@ rmlt_status rmlt_init_chains(rmlt_ctx* ctx, const rmlt_chain_params* params);
  * boundary.  Asynchronous on the context's stream (no host synchronisation);
  * launch errors are returned here, execution errors at the next synchronising
  * call.  A proposal whose ray overflows the traversal stack is given zero
- * contribution and counted in rmlt_stats.stack_overflow. */
+ * contribution and counted in rmlt_stats.stack_overflow.  RMLT_E_STATE for a
+ * sharded context (use rmlt_epoch_mutate / rmlt_epoch_update). */
 rmlt_status rmlt_step(rmlt_ctx* ctx, uint64_t n_mutations);
+
+/* Sharded stepping, one epoch at a time (Alg. 1 with the region statistics
+ * summed over every context of a population split by chain_first /
+ * chains_total; Sec. 6 "Implementation": all chains share i_k and A_k).
+ *   rmlt_exchange_size: *n_counts u64 words and *n_sums doubles of the two
+ *     exchange buffers (3 m + 1 and m, m the region capacity).
+ *   rmlt_epoch_mutate: E mutations of every chain of this context (Alg. 1
+ *     lines 8-12 and 19), then writes what this epoch added to the region
+ *     tables to the caller's device buffers: counts = [i_k (m)][A_k (m)]
+ *     [h_k (m)][large steps (1)], sums = [sum of pi over the large-step
+ *     proposals per region (m)].
+ *   rmlt_epoch_update: takes the same buffers after the caller summed them
+ *     over all contexts (an all-reduce; u64 sums wrap, so a signed 64-bit
+ *     reduction gives the same bits), sets every table to its value at the
+ *     start of the epoch plus the sums, and runs the region update (Alg. 1
+ *     lines 13-18), the weight update of the weighted target and a due
+ *     quadtree pass.  Every context then holds identical region tables.
+ * An unsharded context may use them too (the buffers passed through
+ * unchanged give exactly rmlt_step(epoch_len)).  Both are asynchronous on the
+ * context's stream; the buffers must be device memory.  Errors: RMLT_E_STATE
+ * (no chains, failed, or the two calls out of order), RMLT_E_INVALID_ARG
+ * (NULL or host buffers, the Langevin strategy), RMLT_E_CUDA. */
+rmlt_status rmlt_exchange_size(rmlt_ctx* ctx, int64_t* n_counts, int64_t* n_sums);
+rmlt_status rmlt_epoch_mutate(rmlt_ctx* ctx, uint64_t* counts, double* sums);
+rmlt_status rmlt_epoch_update(rmlt_ctx* ctx, const uint64_t* counts, const double* sums);
 
 /* Image estimate, [height][width][3] doubles.  normalized = 1: radiance
  * I_j * W * H with I_j = (b/N) sum_i f(x_i)/pi(x_i) (Sec. 3.2; region-weighted
  * mode normalises each region by its own mass); normalized = 0: the raw sum
- * of f/pi splats. */
+ * of f/pi splats.  A sharded context returns its chains' share, normalised
+ * with the whole population's N, b and region masses: the sum of the shares
+ * of all contexts is the image. */
 rmlt_status rmlt_read_image(rmlt_ctx* ctx, double* out_rgb, int normalized);
 
 /* Region visit histogram h_k (post-MH state of every mutation), [m] u64, m
@@ -237,6 +286,10 @@ rmlt_status rmlt_read_quadtree(rmlt_ctx* ctx, int32_t* child, int32_t* leaf, int
 rmlt_status rmlt_read_chain_state(rmlt_ctx* ctx, uint32_t* q, float* f, int32_t* k);
 
 rmlt_status rmlt_read_stats(rmlt_ctx* ctx, rmlt_stats* out);
+
+/* The chain parameters in effect (defaults resolved, e.g. lambda_max), as
+ * given to rmlt_init_chains or read from a checkpoint by rmlt_restore. */
+rmlt_status rmlt_read_params(rmlt_ctx* ctx, rmlt_chain_params* out);
 
 /* Test instrument.  While set, rmlt_step writes one rmlt_trace_record per
  * mutation of every chain c with c % chain_stride == 0, in the order
@@ -307,6 +360,14 @@ rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup, int
 rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_ctas_per_sm, int refill_lanes,
                                int flags);
 
+/* Safety bound of the wavefront form: an epoch stops after `waves` waves (0 =
+ * the default E (max_depth + 1) + 2, more than any epoch needs, since every
+ * wave advances each chain with rays by one bounce).  An epoch stopped by the
+ * bound leaves mutations unfinished; the next synchronising call
+ * (rmlt_synchronize, rmlt_read_*, rmlt_save) then returns RMLT_E_OVERFLOW and
+ * marks the context failed. */
+rmlt_status rmlt_set_wave_limit(rmlt_ctx* ctx, uint32_t waves);
+
 /* Bootstrap without any device allocation.  Some callers cannot allocate
  * device memory at the point where they need starting states: code running
  * inside a memory-pool or arena callback, a process whose allocator is
@@ -329,7 +390,9 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_c
  * call shares the array, so calls whose work overlaps on the GPU (other
  * contexts, other streams) race; serialise them.  Errors: RMLT_E_STATE (no
  * scene), RMLT_E_INVALID_ARG (parameters, sizes, host pointers for out_q or
- * out_f), RMLT_E_CUDA. */
+ * out_f), RMLT_E_OVERFLOW (a bootstrap path overflowed the traversal stack,
+ * so b and the starting states would be biased; the outputs are written),
+ * RMLT_E_CUDA. */
 #define RMLT_NOALLOC_MAX_SAMPLES (1 << 18)
 #define RMLT_NOALLOC_MAX_CHAINS (1 << 16)
 #define RMLT_NOALLOC_MAX_REGIONS (1 << 14)
@@ -387,8 +450,13 @@ rmlt_status rmlt_memory_usage(rmlt_ctx* ctx, uint64_t* bytes);
 
 /* Checkpoint: chain state, region tables, image, counters, parameters and the
  * mutation index (Philox counters make resume-then-run equal an uninterrupted
- * run).  rmlt_restore needs the same scene loaded.  Errors: RMLT_E_IO,
- * RMLT_E_INVALID_ARG (file from another scene or version). */
+ * run), with a 64-bit FNV-1a checksum of the header and payload.
+ * rmlt_restore needs the same scene loaded; it checks the checksum, the
+ * parameters and every index the kernels use (chain regions, quadtree sizes,
+ * children and leaves) on the host before anything is launched, and leaves
+ * the context unchanged on error.  Errors: RMLT_E_IO (cannot read, or
+ * truncated), RMLT_E_INVALID_ARG (another scene or version, a checksum
+ * mismatch, an index out of range). */
 rmlt_status rmlt_save(rmlt_ctx* ctx, const char* path);
 rmlt_status rmlt_restore(rmlt_ctx* ctx, const char* path);
 

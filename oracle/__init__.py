@@ -48,6 +48,7 @@ class OrParams(C.Structure):
         ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32), ("qt_split", C.c_int64),
         ("qt_refine", C.c_int64), ("p_mala", C.c_double), ("mala_tau", C.c_double),
         ("mala_drift_max", C.c_double), ("kernel", C.c_int32), ("dir_cells", C.c_int32),
+        ("chain_first", C.c_int32), ("chains_total", C.c_int32),
     ]
 
 
@@ -89,6 +90,9 @@ def lib():
         "or_set_state": (C.c_int32, [C.c_void_p, C.c_uint32, u32p]),
         "or_mutate_one": (C.c_int32, [C.c_void_p, C.c_uint32, C.c_uint64]),
         "or_run_epochs": (C.c_int32, [C.c_void_p, C.c_int64]),
+        "or_epoch_mutate": (C.c_int32, [C.c_void_p, P(C.c_uint64), f64p]),
+        "or_epoch_update": (C.c_int32, [C.c_void_p, P(C.c_uint64), f64p]),
+        "or_region_capacity": (C.c_int32, [C.c_void_p]),
         "or_read_image": (None, [C.c_void_p, f64p]),
         "or_dims": (C.c_int32, [C.c_void_p]),
         "or_regions": (C.c_int32, [C.c_void_p]),
@@ -221,7 +225,7 @@ DEFAULT_PARAMS = dict(
     alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0, lambda_min=-30.0,
     lambda_max=None, w_floor=1e-3, debug_flags=0, partition=0, qt_max_leaves=4096, qt_max_depth=10,
     qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3, mala_drift_max=0.1, kernel=0,
-    dir_cells=0,
+    dir_cells=0, chain_first=0, chains_total=0,
 )
 
 
@@ -286,6 +290,24 @@ class Chains:
     def run_epochs(self, n: int):
         if lib().or_run_epochs(self.h, int(n)) != 0:
             raise RuntimeError("or_run_epochs failed")
+
+    def exchange_buffers(self):
+        """(counts, sums) arrays of one sharded epoch: [3 cap + 1] u64 and [cap] f64."""
+        cap = int(lib().or_region_capacity(self.h))
+        return np.zeros(3 * cap + 1, np.uint64), np.zeros(cap, np.float64)
+
+    def epoch_mutate(self, counts: np.ndarray, sums: np.ndarray):
+        """E mutations of this context's chains; what they added to the region
+        tables goes to `counts` / `sums` (see or_epoch_mutate)."""
+        if lib().or_epoch_mutate(self.h, _ptr(counts, C.c_uint64), _ptr(sums, C.c_double)) != 0:
+            raise RuntimeError("or_epoch_mutate: not initialised, or an update is due")
+
+    def epoch_update(self, counts: np.ndarray, sums: np.ndarray):
+        """The epoch boundary from the additions summed over every context."""
+        counts = np.ascontiguousarray(counts, np.uint64)
+        sums = np.ascontiguousarray(sums, np.float64)
+        if lib().or_epoch_update(self.h, _ptr(counts, C.c_uint64), _ptr(sums, C.c_double)) != 0:
+            raise RuntimeError("or_epoch_update: or_epoch_mutate first")
 
     def set_hooks(self, mut_fn=None, upd_fn=None):
         mh = MUT_HOOK(mut_fn) if mut_fn else MUT_HOOK()

@@ -907,6 +907,9 @@ struct or_ctx {
     uint64_t mala_st[2];          /* Langevin moves proposed, accepted */
     uint32_t T_mala;
     double* g;                    /* [C][D] gradient of log pi at each chain's state (Langevin runs) */
+    /* sharded stepping: i, A, h (cap each), large steps and nU at the start of the epoch; Bk */
+    uint64_t* snap_i;
+    double* snap_B;
     int inited;
     or_mut_hook mh;
     or_upd_hook uh;
@@ -920,6 +923,10 @@ or_ctx* or_ctx_create(const or_scene* s, const or_params* p)
     if (!s || !p) return NULL;
     int32_t D = 2 + 5 * p->max_depth;
     if (D > OR_MAX_DIM || p->n_chains <= 0 || p->width <= 0 || p->height <= 0 || p->region_px <= 0)
+        return NULL;
+    if (p->chain_first < 0 || p->chains_total < 0 ||
+        (p->chains_total > 0 && (int64_t)p->chain_first + p->n_chains > (int64_t)p->chains_total) ||
+        (p->chains_total == 0 && p->chain_first != 0))
         return NULL;
     /* the truncated normal's sigma stays below 4 (lambda_max = 2 ln 4): wider
      * is uniform on the window for every purpose */
@@ -997,6 +1004,7 @@ void or_ctx_destroy(or_ctx* c)
     free(c->img); free(c->Bk);
     free(c->qt_child); free(c->qt_leaf); free(c->qt_depth);
     free(c->g);
+    free(c->snap_i); free(c->snap_B);
     free(c);
 }
 
@@ -1084,12 +1092,17 @@ static void quadtree_refine(or_ctx* c)
 
 static double weight_of(const or_ctx* c, int32_t k) { return c->p.target_mode ? c->w[k] : 1.0; }
 
+/* chains over the whole (possibly sharded) population, and the global id of
+ * this context's chain `chain` (the Philox key of its draws) */
+static int32_t chains_all(const or_ctx* c) { return c->p.chains_total > 0 ? c->p.chains_total : c->p.n_chains; }
+static uint32_t gid(const or_ctx* c, uint32_t chain) { return (uint32_t)c->p.chain_first + chain; }
+
 /* Large step: an independent uniform point of the PSS cube. */
 static void large_step(const or_ctx* c, uint32_t chain, uint64_t mut, uint32_t* qy)
 {
     for (int32_t j = 0; 4 * j < c->D; ++j) {
         uint32_t r[4];
-        draw(c->p.seed, mut, chain, 1u + (uint32_t)j, r);
+        draw(c->p.seed, mut, gid(c, chain), 1u + (uint32_t)j, r);
         for (int a = 0; a < 4 && 4 * j + a < c->D; ++a) qy[4 * j + a] = r[a];
     }
 }
@@ -1102,7 +1115,7 @@ static void small_step(const or_ctx* c, uint32_t chain, uint64_t mut, int32_t kx
     float sigS2 = c->sig[kx] * c->S2;
     for (int32_t j = 0; 2 * j < c->D; ++j) {
         uint32_t r[4];
-        draw(c->p.seed, mut, chain, 1u + (uint32_t)j, r);
+        draw(c->p.seed, mut, gid(c, chain), 1u + (uint32_t)j, r);
         for (int a = 0; a < 2 && 2 * j + a < c->D; ++a) {
             int32_t dim = 2 * j + a;
             if (c->p.kernel == 1) {   /* signed offset; the sign word is not used */
@@ -1240,7 +1253,7 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
     mala_drift(c, gx, tx, mx);
     for (int32_t j = 0; 4 * j < D; ++j) {
         uint32_t r[4];
-        draw(c->p.seed, c->mut, chain, 1u + (uint32_t)j, r);
+        draw(c->p.seed, c->mut, gid(c, chain), 1u + (uint32_t)j, r);
         for (int a = 0; a < 2; ++a) {
             double u1 = ((double)(r[2 * a] >> 8) + 0.5) * (1.0 / 16777216.0);
             double u2 = u24(r[2 * a + 1]);
@@ -1303,7 +1316,7 @@ static void mutate(or_ctx* c, uint32_t chain)
     int32_t D = c->D;
     uint32_t r0[4], qy[OR_MAX_DIM];
     uint32_t* qx = &c->q[(size_t)chain * D];
-    draw(c->p.seed, c->mut, chain, 0u, r0);
+    draw(c->p.seed, c->mut, gid(c, chain), 0u, r0);
     int32_t large = (r0[0] >> 8) < c->T_large;
     double xi = u24(r0[1]);
     if (!large && c->g && (r0[0] >> 8) < c->T_large + c->T_mala) {
@@ -1425,17 +1438,20 @@ static void boot_sample(const or_ctx* c, uint64_t s, uint32_t* q)
 int32_t or_init(or_ctx* c)
 {
     const or_params* p = &c->p;
-    int64_t K = p->n_bootstrap / p->n_chains;
+    const int32_t C_all = chains_all(c);
+    int64_t K = p->n_bootstrap / C_all;
     if (K <= 0) return -1;
     if (p->partition == 1) or_init_tables(c);   /* the region lookup needs the root */
     uint32_t q[OR_MAX_DIM];
     double f[3], total = 0.0;
     memset(c->Bk, 0, sizeof(double) * (size_t)c->m);
-    for (int32_t ch = 0; ch < p->n_chains; ++ch) {
+    /* every chain of the population (all shards): b needs every slice; only
+     * this context's chains take a starting state */
+    for (int32_t g = 0; g < C_all; ++g) {
         double cum = 0.0;
         int64_t sel = -1;
         for (int64_t i = 0; i < K; ++i) {
-            uint64_t s = (uint64_t)ch * (uint64_t)K + (uint64_t)i;
+            uint64_t s = (uint64_t)g * (uint64_t)K + (uint64_t)i;
             boot_sample(c, s, q);
             if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
             double pis = luminance(f);
@@ -1445,8 +1461,10 @@ int32_t or_init(or_ctx* c)
             draw(p->seed, s, 0xFFFFFFFFu, 0x7FFFu, r);
             if (pis > 0 && u24(r[0]) * cum < pis) sel = (int64_t)s;
         }
-        if (sel < 0) sel = (int64_t)ch * K;
+        if (sel < 0) sel = (int64_t)g * K;
         total += cum;
+        const int32_t ch = g - p->chain_first;
+        if (ch < 0 || ch >= p->n_chains) continue;
         c->boot[ch] = sel;
         uint32_t* qc = &c->q[(size_t)ch * c->D];
         boot_sample(c, (uint64_t)sel, qc);
@@ -1458,9 +1476,9 @@ int32_t or_init(or_ctx* c)
             or_path_grad(c->s, p->width, p->height, p->max_depth, qc, fg, &c->g[(size_t)ch * c->D]);
         }
     }
-    c->st[7] = (uint64_t)(K * p->n_chains);
-    c->nU = (uint64_t)(K * p->n_chains);
-    c->bhat = total / (double)(K * p->n_chains);
+    c->st[7] = (uint64_t)(K * C_all);
+    c->nU = (uint64_t)(K * C_all);
+    c->bhat = total / (double)(K * C_all);
     return or_init_tables(c);
 }
 
@@ -1519,28 +1537,91 @@ int32_t or_mutate_one(or_ctx* c, uint32_t chain, uint64_t mut)
     return 0;
 }
 
+/* E mutations of every chain of this context (Alg. 1 lines 8-12, 19) */
+static void epoch_mutations(or_ctx* c)
+{
+    uint64_t mut0 = c->mut;
+    for (uint32_t ch = 0; ch < (uint32_t)c->p.n_chains; ++ch) {
+        c->mut = mut0;
+        for (int32_t j = 0; j < c->p.epoch_len; ++j) {
+            mutate(c, ch);
+            c->mut++;
+        }
+    }
+    c->mut = mut0 + (uint64_t)c->p.epoch_len;
+}
+
+/* the epoch boundary: Alg. 1 lines 13-18, the weighted target's weights, and
+ * a quadtree pass every qt_refine mutations of the whole population */
+static void epoch_boundary(or_ctx* c)
+{
+    region_update(c);
+    if (c->p.target_mode) weight_update(c);
+    if (c->p.partition == 1) {
+        c->since_refine += (uint64_t)chains_all(c) * (uint64_t)c->p.epoch_len;
+        if (c->since_refine >= (uint64_t)c->p.qt_refine) {
+            c->since_refine = 0;
+            quadtree_refine(c);
+        }
+    }
+}
+
 int32_t or_run_epochs(or_ctx* c, int64_t n_epochs)
 {
     if (!c->inited) return -1;
     for (int64_t e = 0; e < n_epochs; ++e) {
-        uint64_t mut0 = c->mut;
-        for (uint32_t ch = 0; ch < (uint32_t)c->p.n_chains; ++ch) {
-            c->mut = mut0;
-            for (int32_t j = 0; j < c->p.epoch_len; ++j) {
-                mutate(c, ch);
-                c->mut++;
-            }
-        }
-        region_update(c);
-        if (c->p.target_mode) weight_update(c);
-        if (c->p.partition == 1) {
-            c->since_refine += (uint64_t)c->p.n_chains * (uint64_t)c->p.epoch_len;
-            if (c->since_refine >= (uint64_t)c->p.qt_refine) {
-                c->since_refine = 0;
-                quadtree_refine(c);
-            }
-        }
+        epoch_mutations(c);
+        epoch_boundary(c);
     }
+    return 0;
+}
+
+int32_t or_region_capacity(const or_ctx* c) { return c->cap; }
+
+/* Sharded stepping: the region tables every context shares are its own
+ * tables at the start of the epoch plus what all contexts' chains added
+ * during it (the paper's threads share i_k and A_k through atomics, Sec. 6;
+ * integer sums do not depend on their order). */
+int32_t or_epoch_mutate(or_ctx* c, uint64_t* counts, double* sums)
+{
+    if (!c->inited || c->snap_i) return -1;
+    const size_t cap = (size_t)c->cap;
+    c->snap_i = (uint64_t*)malloc(sizeof(uint64_t) * (3 * cap + 2));
+    c->snap_B = (double*)malloc(sizeof(double) * cap);
+    memcpy(c->snap_i, c->i, sizeof(uint64_t) * cap);
+    memcpy(c->snap_i + cap, c->A, sizeof(uint64_t) * cap);
+    memcpy(c->snap_i + 2 * cap, c->h, sizeof(uint64_t) * cap);
+    c->snap_i[3 * cap] = c->st[2];
+    c->snap_i[3 * cap + 1] = c->nU;
+    memcpy(c->snap_B, c->Bk, sizeof(double) * cap);
+    epoch_mutations(c);
+    for (size_t k = 0; k < cap; ++k) {
+        counts[k] = c->i[k] - c->snap_i[k];
+        counts[cap + k] = c->A[k] - c->snap_i[cap + k];
+        counts[2 * cap + k] = c->h[k] - c->snap_i[2 * cap + k];
+        sums[k] = c->Bk[k] - c->snap_B[k];
+    }
+    counts[3 * cap] = c->st[2] - c->snap_i[3 * cap];
+    return 0;
+}
+
+int32_t or_epoch_update(or_ctx* c, const uint64_t* counts, const double* sums)
+{
+    if (!c->snap_i) return -1;
+    const size_t cap = (size_t)c->cap;
+    for (size_t k = 0; k < cap; ++k) {
+        c->i[k] = c->snap_i[k] + counts[k];
+        c->A[k] = c->snap_i[cap + k] + counts[cap + k];
+        c->h[k] = c->snap_i[2 * cap + k] + counts[2 * cap + k];
+        c->Bk[k] = c->snap_B[k] + sums[k];
+    }
+    /* uniform samples of the whole population: the bootstrap plus every large step */
+    c->nU = c->snap_i[3 * cap + 1] + counts[3 * cap];
+    free(c->snap_i);
+    free(c->snap_B);
+    c->snap_i = NULL;
+    c->snap_B = NULL;
+    epoch_boundary(c);
     return 0;
 }
 
@@ -1573,7 +1654,7 @@ int32_t or_quadtree(const or_ctx* c, int32_t* child, int32_t* leaf, int32_t* dep
 void or_read_image(const or_ctx* c, double* out)
 {
     const or_params* p = &c->p;
-    double N = (double)c->mut * (double)p->n_chains;
+    double N = (double)c->mut * (double)chains_all(c);   /* a shard returns its share of the image */
     double WH = (double)p->width * (double)p->height;
     for (int32_t y = 0; y < p->height; ++y)
         for (int32_t x = 0; x < p->width; ++x) {

@@ -75,6 +75,10 @@ typedef struct {
     /* 4-D partition: each screen region crossed with a dir_cells^2 grid over
      * (u5, u6), the first bounce's BSDF coordinates; <= 1 screen only */
     int32_t  dir_cells;
+    /* sharded population: this context's chains are the global chains
+     * chain_first .. chain_first + n_chains - 1 of chains_total (0: not
+     * sharded); Philox draws are keyed by the global id */
+    int32_t  chain_first, chains_total;
 } or_params;
 
 /* Gradient of log pi(u), pi = l(f(u)), over the D = 2 + 5 max_depth
@@ -129,6 +133,17 @@ int32_t  or_set_state(or_ctx* c, uint32_t chain, const uint32_t* q);
 /* One mutation of one chain at mutation index `mut` (region tables updated). */
 int32_t  or_mutate_one(or_ctx* c, uint32_t chain, uint64_t mut);
 int32_t  or_run_epochs(or_ctx* c, int64_t n_epochs);
+/* One epoch of a sharded population in two halves.  or_epoch_mutate runs E
+ * mutations of every chain of this context and writes what they added to the
+ * region tables: counts [3 cap + 1] = i_k, A_k, h_k (cap each) and the number
+ * of large steps; sums [cap] = the sum of pi over large-step proposals per
+ * region.  or_epoch_update takes those arrays summed over every context of
+ * the population, sets each table to its value at the start of the epoch
+ * plus the sums, and runs the epoch boundary (Alg. 1 lines 13-18, weights,
+ * quadtree).  cap = or_region_capacity(). */
+int32_t  or_epoch_mutate(or_ctx* c, uint64_t* counts, double* sums);
+int32_t  or_epoch_update(or_ctx* c, const uint64_t* counts, const double* sums);
+int32_t  or_region_capacity(const or_ctx* c);
 void     or_read_image(const or_ctx* c, double* out_rgb);   /* H*W*3 radiance */
 
 int32_t   or_dims(const or_ctx* c);

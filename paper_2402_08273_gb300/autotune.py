@@ -33,19 +33,22 @@ def apply(R, cand: dict) -> None:
                         refill_lanes=cand.get("refill_lanes", 16))
 
 
-def autotune(R, epochs: int = 2, candidates=CANDIDATES):
+def autotune(R, epochs: int = 2, candidates=CANDIDATES, step=None):
     """Time each candidate for `epochs` epochs after one untimed epoch (graph
-    build, caches); set the fastest.  Returns (best, [(cand, ms_per_epoch)])."""
+    build, caches); set the fastest.  `step(n_mutations)` advances the chains
+    (default R.step; a sharded population passes its epoch loop).  Returns
+    (best, [(cand, ms_per_epoch)])."""
     import torch
+    step = step or R.step
     E = R.params["epoch_len"]
     timings = []
     for cand in candidates:
         apply(R, cand)
-        R.step(E)
+        step(E)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(R.stream)
-        R.step(epochs * E)
+        step(epochs * E)
         b.record(R.stream)
         b.synchronize()
         timings.append((dict(cand), a.elapsed_time(b) / epochs))

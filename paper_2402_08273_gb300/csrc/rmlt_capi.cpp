@@ -5,6 +5,7 @@
 // kernel and the region update (Alg. 1), and copies results out.  Every
 // arithmetic step of the method runs in the CUDA kernels (rmlt_kernels.cu).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -59,6 +60,12 @@ uint64_t fnv64(const void* data, size_t n, uint64_t h)
     return h;
 }
 
+// NVTX range for profilers (a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 }  // namespace
 
 struct rmlt_ctx {
@@ -93,8 +100,12 @@ struct rmlt_ctx {
     int batch_shade = 12, batch_setup = 10;
     int large_ahead = 0, adaptive_batch = 0;
     int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0;
+    unsigned wave_limit = 0;     // waves per epoch before the wavefront form stops (0: its default)
+    bool wf_ran = false;         // an epoch ran in the wavefront form since the chains were set up
+    uint64_t wave_hits_seen = 0; // epochs stopped by the wave limit, as of the last check
     DevWave W;                   // wavefront state (allocated on first use)
     WfGraph* wg = nullptr;       // its instantiated wave loop
+    bool in_epoch = false;       // rmlt_epoch_mutate ran, rmlt_epoch_update is due
 
     rmlt_status dalloc(std::vector<Alloc>& pool, size_t bytes, void** out)
     {
@@ -148,6 +159,22 @@ rmlt_status sync(rmlt_ctx* c, const char* what)
     if (e != cudaSuccess) {
         c->failed = true;
         return cuda_fail(e, what);
+    }
+    // an epoch of the wavefront form stopped by its wave limit left
+    // mutations unfinished: the chains are no longer a valid sample
+    if (c->wf_ran && c->have_chains && !c->failed) {
+        unsigned long long hits = 0;
+        e = cudaMemcpy(&hits, c->Ch.stats + kStWaveLimit, sizeof hits, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            c->failed = true;
+            return cuda_fail(e, what);
+        }
+        if (hits > c->wave_hits_seen) {
+            c->wave_hits_seen = hits;
+            c->failed = true;
+            return fail(RMLT_E_OVERFLOW, "%s: %llu epoch(s) stopped at the wave limit of the wavefront form", what,
+                        hits);
+        }
     }
     return RMLT_OK;
 }
@@ -215,6 +242,9 @@ static void drop_chains(rmlt_ctx* c)
     c->d_total = c->d_stage = nullptr;
     c->tr = nullptr;
     c->tr_lam = nullptr;
+    c->wf_ran = false;
+    c->wave_hits_seen = 0;
+    c->in_epoch = false;
 }
 
 rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
@@ -317,40 +347,6 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
         mat4[3 * (size_t)m + 2] = make_float4(emissive ? 1.f : 0.f, black ? 1.f : 0.f, 0.f, 0.f);
     }
 
-    // replace the previous scene (and chains)
-    drop_chains(c);
-    c->release(c->scene_mem);
-    c->have_scene = false;
-    DevScene S;
-    float4 *d_tri = nullptr, *d_nodes = nullptr, *d_mat = nullptr;
-    int32_t* d_lt = nullptr;
-    float* d_lc = nullptr;
-    if ((st = c->alloc_n(c->scene_mem, tri4.size(), &d_tri))) return st;
-    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(8, bvh.nodes.size()), &d_nodes))) return st;
-    if ((st = c->alloc_n(c->scene_mem, mat4.size(), &d_mat))) return st;
-    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, ltri.size()), &d_lt))) return st;
-    if ((st = c->alloc_n(c->scene_mem, std::max<size_t>(1, lcdf.size()), &d_lc))) return st;
-    CK(cudaMemcpyAsync(d_tri, tri4.data(), tri4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload triangles");
-    if (!bvh.nodes.empty())
-        CK(cudaMemcpyAsync(d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload nodes");
-    CK(cudaMemcpyAsync(d_mat, mat4.data(), mat4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "upload materials");
-    if (!ltri.empty()) {
-        CK(cudaMemcpyAsync(d_lt, ltri.data(), ltri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "upload lights");
-        CK(cudaMemcpyAsync(d_lc, lcdf.data(), lcdf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream), "upload light cdf");
-    }
-    if ((st = sync(c, "scene upload"))) return st;
-    S.tris = d_tri;
-    S.nodes = d_nodes;
-    S.mats = d_mat;
-    S.light_tri = d_lt;
-    S.light_cdf = d_lc;
-    S.n_tris = nt;
-    S.n_nodes = (int32_t)(bvh.nodes.size() / (width == 4 ? 8 : 4));
-    S.bvh4 = width == 4 ? 1 : 0;
-    S.n_mats = s->n_mats;
-    S.n_lights = (int32_t)ltri.size();
-    S.brute = brute ? 1 : 0;
-    S.light_area = (float)acc;
     // pinhole camera basis in binary64, stored in binary32
     double pos[3] = {cam.pos[0], cam.pos[1], cam.pos[2]};
     double fw[3] = {(double)cam.look_at[0] - pos[0], (double)cam.look_at[1] - pos[1], (double)cam.look_at[2] - pos[2]};
@@ -363,15 +359,63 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     if (!(rl > 0.0)) return fail(RMLT_E_INVALID_SCENE, "camera up is parallel to the view direction");
     for (double& x : rt) x /= rl;
     const double uo[3] = {rt[1] * fw[2] - rt[2] * fw[1], rt[2] * fw[0] - rt[0] * fw[2], rt[0] * fw[1] - rt[1] * fw[0]};
+
+    // the new scene's device memory, in a pool of its own: on failure it is
+    // released and the previous scene (and chains) stay as they were
+    std::vector<Alloc> fresh;
+    DevScene S;
+    float4 *d_tri = nullptr, *d_nodes = nullptr, *d_mat = nullptr;
+    int32_t* d_lt = nullptr;
+    float* d_lc = nullptr;
+    if ((st = c->alloc_n(fresh, tri4.size(), &d_tri)) ||
+        (st = c->alloc_n(fresh, std::max<size_t>(8, bvh.nodes.size()), &d_nodes)) ||
+        (st = c->alloc_n(fresh, mat4.size(), &d_mat)) ||
+        (st = c->alloc_n(fresh, std::max<size_t>(1, ltri.size()), &d_lt)) ||
+        (st = c->alloc_n(fresh, std::max<size_t>(1, lcdf.size()), &d_lc))) {
+        c->release(fresh);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_tri, tri4.data(), tri4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !bvh.nodes.empty())
+        e = cudaMemcpyAsync(d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_mat, mat4.data(), mat4.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !ltri.empty())
+        e = cudaMemcpyAsync(d_lt, ltri.data(), ltri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !ltri.empty())
+        e = cudaMemcpyAsync(d_lc, lcdf.data(), lcdf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->release(fresh);
+        return cuda_fail(e, "scene upload");
+    }
+    S.tris = d_tri;
+    S.nodes = d_nodes;
+    S.mats = d_mat;
+    S.light_tri = d_lt;
+    S.light_cdf = d_lc;
+    S.n_tris = nt;
+    S.n_nodes = (int32_t)(bvh.nodes.size() / (width == 4 ? 8 : 4));
+    S.bvh4 = width == 4 ? 1 : 0;
+    S.n_mats = s->n_mats;
+    S.n_lights = (int32_t)ltri.size();
+    S.brute = brute ? 1 : 0;
+    S.light_area = (float)acc;
     for (int a = 0; a < 3; ++a) {
         S.cam_pos[a] = (float)pos[a];
         S.cam_fwd[a] = (float)fw[a];
         S.cam_right[a] = (float)rt[a];
         S.cam_up[a] = (float)uo[a];
     }
-    c->tan_half = std::tan((double)cam.vfov_deg * 3.14159265358979323846 / 360.0);
     S.eps = (float)(1e-4 * scale);
     S.toy = 0;
+
+    // replace the previous scene (and chains)
+    drop_chains(c);
+    c->release(c->scene_mem);
+    c->scene_mem = std::move(fresh);
+    c->tan_half = std::tan((double)cam.vfov_deg * 3.14159265358979323846 / 360.0);
     c->S = S;
     uint64_t h = fnv64(tv.data(), tv.size() * sizeof(float), 1469598103934665603ull);
     h = fnv64(s->mat_id, (size_t)nt * sizeof(uint32_t), h);
@@ -403,10 +447,17 @@ rmlt_status rmlt_load_toy_integrand(rmlt_ctx* c, const double* params)
     return RMLT_OK;
 }
 
+// chains over every context of a (possibly sharded) population
+static int32_t chains_all(const rmlt_chain_params* p) { return p->chains_total > 0 ? p->chains_total : p->n_chains; }
+
 static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
 {
     if (!p) return fail(RMLT_E_INVALID_ARG, "params is NULL");
     if (p->n_chains <= 0 || p->n_chains >= 0x7FFFFFFF) return fail(RMLT_E_INVALID_ARG, "n_chains must be in [1, 2^31-1)");
+    if (p->chains_total < 0 || p->chain_first < 0 ||
+        (p->chains_total > 0 && (int64_t)p->chain_first + p->n_chains > (int64_t)p->chains_total) ||
+        (p->chains_total == 0 && p->chain_first != 0))
+        return fail(RMLT_E_INVALID_ARG, "need 0 <= chain_first, chain_first + n_chains <= chains_total (or both 0)");
     if (p->width <= 0 || p->height <= 0 || p->width > (1 << 16) || p->height > (1 << 16))
         return fail(RMLT_E_INVALID_ARG, "image size must be in [1, 65536]");
     if (p->region_px <= 0) return fail(RMLT_E_INVALID_ARG, "region_px must be positive");
@@ -415,8 +466,8 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
     if (p->epoch_len <= 0 || p->L <= 0) return fail(RMLT_E_INVALID_ARG, "epoch_len and L must be positive");
     if (p->target_mode != RMLT_TARGET_PLAIN && p->target_mode != RMLT_TARGET_REGION_WEIGHTED)
         return fail(RMLT_E_INVALID_ARG, "unknown target_mode");
-    if (p->n_bootstrap < p->n_chains || p->n_bootstrap > (1ll << 34))
-        return fail(RMLT_E_INVALID_ARG, "n_bootstrap must be in [n_chains, 2^34]");
+    if (p->n_bootstrap < chains_all(p) || p->n_bootstrap > (1ll << 34))
+        return fail(RMLT_E_INVALID_ARG, "n_bootstrap must be in [chains of the population, 2^34]");
     if (!(p->p_large >= 0.0 && p->p_large <= 1.0)) return fail(RMLT_E_INVALID_ARG, "p_large outside [0,1]");
     if (!(p->s1 > 0.0 && p->s1 < p->s2 && p->s2 <= 0.5)) return fail(RMLT_E_INVALID_ARG, "need 0 < s1 < s2 <= 1/2");
     if (!(p->alpha_star > 0.0 && p->alpha_star < 1.0)) return fail(RMLT_E_INVALID_ARG, "alpha_star outside (0,1)");
@@ -449,6 +500,8 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
         if (!c->scene_lambert)
             return fail(RMLT_E_INVALID_ARG, "the Langevin strategy differentiates the path map: Lambertian scenes only");
     }
+    if (p->chains_total > 0 && p->chains_total != p->n_chains && p->p_mala > 0.0)
+        return fail(RMLT_E_INVALID_ARG, "the Langevin strategy is not available to a sharded population");
     if (p->partition == RMLT_PARTITION_QUADTREE) {
         if (p->target_mode != RMLT_TARGET_PLAIN) return fail(RMLT_E_INVALID_ARG, "the quadtree partition needs the plain target");
         if (p->qt_max_leaves < 1 || p->qt_max_leaves > (1 << 20) || p->qt_max_depth < 0 || p->qt_max_depth > 24 ||
@@ -458,12 +511,36 @@ static rmlt_status check_params(const rmlt_ctx* c, const rmlt_chain_params* p)
     return RMLT_OK;
 }
 
-// allocate chain state and region tables for params P (no initial values)
-static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
+// The parameters as the library uses them: lambda_max = 0 or NaN selects the
+// largest value the kernel allows (Kelemen: sigma s2 <= 1/2, the largest
+// offset on the torus; truncated normal: sigma <= 4), then every field is
+// checked.
+static rmlt_status resolve_params(const rmlt_ctx* c, const rmlt_chain_params* in, rmlt_chain_params* out)
 {
-    drop_chains(c);
+    if (!in) return fail(RMLT_E_INVALID_ARG, "params is NULL");
+    *out = *in;
+    if (out->lambda_max == 0.0 || std::isnan(out->lambda_max)) {
+        if (out->kernel == RMLT_KERNEL_TRUNCNORM) out->lambda_max = 2.0 * std::log(4.0);
+        else if (out->s2 > 0.0 && out->s2 <= 0.5) out->lambda_max = 2.0 * std::log(1.0 / (2.0 * out->s2));
+    }
+    return check_params(c, out);
+}
+
+// Chain state and region tables for params P (no initial values), in a pool
+// of their own; the context is not touched.
+struct ChainAlloc {
+    std::vector<Alloc> pool;
+    DevChains Ch;
+    double* d_total = nullptr;
+    double* d_stage = nullptr;
+};
+
+static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p, ChainAlloc& A)
+{
     DevChains Ch;
     Ch.C = p->n_chains;
+    Ch.C_all = chains_all(p);
+    Ch.chain0 = (uint32_t)p->chain_first;
     Ch.D = 2 + 5 * p->max_depth;
     Ch.W = p->width;
     Ch.H = p->height;
@@ -488,7 +565,7 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     Ch.truncnorm = p->kernel == RMLT_KERNEL_TRUNCNORM ? 1 : 0;
     const size_t C = (size_t)Ch.C, m = (size_t)Ch.m, npx = (size_t)Ch.W * Ch.H * 3;
     rmlt_status st;
-    auto& pool = c->chain_mem;
+    auto& pool = A.pool;
     if ((st = c->alloc_n(pool, C * Ch.D, &Ch.q))) return st;
     Ch.qd = (int64_t)C;
     Ch.qc = 1;
@@ -506,6 +583,9 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     if ((st = c->alloc_n(pool, m, &Ch.sig))) return st;
     if ((st = c->alloc_n(pool, m, &Ch.wf))) return st;
     if ((st = c->alloc_n(pool, m, &Ch.Bk))) return st;
+    if ((st = c->alloc_n(pool, 3 * m + 1, &Ch.snap))) return st;
+    if ((st = c->alloc_n(pool, m, &Ch.snapB))) return st;
+    if ((st = c->alloc_n(pool, 1, &Ch.large_all))) return st;
     if ((st = c->alloc_n(pool, npx, &Ch.img))) return st;
     if ((st = c->alloc_n(pool, (size_t)kStCount, &Ch.stats))) return st;
     if (!c->S.toy && (uint64_t)Ch.E * (uint64_t)Ch.C < (1ull << 32)) {
@@ -514,8 +594,8 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
         if ((st = c->alloc_n(pool, ec, &Ch.llist))) return st;
         if ((st = c->alloc_n(pool, 1, &Ch.lcount))) return st;
     }
-    if ((st = c->alloc_n(pool, 1, &c->d_total))) return st;
-    if ((st = c->alloc_n(pool, npx, &c->d_stage))) return st;
+    if ((st = c->alloc_n(pool, 1, &A.d_total))) return st;
+    if ((st = c->alloc_n(pool, npx, &A.d_stage))) return st;
     if (Ch.quadtree) {
         const size_t nodes = (size_t)4 * Ch.qt_cap / 3 + 8;
         if ((st = c->alloc_n(pool, 4 * nodes, &Ch.qt_child))) return st;
@@ -530,7 +610,6 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
         Ch.mala_tau = (float)p->mala_tau;
         Ch.mala_drift_max = (float)p->mala_drift_max;
     }
-    c->since_refine = 0;
     Ch.seed_lo = (uint32_t)p->seed;
     Ch.seed_hi = (uint32_t)(p->seed >> 32);
     double tl = std::ceil(p->p_large * 16777216.0);
@@ -544,45 +623,77 @@ static rmlt_status alloc_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     Ch.lambda_min = p->lambda_min;
     Ch.lambda_max = p->lambda_max;
     Ch.w_floor = p->w_floor;
-    c->Ch = Ch;
-    c->P = *p;
-    c->S.tan_y = (float)c->tan_half;
-    c->S.tan_x = (float)(c->tan_half * (double)p->width / (double)p->height);
+    A.Ch = Ch;
     return RMLT_OK;
 }
 
-rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* p)
+// the scene as the chains of params p see it (the camera's aspect ratio)
+static DevScene scene_for(const rmlt_ctx* c, const rmlt_chain_params* p)
+{
+    DevScene S = c->S;
+    S.tan_y = (float)c->tan_half;
+    S.tan_x = (float)(c->tan_half * (double)p->width / (double)p->height);
+    return S;
+}
+
+// replace the context's chains with freshly set-up ones
+static void adopt_chains(rmlt_ctx* c, ChainAlloc& A, const rmlt_chain_params* p)
+{
+    drop_chains(c);
+    c->chain_mem = std::move(A.pool);
+    c->Ch = A.Ch;
+    c->d_total = A.d_total;
+    c->d_stage = A.d_stage;
+    c->P = *p;
+    c->S = scene_for(c, p);
+    c->since_refine = 0;
+}
+
+rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* pin)
 {
     rmlt_status st = enter(c);
     if (st) return st;
     if (!c->have_scene) return fail(RMLT_E_STATE, "load a scene before rmlt_init_chains");
-    if ((st = check_params(c, p))) return st;
-    if ((st = alloc_chains(c, p))) return st;
-    DevChains& Ch = c->Ch;
-    const size_t npx = (size_t)Ch.W * Ch.H * 3;
-    CK(cudaMemsetAsync(Ch.img, 0, npx * sizeof(double), c->stream), "clear image");
-    CK(cudaMemsetAsync(Ch.stats, 0, kStCount * sizeof(unsigned long long), c->stream), "clear stats");
-    CK(launch_fill_regions(Ch, p->lambda_init, c->stream), "region init");
-    // bootstrap with scratch buffers released afterwards
-    std::vector<Alloc> scratch;
-    BootScratch B;
-    const int64_t K = p->n_bootstrap / p->n_chains;
-    const int64_t nb = K * p->n_chains;
-    if ((st = c->alloc_n(scratch, (size_t)nb, &B.pi)) || (st = c->alloc_n(scratch, (size_t)nb * 3, &B.f)) ||
-        (st = c->alloc_n(scratch, (size_t)Ch.C, &B.partial))) {
-        c->release(scratch);
-        drop_chains(c);
+    rmlt_chain_params P;
+    if ((st = resolve_params(c, pin, &P))) return st;
+    const rmlt_chain_params* p = &P;
+    NvtxRange nv("rmlt_init_chains");
+    // the new chains are set up completely before they replace the old ones
+    ChainAlloc A;
+    if ((st = alloc_chains(c, p, A))) {
+        c->release(A.pool);
         return st;
     }
-    B.total = c->d_total;
-    cudaError_t e = launch_bootstrap(c->S, Ch, nb, B, c->stream);
-    if (e == cudaSuccess && Ch.G) e = launch_state_gradients(c->S, Ch, c->stream);
+    DevChains& Ch = A.Ch;
+    const DevScene S = scene_for(c, p);
+    const size_t npx = (size_t)Ch.W * Ch.H * 3;
+    // bootstrap with scratch buffers released afterwards: every context of a
+    // sharded population draws all K C_all samples
+    std::vector<Alloc> scratch;
+    BootScratch B;
+    const int64_t K = p->n_bootstrap / Ch.C_all;
+    const int64_t nb = K * Ch.C_all;
+    if ((st = c->alloc_n(scratch, (size_t)nb, &B.pi)) || (st = c->alloc_n(scratch, (size_t)nb * 3, &B.f)) ||
+        (st = c->alloc_n(scratch, (size_t)Ch.C_all, &B.partial))) {
+        c->release(scratch);
+        c->release(A.pool);
+        return st;
+    }
+    B.total = A.d_total;
+    B.overflow = Ch.stats + kStBootOverflow;
+    cudaError_t e = cudaMemsetAsync(Ch.img, 0, npx * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Ch.stats, 0, kStCount * sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Ch.large_all, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_fill_regions(Ch, p->lambda_init, c->stream);
+    if (e == cudaSuccess) e = launch_bootstrap(S, Ch, nb, B, c->stream);
+    if (e == cudaSuccess && Ch.G) e = launch_state_gradients(S, Ch, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->release(scratch);
     if (e != cudaSuccess) {
-        drop_chains(c);
+        c->release(A.pool);
         return cuda_fail(e, "bootstrap");
     }
+    adopt_chains(c, A, p);
     c->n_boot = nb;
     c->mut = 0;
     c->epochs = 0;
@@ -591,73 +702,163 @@ rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* p)
     return RMLT_OK;
 }
 
+// One epoch's chain kernel (Alg. 1 lines 8-12, 19 for every chain).
+static rmlt_status epoch_kernels(rmlt_ctx* c)
+{
+    const uint64_t E = (uint64_t)c->Ch.E;
+    const uint32_t n_traced = (uint32_t)(((uint64_t)c->Ch.C + c->tr_stride - 1) / c->tr_stride);
+    DevChains Ch = c->Ch;
+    Ch.batch_shade = c->batch_shade;
+    Ch.batch_setup = c->batch_setup;
+    Ch.adaptive_batch = c->adaptive_batch;
+    if (!c->large_ahead) Ch.lf = nullptr;
+    const bool trace = c->tr != nullptr;
+    if (trace) {
+        Ch.trace = c->tr;
+        Ch.trace_cap = c->tr_cap;
+        Ch.trace_stride = c->tr_stride;
+        Ch.trace_base = c->tr_epoch * (unsigned long long)n_traced * E;
+    }
+    const DevScene& S = c->S;
+    rmlt_status st;
+    if (c->wavefront && !c->W.s) {
+        void* mem = nullptr;
+        if ((st = c->dalloc(c->chain_mem, wf_bytes(Ch.C, Ch.D), &mem))) return st;
+        wf_carve(mem, Ch.C, Ch.D, c->W);
+    }
+    cudaError_t err = cudaSuccess;
+    if (Ch.lf) err = launch_large_steps(S, Ch, c->mut, c->stream);
+    if (err == cudaSuccess) {
+        if (c->wavefront) {
+            c->W.refill = c->wf_refill;
+            c->wf_ran = true;
+            err = wf_epoch(&c->wg, S, Ch, c->W, c->mut, Ch.trace_base, trace, c->count_work, c->wf_trace_cps,
+                           c->wf_setup_cps, (c->wf_flags & RMLT_WAVEFRONT_HOST_LOOP) != 0, c->wave_limit,
+                           c->stream);
+        } else {
+            err = launch_chain_epoch(S, Ch, c->mut, trace, c->count_work, c->stream);
+        }
+    }
+    if (err != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(err, "epoch launch");
+    }
+    return RMLT_OK;
+}
+
+// The epoch boundary (Alg. 1 lines 13-18), a due quadtree pass, the trace
+// instrument's lambda record; the epoch is then complete.
+static rmlt_status epoch_boundary(rmlt_ctx* c)
+{
+    const uint64_t E = (uint64_t)c->Ch.E;
+    cudaError_t err = launch_region_update(c->Ch, false, c->stream);
+    if (err == cudaSuccess && c->Ch.quadtree) {
+        // M_refine counts the mutations of the whole population
+        c->since_refine += (uint64_t)c->Ch.C_all * E;
+        if (c->since_refine >= (uint64_t)c->P.qt_refine) {
+            c->since_refine = 0;
+            err = launch_quadtree_refine(c->Ch, c->stream);
+        }
+    }
+    if (err != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(err, "region update");
+    }
+    const bool trace = c->tr != nullptr;
+    if (trace && c->tr_lam && (c->tr_epoch + 1) * (uint64_t)c->Ch.m <= c->tr_lam_cap) {
+        err = cudaMemcpyAsync(c->tr_lam + c->tr_epoch * (uint64_t)c->Ch.m, c->Ch.lam, sizeof(double) * c->Ch.m,
+                              cudaMemcpyDeviceToDevice, c->stream);
+        if (err != cudaSuccess) return cuda_fail(err, "trace lambda copy");
+    }
+    if (trace) c->tr_epoch++;
+    c->mut += E;
+    c->epochs++;
+    return RMLT_OK;
+}
+
+static rmlt_status check_steppable(rmlt_ctx* c)
+{
+    if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
+    if (c->failed) return fail(RMLT_E_STATE, "context failed earlier: %s", g_err.c_str());
+    if (c->Ch.T_mala && (c->wavefront || c->tr))
+        return fail(RMLT_E_STATE, "the Langevin strategy runs in the chain kernel without the trace instrument");
+    return RMLT_OK;
+}
+
 rmlt_status rmlt_step(rmlt_ctx* c, uint64_t n_mutations)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if ((st = check_steppable(c))) return st;
+    if (c->Ch.C_all != c->Ch.C)
+        return fail(RMLT_E_STATE, "a sharded context steps with rmlt_epoch_mutate / rmlt_epoch_update");
+    if (c->in_epoch) return fail(RMLT_E_STATE, "rmlt_epoch_update is due first");
+    const uint64_t E = (uint64_t)c->Ch.E;
+    const uint64_t n_ep = (n_mutations + E - 1) / E;
+    for (uint64_t e = 0; e < n_ep; ++e) {
+        NvtxRange nv("rmlt epoch");
+        if ((st = epoch_kernels(c))) return st;
+        if ((st = epoch_boundary(c))) return st;
+    }
+    return RMLT_OK;
+}
+
+static rmlt_status check_device_buffer(const void* ptr, const char* what)
+{
+    cudaPointerAttributes at{};
+    if (!ptr || cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(RMLT_E_INVALID_ARG, "%s must be device memory", what);
+    }
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_exchange_size(rmlt_ctx* c, int64_t* n_counts, int64_t* n_sums)
+{
+    if (!c || !n_counts || !n_sums) return fail(RMLT_E_INVALID_ARG, "null argument");
+    if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
+    *n_counts = 3 * (int64_t)c->Ch.m + 1;
+    *n_sums = (int64_t)c->Ch.m;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_epoch_mutate(rmlt_ctx* c, uint64_t* counts, double* sums)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if ((st = check_steppable(c))) return st;
+    if (c->in_epoch) return fail(RMLT_E_STATE, "rmlt_epoch_update is due first");
+    if (c->Ch.T_mala) return fail(RMLT_E_INVALID_ARG, "the Langevin strategy steps with rmlt_step only");
+    if ((st = check_device_buffer(counts, "counts")) || (st = check_device_buffer(sums, "sums"))) return st;
+    NvtxRange nv("rmlt_epoch_mutate");
+    cudaError_t e = launch_epoch_snapshot(c->Ch, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "epoch snapshot");
+    if ((st = epoch_kernels(c))) return st;
+    e = launch_epoch_pack(c->Ch, (unsigned long long*)counts, sums, c->stream);
+    if (e != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(e, "epoch pack");
+    }
+    c->in_epoch = true;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_epoch_update(rmlt_ctx* c, const uint64_t* counts, const double* sums)
 {
     rmlt_status st = enter(c);
     if (st) return st;
     if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
     if (c->failed) return fail(RMLT_E_STATE, "context failed earlier: %s", g_err.c_str());
-    if (c->Ch.T_mala && (c->wavefront || c->tr))
-        return fail(RMLT_E_STATE, "the Langevin strategy runs in the chain kernel without the trace instrument");
-    const uint64_t E = (uint64_t)c->Ch.E;
-    const uint64_t n_ep = (n_mutations + E - 1) / E;
-    const uint32_t n_traced = (uint32_t)(((uint64_t)c->Ch.C + c->tr_stride - 1) / c->tr_stride);
-    for (uint64_t e = 0; e < n_ep; ++e) {
-        DevChains Ch = c->Ch;
-        Ch.batch_shade = c->batch_shade;
-        Ch.batch_setup = c->batch_setup;
-        Ch.adaptive_batch = c->adaptive_batch;
-        if (!c->large_ahead) Ch.lf = nullptr;
-        const bool trace = c->tr != nullptr;
-        if (trace) {
-            Ch.trace = c->tr;
-            Ch.trace_cap = c->tr_cap;
-            Ch.trace_stride = c->tr_stride;
-            Ch.trace_base = c->tr_epoch * (unsigned long long)n_traced * E;
-        }
-        const DevScene& S = c->S;
-        cudaError_t err = cudaSuccess;
-        if (c->wavefront && !c->W.s) {
-            void* mem = nullptr;
-            if ((st = c->dalloc(c->chain_mem, wf_bytes(Ch.C, Ch.D), &mem))) return st;
-            wf_carve(mem, Ch.C, Ch.D, c->W);
-        }
-        if (Ch.lf) err = launch_large_steps(S, Ch, c->mut, c->stream);
-        if (err == cudaSuccess) {
-            if (c->wavefront) {
-                c->W.refill = c->wf_refill;
-                err = wf_epoch(&c->wg, S, Ch, c->W, c->mut, Ch.trace_base, trace, c->count_work, c->wf_trace_cps,
-                               c->wf_setup_cps, (c->wf_flags & RMLT_WAVEFRONT_HOST_LOOP) != 0, c->stream);
-            } else {
-                err = launch_chain_epoch(S, Ch, c->mut, trace, c->count_work, c->stream);
-            }
-        }
-        if (err == cudaSuccess) err = launch_region_update(c->Ch, false, c->stream);
-        if (err != cudaSuccess) {
-            c->failed = true;
-            return cuda_fail(err, "rmlt_step launch");
-        }
-        if (err == cudaSuccess && c->Ch.quadtree) {
-            c->since_refine += (uint64_t)c->Ch.C * E;
-            if (c->since_refine >= (uint64_t)c->P.qt_refine) {
-                c->since_refine = 0;
-                err = launch_quadtree_refine(c->Ch, c->stream);
-            }
-            if (err != cudaSuccess) {
-                c->failed = true;
-                return cuda_fail(err, "quadtree refinement");
-            }
-        }
-        if (trace && c->tr_lam && (c->tr_epoch + 1) * (uint64_t)c->Ch.m <= c->tr_lam_cap) {
-            err = cudaMemcpyAsync(c->tr_lam + c->tr_epoch * (uint64_t)c->Ch.m, c->Ch.lam, sizeof(double) * c->Ch.m,
-                                  cudaMemcpyDeviceToDevice, c->stream);
-            if (err != cudaSuccess) return cuda_fail(err, "trace lambda copy");
-        }
-        if (trace) c->tr_epoch++;
-        c->mut += E;
-        c->epochs++;
+    if (!c->in_epoch) return fail(RMLT_E_STATE, "rmlt_epoch_mutate first");
+    if ((st = check_device_buffer(counts, "counts")) || (st = check_device_buffer(sums, "sums"))) return st;
+    NvtxRange nv("rmlt_epoch_update");
+    cudaError_t e = launch_epoch_unpack(c->Ch, (const unsigned long long*)counts, sums, c->stream);
+    if (e != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(e, "epoch unpack");
     }
-    return RMLT_OK;
+    c->in_epoch = false;
+    return epoch_boundary(c);
 }
 
 rmlt_status rmlt_set_trace(rmlt_ctx* c, rmlt_trace_record* records, uint64_t capacity, double* lambdas,
@@ -680,7 +881,9 @@ rmlt_status rmlt_read_image(rmlt_ctx* c, double* out, int normalized)
     if (st) return st;
     if (!out) return fail(RMLT_E_INVALID_ARG, "out is NULL");
     if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
-    const double n_total = (double)c->mut * (double)c->Ch.C;
+    if (c->in_epoch) return fail(RMLT_E_STATE, "rmlt_epoch_update is due first");
+    // mutations of the whole population (a sharded context returns its share)
+    const double n_total = (double)c->mut * (double)c->Ch.C_all;
     CK(launch_read_image(c->Ch, c->d_total, c->n_boot, n_total, normalized, c->d_stage, c->stream), "read image");
     if ((st = copy_out(c, out, c->d_stage, sizeof(double) * 3 * (size_t)c->Ch.W * c->Ch.H))) return st;
     return sync(c, "read image");
@@ -790,6 +993,22 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->wave_limit_hits = s[kStWaveLimit];
     out->mala = s[kStMala];
     out->mala_accepted = s[kStMalaAcc];
+    out->boot_overflow = s[kStBootOverflow];
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_read_params(rmlt_ctx* c, rmlt_chain_params* out)
+{
+    if (!c || !out) return fail(RMLT_E_INVALID_ARG, "null argument");
+    if (!c->have_chains) return fail(RMLT_E_STATE, "no chains");
+    *out = c->P;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_wave_limit(rmlt_ctx* c, uint32_t waves)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    c->wave_limit = waves;
     return RMLT_OK;
 }
 
@@ -861,13 +1080,15 @@ rmlt_status rmlt_set_work_counters(rmlt_ctx* c, int enable)
     return RMLT_OK;
 }
 
-rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint32_t* out_q, float* out_f,
+rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* pin, uint32_t* out_q, float* out_f,
                                    double* out_bhat)
 {
     rmlt_status st = enter(c);
     if (st) return st;
     if (!c->have_scene) return fail(RMLT_E_STATE, "load a scene before rmlt_bootstrap_noalloc");
-    if ((st = check_params(c, p))) return st;
+    rmlt_chain_params P;
+    if ((st = resolve_params(c, pin, &P))) return st;
+    const rmlt_chain_params* p = &P;
     if (!out_q || !out_f || !out_bhat) return fail(RMLT_E_INVALID_ARG, "output pointers must not be NULL");
     for (const void* ptr : {(const void*)out_q, (const void*)out_f}) {
         cudaPointerAttributes at{};
@@ -876,13 +1097,14 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint
             return fail(RMLT_E_INVALID_ARG, "out_q and out_f must be device memory");
         }
     }
-    const int64_t K = p->n_bootstrap / p->n_chains;
-    const int64_t nb = K * p->n_chains;
+    const int32_t C_all = chains_all(p);
+    const int64_t K = p->n_bootstrap / C_all;
+    const int64_t nb = K * C_all;
     const int nx = (p->width + p->region_px - 1) / p->region_px;
     const int64_t m = (int64_t)nx * ((p->height + p->region_px - 1) / p->region_px);
-    if (nb > RMLT_NOALLOC_MAX_SAMPLES || p->n_chains > RMLT_NOALLOC_MAX_CHAINS || m > RMLT_NOALLOC_MAX_REGIONS)
+    if (nb > RMLT_NOALLOC_MAX_SAMPLES || C_all > RMLT_NOALLOC_MAX_CHAINS || m > RMLT_NOALLOC_MAX_REGIONS)
         return fail(RMLT_E_INVALID_ARG, "sizes above the fixed scratch: %lld samples (max %d), %d chains (max %d), "
-                    "%lld regions (max %d)", (long long)nb, RMLT_NOALLOC_MAX_SAMPLES, p->n_chains,
+                    "%lld regions (max %d)", (long long)nb, RMLT_NOALLOC_MAX_SAMPLES, C_all,
                     RMLT_NOALLOC_MAX_CHAINS, (long long)m, RMLT_NOALLOC_MAX_REGIONS);
     NoAllocScratch na;
     CK(noalloc_scratch(c->device, na), "scratch lookup");
@@ -890,6 +1112,8 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint
     // written to the caller's buffers, everything else in the fixed scratch
     DevChains Ch;
     Ch.C = p->n_chains;
+    Ch.C_all = C_all;
+    Ch.chain0 = (uint32_t)p->chain_first;
     Ch.D = 2 + 5 * p->max_depth;
     Ch.W = p->width;
     Ch.H = p->height;
@@ -906,17 +1130,22 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* c, const rmlt_chain_params* p, uint
     Ch.pi = na.chain_pi;
     Ch.k = na.chain_k;
     Ch.Bk = na.Bk;
-    DevScene S = c->S;
-    S.tan_y = (float)c->tan_half;
-    S.tan_x = (float)(c->tan_half * (double)p->width / (double)p->height);
-    // the array keeps the previous call's contents: the region sums start at zero
+    const DevScene S = scene_for(c, p);
+    // the array keeps the previous call's contents: the region sums and the
+    // overflow count start at zero
     CK(cudaMemsetAsync(na.Bk, 0, sizeof(double) * (size_t)m, c->stream), "clear scratch");
+    CK(cudaMemsetAsync(na.overflow, 0, sizeof(unsigned long long), c->stream), "clear scratch");
     CK(launch_bootstrap(S, Ch, nb, na.boot, c->stream), "bootstrap");
     double total = 0.0;
+    unsigned long long overflow = 0;
     CK(cudaMemcpyAsync(&total, na.boot.total, sizeof total, cudaMemcpyDeviceToHost, c->stream), "read total");
-    if ((st = sync(c, "bootstrap"))) return st;
+    CK(cudaMemcpyAsync(&overflow, na.overflow, sizeof overflow, cudaMemcpyDeviceToHost, c->stream), "read overflow");
+    CK(cudaStreamSynchronize(c->stream), "bootstrap");
     const double bhat = total / (double)nb;
     CK(cudaMemcpy(out_bhat, &bhat, sizeof bhat, cudaMemcpyDefault), "write bhat");
+    if (overflow)
+        return fail(RMLT_E_OVERFLOW, "%llu bootstrap path(s) overflowed the traversal stack (dropped; b and the "
+                    "starting states are biased)", overflow);
     return RMLT_OK;
 }
 
@@ -946,25 +1175,65 @@ struct CkptHeader {
     uint64_t mut, epochs;
     int64_t n_boot;
     uint64_t since_refine;
+    uint64_t payload_bytes;
+    uint64_t checksum;        // FNV-1a (64 bit) of this header with checksum = 0, then the payload
 };
+constexpr char kCkptMagic[8] = {'R', 'M', 'L', 'T', 'C', 'K', 'P', '2'};
 
 struct Field {
     void* dev;
     size_t bytes;
 };
 
-std::vector<Field> fields(rmlt_ctx* c)
+// the device arrays a checkpoint holds, in file order
+std::vector<Field> fields(DevChains& Ch, double* d_total)
 {
-    DevChains& Ch = c->Ch;
     const size_t C = (size_t)Ch.C, m = (size_t)Ch.m, npx = (size_t)Ch.W * Ch.H * 3;
+    const size_t qn = Ch.quadtree ? (size_t)4 * Ch.qt_cap / 3 + 8 : 0;
     return {{Ch.q, C * Ch.D * 4}, {Ch.f, C * 12}, {Ch.pi, C * 4}, {Ch.k, C * 4},
             {Ch.lam, m * 8}, {Ch.n, m * 8}, {Ch.vis, m * 8}, {Ch.acc, m * 8}, {Ch.hist, m * 8},
             {Ch.hprev, m * 8}, {Ch.w, m * 8}, {Ch.Rc, m * 8}, {Ch.sig, m * 4}, {Ch.wf, m * 4},
-            {Ch.Bk, m * 8}, {Ch.img, npx * 8}, {Ch.stats, kStCount * 8}, {c->d_total, 8},
-            {Ch.qt_child, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 16 : 0},
-            {Ch.qt_leaf, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 4 : 0},
-            {Ch.qt_depth, Ch.quadtree ? ((size_t)4 * Ch.qt_cap / 3 + 8) * 4 : 0},
+            {Ch.Bk, m * 8}, {Ch.img, npx * 8}, {Ch.stats, kStCount * 8}, {d_total, 8}, {Ch.large_all, 8},
+            {Ch.qt_child, qn * 16}, {Ch.qt_leaf, qn * 4}, {Ch.qt_depth, qn * 4},
             {Ch.qt_state, Ch.quadtree ? (size_t)8 : (size_t)0}};
+}
+
+// Every index a kernel takes from the checkpoint, checked on the host: the
+// chains' regions and the quadtree (sizes, children below their parent,
+// leaf ids, depths).
+rmlt_status validate_payload(const DevChains& Ch, const std::vector<Field>& fl, const std::vector<unsigned char>& pay)
+{
+    std::vector<size_t> off(fl.size() + 1, 0);
+    for (size_t i = 0; i < fl.size(); ++i) off[i + 1] = off[i] + fl[i].bytes;
+    auto at = [&](int i) { return pay.data() + off[(size_t)i]; };
+    int m_now = Ch.m;
+    if (Ch.quadtree) {
+        int32_t st[2];
+        std::memcpy(st, at(22), sizeof st);
+        const int32_t cap_nodes = 4 * Ch.qt_cap / 3 + 8;
+        if (st[0] < 1 || st[0] > Ch.qt_cap || st[1] < 1 || st[1] > cap_nodes)
+            return fail(RMLT_E_INVALID_ARG, "checkpoint: quadtree sizes out of range");
+        const int32_t* child = (const int32_t*)at(19);
+        const int32_t* leaf = (const int32_t*)at(20);
+        const int32_t* depth = (const int32_t*)at(21);
+        for (int32_t nd = 0; nd < st[1]; ++nd) {
+            const bool is_leaf = child[4 * nd] < 0;
+            for (int j = 0; j < 4; ++j) {
+                const int32_t ch = child[4 * nd + j];
+                if (is_leaf ? ch != -1 : (ch <= nd || ch >= st[1]))
+                    return fail(RMLT_E_INVALID_ARG, "checkpoint: quadtree node %d has a bad child", nd);
+            }
+            if (is_leaf ? (leaf[nd] < 0 || leaf[nd] >= st[0]) : leaf[nd] != -1)
+                return fail(RMLT_E_INVALID_ARG, "checkpoint: quadtree node %d has a bad leaf id", nd);
+            if (depth[nd] < 0 || depth[nd] > Ch.qt_max_depth)
+                return fail(RMLT_E_INVALID_ARG, "checkpoint: quadtree node %d has a bad depth", nd);
+        }
+        m_now = st[0];
+    }
+    const int32_t* k = (const int32_t*)at(3);
+    for (int c = 0; c < Ch.C; ++c)
+        if (k[c] < 0 || k[c] >= m_now) return fail(RMLT_E_INVALID_ARG, "checkpoint: chain %d has region %d", c, k[c]);
+    return RMLT_OK;
 }
 }  // namespace
 
@@ -974,11 +1243,20 @@ rmlt_status rmlt_save(rmlt_ctx* c, const char* path)
     if (st) return st;
     if (!path) return fail(RMLT_E_INVALID_ARG, "path is NULL");
     if (!c->have_chains || c->failed) return fail(RMLT_E_STATE, "no valid chains");
+    if (c->in_epoch) return fail(RMLT_E_STATE, "rmlt_epoch_update is due first");
     if ((st = sync(c, "save"))) return st;
-    FILE* fp = std::fopen(path, "wb");
-    if (!fp) return fail(RMLT_E_IO, "cannot open %s for writing", path);
+    const std::vector<Field> fl = fields(c->Ch, c->d_total);
+    size_t total = 0;
+    for (const Field& f : fl) total += f.bytes;
+    std::vector<unsigned char> pay(total);
+    size_t o = 0;
+    for (const Field& f : fl) {
+        if (f.bytes && cudaMemcpy(pay.data() + o, f.dev, f.bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "save copy");
+        o += f.bytes;
+    }
     CkptHeader h{};
-    std::memcpy(h.magic, "RMLTCKP1", 8);
+    std::memcpy(h.magic, kCkptMagic, 8);
     h.abi = RMLT_ABI_VERSION;
     h.scene_hash = c->scene_hash;
     h.P = c->P;
@@ -986,18 +1264,12 @@ rmlt_status rmlt_save(rmlt_ctx* c, const char* path)
     h.epochs = c->epochs;
     h.n_boot = c->n_boot;
     h.since_refine = c->since_refine;
-    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1;
-    std::vector<unsigned char> buf;
-    for (const Field& f : fields(c)) {
-        if (!ok) break;
-        if (f.bytes == 0) continue;
-        buf.resize(f.bytes);
-        if (cudaMemcpy(buf.data(), f.dev, f.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
-            std::fclose(fp);
-            return cuda_fail(cudaGetLastError(), "save copy");
-        }
-        ok = std::fwrite(buf.data(), 1, f.bytes, fp) == f.bytes;
-    }
+    h.payload_bytes = total;
+    h.checksum = 0;
+    h.checksum = fnv64(pay.data(), pay.size(), fnv64(&h, sizeof h, 1469598103934665603ull));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(RMLT_E_IO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 && std::fwrite(pay.data(), 1, pay.size(), fp) == pay.size();
     ok = (std::fclose(fp) == 0) && ok;
     if (!ok) return fail(RMLT_E_IO, "write to %s failed", path);
     return RMLT_OK;
@@ -1012,46 +1284,63 @@ rmlt_status rmlt_restore(rmlt_ctx* c, const char* path)
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(RMLT_E_IO, "cannot open %s", path);
     CkptHeader h{};
-    if (std::fread(&h, sizeof h, 1, fp) != 1 || std::memcmp(h.magic, "RMLTCKP1", 8) != 0 || h.abi != RMLT_ABI_VERSION) {
+    if (std::fread(&h, sizeof h, 1, fp) != 1) {
+        std::fclose(fp);
+        return fail(RMLT_E_IO, "truncated checkpoint %s (header)", path);
+    }
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.abi != RMLT_ABI_VERSION) {
         std::fclose(fp);
         return fail(RMLT_E_INVALID_ARG, "%s is not a checkpoint of this library version", path);
     }
-    if (h.scene_hash != c->scene_hash) {
+    if (h.payload_bytes > ((uint64_t)1 << 40)) {
         std::fclose(fp);
-        return fail(RMLT_E_INVALID_ARG, "checkpoint was taken on another scene");
+        return fail(RMLT_E_INVALID_ARG, "checkpoint %s: implausible payload size", path);
     }
-    if ((st = check_params(c, &h.P))) {
-        std::fclose(fp);
-        return st;
-    }
-    if ((st = alloc_chains(c, &h.P))) {
-        std::fclose(fp);
-        return st;
-    }
-    std::vector<unsigned char> buf;
-    for (const Field& f : fields(c)) {
-        if (f.bytes == 0) continue;
-        buf.resize(f.bytes);
-        if (std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
-            std::fclose(fp);
-            drop_chains(c);
-            return fail(RMLT_E_IO, "truncated checkpoint %s", path);
-        }
-        if (cudaMemcpy(f.dev, buf.data(), f.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-            std::fclose(fp);
-            drop_chains(c);
-            return cuda_fail(cudaGetLastError(), "restore copy");
-        }
-    }
+    std::vector<unsigned char> pay((size_t)h.payload_bytes);
+    const size_t got = std::fread(pay.data(), 1, pay.size(), fp);
     std::fclose(fp);
-    if (c->Ch.G) {   // gradients of the restored states (not stored: a function of q)
-        cudaError_t e = launch_state_gradients(c->S, c->Ch, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            drop_chains(c);
-            return cuda_fail(e, "restore gradients");
-        }
+    if (got != pay.size()) return fail(RMLT_E_IO, "truncated checkpoint %s", path);
+    CkptHeader hz = h;
+    hz.checksum = 0;
+    if (fnv64(pay.data(), pay.size(), fnv64(&hz, sizeof hz, 1469598103934665603ull)) != h.checksum)
+        return fail(RMLT_E_INVALID_ARG, "checkpoint %s: checksum mismatch (corrupted file)", path);
+    if (h.scene_hash != c->scene_hash) return fail(RMLT_E_INVALID_ARG, "checkpoint was taken on another scene");
+    if ((st = check_params(c, &h.P))) return st;
+    if (h.n_boot < (int64_t)chains_all(&h.P)) return fail(RMLT_E_INVALID_ARG, "checkpoint: bad bootstrap count");
+    ChainAlloc A;
+    if ((st = alloc_chains(c, &h.P, A))) {
+        c->release(A.pool);
+        return st;
     }
+    const std::vector<Field> fl = fields(A.Ch, A.d_total);
+    size_t total = 0;
+    for (const Field& f : fl) total += f.bytes;
+    if (total != pay.size()) {
+        c->release(A.pool);
+        return fail(RMLT_E_INVALID_ARG, "checkpoint %s: payload size does not match its parameters", path);
+    }
+    if ((st = validate_payload(A.Ch, fl, pay))) {
+        c->release(A.pool);
+        return st;
+    }
+    size_t o = 0;
+    cudaError_t e = cudaSuccess;
+    for (const Field& f : fl) {
+        if (f.bytes && e == cudaSuccess) e = cudaMemcpy(f.dev, pay.data() + o, f.bytes, cudaMemcpyHostToDevice);
+        o += f.bytes;
+    }
+    const DevScene S = scene_for(c, &h.P);
+    // the regions follow from the states (validated above; recomputed so that
+    // the two cannot disagree)
+    if (e == cudaSuccess) e = launch_chain_regions(A.Ch, c->stream);
+    // gradients of the restored states (not stored: a function of q)
+    if (e == cudaSuccess && A.Ch.G) e = launch_state_gradients(S, A.Ch, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->release(A.pool);
+        return cuda_fail(e, "restore");
+    }
+    adopt_chains(c, A, &h.P);
     c->mut = h.mut;
     c->epochs = h.epochs;
     c->n_boot = h.n_boot;
@@ -1112,6 +1401,8 @@ rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
     if (c->wavefront) return fail(RMLT_E_STATE, "member %d: the wavefront form is set", i);
     if (c->Ch.T_mala) return fail(RMLT_E_STATE, "member %d: the Langevin strategy is set", i);
     if (c->Ch.dcells > 1) return fail(RMLT_E_STATE, "member %d: the 4-D partition is set", i);
+    if (c->Ch.C_all != c->Ch.C) return fail(RMLT_E_STATE, "member %d is a shard of a larger population", i);
+    if (c->in_epoch) return fail(RMLT_E_STATE, "member %d: rmlt_epoch_update is due", i);
     return RMLT_OK;
 }
 

@@ -834,7 +834,7 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
     double sf = 0.0;   // |delta - m_x|^2
     float delta[kMaxDim];
     for (int jj = 0; 4 * jj < D; ++jj) {
-        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        const uint4 r = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
@@ -919,7 +919,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
     const int C = Ch.C, D = Ch.D;
     const uint64_t mut = mut0 + (uint64_t)L.j;
     const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
-    const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+    const uint4 r0 = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
     L.large = (r0.x >> 8) < Ch.T_large;
     L.xi = u24(r0.y);
     L.R = 1.0f;
@@ -933,7 +933,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
     int R = 1;
     if (L.large) {
         for (int jj = 0; 4 * jj < D; ++jj) {
-            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            const uint4 r = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
             y[4 * jj] = r.x;
             if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
             if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
@@ -950,7 +950,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
         const float zx = erff(0.353553390593273762f / sx);
         double s2 = 0.0;
         for (int jj = 0; 2 * jj < D; ++jj) {
-            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            const uint4 r = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int d = 2 * jj + e;
@@ -983,7 +983,7 @@ __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChain
         float lo = 0.f, hi = 0.f;
         bool check = false;
         for (int jj = 0; 2 * jj < D; ++jj) {
-            const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+            const uint4 r = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
             const int d0 = 2 * jj;
             const uint32_t o0 = kelemen_offset(r.x, sigS2, Ch.log2_ratio);
             y[d0] = (r.y >> 31) ? y[d0] - o0 : y[d0] + o0;

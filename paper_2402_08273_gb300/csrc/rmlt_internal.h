@@ -34,6 +34,8 @@ enum StatSlot {
     kStWaves, kStWaveLimit,
     // Langevin moves proposed and accepted
     kStMala, kStMalaAcc,
+    // bootstrap paths dropped by a traversal-stack overflow
+    kStBootOverflow,
     kStCount = 32
 };
 
@@ -68,6 +70,10 @@ struct DevChains {
     int32_t weighted = 0;
     int32_t truncnorm = 0;        // small-step kernel: 0 Kelemen, 1 truncated normal
     int32_t dcells = 0;           // 4-D partition: cells per axis over (u5, u6); <= 1 screen only
+    // sharded population: chain c of this context has the global id chain0 + c
+    // (its Philox key), of C_all chains over every context (C_all = C unsharded)
+    uint32_t chain0 = 0;
+    int32_t C_all = 0;
     uint32_t* q = nullptr;        // word d of chain c at q[d qd + c qc]: [D][C] (qd = C, qc = 1)
     int64_t qd = 0, qc = 1;       //   or, inside the wavefront form's epoch, a [C][D] copy (qd = 1, qc = D)
     float* f = nullptr;           // [3][C]
@@ -84,6 +90,12 @@ struct DevChains {
     float* sig = nullptr;         // sigma_k [m]
     float* wf = nullptr;          // w_k as float [m]
     double* Bk = nullptr;         // sum of pi over uniform samples per region [m]
+    // epoch-wise stepping (rmlt_epoch_mutate / rmlt_epoch_update): the region
+    // tables at the start of the epoch, i [m] A [m] h [m] and the large-step
+    // count [1], and Bk [m]; the whole population's large steps [1]
+    unsigned long long* snap = nullptr;
+    double* snapB = nullptr;
+    unsigned long long* large_all = nullptr;
     // quadtree partition (Sec. 6.2); m is then the region capacity and the
     // current leaf count lives in qt_state[0] (nodes in qt_state[1])
     int32_t quadtree = 0;
@@ -159,9 +171,10 @@ void wf_carve(void* base, int C, int D, DevWave& w);
 struct WfGraph;   // the instantiated wave loop, rebuilt when its launch parameters change
 void wf_graph_destroy(WfGraph* g);
 // One epoch of E mutations per chain in the wavefront form.
+// wave_limit: waves after which the epoch stops (0: E (max_depth + 1) + 2)
 cudaError_t wf_epoch(WfGraph** g, const DevScene& s, const DevChains& c, DevWave& w, uint64_t mut0,
                      unsigned long long trace_base, bool trace, bool count_work, int trace_ctas_per_sm,
-                     int setup_ctas_per_sm, bool host_loop, cudaStream_t st);
+                     int setup_ctas_per_sm, bool host_loop, unsigned wave_limit, cudaStream_t st);
 
 // One member of a batched epoch (rmlt_batch_step): its scene, its chains,
 // the mutation index of its next epoch and its first block in the launch.
@@ -182,11 +195,15 @@ cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const Batch
 cudaError_t launch_region_update_batch(BatchMember* members, int n, cudaStream_t st);
 
 // Scratch of the bootstrap (n = K C samples, K = n_bootstrap / C per chain).
+// The bootstrap draws n = K C_all samples (every context of a sharded
+// population draws all of them) and selects starting states for its own
+// chains.
 struct BootScratch {
     float* pi = nullptr;          // [n]
     float* f = nullptr;           // [3][n]
-    double* partial = nullptr;    // [C] per-chain slice sums
+    double* partial = nullptr;    // [C_all] per-chain slice sums
     double* total = nullptr;      // [1] sum of pi over all samples (kept)
+    unsigned long long* overflow = nullptr;   // [1] paths dropped by a traversal-stack overflow (added to)
 };
 
 cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace,
@@ -204,6 +221,15 @@ cudaError_t launch_read_image(const DevChains& c, const double* bhat_total, int6
                               double n_total, int normalized, double* out, cudaStream_t st);
 cudaError_t launch_fill_regions(const DevChains& c, double lambda_init, cudaStream_t st);
 cudaError_t launch_quadtree_refine(const DevChains& c, cudaStream_t st);
+// epoch-wise stepping: copy the region tables to c.snap / c.snapB; write what
+// the epoch added to them (counts [3m + 1], sums [m]); set them to the
+// snapshot plus the summed additions
+cudaError_t launch_epoch_snapshot(const DevChains& c, cudaStream_t st);
+cudaError_t launch_epoch_pack(const DevChains& c, unsigned long long* counts, double* sums, cudaStream_t st);
+cudaError_t launch_epoch_unpack(const DevChains& c, const unsigned long long* counts, const double* sums,
+                                cudaStream_t st);
+// the chains' regions recomputed from their states (after a restore)
+cudaError_t launch_chain_regions(const DevChains& c, cudaStream_t st);
 
 // Pointers into the library's fixed scratch array (rmlt_bootstrap_noalloc).
 struct NoAllocScratch {
@@ -211,6 +237,7 @@ struct NoAllocScratch {
     float* chain_pi = nullptr;
     int32_t* chain_k = nullptr;
     double* Bk = nullptr;
+    unsigned long long* overflow = nullptr;
 };
 // Looks the array up on the current device (first call per device) and
 // fills `out`; allocates nothing.

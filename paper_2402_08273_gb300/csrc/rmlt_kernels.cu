@@ -42,7 +42,7 @@ constexpr int kMalaBatch = 8;
 __device__ __forceinline__ bool next_is_mala(const DevChains& Ch, int c, uint64_t mut0, const ChainLane& L)
 {
     const uint64_t mut = mut0 + (uint64_t)L.j;
-    const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+    const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), Ch.chain0 + (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
     const uint32_t h = r0.x >> 8;
     return h >= Ch.T_large && h < Ch.T_large + Ch.T_mala;
 }
@@ -250,7 +250,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
                     // the fields mutation_setup sets before it hands over
                     const uint64_t mut = mut0 + (uint64_t)L.j;
                     const uint32_t mlo = (uint32_t)mut, mhi = (uint32_t)(mut >> 32);
-                    const uint4 r0 = philox(mlo, mhi, (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+                    const uint4 r0 = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
                     L.large = 0;
                     L.xi = u24(r0.y);
                     L.R = 1.0f;
@@ -430,7 +430,7 @@ __global__ void large_collect_kernel(const DevChains Ch, uint64_t mut0)
         j = (int)(i / Ch.C);
         c = (int)(i % Ch.C);
         const uint64_t mut = mut0 + (uint64_t)j;
-        const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
+        const uint4 r0 = philox((uint32_t)mut, (uint32_t)(mut >> 32), Ch.chain0 + (uint32_t)c, 0u, Ch.seed_lo, Ch.seed_hi);
         large = (r0.x >> 8) < Ch.T_large;
     }
     // warp-aggregated append to the work list
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
     const int D = Ch.D;
     uint32_t y[kMaxDim];
     for (int jj = 0; 4 * jj < D; ++jj) {
-        const uint4 r = philox(mlo, mhi, (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
+        const uint4 r = philox(mlo, mhi, Ch.chain0 + (uint32_t)c, 1u + (uint32_t)jj, Ch.seed_lo, Ch.seed_hi);
         y[4 * jj] = r.x;
         if (4 * jj + 1 < D) y[4 * jj + 1] = r.y;
         if (4 * jj + 2 < D) y[4 * jj + 2] = r.z;
@@ -608,7 +608,65 @@ __global__ void chain_regions_kernel(const DevChains Ch)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= Ch.C) return;
-    Ch.k[c] = region_of(Ch, Ch.q[c], Ch.q[(size_t)Ch.C + c]);
+    const size_t C = (size_t)Ch.C;
+    uint32_t qv[7] = {Ch.q[c], Ch.q[C + c], 0u, 0u, 0u, 0u, 0u};
+    if (Ch.dcells > 1) {
+        qv[5] = Ch.q[5 * C + c];
+        qv[6] = Ch.q[6 * C + c];
+    }
+    Ch.k[c] = region_y(Ch, qv);
+}
+
+// ---------------------------------------------------------------------------
+// epoch-wise stepping of a sharded population: the region statistics the
+// chains of every context add during an epoch are summed (by the caller, an
+// all-reduce) before the region update, so that all contexts update from the
+// same i_k, A_k and h_k (the paper's threads share these counters, Sec. 6).
+// Integer sums commute: the tables are identical on every context.
+// ---------------------------------------------------------------------------
+__global__ void epoch_snapshot_kernel(const DevChains Ch)
+{
+    const int m = Ch.m;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += gridDim.x * blockDim.x) {
+        if (k == m) {
+            Ch.snap[3 * (size_t)m] = Ch.stats[kStLarge];
+            continue;
+        }
+        Ch.snap[k] = Ch.vis[k];
+        Ch.snap[(size_t)m + k] = Ch.acc[k];
+        Ch.snap[2 * (size_t)m + k] = Ch.hist[k];
+        Ch.snapB[k] = Ch.Bk[k];
+    }
+}
+
+__global__ void epoch_pack_kernel(const DevChains Ch, unsigned long long* counts, double* sums)
+{
+    const int m = Ch.m;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += gridDim.x * blockDim.x) {
+        if (k == m) {
+            counts[3 * (size_t)m] = Ch.stats[kStLarge] - Ch.snap[3 * (size_t)m];
+            continue;
+        }
+        counts[k] = Ch.vis[k] - Ch.snap[k];
+        counts[(size_t)m + k] = Ch.acc[k] - Ch.snap[(size_t)m + k];
+        counts[2 * (size_t)m + k] = Ch.hist[k] - Ch.snap[2 * (size_t)m + k];
+        sums[k] = Ch.Bk[k] - Ch.snapB[k];
+    }
+}
+
+__global__ void epoch_unpack_kernel(const DevChains Ch, const unsigned long long* counts, const double* sums)
+{
+    const int m = Ch.m;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= m; k += gridDim.x * blockDim.x) {
+        if (k == m) {
+            Ch.large_all[0] += counts[3 * (size_t)m];
+            continue;
+        }
+        Ch.vis[k] = Ch.snap[k] + counts[k];
+        Ch.acc[k] = Ch.snap[(size_t)m + k] + counts[(size_t)m + k];
+        Ch.hist[k] = Ch.snap[2 * (size_t)m + k] + counts[2 * (size_t)m + k];
+        Ch.Bk[k] = Ch.snapB[k] + sums[k];
+    }
 }
 
 __global__ void quadtree_init_kernel(const DevChains Ch)
@@ -660,6 +718,7 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     }
     V3 f = {0.f, 0.f, 0.f};
     unsigned nn = 0, nt = 0;
+    bool overflow = false;
     if (S.toy) {
         const float v = toy_eval(S, y[0], y[1]);
         f = {v, v, v};
@@ -672,11 +731,16 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
             trav_begin(T, p.o, p.d, p.tmax, p.any);
             while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
             }
-            if (T.overflow) { p.L = {0.f, 0.f, 0.f}; break; }
+            if (T.overflow) {
+                p.L = {0.f, 0.f, 0.f};
+                overflow = true;
+                break;
+            }
             path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
         }
         f = p.L;
     }
+    if (overflow) atomicAdd(B.overflow, 1ull);   // counted: such a path biases b and the starting states
     float pv = lum(f.x, f.y, f.z);
     if (!isfinite(pv)) { f = {0.f, 0.f, 0.f}; pv = 0.f; }
     B.pi[s] = pv;
@@ -687,27 +751,31 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     if (pv != 0.f) atomicAdd(&Ch.Bk[k], (double)pv);
 }
 
-// Initial state of chain c: weighted reservoir sampling over its own K
-// uniform samples s in [cK, (c+1)K): keep s when v_s cum_s < pi_s, which picks
-// s with probability pi_s / sum(pi) (v_s a uniform of its own).  The slice sum
-// goes to `partial` for the normaliser b.
+// Initial state of chain g (global id): weighted reservoir sampling over its
+// own K uniform samples s in [gK, (g+1)K): keep s when v_s cum_s < pi_s, which
+// picks s with probability pi_s / sum(pi) (v_s a uniform of its own).  The
+// slice sum goes to `partial` for the normaliser b.  Every chain of the
+// population computes its slice sum; only this context's chains
+// [chain0, chain0 + C) write a state.
 __global__ void bootstrap_select_kernel(const DevChains Ch, long long K, const BootScratch B)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Ch.C) return;
-    const long long n_eff = K * Ch.C;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Ch.C_all) return;
+    const long long n_eff = K * Ch.C_all;
     double cum = 0.0;
     long long sel = -1;
     for (long long i = 0; i < K; ++i) {
-        const long long s = (long long)c * K + i;
+        const long long s = (long long)g * K + i;
         const double v = (double)B.pi[s];
         cum += v;
         const uint4 r = philox((uint32_t)s, (uint32_t)((unsigned long long)s >> 32), 0xFFFFFFFFu, 0x7FFFu,
                                Ch.seed_lo, Ch.seed_hi);
         if (v > 0.0 && (double)u24(r.x) * cum < v) sel = s;
     }
-    if (sel < 0) sel = (long long)c * K;
-    B.partial[c] = cum;
+    if (sel < 0) sel = (long long)g * K;
+    B.partial[g] = cum;
+    const int c = g - (int)Ch.chain0;
+    if (c < 0 || c >= Ch.C) return;
     const int D = Ch.D, C = Ch.C;
     uint32_t q0 = 0, q1 = 0, q5 = 0, q6 = 0;
     for (int jj = 0; 4 * jj < D; ++jj) {
@@ -764,7 +832,9 @@ __global__ void read_image_kernel(const DevChains Ch, const double* bhat_total, 
                 const int x = (int)(i % Ch.W), y = (int)(i / Ch.W);
                 const int k = x / Ch.region_px + (y / Ch.region_px) * Ch.nx;
                 // uniform samples: the bootstrap plus every large-step proposal
-                const double nU = (double)n_boot + (double)Ch.stats[kStLarge];
+                // (of the whole population when sharded)
+                const double nL = Ch.C_all != Ch.C ? (double)Ch.large_all[0] : (double)Ch.stats[kStLarge];
+                const double nU = (double)n_boot + nL;
                 s = (Ch.hist[k] > 0 && nU > 0.0) ? WH * (Ch.Bk[k] / nU) / (double)Ch.hist[k] : 0.0;
             }
         }
@@ -946,11 +1016,42 @@ cudaError_t launch_quadtree_refine(const DevChains& c, cudaStream_t st)
     return cudaGetLastError();
 }
 
+static unsigned region_blocks(const DevChains& c)
+{
+    const long long b = ((long long)c.m + 256) / 256;
+    return (unsigned)(b < 1024 ? b : 1024);
+}
+
+cudaError_t launch_epoch_snapshot(const DevChains& c, cudaStream_t st)
+{
+    epoch_snapshot_kernel<<<region_blocks(c), 256, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epoch_pack(const DevChains& c, unsigned long long* counts, double* sums, cudaStream_t st)
+{
+    epoch_pack_kernel<<<region_blocks(c), 256, 0, st>>>(c, counts, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epoch_unpack(const DevChains& c, const unsigned long long* counts, const double* sums,
+                                cudaStream_t st)
+{
+    epoch_unpack_kernel<<<region_blocks(c), 256, 0, st>>>(c, counts, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_regions(const DevChains& c, cudaStream_t st)
+{
+    chain_regions_kernel<<<(c.C + 255) / 256, 256, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot, const BootScratch& b,
                              cudaStream_t st)
 {
-    const long long K = n_boot / c.C;
-    const long long n_eff = K * c.C;
+    const long long K = n_boot / c.C_all;
+    const long long n_eff = K * c.C_all;
     const long long blocks = (n_eff + kChainBlock - 1) / kChainBlock;
     const size_t shm = s.brute ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
     cudaError_t e;
@@ -964,9 +1065,9 @@ cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_bo
         bootstrap_eval_kernel<false><<<(unsigned)blocks, kChainBlock, 0, st>>>(s, c, n_eff, b);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bootstrap_select_kernel<<<(c.C + 127) / 128, 128, 0, st>>>(c, K, b);
+    bootstrap_select_kernel<<<(c.C_all + 127) / 128, 128, 0, st>>>(c, K, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bootstrap_total_kernel<<<1, 256, 0, st>>>(c.C, b);
+    bootstrap_total_kernel<<<1, 256, 0, st>>>(c.C_all, b);
     return cudaGetLastError();
 }
 
@@ -983,7 +1084,8 @@ constexpr size_t kNaTotal = na_align(kNaPartial + sizeof(double) * RMLT_NOALLOC_
 constexpr size_t kNaChainPi = na_align(kNaTotal + sizeof(double));
 constexpr size_t kNaChainK = na_align(kNaChainPi + sizeof(float) * RMLT_NOALLOC_MAX_CHAINS);
 constexpr size_t kNaBk = na_align(kNaChainK + sizeof(int32_t) * RMLT_NOALLOC_MAX_CHAINS);
-constexpr size_t kNaBytes = na_align(kNaBk + sizeof(double) * RMLT_NOALLOC_MAX_REGIONS);
+constexpr size_t kNaOverflow = na_align(kNaBk + sizeof(double) * RMLT_NOALLOC_MAX_REGIONS);
+constexpr size_t kNaBytes = na_align(kNaOverflow + sizeof(unsigned long long));
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1015,6 +1117,8 @@ cudaError_t noalloc_scratch(int device, NoAllocScratch& out)
     out.chain_pi = (float*)(base + kNaChainPi);
     out.chain_k = (int32_t*)(base + kNaChainK);
     out.Bk = (double*)(base + kNaBk);
+    out.overflow = (unsigned long long*)(base + kNaOverflow);
+    out.boot.overflow = out.overflow;
     return cudaSuccess;
 }
 

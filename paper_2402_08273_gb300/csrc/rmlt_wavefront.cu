@@ -636,7 +636,8 @@ cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int tr
 
 template <bool B, bool T, bool K>
 cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWave& W, uint64_t mut0,
-                    unsigned long long trace_base, int trace_cps, int setup_cps, bool host_loop, cudaStream_t st)
+                    unsigned long long trace_base, int trace_cps, int setup_cps, bool host_loop, unsigned wave_limit,
+                    cudaStream_t st)
 {
     const int sms = sm_count();
     const int tocc = trace_occupancy<B, T, K>(S), socc = setup_occupancy<T>();
@@ -645,7 +646,9 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
     int sc = sms * (setup_cps > 0 && setup_cps < socc ? setup_cps : socc);
     if (sc > max_setup) sc = max_setup;
     if (sc < 1) sc = 1;
-    W.wave_cap = (unsigned)Ch.E * (unsigned)(Ch.max_depth + 1) + 2u;
+    // every wave advances each chain with rays by one bounce: E (d + 1) + 2
+    // waves finish any epoch; a smaller limit stops it early (counted)
+    W.wave_cap = wave_limit ? wave_limit : (unsigned)Ch.E * (unsigned)(Ch.max_depth + 1) + 2u;
     // during the epoch the waves address the states in the row-major copy: a
     // wave's setup list is a sparse subset of the chains, and one chain's
     // words in a row share cache lines where a column layout would give
@@ -704,12 +707,12 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
 
 cudaError_t wf_epoch(WfGraph** g, const DevScene& s, const DevChains& c, DevWave& w, uint64_t mut0,
                      unsigned long long trace_base, bool trace, bool count_work, int trace_ctas_per_sm,
-                     int setup_ctas_per_sm, bool host_loop, cudaStream_t st)
+                     int setup_ctas_per_sm, bool host_loop, unsigned wave_limit, cudaStream_t st)
 {
     if (w.refill < 1) w.refill = 1;
     if (w.refill > 32) w.refill = 32;
 #define RMLT_WF(B, T, K) \
-    epoch_t<B, T, K>(g, s, c, w, mut0, trace_base, trace_ctas_per_sm, setup_ctas_per_sm, host_loop, st)
+    epoch_t<B, T, K>(g, s, c, w, mut0, trace_base, trace_ctas_per_sm, setup_ctas_per_sm, host_loop, wave_limit, st)
     if (s.brute) {
         if (trace) return count_work ? RMLT_WF(true, true, true) : RMLT_WF(true, true, false);
         return count_work ? RMLT_WF(true, false, true) : RMLT_WF(true, false, false);

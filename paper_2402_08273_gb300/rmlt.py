@@ -8,7 +8,6 @@ library cannot be built or loaded, or no GPU is present, the calls raise.
 from __future__ import annotations
 
 import ctypes as C
-import math
 from pathlib import Path
 
 import numpy as np
@@ -17,8 +16,7 @@ from . import _build
 
 RMLT_OK = 0
 STATUS = {0: "RMLT_OK", -1: "RMLT_E_INVALID_ARG", -2: "RMLT_E_INVALID_SCENE", -3: "RMLT_E_OOM",
-          -4: "RMLT_E_CUDA", -5: "RMLT_E_STATE", -6: "RMLT_E_TIMEOUT", -7: "RMLT_E_OVERFLOW",
-          -8: "RMLT_E_IO"}
+          -4: "RMLT_E_CUDA", -5: "RMLT_E_STATE", -7: "RMLT_E_OVERFLOW", -8: "RMLT_E_IO"}
 LAMBERT, GGX = 0, 1
 TARGET_PLAIN, TARGET_REGION_WEIGHTED = 0, 1
 KERNEL_KELEMEN, KERNEL_TRUNCNORM = 0, 1
@@ -59,7 +57,8 @@ class ChainParams(C.Structure):
                 ("partition", C.c_int32), ("qt_max_leaves", C.c_int32), ("qt_max_depth", C.c_int32),
                 ("qt_pad_", C.c_int32), ("qt_split", C.c_int64), ("qt_refine", C.c_int64),
                 ("p_mala", C.c_double), ("mala_tau", C.c_double), ("mala_drift_max", C.c_double),
-                ("kernel", C.c_int32), ("dir_cells", C.c_int32)]
+                ("kernel", C.c_int32), ("dir_cells", C.c_int32), ("chain_first", C.c_int32),
+                ("chains_total", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -69,7 +68,7 @@ class Stats(C.Structure):
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
                 ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6),
                 ("cycles", C.c_uint64 * 5), ("waves", C.c_uint64), ("wave_limit_hits", C.c_uint64),
-                ("mala", C.c_uint64), ("mala_accepted", C.c_uint64)]
+                ("mala", C.c_uint64), ("mala_accepted", C.c_uint64), ("boot_overflow", C.c_uint64)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -90,6 +89,11 @@ _SIGS = [
     ("rmlt_load_toy_integrand", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("rmlt_init_chains", C.c_int, [C.c_void_p, _P(ChainParams)]),
     ("rmlt_step", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("rmlt_exchange_size", C.c_int, [C.c_void_p, _P(C.c_int64), _P(C.c_int64)]),
+    ("rmlt_epoch_mutate", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rmlt_epoch_update", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("rmlt_read_params", C.c_int, [C.c_void_p, _P(ChainParams)]),
+    ("rmlt_set_wave_limit", C.c_int, [C.c_void_p, C.c_uint32]),
     ("rmlt_read_image", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("rmlt_read_region_hist", C.c_int, [C.c_void_p, C.c_void_p]),
     ("rmlt_read_region_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -149,18 +153,17 @@ def _check(st: int):
 
 def default_params(**kw) -> dict:
     """Chain parameters: Sec. 7.1 values (L = 10, gamma_max = 1, gamma_scale = 5,
-    lambda_min = -30, alpha* = 0.5) with Kelemen's s1 = 1/1024, s2 = 1/64."""
+    lambda_min = -30, alpha* = 0.5) with Kelemen's s1 = 1/1024, s2 = 1/64.
+    lambda_max = 0 lets the library choose its default."""
     p = dict(n_chains=64, width=64, height=64, region_px=8, max_depth=5, epoch_len=16, L=10,
              target_mode=TARGET_PLAIN, n_bootstrap=1 << 16, seed=1, p_large=0.3, s1=1 / 1024,
              s2=1 / 64, alpha_star=0.5, gamma_max=1.0, gamma_scale=5.0, lambda_init=0.0,
-             lambda_min=-30.0, lambda_max=None, w_floor=1e-3, partition=0, qt_max_leaves=4096,
+             lambda_min=-30.0, lambda_max=0.0, w_floor=1e-3, partition=0, qt_max_leaves=4096,
              qt_max_depth=10, qt_pad_=0, qt_split=5000, qt_refine=10_000_000, p_mala=0.0, mala_tau=1e-3,
-             mala_drift_max=0.1, kernel=KERNEL_KELEMEN, dir_cells=0)
+             mala_drift_max=0.1, kernel=KERNEL_KELEMEN, dir_cells=0, chain_first=0, chains_total=0)
     p.update(kw)
     if p["lambda_max"] is None:
-        # Kelemen: sigma s2 <= 1/2; truncated normal: sigma <= 4
-        p["lambda_max"] = (2.0 * math.log(4.0) if p["kernel"] == KERNEL_TRUNCNORM
-                           else 2.0 * math.log(1.0 / (2.0 * p["s2"])))
+        p["lambda_max"] = 0.0
     return p
 
 
@@ -253,9 +256,15 @@ class Renderer:
 
     # -- chains --------------------------------------------------------------
     def init_chains(self, **kw):
-        p = default_params(**kw)
-        cp = ChainParams(**p)
+        cp = ChainParams(**default_params(**kw))
         _check(lib().rmlt_init_chains(self.h, C.byref(cp)))
+        self._read_params()
+
+    def _read_params(self):
+        """The parameters in effect (defaults resolved by the library) and the sizes they fix."""
+        cp = ChainParams()
+        _check(lib().rmlt_read_params(self.h, C.byref(cp)))
+        p = {name: getattr(cp, name) for name, _ in ChainParams._fields_}
         self.params = p
         self.D = 2 + 5 * p["max_depth"]
         nx = -(-p["width"] // p["region_px"])
@@ -265,6 +274,26 @@ class Renderer:
 
     def step(self, n_mutations: int):
         _check(lib().rmlt_step(self.h, int(n_mutations)))
+
+    # -- sharded stepping (one epoch at a time around a sum over contexts) ---
+    def exchange_buffers(self):
+        """Two device tensors for rmlt_epoch_mutate / rmlt_epoch_update: the
+        region counts (int64 holding u64 bits) and the per-region sums."""
+        torch = self._torch
+        nc, ns = C.c_int64(), C.c_int64()
+        _check(lib().rmlt_exchange_size(self.h, C.byref(nc), C.byref(ns)))
+        dev = torch.device("cuda", self.device)
+        return (torch.zeros(nc.value, dtype=torch.int64, device=dev),
+                torch.zeros(ns.value, dtype=torch.float64, device=dev))
+
+    def epoch_mutate(self, counts, sums):
+        _check(lib().rmlt_epoch_mutate(self.h, _ptr(counts), _ptr(sums)))
+
+    def epoch_update(self, counts, sums):
+        _check(lib().rmlt_epoch_update(self.h, _ptr(counts), _ptr(sums)))
+
+    def set_wave_limit(self, waves: int = 0):
+        _check(lib().rmlt_set_wave_limit(self.h, int(waves)))
 
     def synchronize(self):
         _check(lib().rmlt_synchronize(self.h))
@@ -392,15 +421,7 @@ class Renderer:
 
     def restore(self, path):
         _check(lib().rmlt_restore(self.h, str(path).encode()))
-        # the checkpoint header: magic[8], abi u32, pad u32, scene hash u64, params
-        raw = Path(path).read_bytes()[24:24 + C.sizeof(ChainParams)]
-        cp = ChainParams.from_buffer_copy(raw)
-        self.params = {name: getattr(cp, name) for name, _ in ChainParams._fields_}
-        self.D = 2 + 5 * self.params["max_depth"]
-        nx = -(-self.params["width"] // self.params["region_px"])
-        ny = -(-self.params["height"] // self.params["region_px"])
-        g = self.params["dir_cells"] if self.params["dir_cells"] > 1 else 1
-        self.m = self.params["qt_max_leaves"] if self.params["partition"] == 1 else nx * ny * g * g
+        self._read_params()
 
 
 def u_to_words(u):

@@ -60,19 +60,22 @@ class _Builder:
         """Quad p0 p1 p2 p3 (counter-clockwise seen from the front side)."""
         self.mesh(np.array([p0, p1, p2, p3]), np.array([[0, 1, 2], [0, 2, 3]]), mat)
 
-    def box(self, lo, hi, mat: int, inward=False):
+    def box(self, lo, hi, mat: int, inward=False, open_faces=()):
+        """Axis-aligned box; `open_faces` names faces left out ("x0", "y1", ...)."""
         x0, y0, z0 = lo
         x1, y1, z1 = hi
         c = [(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0),
              (x0, y0, z1), (x1, y0, z1), (x1, y1, z1), (x0, y1, z1)]
         # outward-facing quads (counter-clockwise seen from outside)
-        faces = [(0, 3, 2, 1),  # z0
-                 (4, 5, 6, 7),  # z1
-                 (0, 4, 7, 3),  # x0
-                 (1, 2, 6, 5),  # x1
-                 (0, 1, 5, 4),  # y0
-                 (3, 7, 6, 2)]  # y1
-        for f in faces:
+        faces = [("z0", (0, 3, 2, 1)),
+                 ("z1", (4, 5, 6, 7)),
+                 ("x0", (0, 4, 7, 3)),
+                 ("x1", (1, 2, 6, 5)),
+                 ("y0", (0, 1, 5, 4)),
+                 ("y1", (3, 7, 6, 2))]
+        for name, f in faces:
+            if name in open_faces:
+                continue
             q = [c[i] for i in f]
             if inward:
                 q = q[::-1]
@@ -272,7 +275,9 @@ def glossy_corridor(n_tris: int = 2_000_000, seed: int = 0) -> dict:
     b.box((18.0, 3.0, s0), (20.0, 3.1, s1), ceil)
     y = 3.4
     b.quad((2.0, y, 0.5), (18.0, y, 0.5), (18.0, y, 2.5), (2.0, y, 2.5), light)  # faces -y
-    b.box((0.0, 3.1, 0.0), (20.0, 3.5, 3.0), ceil, inward=True)  # light box above slit
+    # light box above the slit, open at the bottom: its light reaches the
+    # corridor only through the slit in the ceiling slab below it
+    b.box((0.0, 3.1, 0.0), (20.0, 3.5, 3.0), ceil, inward=True, open_faces=("y0",))
     v, t = _sphere(rng, np.array([10.0, 0.8, 1.5]), 0.8, 96, 48, 0.0)
     b.mesh(v, t, mirror)
     cam = np.array([0.6, 1.6, 1.5])
