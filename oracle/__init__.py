@@ -74,6 +74,10 @@ def lib():
         "or_scene_create": (C.c_void_p, [C.c_int32, f32p, C.c_int32, u32p, u32p, C.c_int32, i32p,
                                          f32p, f32p, f32p, f32p, C.c_int32]),
         "or_scene_create_toy": (C.c_void_p, [f64p]),
+        "or_scene_plant_uniform_lights": (None, [C.c_void_p]),
+        "or_ggx_sample_n": (None, [C.c_double, f64p, f64p, C.c_int64, f64p, f64p, C.c_int32, f64p, f64p, f64p]),
+        "or_ggx_eval_n": (None, [C.c_double, f64p, f64p, C.c_int64, f64p, f64p]),
+        "or_ggx_g1": (C.c_double, [C.c_double, C.c_double]),
         "or_scene_destroy": (None, [C.c_void_p]),
         "or_scene_scale": (C.c_double, [C.c_void_p]),
         "or_closest_hit": (C.c_int32, [C.c_void_p, f64p, f64p, C.c_double, C.c_double, C.c_int32,
@@ -145,6 +149,36 @@ def truncnorm_delta(xmag: int, sigma: float) -> int:
     return int(lib().or_truncnorm_delta(xmag, float(sigma)))
 
 
+def ggx_sample(alpha: float, F0, wo, bu, bv, planted: int = 0):
+    """The path map's GGX continuation in the local frame n = z, for arrays of
+    uniforms (bu, bv): (wi [n,3], weight [n,3], m [n,3])."""
+    bu = np.ascontiguousarray(bu, np.float64).ravel()
+    bv = np.ascontiguousarray(bv, np.float64).ravel()
+    n = len(bu)
+    F0 = np.ascontiguousarray(F0, np.float64)
+    wo = np.ascontiguousarray(wo, np.float64)
+    wi, w, m = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    lib().or_ggx_sample_n(float(alpha), _ptr(F0, C.c_double), _ptr(wo, C.c_double), n, _ptr(bu, C.c_double),
+                          _ptr(bv, C.c_double), int(planted), _ptr(wi, C.c_double), _ptr(w, C.c_double),
+                          _ptr(m, C.c_double))
+    return wi, w, m
+
+
+def ggx_eval(alpha: float, F0, wo, wi) -> np.ndarray:
+    """f_r(wo, wi) [n,3] of one GGX lobe in the local frame n = z."""
+    wi = np.ascontiguousarray(wi, np.float64).reshape(-1, 3)
+    F0 = np.ascontiguousarray(F0, np.float64)
+    wo = np.ascontiguousarray(wo, np.float64)
+    fr = np.zeros_like(wi)
+    lib().or_ggx_eval_n(float(alpha), _ptr(F0, C.c_double), _ptr(wo, C.c_double), len(wi), _ptr(wi, C.c_double),
+                        _ptr(fr, C.c_double))
+    return fr
+
+
+def ggx_g1(cos_theta: float, alpha: float) -> float:
+    return float(lib().or_ggx_g1(float(cos_theta), float(alpha)))
+
+
 class Scene:
     """An oracle scene built from a scene dict (see the package's scenes module)."""
 
@@ -179,6 +213,10 @@ class Scene:
     @property
     def scale(self) -> float:
         return lib().or_scene_scale(self.h)
+
+    def plant_uniform_lights(self):
+        """Tests only: a planted mistake (light triangles chosen uniformly, not by area)."""
+        lib().or_scene_plant_uniform_lights(self.h)
 
     def closest_hit(self, o, d, tmin=0.0, tmax=float("inf"), brute=False, margin=False):
         o = np.ascontiguousarray(o, np.float64)

@@ -346,6 +346,14 @@ void or_scene_destroy(or_scene* s)
 
 double or_scene_scale(const or_scene* s) { return s->scale; }
 
+/* Tests only, a planted mistake: choose the next-event light triangle
+ * uniformly instead of in proportion to its area (the weight still assumes
+ * the area density).  The furnace pins must catch it. */
+void or_scene_plant_uniform_lights(or_scene* s)
+{
+    for (int32_t j = 0; j < s->nl; ++j) s->light_cdf[j] = (double)(j + 1) / (double)s->nl;
+}
+
 /* ------------------------------------------------------------------------ */
 /* ray casting                                                               */
 /* ------------------------------------------------------------------------ */
@@ -554,6 +562,71 @@ static void bsdf_eval(const or_mat* M, const double wo[3], const double wi[3], c
     }
 }
 
+/* GGX continuation at an interaction: the half vector m is drawn with
+ * density D(m) cos(theta_m) (Walter et al. 2007: tan^2 theta_m = a^2 bu /
+ * (1 - bu), phi = 2 pi bv), wi is wo reflected about m, and the throughput
+ * weight is f_r cos(theta_i) / pdf(wi) with pdf(wi) = D(m) cos(theta_m) /
+ * (4 wo.m), i.e. F G (wo.m) / (cos(theta_o) cos(theta_m)).  Returns 0 when
+ * the path ends (m faces away from wo, or wi is below the surface).  m_out
+ * (optional) receives m.  `planted` (tests only): 1 drops the reflection
+ * Jacobian 4 (wo.m) from the weight, a planted mistake the pins must catch. */
+static int ggx_continue(const or_mat* M, const double wo[3], const double ns[3], const double ft[3],
+                        const double fb[3], double bu, double bv, double wi[3], double w[3], double* mloc,
+                        double* m_out, int planted)
+{
+    double a2 = M->rough * M->rough;
+    double tan2 = a2 * bu / (1.0 - bu);
+    double cm = 1.0 / sqrt(1.0 + tan2);
+    double sm = sqrt(dmax(0.0, 1.0 - cm * cm));
+    double phi = 2.0 * OR_PI * bv;
+    double loc[3] = {sm * cos(phi), sm * sin(phi), cm}, mv[3];
+    to_world(loc, ft, fb, ns, mv);
+    if (m_out) for (int a = 0; a < 3; ++a) m_out[a] = mv[a];
+    double dom = v_dot(wo, mv);
+    w[0] = w[1] = w[2] = 0.0;
+    if (dom <= 0) return 0;
+    for (int a = 0; a < 3; ++a) wi[a] = 2.0 * dom * mv[a] - wo[a];
+    double ci = v_dot(wi, ns), co = v_dot(wo, ns);
+    if (mloc) *mloc = dmin(*mloc, 0.01 * dmin(dom, dmin(fabs(ci), co)));
+    if (ci <= 0) return 0;
+    double G = ggx_g1(co, a2) * ggx_g1(ci, a2);
+    double c5 = pow(1.0 - dom, 5.0);
+    for (int a = 0; a < 3; ++a) {
+        double F = M->albedo[a] + (1.0 - M->albedo[a]) * c5;
+        w[a] = planted == 1 ? F * G / (4.0 * co * cm) : F * G * dom / (co * cm);
+    }
+    return 1;
+}
+
+/* test entry points: one GGX lobe in the local frame n = z */
+static void local_material(or_mat* M, double alpha, const double F0[3])
+{
+    memset(M, 0, sizeof *M);
+    M->type = 1;
+    M->rough = alpha;
+    for (int a = 0; a < 3; ++a) M->albedo[a] = F0[a];
+}
+
+void or_ggx_sample_n(double alpha, const double F0[3], const double wo[3], int64_t n, const double* bu,
+                     const double* bv, int32_t planted, double* wi, double* w, double* m)
+{
+    or_mat M;
+    local_material(&M, alpha, F0);
+    const double ns[3] = {0, 0, 1}, ft[3] = {1, 0, 0}, fb[3] = {0, 1, 0};
+    for (int64_t i = 0; i < n; ++i)
+        ggx_continue(&M, wo, ns, ft, fb, bu[i], bv[i], &wi[3 * i], &w[3 * i], NULL, &m[3 * i], planted);
+}
+
+void or_ggx_eval_n(double alpha, const double F0[3], const double wo[3], int64_t n, const double* wi, double* fr)
+{
+    or_mat M;
+    local_material(&M, alpha, F0);
+    const double ns[3] = {0, 0, 1};
+    for (int64_t i = 0; i < n; ++i) bsdf_eval(&M, wo, &wi[3 * i], ns, &fr[3 * i]);
+}
+
+double or_ggx_g1(double cos_theta, double alpha) { return ggx_g1(cos_theta, alpha * alpha); }
+
 static double toy_eval(const double* p, double u0, double u1)
 {
     double f = p[0];
@@ -660,26 +733,9 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
             to_world(loc, ft, fb, ns, wi);
             for (int a = 0; a < 3; ++a) T[a] *= M->albedo[a];
         } else {
-            /* half vector with density D(m) cos(theta_m) (Walter et al. 2007) */
-            double a2 = M->rough * M->rough;
-            double tan2 = a2 * bu / (1.0 - bu);
-            double cm = 1.0 / sqrt(1.0 + tan2);
-            double sm = sqrt(dmax(0.0, 1.0 - cm * cm));
-            double mv[3];
-            loc[0] = sm * cos(phi); loc[1] = sm * sin(phi); loc[2] = cm;
-            to_world(loc, ft, fb, ns, mv);
-            double dom = v_dot(wo, mv);
-            if (dom <= 0) break;
-            for (int a = 0; a < 3; ++a) wi[a] = 2.0 * dom * mv[a] - wo[a];
-            double ci = v_dot(wi, ns), co = v_dot(wo, ns);
-            mloc = dmin(mloc, 0.01 * dmin(dom, dmin(fabs(ci), co)));
-            if (ci <= 0) break;
-            double G = ggx_g1(co, a2) * ggx_g1(ci, a2);
-            double c5 = pow(1.0 - dom, 5.0);
-            for (int a = 0; a < 3; ++a) {
-                double F = M->albedo[a] + (1.0 - M->albedo[a]) * c5;
-                T[a] *= F * G * dom / (co * cm);
-            }
+            double w[3];
+            if (!ggx_continue(M, wo, ns, ft, fb, bu, bv, wi, w, &mloc, NULL, 0)) break;
+            for (int a = 0; a < 3; ++a) T[a] *= w[a];
         }
         for (int a = 0; a < 3; ++a) { o[a] = x[a] + s->eps * ns[a]; d[a] = wi[a]; }
     }

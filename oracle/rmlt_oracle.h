@@ -105,6 +105,21 @@ or_scene* or_scene_create(int32_t nv, const float* verts, int32_t nt, const uint
                           const float* albedo, const float* emission, const float* roughness,
                           const float* camera, int32_t use_bvh);
 or_scene* or_scene_create_toy(const double* params10);
+/* Tests only, a planted mistake: next-event light triangles chosen uniformly
+ * instead of by area. */
+void      or_scene_plant_uniform_lights(or_scene* s);
+
+/* One GGX lobe (roughness alpha, Schlick F0) in the local frame n = (0,0,1),
+ * the code the path map uses, for the BSDF pins.  or_ggx_sample_n: for each
+ * (bu[i], bv[i]) the continuation direction wi, its throughput weight
+ * f_r cos(theta_i) / pdf(wi) (0 where the path ends) and the sampled half
+ * vector m; planted = 1 (tests) drops the reflection Jacobian.
+ * or_ggx_eval_n: f_r(wo, wi) for n directions.  or_ggx_g1: Smith masking. */
+void   or_ggx_sample_n(double alpha, const double F0[3], const double wo[3], int64_t n, const double* bu,
+                       const double* bv, int32_t planted, double* wi, double* w, double* m);
+void   or_ggx_eval_n(double alpha, const double F0[3], const double wo[3], int64_t n, const double* wi,
+                     double* fr);
+double or_ggx_g1(double cos_theta, double alpha);
 void      or_scene_destroy(or_scene* s);
 double    or_scene_scale(const or_scene* s);
 

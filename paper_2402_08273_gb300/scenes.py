@@ -140,6 +140,33 @@ def furnace(rho: float = 0.5, le: float = 1.0) -> dict:
     return b.build(camera=(0.5, 0.5, 0.5, 0.5, 0.5, 1.0, 0.0, 1.0, 0.0, 60.0))
 
 
+def furnace_uneven(rho: float = 0.5, le: float = 1.0, hub=(0.93, 0.9)) -> dict:
+    """The furnace cube of furnace() with every face split into four
+    triangles of very different areas: a fan from an off-centre point `hub`
+    (in the face's own coordinates) to its corners.  The closed form is the
+    same (le * sum_{i<=d} rho^i at every pixel), but next-event estimation
+    is unbiased only if it picks a light triangle in proportion to its area.
+    """
+    b = _Builder()
+    m = b.material(LAMBERT, (rho, rho, rho), (le, le, le))
+    h0, h1 = hub
+    # each face: origin o, in-face axes a1, a2, oriented so that a1 x a2 points into the cube
+    faces = [((0, 0, 0), (0, 0, 1), (1, 0, 0)),   # y = 0, normal +y
+             ((0, 1, 0), (1, 0, 0), (0, 0, 1)),   # y = 1, normal -y
+             ((0, 0, 0), (1, 0, 0), (0, 1, 0)),   # z = 0, normal +z
+             ((0, 0, 1), (0, 1, 0), (1, 0, 0)),   # z = 1, normal -z
+             ((0, 0, 0), (0, 1, 0), (0, 0, 1)),   # x = 0, normal +x
+             ((1, 0, 0), (0, 0, 1), (0, 1, 0))]   # x = 1, normal -x
+    for o, a1, a2 in faces:
+        o, a1, a2 = np.array(o, float), np.array(a1, float), np.array(a2, float)
+        corners = [o, o + a1, o + a1 + a2, o + a2]
+        hubp = o + h0 * a1 + h1 * a2
+        v = np.array([hubp] + corners)
+        t = np.array([[0, 1 + i, 1 + (i + 1) % 4] for i in range(4)])
+        b.mesh(v, t, m)
+    return b.build(camera=(0.5, 0.5, 0.5, 0.5, 0.5, 1.0, 0.0, 1.0, 0.0, 60.0))
+
+
 def _sphere(rng, center, radius, n_seg, n_ring, jitter):
     th = np.linspace(0.0, math.pi, n_ring + 1)
     ph = np.linspace(0.0, 2.0 * math.pi, n_seg, endpoint=False)
