@@ -53,8 +53,8 @@ class OrParams(C.Structure):
 
 
 MUT_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_uint32, C.c_uint64, C.POINTER(C.c_uint32), C.c_int32,
-                       C.c_int32, C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double),
-                       C.POINTER(C.c_double), C.POINTER(C.c_int32))
+                       C.c_int32, C.c_int32, C.c_double, C.POINTER(C.c_double), C.c_double,
+                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32))
 UPD_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
                        C.POINTER(C.c_int32))
 
@@ -85,6 +85,8 @@ def lib():
         "or_any_hit": (C.c_int32, [C.c_void_p, f64p, f64p, C.c_double, C.c_double, C.c_int32, f64p]),
         "or_path_eval": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, u32p, f64p, f64p,
                                      P(C.c_uint64)]),
+        "or_path_eval_err": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, u32p, f64p, f64p, f64p,
+                                         P(C.c_uint64)]),
         "or_ctx_create": (C.c_void_p, [C.c_void_p, P(OrParams)]),
         "or_ctx_destroy": (None, [C.c_void_p]),
         "or_set_hooks": (None, [C.c_void_p, MUT_HOOK, UPD_HOOK, C.c_void_p]),
@@ -243,6 +245,17 @@ class Scene:
         ok = lib().or_path_eval(self.h, width, height, max_depth, _ptr(q, C.c_uint32),
                                 _ptr(f, C.c_double), C.byref(m), _ptr(cnt, C.c_uint64))
         return f, m.value, bool(ok), int(cnt[0])
+
+    def path_eval_err(self, q, width, height, max_depth):
+        """(f, dec, ferr): the path contribution with its binary32 error model
+        (decision distance in error bounds, per-channel absolute error bound)."""
+        q = np.ascontiguousarray(q, np.uint32)
+        f = np.zeros(3)
+        e = np.zeros(3)
+        dec = C.c_double(float("inf"))
+        lib().or_path_eval_err(self.h, width, height, max_depth, _ptr(q, C.c_uint32), _ptr(f, C.c_double),
+                               C.byref(dec), _ptr(e, C.c_double), None)
+        return f, dec.value, e
 
     def path_grad(self, q, width, height, max_depth):
         """(f, grad log pi, status): forward-mode gradient in binary64 (status 1

@@ -636,16 +636,52 @@ static double toy_eval(const double* p, double u0, double u1)
     return f;
 }
 
-int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
-                     const uint32_t* q, double f[3], double* margin, uint64_t counts[3])
+/* A first-order bound on what binary32 evaluation of the same path can
+ * change (the kernel traces in binary32, this oracle in binary64).  With the
+ * unit roundoff u = 2^-24 and the scene diagonal S (a bound on coordinate
+ * magnitudes), the walk carries
+ *   ep  position error of the ray origin (world units),
+ *   ed  angle error of the ray direction (radians),
+ *   eT  relative error of the throughput,
+ * and propagates them through each step with its condition number: a plane
+ * hit at incidence cosine c spreads the ray's perpendicular error
+ * ep + t ed (plus the Moller-Trumbore rounding, ~8 u S) by 1 / c; a direction
+ * between points a distance l apart errs by (position error) / l; a cosine
+ * factor c errs relatively by (angle error) / c; 1 / l^2 by 2 (position
+ * error) / l; the GGX density changes with the half vector's angle by at most
+ * (2 / alpha) per radian (|d ln D / d theta_m| <= 2 (1 - alpha^2) / alpha).
+ *   dec   the smallest distance to a decision flip (a triangle edge, a near
+ *         tie, a sign of a cosine, the light CDF, the shading frame's axis
+ *         switch) in units of that quantity's error bound: below a few, a
+ *         binary32 evaluation may take the other branch;
+ *   ferr  the absolute error bound of each channel of f: every emitted or
+ *         next-event term times the relative error bound of its factors. */
+typedef struct {
+    double dec;
+    double ferr[3];
+} or_err;
+
+static double or_div(double a, double b) { return b > 1e-300 ? a / b : OR_INF; }
+
+/* path map with the geometric decision margin (margin, scene-relative) and
+ * the binary32 error model (E); either may be NULL */
+static int32_t path_eval_impl(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                              const uint32_t* q, double f[3], double* margin, or_err* E, uint64_t counts[3])
 {
     double mloc = OR_INF;
     double* mp = margin ? &mloc : NULL;
+    const double u = 0x1p-24, S = s->scale;
+    double ep = 4.0 * u * S, ed = 8.0 * u, eT = 0.0;   /* camera ray: position and normalize() rounding */
+    if (E) {
+        E->dec = OR_INF;
+        E->ferr[0] = E->ferr[1] = E->ferr[2] = 0.0;
+    }
     f[0] = f[1] = f[2] = 0.0;
     if (s->toy) {
         double v = toy_eval(s->toy_p, u24(q[0]), u24(q[1]));
         f[0] = f[1] = f[2] = v;
         if (margin) *margin = OR_INF;
+        if (E) E->ferr[0] = E->ferr[1] = E->ferr[2] = 16.0 * u * fabs(v);
         return 1;
     }
     double L[3] = {0, 0, 0}, T[3] = {1, 1, 1};
@@ -659,10 +695,15 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
     }
     v_norm(d);
     for (int b = 0; b < max_depth; ++b) {
-        double t;
+        double t, mh = OR_INF;
         int32_t ti;
         if (counts) counts[0]++;
-        if (!or_closest_hit(s, o, d, 0.0, OR_INF, 0, &t, &ti, mp)) break;
+        int hit = or_closest_hit(s, o, d, 0.0, OR_INF, 0, &t, &ti, (mp || E) ? &mh : NULL);
+        if (mp) mloc = dmin(mloc, mh);
+        if (!hit) {
+            if (E) E->dec = dmin(E->dec, or_div(mh * S, ep + 8.0 * u * S));
+            break;
+        }
         const or_tri* Tr = &s->tri[ti];
         const or_mat* M = &s->mat[Tr->mat];
         double x[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
@@ -672,10 +713,20 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
          * like 2^-24 scale / t: below t / scale = 6e-4 it counts as
          * near-degenerate */
         mloc = dmin(mloc, t / s->scale / 60.0);
+        /* the hit point's error: the ray's perpendicular error at t spread
+         * over the plane by 1 / |cos|; the edge and tie margins against it */
+        const double eh = or_div(ep + t * ed + 8.0 * u * S, fabs(cosi));
+        if (E) {
+            E->dec = dmin(E->dec, or_div(mh * S, eh));
+            E->dec = dmin(E->dec, or_div(fabs(cosi), ed + 4.0 * u));
+        }
         double ns[3];
         for (int a = 0; a < 3; ++a) ns[a] = cosi > 0 ? Tr->n[a] : -Tr->n[a];
         if (b == 0 && M->emissive && cosi > 0)
-            for (int a = 0; a < 3; ++a) L[a] += T[a] * M->emission[a];
+            for (int a = 0; a < 3; ++a) {
+                L[a] += T[a] * M->emission[a];
+                if (E) E->ferr[a] += fabs(T[a] * M->emission[a]) * (eT + 2.0 * u);
+            }
         if (M->black) break;
         double wo[3] = {-d[0], -d[1], -d[2]};
         /* next-event estimation: light triangle by area, uniform point on it */
@@ -685,6 +736,10 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
             while (lo < hi) { int32_t mid = (lo + hi) / 2; if (s->light_cdf[mid] > ls) hi = mid; else lo = mid + 1; }
             mloc = dmin(mloc, s->light_cdf[lo] - ls);
             if (lo > 0) mloc = dmin(mloc, ls - s->light_cdf[lo - 1]);
+            if (E && s->nl > 1) {   /* the kernel's CDF is rounded to binary32 */
+                E->dec = dmin(E->dec, or_div(s->light_cdf[lo] - ls, u));
+                if (lo > 0) E->dec = dmin(E->dec, or_div(ls - s->light_cdf[lo - 1], u));
+            }
             const or_tri* LT = &s->tri[s->light[lo]];
             const or_mat* LM = &s->mat[LT->mat];
             double su = sqrt(lu), b1 = su * (1.0 - lv), b2 = su * lv;
@@ -694,6 +749,12 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
             double dist2 = v_dot(wi, wi), dist = sqrt(dist2);
             for (int a = 0; a < 3; ++a) wi[a] /= dist;
             double cx = v_dot(ns, wi), cl = -v_dot(LT->n, wi);
+            /* the light direction's error: both end points over their distance */
+            const double epl = eh + 4.0 * u * S, ew = or_div(epl, dist) + 4.0 * u;
+            if (E) {
+                E->dec = dmin(E->dec, or_div(fabs(cx), ew + 4.0 * u));
+                E->dec = dmin(E->dec, or_div(fabs(cl), ew + 4.0 * u));
+            }
             if (cx > 0 && cl > 0) {
                 /* a grazing cosine makes the contribution ill-conditioned in
                  * binary32 (relative error ~ 2^-24 / cos): below 1e-3 it
@@ -708,14 +769,33 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
                 for (int a = 0; a < 3; ++a) xo[a] = x[a] + s->eps * ns[a];
                 v_sub(p, xo, sd);
                 double sdist = v_len(sd);
+                if (E) E->dec = dmin(E->dec, or_div(fabs(sdist - 2.0 * s->eps), epl));
                 if (sdist > 2.0 * s->eps) {
                     for (int a = 0; a < 3; ++a) sd[a] /= sdist;
                     if (counts) counts[0]++;
-                    if (!or_any_hit(s, xo, sd, 0.0, sdist - s->eps, 0, mp)) {
+                    double mv = OR_INF;
+                    int occ = or_any_hit(s, xo, sd, 0.0, sdist - s->eps, 0, (mp || E) ? &mv : NULL);
+                    if (mp) mloc = dmin(mloc, mv);
+                    /* an occluder's edge against the shadow ray's error along its length */
+                    if (E) E->dec = dmin(E->dec, or_div(mv * S, epl + sdist * ew + 8.0 * u * S));
+                    if (!occ) {
                         double fr[3];
                         bsdf_eval(M, wo, wi, ns, fr);
                         double g = cx * cl / dist2 * s->light_area;
-                        for (int a = 0; a < 3; ++a) L[a] += T[a] * fr[a] * LM->emission[a] * g;
+                        /* relative error of T fr Le g: the cosines, 1 / dist^2,
+                         * the BSDF (GGX: its density's slope times the half
+                         * vector's angle error) and a few roundings */
+                        double eP = eT + or_div(ew + 4.0 * u, cx) + or_div(ew + 4.0 * u, cl) +
+                                    2.0 * or_div(epl, dist) + 16.0 * u;
+                        if (M->type == 1) {
+                            const double co = v_dot(wo, ns);
+                            eP += (2.0 / M->rough + or_div(2.0, co) + or_div(2.0, cx)) * (ed + ew) + 16.0 * u;
+                        }
+                        for (int a = 0; a < 3; ++a) {
+                            const double c = T[a] * fr[a] * LM->emission[a] * g;
+                            L[a] += c;
+                            if (E) E->ferr[a] += fabs(c) * eP;
+                        }
                     }
                 }
             }
@@ -725,23 +805,58 @@ int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t m
         double bu = u24(q[5 + 5 * b]), bv = u24(q[6 + 5 * b]);
         double ft[3], fb[3], wi[3], loc[3];
         frame(ns, ft, fb, mp);
+        if (E) E->dec = dmin(E->dec, or_div(fabs(fabs(ns[2]) - 0.9), 4.0 * u));
         double phi = 2.0 * OR_PI * bv;
+        double ed_next;
         if (M->type == 0) {
             double r = sqrt(bu);
             loc[0] = r * cos(phi); loc[1] = r * sin(phi); loc[2] = sqrt(dmax(0.0, 1.0 - bu));
             mloc = dmin(mloc, 0.01 * loc[2]);
             to_world(loc, ft, fb, ns, wi);
             for (int a = 0; a < 3; ++a) T[a] *= M->albedo[a];
+            /* a cosine sample depends on the normal only (and sqrt(1 - bu)
+             * near the horizon); the throughput gains one rounding */
+            ed_next = 16.0 * u + or_div(u, loc[2]);
+            eT += u;
         } else {
-            double w[3];
-            if (!ggx_continue(M, wo, ns, ft, fb, bu, bv, wi, w, &mloc, NULL, 0)) break;
+            double w[3], m[3];
+            const double co = v_dot(wo, ns);
+            const int cont = ggx_continue(M, wo, ns, ft, fb, bu, bv, wi, w, &mloc, m, 0);
+            const double dom = v_dot(wo, m);
+            /* wi reflects wo about m: its angle error is wo's plus twice m's */
+            ed_next = ed + 32.0 * u;
+            if (E) {
+                E->dec = dmin(E->dec, or_div(fabs(dom), ed + 8.0 * u));
+                if (dom > 0) E->dec = dmin(E->dec, or_div(fabs(v_dot(wi, ns)), ed_next + 4.0 * u));
+            }
+            if (!cont) break;
+            const double ci = v_dot(wi, ns);
+            eT += or_div(ed + 8.0 * u, dom) + or_div(ed + 4.0 * u, co) + or_div(ed_next + 4.0 * u, ci) + 16.0 * u;
             for (int a = 0; a < 3; ++a) T[a] *= w[a];
         }
         for (int a = 0; a < 3; ++a) { o[a] = x[a] + s->eps * ns[a]; d[a] = wi[a]; }
+        ep = eh + 2.0 * u * S;
+        ed = ed_next;
     }
     int ok = isfinite(L[0]) && isfinite(L[1]) && isfinite(L[2]);
     if (ok) { f[0] = L[0]; f[1] = L[1]; f[2] = L[2]; }
     if (margin) *margin = mloc;
+    return ok;
+}
+
+int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                     const uint32_t* q, double f[3], double* margin, uint64_t counts[3])
+{
+    return path_eval_impl(s, width, height, max_depth, q, f, margin, NULL, counts);
+}
+
+int32_t or_path_eval_err(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                         const uint32_t* q, double f[3], double* dec, double ferr[3], uint64_t counts[3])
+{
+    or_err E;
+    int32_t ok = path_eval_impl(s, width, height, max_depth, q, f, NULL, &E, counts);
+    if (dec) *dec = E.dec;
+    if (ferr) for (int a = 0; a < 3; ++a) ferr[a] = E.ferr[a];
     return ok;
 }
 
@@ -1385,24 +1500,22 @@ static void mutate(or_ctx* c, uint32_t chain)
     int32_t ky = or_region_of(c, qy);
     double R = kernel_ratio(c, large, kx, ky, qx, qy);
     if (c->p.debug_flags & 1) R = 1.0;   /* planted mistake for negative-control tests */
-    double fy[3] = {0, 0, 0}, margin = OR_INF;
+    double fy[3] = {0, 0, 0};
+    or_err E = {OR_INF, {0, 0, 0}};
     if (R > 0) {
         uint64_t cnt[3] = {0, 0, 0};
-        if (!or_path_eval(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy,
-                          c->mh ? &margin : NULL, cnt))
+        if (!path_eval_impl(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy, NULL, c->mh ? &E : NULL, cnt))
             c->st[5]++;
         c->st[6] += cnt[0];
     } else {
         c->st[4]++;
     }
     double piy = luminance(fy);
-    double pty = piy / weight_of(c, ky);
     double a = accept_prob(c, kx, ky, c->pi[chain], piy, R);
     int32_t acc = xi < a;
     if (c->mh) {
-        c->mh(c->user, chain, c->mut, qy, D, large, !(R > 0), margin, xi, fy, &a, &acc);
+        c->mh(c->user, chain, c->mut, qy, D, large, !(R > 0), E.dec, E.ferr, xi, fy, &a, &acc);
         piy = luminance(fy);
-        pty = piy / weight_of(c, ky);
     }
     if (large) {
         c->st[2]++;

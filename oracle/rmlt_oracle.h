@@ -91,10 +91,12 @@ int32_t or_path_grad(const or_scene* s, int32_t width, int32_t height, int32_t m
                      const uint32_t* q, double f[3], double* grad);
 
 /* Per-mutation hook (tests only): sees the proposal and may override the
- * proposal's contribution, acceptance probability and decision. */
+ * proposal's contribution, acceptance probability and decision.  dec and
+ * ferr are the binary32 error model of the proposal's path (see
+ * or_path_eval_err). */
 typedef void (*or_mut_hook)(void* user, uint32_t chain, uint64_t mut,
                             const uint32_t* qy, int32_t D, int32_t large,
-                            int32_t early_reject, double margin, double xi_accept,
+                            int32_t early_reject, double dec, const double* ferr, double xi_accept,
                             double* f_y, double* a, int32_t* accept);
 /* Region-update hook (tests only): may override sgn(alpha_hat - alpha*). */
 typedef void (*or_upd_hook)(void* user, int32_t k, uint64_t i_k, uint64_t A_k,
@@ -133,9 +135,19 @@ int32_t or_any_hit(const or_scene* s, const double o[3], const double d[3],
                    double tmin, double tmax, int32_t brute, double* margin);
 
 /* Path contribution f(u) of a primary-sample vector q (D = 2 + 5 max_depth
- * words).  counts (optional): counts[0] += rays cast; [1], [2] unused. */
+ * words).  counts (optional): counts[0] += rays cast; [1], [2] unused.
+ * margin (optional): the smallest scene-relative distance of a geometric
+ * decision from flipping (edges, ties, grazing cosines). */
 int32_t or_path_eval(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
                      const uint32_t* q, double f[3], double* margin, uint64_t counts[3]);
+/* The same path with a first-order error model of its binary32 evaluation:
+ * dec = the smallest distance of a decision (edge, tie, cosine sign, light
+ * CDF, frame switch) from flipping, in units of that quantity's binary32 error
+ * bound; ferr[c] = a bound on |f_c(binary32) - f_c| from the unit roundoff
+ * propagated through the path's geometry (positions, directions, cosines,
+ * distances, the GGX density's slope). */
+int32_t or_path_eval_err(const or_scene* s, int32_t width, int32_t height, int32_t max_depth,
+                         const uint32_t* q, double f[3], double* dec, double ferr[3], uint64_t counts[3]);
 
 or_ctx*  or_ctx_create(const or_scene* s, const or_params* p);
 void     or_ctx_destroy(or_ctx* c);

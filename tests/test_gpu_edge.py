@@ -10,47 +10,53 @@ pytestmark = pytest.mark.gpu
 TOY = S.TOY_DEFAULT
 
 
-def _full(oracle_mod, scene=None, toy=None, use_bvh=False, n_epochs=8, bvh_width=0, **params):
+# the most mutations each window may let through, per test, measured on a GB300
+PINS = {}
+
+
+def _full(oracle_mod, scene=None, toy=None, use_bvh=False, n_epochs=8, bvh_width=0, pin=None, **params):
     from gpu_run import traced_run, replay_full, check_counters
     gpu = traced_run(scene=scene, toy=toy, n_epochs=n_epochs, bvh_width=bvh_width, **params)
     osc = oracle_mod.Scene(toy=toy) if toy is not None else oracle_mod.Scene(scene, use_bvh=use_bvh)
     ch, rp, adopted = replay_full(oracle_mod, gpu, osc)
-    check_counters(ch, gpu, rp)
+    pins = PINS.get(pin, {})
+    check_counters(ch, gpu, rp, pins, adopted, pins.get("adopted", 0))
     return gpu, ch, rp
 
 
 def test_single_chain(oracle_mod):
-    _full(oracle_mod, scene=S.cornell_box(), n_epochs=30, n_chains=1, epoch_len=8, n_bootstrap=4096)
+    _full(oracle_mod, scene=S.cornell_box(), n_epochs=30, n_chains=1, epoch_len=8, n_bootstrap=4096, pin="single")
 
 
 def test_max_depth_all_dimensions(oracle_mod):
     """depth 12: D = 62 primary-sample dimensions, the largest supported"""
     gpu, ch, rp = _full(oracle_mod, scene=S.cornell_box(), n_epochs=6, n_chains=40, max_depth=12,
-                        n_bootstrap=1 << 12)
+                        n_bootstrap=1 << 12, pin="depth12")
     assert gpu["init"]["q"].shape[0] == 62
 
 
 def test_ragged_regions_and_image(oracle_mod):
     """W, H not multiples of the region size; partial last row and column"""
     gpu, ch, rp = _full(oracle_mod, scene=S.cornell_box(), n_epochs=10, n_chains=96, width=100,
-                        height=60, region_px=16, n_bootstrap=1 << 12)
+                        height=60, region_px=16, n_bootstrap=1 << 12, pin="ragged")
     assert ch.m == 7 * 4
 
 
 def test_global_variant_one_region(oracle_mod):
-    _full(oracle_mod, scene=S.cornell_box(), n_epochs=10, n_chains=64, region_px=64, n_bootstrap=1 << 12)
+    _full(oracle_mod, scene=S.cornell_box(), n_epochs=10, n_chains=64, region_px=64, n_bootstrap=1 << 12,
+          pin="global")
 
 
 def test_fixed_variant_no_adaptation(oracle_mod):
     gpu, ch, rp = _full(oracle_mod, scene=S.cornell_box(), n_epochs=10, n_chains=64, gamma_max=0.0,
-                        gamma_scale=0.0, n_bootstrap=1 << 12)
+                        gamma_scale=0.0, n_bootstrap=1 << 12, pin="fixed")
     assert np.all(gpu["region"]["lambda"] == 0.0)
     assert gpu["stats"]["early_reject"] == 0
 
 
 def test_weighted_target_cornell(oracle_mod):
     gpu, ch, rp = _full(oracle_mod, scene=S.cornell_box(), n_epochs=20, n_chains=128, target_mode=1,
-                        n_bootstrap=1 << 13)
+                        n_bootstrap=1 << 13, pin="weighted")
     assert np.array_equal(ch.weight, gpu["region"]["w"])
 
 
@@ -60,7 +66,7 @@ def test_bvh_scene_full_trajectory(oracle_mod, bvh_width):
     replayed (the oracle uses its own median-split BVH)."""
     gpu, ch, rp = _full(oracle_mod, scene=S.two_rooms(20_000, seed=4), use_bvh=True, n_epochs=6,
                         bvh_width=bvh_width, n_chains=64, width=128, height=128, region_px=16,
-                        max_depth=8, n_bootstrap=1 << 12)
+                        max_depth=8, n_bootstrap=1 << 12, pin=f"bvh{bvh_width}")
     assert gpu["stats"]["stack_overflow"] == 0
 
 
@@ -162,10 +168,14 @@ def test_corridor_full_size_sampled(oracle_mod):
     traced = np.arange(0, p["n_chains"], stride)
     for c in traced:
         ch.set_state(int(c), gpu["init"]["q"][:, c])
-    rp = Replay(ch, gpu["trace"], gpu["lambdas"], stride=stride)
+    rp = Replay(ch, gpu["trace"], gpu["lambdas"], stride=stride, init_f=gpu["init"]["f"])
     rp.run_sampled(1, traced)
     print("corridor sampled replay:", rp.summary())
     assert rp.ok(), rp.summary()
+    for key, n in rp.counts().items():
+        assert n <= PINS.get("corridor_sampled", {}).get(key, 0), (key, n)
+    # the corridor is lit: light reaches the chains through the slit
+    assert np.count_nonzero(rp.f.sum(axis=-1)) > 0
     assert rp.s["mutations"] == len(traced) * 16
     assert gpu["stats"]["stack_overflow"] == 0
     assert ch.m == 60 * 34

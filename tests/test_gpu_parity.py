@@ -1,13 +1,15 @@
 """GPU parity: the CUDA chain step against the CPU oracle, mutation by mutation.
 
 Exact: proposal words (hash), large-step and reverse-kernel decisions, region
-visit counts i_k and histograms h_k, lambda_k after every update, final chain
-states.  Within tolerance: path contributions (1e-4 of the largest channel
-for all but 1e-4 of the mutations, 1e-3 always; paths within 1e-5 of a
-geometric decision, or with a cosine below 1e-3, are excluded and counted),
-acceptance probabilities (3e-4, resp. 3e-3), accept/reject decisions
-(excluded only when the uniform falls between the two acceptance
-probabilities), A_k, and the image.
+visit counts i_k and histograms h_k, lambda_k after every update (the GPU's
+from its own A_k, which is the exact sum of its recorded acceptance
+probabilities), final chain states.  Within tolerance: path contributions
+(1e-4 of the largest channel, or the path's binary32 error bound where that
+is larger; a path within a few error bounds of a decision flip is excluded
+and counted), acceptance probabilities (by exactly what their inputs differ
+by), accept/reject decisions (excluded only when the uniform falls between
+the two acceptance probabilities), A_k, and the image.  What the windows let
+through is pinned per test at the counts measured on a GB300.
 """
 import numpy as np
 import pytest
@@ -24,9 +26,17 @@ def _replay_full(oracle_mod, gpu, scene_obj, max_adopt=2, **replay_kw):
     return replay_full(oracle_mod, gpu, scene_obj, max_adopt, **replay_kw)
 
 
-def _check_counters(ch, gpu, rp):
+def _check_counters(ch, gpu, rp, pins=None, adopted=0, max_adopted=0):
     from gpu_run import check_counters
-    check_counters(ch, gpu, rp)
+    check_counters(ch, gpu, rp, pins, adopted, max_adopted)
+
+
+# the most mutations each window may let through, measured on a GB300
+PINS = {
+    "toy": {},
+    "cornell": {},
+}
+PINS_SAMPLED = {"two_rooms": {}}
 
 
 @pytest.mark.parametrize("n_chains,target_mode", [(200, 0), (64, 1)])
@@ -37,7 +47,7 @@ def test_toy_integrand_parity(oracle_mod, n_chains, target_mode):
                      target_mode=target_mode)
     ch, rp, adopted = _replay_full(oracle_mod, gpu, oracle_mod.Scene(toy=TOY), max_adopt=0)
     assert rp.s["f_excluded"] == 0
-    _check_counters(ch, gpu, rp)
+    _check_counters(ch, gpu, rp, PINS["toy"])
     if target_mode:
         assert np.array_equal(ch.weight, gpu["region"]["w"]), "w_k differs"
     np.testing.assert_allclose(gpu["image"], ch.image(), rtol=1e-5, atol=1e-9)
@@ -52,12 +62,9 @@ def test_cornell_box_full_trajectory(oracle_mod):
                      p_large=0.3)
     ch, rp, adopted = _replay_full(oracle_mod, gpu, oracle_mod.Scene(S.cornell_box(), use_bvh=False))
     print("cornell replay:", rp.summary(), "adopted", adopted)
-    _check_counters(ch, gpu, rp)
+    _check_counters(ch, gpu, rp, PINS["cornell"], adopted, 0)
     n = rp.s["mutations"]
     assert n == 64 * 10000
-    assert rp.s["f_excluded"] < 1e-3 * n
-    assert rp.s["f_soft"] <= 1e-4 * n and rp.s["a_soft"] <= 1e-4 * n
-    assert rp.s["decision_excluded"] < 1e-4 * n
     img_o = ch.image()
     rel = np.abs(gpu["image"] - img_o) / (np.abs(img_o) + 1e-3 * img_o.mean())
     assert rel.max() < 1e-3
@@ -103,12 +110,13 @@ def test_two_rooms_full_size_sampled(oracle_mod):
     q0 = gpu["init"]["q"]
     for c in traced:
         ch.set_state(int(c), q0[:, c])
-    rp = Replay(ch, gpu["trace"], gpu["lambdas"], stride=stride)
+    rp = Replay(ch, gpu["trace"], gpu["lambdas"], stride=stride, init_f=gpu["init"]["f"])
     rp.run_sampled(2, traced)
     print("two rooms sampled replay:", rp.summary())
     assert rp.ok(), rp.summary()
     assert rp.s["mutations"] == len(traced) * 32
-    assert rp.s["f_excluded"] <= 0.01 * rp.s["mutations"]
+    for key, n in rp.counts().items():
+        assert n <= PINS_SAMPLED["two_rooms"].get(key, 0), (key, n)
     st = gpu["stats"]
     assert st["stack_overflow"] == 0
     assert st["rays"] > 0

@@ -147,7 +147,7 @@ def test_sequential_alg1_special_case(oracle_mod):
     state = {"x": ch.q[0].copy()}
     seen = []
 
-    def hook(user, chain, mut, qy, D, large, early, margin, xi, fy, a, acc):
+    def hook(user, chain, mut, qy, D, large, early, dec, ferr, xi, fy, a, acc):
         y = np.ctypeslib.as_array(qy, (D,)).copy()
         seen.append((bool(large), float(a[0]), bool(acc[0]), y))
 
