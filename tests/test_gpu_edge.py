@@ -11,7 +11,8 @@ TOY = S.TOY_DEFAULT
 
 
 # the most mutations each window may let through, per test, measured on a GB300
-PINS = {}
+PINS = {"depth12": {"f_bounded": 1}, "global": {"f_bounded": 3}, "fixed": {"f_bounded": 1},
+        "weighted": {"f_bounded": 8}}
 
 
 def _full(oracle_mod, scene=None, toy=None, use_bvh=False, n_epochs=8, bvh_width=0, pin=None, **params):

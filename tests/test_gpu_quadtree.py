@@ -9,17 +9,17 @@ from paper_2402_08273_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 # the most mutations each window may let through, measured on a GB300
-PINS = {}
+PINS = {"toy": {}, "cornell": {"f_bounded": 6}}
 
 QT = dict(partition=1, qt_max_leaves=256, qt_max_depth=6)
 
 
-def _run(oracle_mod, scene=None, toy=None, n_epochs=40, **params):
+def _run(oracle_mod, scene=None, toy=None, n_epochs=40, pin="toy", **params):
     from gpu_run import traced_run, replay_full, check_counters
     gpu = traced_run(scene=scene, toy=toy, n_epochs=n_epochs, **params)
     osc = oracle_mod.Scene(toy=toy) if toy is not None else oracle_mod.Scene(scene, use_bvh=False)
     ch, rp, adopted = replay_full(oracle_mod, gpu, osc)
-    check_counters(ch, gpu, rp, PINS, adopted, PINS.get("adopted", 0))
+    check_counters(ch, gpu, rp, PINS[pin], adopted, 0)
     child_g, leaf_g, depth_g = gpu["quadtree"]
     child_o, leaf_o, depth_o = ch.quadtree()
     assert np.array_equal(child_g, child_o) and np.array_equal(leaf_g, leaf_o)
@@ -35,7 +35,7 @@ def test_quadtree_toy_full_trajectory(oracle_mod):
 
 
 def test_quadtree_cornell_full_trajectory(oracle_mod):
-    gpu, ch = _run(oracle_mod, scene=S.cornell_box(), n_epochs=80, n_chains=64, epoch_len=16,
+    gpu, ch = _run(oracle_mod, scene=S.cornell_box(), n_epochs=80, n_chains=64, epoch_len=16, pin="cornell",
                    n_bootstrap=1 << 14, qt_split=400, qt_refine=64 * 16 * 5, **QT)
     assert gpu["stats"]["n_regions"] > 10
 
