@@ -322,6 +322,23 @@ rmlt_status rmlt_path_grad(rmlt_ctx* ctx, const uint32_t* q, int64_t n, float* f
  * RMLT_E_STATE without the Langevin strategy. */
 rmlt_status rmlt_read_chain_grad(rmlt_ctx* ctx, float* g);
 
+/* Measurement instruments for the traversal roofline.
+ * rmlt_record_paths: the paths of n points q [D][n] (device; D = 2 + 5
+ * max_depth of the chains) evaluated with the chain kernel's own path and
+ * traversal functions.  Every ray cast is written to rays [n][2 max_depth][8]
+ * floats (origin xyz, tmax, direction xyz, 1 for a shadow ray; tmax = -1
+ * marks an unused slot) and what the traversal found and did for it to work
+ * [n][2 max_depth][4] u32 (hit triangle's original index or 0xFFFFFFFF,
+ * distance as float bits, BVH internal nodes visited, triangles tested).
+ * Device outputs, asynchronous on the context's stream.
+ * rmlt_walk_rays_host: the same ray records (host [n][8]) walked on the host
+ * in binary64 through the uploaded BVH, nearest child first: an independent
+ * reference traversal of the same nodes and triangles.  out (host) [n][4]
+ * u32 as for work.  Errors: RMLT_E_STATE (no scene / chains, the toy
+ * integrand), RMLT_E_INVALID_ARG. */
+rmlt_status rmlt_record_paths(rmlt_ctx* ctx, const uint32_t* q, int64_t n, float* rays, uint32_t* work);
+rmlt_status rmlt_walk_rays_host(rmlt_ctx* ctx, const float* rays, int64_t n, uint32_t* out);
+
 /* Count BVH node visits and triangle tests in rmlt_stats (enable = 1), using
  * an instrumented build of the same chain kernel; enable = 0 returns to the
  * uninstrumented kernel.  The chain trajectory does not depend on it. */

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # kernels inlining the same helpers round identically (fused operations are
 # written out as fmaf where wanted)
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O3", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["rmlt_kernels.cu", "rmlt_wavefront.cu", "rmlt_probe.cu", "rmlt_capi.cpp", "bvh_build.cpp"]
+SOURCES = ["rmlt_kernels.cu", "rmlt_wavefront.cu", "rmlt_probe.cu", "rmlt_capi.cpp", "bvh_build.cpp", "bvh_walk.cpp"]
 
 
 def _stale() -> bool:

@@ -78,6 +78,8 @@ struct rmlt_ctx {
     uint64_t held = 0;
 
     bool have_scene = false, have_chains = false, failed = false;
+    std::vector<float4> h_nodes, h_tris;   // host copies of the uploaded BVH nodes and triangles
+    int h_width = 4;
     bool scene_lambert = true;   // every material Lambertian: the path map is differentiable (Langevin strategy)
     DevScene S;
     double tan_half = 1.0;
@@ -415,6 +417,9 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     drop_chains(c);
     c->release(c->scene_mem);
     c->scene_mem = std::move(fresh);
+    c->h_nodes = std::move(bvh.nodes);
+    c->h_tris = std::move(tri4);
+    c->h_width = width;
     c->tan_half = std::tan((double)cam.vfov_deg * 3.14159265358979323846 / 360.0);
     c->S = S;
     uint64_t h = fnv64(tv.data(), tv.size() * sizeof(float), 1469598103934665603ull);
@@ -1070,6 +1075,44 @@ rmlt_status rmlt_path_grad(rmlt_ctx* c, const uint32_t* q, int64_t n, float* f, 
         }
     }
     CK(launch_path_grad(c->S, c->Ch, q, n, f, logpi, grad, c->stream), "rmlt_path_grad");
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_record_paths(rmlt_ctx* c, const uint32_t* q, int64_t n, float* rays, uint32_t* work)
+{
+    rmlt_status st = enter(c);
+    if (st) return st;
+    if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first (it fixes depth and image size)");
+    if (c->S.toy) return fail(RMLT_E_STATE, "the toy integrand casts no rays");
+    if (n < 0 || n > (1ll << 24)) return fail(RMLT_E_INVALID_ARG, "n outside [0, 2^24]");
+    if ((st = check_device_buffer(q, "q")) || (st = check_device_buffer(rays, "rays")) ||
+        (st = check_device_buffer(work, "work")))
+        return st;
+    CK(launch_record_paths(c->S, c->Ch, q, n, rays, work, c->stream), "rmlt_record_paths");
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_walk_rays_host(rmlt_ctx* c, const float* rays, int64_t n, uint32_t* out)
+{
+    if (!c || !rays || !out) return fail(RMLT_E_INVALID_ARG, "null argument");
+    if (!c->have_scene || c->S.toy) return fail(RMLT_E_STATE, "load a scene first");
+    if (n < 0) return fail(RMLT_E_INVALID_ARG, "negative n");
+    const bool brute = c->S.brute != 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float* r = rays + 8 * i;
+        uint32_t* o = out + 4 * i;
+        if (!(r[3] >= 0.0f)) {   // an unused slot
+            o[0] = 0xFFFFFFFFu;
+            o[1] = o[2] = o[3] = 0u;
+            continue;
+        }
+        const WalkResult w = walk_ray(c->h_nodes, c->h_width, c->h_tris, brute, r);
+        const float tf = (float)w.t;
+        o[0] = w.tri >= 0 ? (uint32_t)w.tri : 0xFFFFFFFFu;
+        std::memcpy(&o[1], &tf, 4);
+        o[2] = w.nodes;
+        o[3] = w.tris;
+    }
     return RMLT_OK;
 }
 

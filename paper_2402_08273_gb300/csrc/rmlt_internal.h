@@ -214,6 +214,10 @@ cudaError_t launch_state_gradients(const DevScene& s, const DevChains& c, cudaSt
 cudaError_t launch_path_grad(const DevScene& s, const DevChains& c, const uint32_t* q, long long n, float* f,
                              float* logpi, float* grad, cudaStream_t st);
 cudaError_t launch_region_update(const DevChains& c, bool init_only, cudaStream_t st);
+// the paths of n points q [D][n]: every ray [n][2 max_depth][8] floats and the
+// traversal's work for it [n][2 max_depth][4] u32 (rmlt_record_paths)
+cudaError_t launch_record_paths(const DevScene& s, const DevChains& c, const uint32_t* q, long long n, float* rays,
+                                uint32_t* out, cudaStream_t st);
 cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st);
 cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_boot,
                              const BootScratch& b, cudaStream_t st);
@@ -251,5 +255,16 @@ struct HostBVH {
     int max_depth = 0;
 };
 void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out);
+
+// Reference traversal on the host (bvh_walk.cpp): the uploaded node and
+// triangle arrays walked in binary64, nearest child first, counting the
+// internal nodes visited and the triangles tested for one ray.
+struct WalkResult {
+    int32_t tri;          // original index of the closest (any-hit: first found) triangle, -1 if none
+    double t;
+    uint32_t nodes, tris;
+};
+WalkResult walk_ray(const std::vector<float4>& nodes, int width, const std::vector<float4>& tris, bool brute,
+                    const float ray[8]);
 
 }  // namespace rmlt

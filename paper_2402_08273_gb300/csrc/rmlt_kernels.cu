@@ -389,6 +389,49 @@ __global__ void __launch_bounds__(kChainBlock) path_grad_kernel(const DevScene S
 }
 
 // ---------------------------------------------------------------------------
+// measurement instrument: the paths of n given points, each ray recorded
+// with the chain kernel's traversal work for it (nodes visited, triangles
+// tested), for an independent host traversal to re-count
+// ---------------------------------------------------------------------------
+template <bool BRUTE>
+__global__ void __launch_bounds__(kChainBlock) record_paths_kernel(const DevScene S, const DevChains Ch,
+                                                                   const uint32_t* q, long long n, float* rays,
+                                                                   uint32_t* out)
+{
+    extern __shared__ float4 s_tris[];
+    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    if (BRUTE) stage_triangles(S, s_tris);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int D = Ch.D, R = 2 * Ch.max_depth;
+    uint32_t y[kMaxDim];
+    for (int d = 0; d < D; ++d) y[d] = q[(size_t)d * n + i];
+    Path p;
+    Trav T;
+    uint32_t* stack = thread_stack(s_stack);
+    path_begin(p, S, y);
+    int r = 0;
+    while (!p.done && r < R) {
+        trav_begin(T, p.o, p.d, p.tmax, p.any);
+        unsigned nn = 0, nt = 0;
+        while (!trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        }
+        float* rr = rays + ((size_t)i * R + r) * 8;
+        rr[0] = p.o.x; rr[1] = p.o.y; rr[2] = p.o.z; rr[3] = p.tmax;
+        rr[4] = p.d.x; rr[5] = p.d.y; rr[6] = p.d.z; rr[7] = (float)p.any;
+        uint32_t* oo = out + ((size_t)i * R + r) * 4;
+        oo[0] = T.tri >= 0 ? __float_as_uint(T.tb.w) : 0xFFFFFFFFu;   // the hit's original triangle index
+        oo[1] = __float_as_uint(T.t);
+        oo[2] = nn;
+        oo[3] = nt;
+        ++r;
+        if (T.overflow) break;
+        path_on_hit<BRUTE>(p, S, s_tris, y, Ch.max_depth, Hit{T.t, T.tri, T.ta, T.tb, T.tc});
+    }
+    for (; r < R; ++r) rays[((size_t)i * R + r) * 8 + 3] = -1.0f;   // no ray in this slot
+}
+
+// ---------------------------------------------------------------------------
 // batched epoch: the chains of several contexts (scenes, resolutions, chain
 // counts of any size) in one launch.  Block b runs chains of member
 // block_member[b]; the member's scene and chain tables are copied to shared
@@ -929,6 +972,22 @@ cudaError_t launch_path_grad(const DevScene& s, const DevChains& c, const uint32
         path_grad_kernel<true><<<blocks, kChainBlock, shm, st>>>(s, c, q, n, f, logpi, grad);
     } else {
         path_grad_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c, q, n, f, logpi, grad);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record_paths(const DevScene& s, const DevChains& c, const uint32_t* q, long long n, float* rays,
+                                uint32_t* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    size_t shm = 0;
+    const unsigned blocks = (unsigned)((n + kChainBlock - 1) / kChainBlock);
+    cudaError_t e;
+    if (s.brute) {
+        if ((e = launch_per_point(record_paths_kernel<true>, s, n, st, &shm)) != cudaSuccess) return e;
+        record_paths_kernel<true><<<blocks, kChainBlock, shm, st>>>(s, c, q, n, rays, out);
+    } else {
+        record_paths_kernel<false><<<blocks, kChainBlock, 0, st>>>(s, c, q, n, rays, out);
     }
     return cudaGetLastError();
 }

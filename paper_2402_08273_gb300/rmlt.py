@@ -114,6 +114,8 @@ _SIGS = [
     ("rmlt_batch_step", C.c_int, [C.c_void_p, C.c_uint64]),
     ("rmlt_batch_destroy", None, [C.c_void_p]),
     ("rmlt_set_work_counters", C.c_int, [C.c_void_p, C.c_int]),
+    ("rmlt_record_paths", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    ("rmlt_walk_rays_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("rmlt_set_tuning", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     ("rmlt_set_wavefront", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     ("rmlt_bootstrap_noalloc", C.c_int, [C.c_void_p, _P(ChainParams), C.c_void_p, C.c_void_p,
@@ -396,6 +398,30 @@ class Renderer:
                                         C.c_void_p(f.data_ptr() if f is not None else 0),
                                         C.c_void_p(logpi.data_ptr()), C.c_void_p(grad.data_ptr())))
         return logpi, grad, f
+
+    def record_paths(self, q):
+        """(rays [n, R, 8] float32, work [n, R, 4] uint32) on the host for the
+        paths of points q (a CUDA int32 tensor [D, n]; R = 2 max_depth): every
+        ray the chain kernel's path code casts, and its traversal's result and
+        work (hit triangle, distance bits, nodes visited, triangles tested)."""
+        torch = self._torch
+        q = q.to(torch.int32).contiguous()
+        n = q.shape[1]
+        R = 2 * self.params["max_depth"]
+        rays = torch.empty((n, R, 8), dtype=torch.float32, device=q.device)
+        work = torch.empty((n, R, 4), dtype=torch.int32, device=q.device)
+        _check(lib().rmlt_record_paths(self.h, _ptr(q), n, _ptr(rays), _ptr(work)))
+        self.synchronize()
+        return rays.cpu().numpy(), work.cpu().numpy().view(np.uint32)
+
+    def walk_rays_host(self, rays: np.ndarray) -> np.ndarray:
+        """The reference host traversal of ray records [..., 8] through the
+        uploaded BVH: [..., 4] uint32 (hit triangle, distance bits, nodes, triangles)."""
+        r = np.ascontiguousarray(rays, np.float32)
+        n = r.size // 8
+        out = np.zeros(r.shape[:-1] + (4,), np.uint32)
+        _check(lib().rmlt_walk_rays_host(self.h, _ptr(r), n, _ptr(out)))
+        return out
 
     def set_work_counters(self, enable: bool):
         _check(lib().rmlt_set_work_counters(self.h, int(enable)))

@@ -8,6 +8,10 @@ and unused BVH4 slots hold the empty reference with an inverted infinite box
 (which the traversal relies on to skip them without a test).  Cases: random
 small triangles, triangles with one shared centroid (the builder splits by
 count), long slivers, and a tiny scene; both node widths.
+
+`tests/bvh_walk_check.cpp` checks the reference traversal the bench measures
+the kernel's traversal work against (`csrc/bvh_walk.cpp`): through the
+built BVH it finds the same closest hits as a loop over every triangle.
 """
 import os
 import shutil
@@ -41,3 +45,25 @@ def test_bvh_structure(checker, width, n_tris, mode, seed):
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok ")
+
+
+@pytest.fixture(scope="module")
+def walker(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None or not (CUDA_INC / "cuda_runtime.h").exists():
+        pytest.skip("needs a host C++ compiler and the CUDA headers")
+    exe = tmp_path_factory.mktemp("walk") / "bvh_walk_check"
+    subprocess.run([cxx, "-O2", "-std=c++17", f"-I{CUDA_INC}", f"-I{ROOT / 'include'}", f"-I{CSRC}",
+                    str(ROOT / "tests" / "bvh_walk_check.cpp"), str(CSRC / "bvh_build.cpp"),
+                    str(CSRC / "bvh_walk.cpp"), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    return exe
+
+
+@pytest.mark.parametrize("width", [4, 2])
+@pytest.mark.parametrize("n_tris,seed", [(3000, 1), (40, 2)])
+def test_reference_traversal_matches_brute_force(walker, width, n_tris, seed):
+    r = subprocess.run([str(walker), str(width), str(n_tris), str(seed)], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok ") and int(r.stdout.split()[1]) > (100 if n_tris > 1000 else 0)
