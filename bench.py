@@ -60,7 +60,7 @@ WORKLOADS = {
                      params=dict(n_chains=1 << 20, width=1920, height=1080, region_px=32,
                                  max_depth=12, epoch_len=16, n_bootstrap=1 << 21, p_large=0.3,
                                  seed=1),
-                     mutations=256, cpu_chains=512, cpu_epochs=2, relmse_budget=64),
+                     mutations=256, cpu_chains=512, cpu_epochs=2, relmse_budget=128),
     "two_rooms": dict(desc="two rooms joined by a 5 cm door gap, 200k triangles, 512x512, 16-px "
                            "regions, depth 10, 2^16 chains x 1024 mutations",
                       scene=("two_rooms", dict(n_tris=200_000, seed=0)),

@@ -425,8 +425,9 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* ctx, const rmlt_chain_params* param
  * same kernel body, Philox streams and order of updates); only the launch is
  * shared, so small populations fill the GPU together.  Members must be on
  * one device, have chains, share epoch_len, use a BVH scene (more triangles
- * than brute_force_max), and have neither the trace instrument nor the
- * wavefront form set; large steps are traced in the chain kernel.  The batch
+ * than brute_force_max), not have the wavefront form set, and be unsharded;
+ * large steps are traced in the chain kernel.  A member with the trace
+ * instrument set is traced as by rmlt_step (one-launch mode only).  The batch
  * holds the member handles, not their ownership: destroy the batch before its
  * members.  rmlt_batch_step orders itself after and before each member's
  * stream, so rmlt_read_* on a member sees its result.  Errors:

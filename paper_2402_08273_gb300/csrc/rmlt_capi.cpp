@@ -1440,7 +1440,8 @@ rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
         return fail(RMLT_E_INVALID_ARG, "member %d: batched members need a BVH scene (more than brute_force_max "
                     "triangles)", i);
     if (c->Ch.E != b->m[0]->Ch.E) return fail(RMLT_E_INVALID_ARG, "member %d: epoch_len differs from member 0", i);
-    if (c->tr) return fail(RMLT_E_STATE, "member %d: the trace instrument is set", i);
+    if (c->tr && b->mode != RMLT_BATCH_ONE_LAUNCH)
+        return fail(RMLT_E_STATE, "member %d: the trace instrument needs the one-launch mode", i);
     if (c->wavefront) return fail(RMLT_E_STATE, "member %d: the wavefront form is set", i);
     if (c->Ch.T_mala) return fail(RMLT_E_STATE, "member %d: the Langevin strategy is set", i);
     if (c->Ch.dcells > 1) return fail(RMLT_E_STATE, "member %d: the 4-D partition is set", i);
@@ -1451,12 +1452,12 @@ rmlt_status batch_check_member(const rmlt_batch* b, const rmlt_ctx* c, int i)
 
 // one launch of the chain kernel over every member's blocks, then one launch
 // of every member's region update; replayed once per epoch
-cudaError_t capture_one_launch(rmlt_batch* b, bool count)
+cudaError_t capture_one_launch(rmlt_batch* b, bool count, bool trace)
 {
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t e1 = launch_chain_epoch_batch(b->d_members, b->d_block_member, 0, b->n_blocks, count,
-                                              b->ctas_per_sm, b->stream);
+                                              b->ctas_per_sm, trace, b->stream);
     cudaError_t e2 = launch_region_update_batch(b->d_members, (int)b->m.size(), b->stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->stream, &g);
@@ -1597,6 +1598,14 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
         bm.Ch.lf = nullptr;
         bm.mut0 = c->mut;
         bm.block0 = blocks;
+        if (c->tr) {
+            bm.Ch.trace = c->tr;
+            bm.Ch.trace_cap = c->tr_cap;
+            bm.Ch.trace_stride = c->tr_stride;
+            bm.trace_mut0 = c->mut - c->tr_epoch * (uint64_t)c->Ch.E;
+            bm.tr_lam = c->tr_lam;
+            bm.tr_lam_cap = c->tr_lam_cap;
+        }
         const int nb = (c->Ch.C + kChainBlock - 1) / kChainBlock;
         b->nblk[(size_t)i] = nb;
         table.insert(table.end(), (size_t)nb, i);
@@ -1612,8 +1621,11 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
         b->table_dirty = false;
         b->drop_graph();
     }
-    bool count = false;
-    for (rmlt_ctx* c : b->m) count = count || c->count_work;
+    bool count = false, trace = false;
+    for (rmlt_ctx* c : b->m) {
+        count = count || c->count_work;
+        trace = trace || c->tr != nullptr;
+    }
     const uint64_t E = (uint64_t)b->m[0]->Ch.E;
     const uint64_t n_ep = (n_mutations + E - 1) / E;
     if (n_ep == 0) return RMLT_OK;
@@ -1642,6 +1654,7 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
         key.insert(key.end(), p, p + sizeof k);
     }
     key.push_back(count ? 1 : 0);
+    key.push_back(trace ? 1 : 0);
     key.push_back((unsigned char)b->mode);
     key.push_back((unsigned char)b->ctas_per_sm);
     if (b->mode == RMLT_BATCH_BRANCHES) {
@@ -1659,7 +1672,7 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
     if (!b->exec || key != b->graph_key) {
         b->drop_graph();
         cudaError_t e = b->mode == RMLT_BATCH_BRANCHES ? capture_branches(b, count, n_ep, refine)
-                                                       : capture_one_launch(b, count);
+                                                       : capture_one_launch(b, count, trace);
         if (e != cudaSuccess) {
             b->drop_graph();
             return cuda_fail(e, "batch graph capture");
@@ -1685,6 +1698,7 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
         c->mut += n_ep * E;
         c->epochs += n_ep;
         c->since_refine = since[(size_t)i];
+        if (c->tr) c->tr_epoch += n_ep;
     }
     CK(cudaEventRecord(b->ev, b->stream), "batch event");
     for (rmlt_ctx* c : b->m) CK(cudaStreamWaitEvent(c->stream, b->ev, 0), "batch wait");

@@ -183,10 +183,15 @@ struct BatchMember {
     DevChains Ch;
     unsigned long long mut0 = 0;
     int32_t block0 = 0, pad_ = 0;
+    // trace instrument (Ch.trace set): the mutation index at which tracing
+    // started, and lambda after each epoch's update [epoch][m] (may be null)
+    unsigned long long trace_mut0 = 0;
+    double* tr_lam = nullptr;
+    unsigned long long tr_lam_cap = 0;
 };
 // blocks [block_base, block_base + n_blocks) of the batch's block table
 cudaError_t launch_chain_epoch_batch(const BatchMember* members, const int* block_member, int block_base,
-                                     int n_blocks, bool count_work, int ctas_per_sm, cudaStream_t st);
+                                     int n_blocks, bool count_work, int ctas_per_sm, bool trace, cudaStream_t st);
 // the chain kernel of one member (its scene and chains as launch parameters),
 // reading the epoch's first mutation index from member_dev->mut0
 cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const BatchMember& member, bool count_work,

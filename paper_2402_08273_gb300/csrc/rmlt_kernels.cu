@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kChainBlock) record_paths_kernel(const DevScen
 // block_member[b]; the member's scene and chain tables are copied to shared
 // memory once per block.
 // ---------------------------------------------------------------------------
-template <bool COUNT, int MIN_BLOCKS>
+template <bool COUNT, int MIN_BLOCKS, bool TRACE = false>
 __global__ void __launch_bounds__(kChainBlock, MIN_BLOCKS) chain_epoch_batch_kernel(const BatchMember* members,
                                                                                  const int* block_member,
                                                                                  int block_base)
@@ -452,8 +452,14 @@ __global__ void __launch_bounds__(kChainBlock, MIN_BLOCKS) chain_epoch_batch_ker
         for (int i = threadIdx.x; i < (int)(sizeof(BatchMember) / 4); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    if (TRACE && threadIdx.x == 0 && m.Ch.trace) {
+        // this epoch's records follow the traced epochs before it
+        const unsigned long long n_traced = ((unsigned long long)m.Ch.C + m.Ch.trace_stride - 1) / m.Ch.trace_stride;
+        m.Ch.trace_base = (m.mut0 - m.trace_mut0) * n_traced;
+    }
+    if (TRACE) __syncthreads();
     const int c = (bx - m.block0) * kChainBlock + threadIdx.x;
-    chain_epoch_body<false, false, COUNT>(m.S, m.Ch, m.mut0, c, nullptr, s_stack);
+    chain_epoch_body<false, TRACE, COUNT>(m.S, m.Ch, m.mut0, c, nullptr, s_stack);
 }
 
 // ---------------------------------------------------------------------------
@@ -601,6 +607,14 @@ __global__ void region_update_batch_kernel(BatchMember* members)
     BatchMember* mb = members + blockIdx.x;
     region_update_body(mb->Ch, 0);
     __syncthreads();
+    if (mb->tr_lam) {
+        // trace instrument: lambda after this epoch's update
+        const unsigned long long ep = (mb->mut0 - mb->trace_mut0) / (unsigned long long)mb->Ch.E;
+        const unsigned long long m = (unsigned long long)mb->Ch.m;
+        if ((ep + 1) * m <= mb->tr_lam_cap)
+            for (unsigned long long k = threadIdx.x; k < m; k += blockDim.x) mb->tr_lam[ep * m + k] = mb->Ch.lam[k];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) mb->mut0 += (unsigned long long)mb->Ch.E;
 }
 
@@ -1030,11 +1044,15 @@ cudaError_t launch_large_steps(const DevScene& s, const DevChains& c, uint64_t m
 }
 
 cudaError_t launch_chain_epoch_batch(const BatchMember* members, const int* block_member, int block_base,
-                                     int n_blocks, bool count_work, int ctas_per_sm, cudaStream_t st)
+                                     int n_blocks, bool count_work, int ctas_per_sm, bool trace, cudaStream_t st)
 {
     // 4 resident blocks per SM caps the kernel at 128 registers (a few
     // spills); 3 leaves it unspilled
     const int bb = block_base;
+    if (trace) {   // the trace instrument: one instance, speed does not matter
+        chain_epoch_batch_kernel<false, 3, true><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
+        return cudaGetLastError();
+    }
     if (ctas_per_sm == 3) {
         if (count_work) chain_epoch_batch_kernel<true, 3><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);
         else chain_epoch_batch_kernel<false, 3><<<n_blocks, kChainBlock, 0, st>>>(members, block_member, bb);

@@ -110,3 +110,56 @@ def test_batch_rejects_unsupported_members():
         b.set_order([0, 0])
     b.step(16)
     b.close()
+
+
+# the most mutations each window may let through, measured on a GB300
+PINS_REPLAY = {0: {}, 1: {}}
+
+
+def test_batched_members_replayed_by_the_oracle(oracle_mod):
+    """Two members of one batched launch (a BVH scene on the grid partition and
+    one on the quadtree partition), traced inside the batched kernel and
+    replayed mutation by mutation by the oracle: proposals, decisions, region
+    tables, lambda after every update, the quadtree and final states."""
+    import torch
+    from paper_2402_08273_gb300 import rmlt
+    from gpu_run import check_counters, oracle_params
+    from oracle.replay import Replay, adopt_initial_states
+    scenes = [S.two_rooms(20_000, seed=6), S.two_rooms(20_000, seed=7)]
+    params = [dict(n_chains=96, width=96, height=96, region_px=16, max_depth=6, n_bootstrap=1 << 12, seed=8),
+              dict(n_chains=160, width=64, height=64, region_px=16, max_depth=5, n_bootstrap=1 << 12, seed=9,
+                   partition=1, qt_max_leaves=64, qt_max_depth=4, qt_split=150, qt_refine=160 * 16 * 3)]
+    n_ep = 12
+    Rs, bufs, init = [], [], []
+    for scene, p in zip(scenes, params):
+        R = rmlt.Renderer()
+        R.load_scene(scene)
+        R.init_chains(**p)
+        E = R.params["epoch_len"]
+        rec = torch.zeros(n_ep * p["n_chains"] * E * rmlt.TRACE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        lam = torch.zeros(n_ep * R.m, dtype=torch.float64, device="cuda")
+        R.set_trace(rec, lam, 1)
+        init.append(R.read_chain_state())
+        Rs.append(R)
+        bufs.append((rec, lam))
+    B = rmlt.Batch(Rs)
+    B.set_shape(4, False)
+    B.step(n_ep * 16)
+    torch.cuda.synchronize()
+    for i, (R, scene) in enumerate(zip(Rs, scenes)):
+        p = R.params
+        gpu = {"trace": rmlt.trace_to_numpy(bufs[i][0]).reshape(n_ep, p["n_chains"], p["epoch_len"]),
+               "lambdas": bufs[i][1].cpu().numpy().reshape(n_ep, R.m), "init": init[i],
+               "final": R.read_chain_state(), "hist": R.read_region_hist(), "region": R.read_region_params(),
+               "image_raw": R.read_image(normalized=False)}
+        ch = oracle_mod.Chains(oracle_mod.Scene(scene, use_bvh=True), **oracle_params(p))
+        ch.init()
+        adopted = adopt_initial_states(ch, gpu["init"]["q"], 0)
+        rp = Replay(ch, gpu["trace"], gpu["lambdas"], init_f=gpu["init"]["f"])
+        rp.run_full(n_ep)
+        check_counters(ch, gpu, rp, PINS_REPLAY[i], adopted, 0)
+        if p["partition"] == 1:
+            for a, b in zip(R.read_quadtree(), ch.quadtree()):
+                assert np.array_equal(a, b), "quadtree differs"
+            assert R.read_stats()["n_regions"] > 1
+    B.close()

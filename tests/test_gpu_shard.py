@@ -107,7 +107,8 @@ def test_unsharded_epoch_calls_equal_step():
     for key in ("h", "i", "A", "n", "lam"):
         assert np.array_equal(ta[key], tb[key]), key
     assert np.array_equal(ta["st"]["q"], tb["st"]["q"])
-    assert np.array_equal(ta["img"], tb["img"])
+    # binary64 splat atomics add in any order
+    np.testing.assert_allclose(ta["img"], tb["img"], rtol=1e-12, atol=1e-300)
 
 
 def test_sharded_context_call_order():
