@@ -118,7 +118,7 @@ typedef struct {
      * scaled to norm <= mala_drift_max, xi standard normal; the acceptance
      * carries the ratio of the state-dependent proposal densities.  Its moves
      * do not feed the adaptation statistics.  Needs a Lambertian scene (or the
-     * toy integrand), the chain kernel, and no trace instrument.  0 = off. */
+     * toy integrand) and the chain kernel.  0 = off. */
     double p_mala, mala_tau, mala_drift_max;
     /* small-step kernel: RMLT_KERNEL_KELEMEN (log-uniform offsets on
      * [sigma s1, sigma s2], random sign) or RMLT_KERNEL_TRUNCNORM (the
@@ -173,7 +173,7 @@ typedef struct {
     float f[3];                /* contribution of the proposal y (0 if rejected early) */
     float a;                   /* acceptance probability */
     uint32_t qhash;            /* FNV-1a of the proposal's D words */
-    uint32_t flags;            /* bit 0 accepted, 1 large step, 2 early reject, 3 invalid */
+    uint32_t flags;            /* bit 0 accepted, 1 large step, 2 early reject, 3 invalid, 4 Langevin move */
 } rmlt_trace_record;
 
 typedef void* (*rmlt_alloc_fn)(void* user, size_t bytes, void* stream);
@@ -301,6 +301,12 @@ rmlt_status rmlt_read_params(rmlt_ctx* ctx, rmlt_chain_params* out);
  * record stores enabled. */
 rmlt_status rmlt_set_trace(rmlt_ctx* ctx, rmlt_trace_record* records, uint64_t capacity,
                            double* lambdas, uint64_t lambda_capacity, uint32_t chain_stride);
+/* Test instrument, with rmlt_set_trace: each record's D proposal words y (u32)
+ * are also written to words[record][D] (device memory, capacity_words >=
+ * capacity x D), so that a replay can adopt proposals whose last bits depend
+ * on binary32 rounding (truncated-normal offsets, Langevin moves).
+ * rmlt_set_trace clears it; words = NULL switches it off. */
+rmlt_status rmlt_set_trace_words(rmlt_ctx* ctx, uint32_t* words, uint64_t capacity_words);
 
 /* Gradient of log pi(u), pi = l(f(u)), at n points: q [D][n] u32 primary-
  * sample words (u = q 2^-32, D = 2 + 5 max_depth of the chains, 2 for the toy

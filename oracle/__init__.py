@@ -57,6 +57,7 @@ MUT_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_uint32, C.c_uint64, C.POINTER(C.c_u
                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32))
 UPD_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_int32, C.c_uint64, C.c_uint64, C.c_double,
                        C.POINTER(C.c_int32))
+PROP_HOOK = C.CFUNCTYPE(None, C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.POINTER(C.c_uint32), C.c_int32)
 
 
 def lib():
@@ -90,6 +91,8 @@ def lib():
         "or_ctx_create": (C.c_void_p, [C.c_void_p, P(OrParams)]),
         "or_ctx_destroy": (None, [C.c_void_p]),
         "or_set_hooks": (None, [C.c_void_p, MUT_HOOK, UPD_HOOK, C.c_void_p]),
+        "or_set_prop_hook": (None, [C.c_void_p, PROP_HOOK]),
+        "or_last_mala": (None, [C.c_void_p, f64p, f64p, f64p]),
         "or_init": (C.c_int32, [C.c_void_p]),
         "or_init_tables": (C.c_int32, [C.c_void_p]),
         "or_refresh_sigma": (None, [C.c_void_p]),
@@ -360,11 +363,21 @@ class Chains:
         if lib().or_epoch_update(self.h, _ptr(counts, C.c_uint64), _ptr(sums, C.c_double)) != 0:
             raise RuntimeError("or_epoch_update: or_epoch_mutate first")
 
-    def set_hooks(self, mut_fn=None, upd_fn=None):
+    def set_hooks(self, mut_fn=None, upd_fn=None, prop_fn=None):
         mh = MUT_HOOK(mut_fn) if mut_fn else MUT_HOOK()
         uh = UPD_HOOK(upd_fn) if upd_fn else UPD_HOOK()
-        self._hooks = (mh, uh)
+        ph = PROP_HOOK(prop_fn) if prop_fn else PROP_HOOK()
+        self._hooks = (mh, uh, ph)
         lib().or_set_hooks(self.h, mh, uh, None)
+        lib().or_set_prop_hook(self.h, ph)
+
+    def last_mala(self):
+        """(m_x [D], z [D], tau_x, S) of the last Langevin move (see or_last_mala)."""
+        m = np.zeros(max(self.D, 1))
+        z = np.zeros(max(self.D, 1))
+        o = np.zeros(2)
+        lib().or_last_mala(self.h, _ptr(m, C.c_double), _ptr(z, C.c_double), _ptr(o, C.c_double))
+        return m[:self.D], z[:self.D], float(o[0]), float(o[1])
 
     def image(self) -> np.ndarray:
         out = np.zeros((self.params.height, self.params.width, 3))

@@ -25,6 +25,13 @@ from the failures it removes:
 * the decision: exact, except when the uniform lies between the two
   acceptance probabilities (counted as `decision_excluded`; the oracle follows
   the GPU);
+* proposals whose last bits depend on binary32 rounding (the truncated-normal
+  kernel's erfinv offsets, Langevin moves) are adopted from the GPU's
+  recorded words (`words`) when they lie within the first-order bound of that
+  rounding around the oracle's own proposal (counted as `proposal_adopted`;
+  beyond it, `proposal_mismatch`); the Langevin acceptance may further differ
+  by what a relative error `EPS_G` of the drifts (the adjoint's gradient
+  against the oracle's) changes in it, ln a +- EPS_G S (S from the oracle);
 * the region update (Alg. 1 lines 13-18): with every chain traced, the GPU's
   A_k is rebuilt exactly from its own recorded acceptance probabilities
   (sum of round(a 2^32) over the small steps of region k), and the GPU's
@@ -40,6 +47,10 @@ import numpy as np
 
 FNV_OFF, FNV_PRIME = 2166136261, 16777619
 U = 2.0 ** -24
+# relative accuracy assumed for the adjoint kernel's gradient against the
+# oracle's forward-mode gradient: twice the largest relative difference
+# measured on 4096 Cornell-box paths at depth 10 (5.3e-4)
+EPS_G = 1e-3
 
 
 def fnv32(words, n: int) -> int:
@@ -64,9 +75,11 @@ def _log_ratio(a: float, b: float) -> float:
 class Replay:
     def __init__(self, chains, trace: np.ndarray, lambdas: np.ndarray | None, stride: int = 1,
                  init_f: np.ndarray | None = None, f_rtol: float = 1e-4, err_factor: float = 4.0,
-                 dec_thr: float = 4.0, epoch0: int = 0, max_fail_log: int = 20):
+                 dec_thr: float = 4.0, epoch0: int = 0, max_fail_log: int = 20, words: np.ndarray | None = None):
         """init_f: the GPU's contributions of the chains' states when the
-        replay starts ([3][C] floats), for the acceptance check."""
+        replay starts ([3][C] floats), for the acceptance check.  words: the
+        GPU's proposal words of every record ([epoch][traced chain][mutation][D]
+        u32) for the proposals the replay adopts."""
         self.ch = chains
         self.E = chains.params.epoch_len
         self.stride = stride
@@ -90,21 +103,67 @@ class Replay:
         cap = int(chains.exchange_buffers()[1].shape[0])
         self.A_g = np.zeros(cap, dtype=object)
         self.i_g = np.zeros(cap, dtype=np.int64)
+        self.words = words
         self.s = dict(mutations=0, q_mismatch=0, large_mismatch=0, early_mismatch=0, f_mismatch=0,
                       f_bounded=0, f_excluded=0, a_mismatch=0, decision_mismatch=0, decision_excluded=0,
-                      update_mismatch=0, update_excluded=0, lambda_mismatch=0, visits_mismatch=0, updates=0)
+                      update_mismatch=0, update_excluded=0, lambda_mismatch=0, visits_mismatch=0, updates=0,
+                      proposal_adopted=0, proposal_mismatch=0, langevin=0, kind_mismatch=0)
+        self.prop_use = 0.0      # largest proposal difference as a fraction of its bound
         self.f_max_rel = 0.0
         self.a_max_rel = 0.0
         self.bound_use = 0.0     # largest f error as a fraction of its allowed bound
         self.failures: list[str] = []
         assert len(self.px_o) == C
-        chains.set_hooks(self._mut, self._upd)
+        chains.set_hooks(self._mut, self._upd, self._prop if words is not None else None)
 
     def _fail(self, msg):
         if len(self.failures) < self.max_fail_log:
             self.failures.append(msg)
 
     # ---------------------------------------------------------------- hooks
+    def _prop(self, user, chain, mut, kind, qy, D):
+        """Adopt the GPU's proposal where binary32 rounding decides its last
+        bits, after checking it against the oracle's own within that rounding's
+        first-order bound (in units of 2^-32 per dimension)."""
+        if chain % self.stride:
+            return
+        e = mut // self.E - self.epoch0
+        j = mut % self.E
+        t = chain // self.stride
+        g = self.words[e, t, j, :D].astype(np.int64)
+        own = np.ctypeslib.as_array(qy, (D,)).astype(np.int64)
+        truncnorm = kind == 0 and self.ch.params.kernel == 1
+        if not (truncnorm or kind == 2):
+            return                      # Philox words and Kelemen offsets are exact: compared by the hash
+        qx = self.ch.q[chain].astype(np.int64)
+        off_o = ((own - qx + 2 ** 31) % 2 ** 32) - 2 ** 31
+        off_g = ((g - qx + 2 ** 31) % 2 ** 32) - 2 ** 31
+        if truncnorm:
+            # dl = sigma sqrt(2) erfinv(x), x = (2u - 1) Z(sigma): binary32 x errs by
+            # ~6 u |x|, erfinv amplifies it by (sqrt(pi) / 2) exp(y^2), the rest ~6 u |y|
+            sigma = float(self.ch.sigma[int(self.ch.k[chain])])
+            y = off_o * 2.0 ** -32 / (sigma * math.sqrt(2.0))
+            x = np.array([math.erf(v) for v in y])
+            amp = np.exp(np.minimum(y * y, 700.0))
+            tol = 4.0 * (2.0 ** 32 * sigma * math.sqrt(2.0) * (0.5 * math.sqrt(math.pi) * amp * 6 * U * np.abs(x)
+                                                                 + 6 * U * np.abs(y))) + 2.0
+        else:
+            # step = m + sqrt(tau) z: the drift errs by EPS_G |m| (gradient), the
+            # Box-Muller normals by ~8 u |z|, the sum by ~4 u |step|
+            m, z, tau, _ = self.ch.last_mala()
+            step = m + math.sqrt(tau) * z
+            tol = 4.0 * 2.0 ** 32 * (EPS_G * np.abs(m) + math.sqrt(tau) * 8 * U * np.abs(z) + 4 * U * np.abs(step)) + 2.0
+        diff = np.abs(off_g - off_o)
+        self.prop_use = max(self.prop_use, float(np.max(diff / tol)))
+        if np.all(diff <= tol):
+            self.s["proposal_adopted"] += 1
+        else:
+            self.s["proposal_mismatch"] += 1
+            d = int(np.argmax(diff / tol))
+            self._fail(f"chain {chain} mut {mut}: proposal word {d} oracle {int(own[d])} gpu {int(g[d])} "
+                       f"(allowed {tol[d]:.3g})")
+        np.ctypeslib.as_array(qy, (D,))[:] = self.words[e, t, j, :D]
+
     def _mut(self, user, chain, mut, qy, D, large, early, dec, ferr, xi, fy, a, acc):
         e = mut // self.E - self.epoch0
         j = mut % self.E
@@ -117,6 +176,13 @@ class Replay:
         if fnv32(qy, D) != int(self.qh[e, t, j]):
             s["q_mismatch"] += 1
             self._fail(f"chain {chain} mut {mut}: proposal hash differs")
+        langevin = large == 2
+        if bool(flags & 16) != langevin:
+            s["kind_mismatch"] += 1
+            self._fail(f"chain {chain} mut {mut}: Langevin flag differs")
+        if langevin:
+            s["langevin"] += 1
+            large = 0
         if bool(flags & 2) != bool(large):
             s["large_mismatch"] += 1
             self._fail(f"chain {chain} mut {mut}: large-step flag differs")
@@ -152,6 +218,10 @@ class Replay:
         # the two sides' inputs: pi of the proposal and of the current state
         py_o, py_g = lum((fy[0], fy[1], fy[2])), lum(fg)
         pred = _log_ratio(py_g, py_o) + _log_ratio(self.px_g[chain], self.px_o[chain]) + 32 * U
+        if langevin:
+            pred += EPS_G * self.ch.last_mala()[3] + 64 * U * D
+        elif self.ch.params.kernel == 1 and not large:
+            pred += 8 * U * D          # the truncated normal's Z(sigma) in binary32 (erff), D times
         da = abs(ao - ag)
         amax = max(ao, ag)
         if amax > 0:
@@ -167,7 +237,7 @@ class Replay:
                 s["decision_mismatch"] += 1
                 self._fail(f"chain {chain} mut {mut}: decision oracle {go} gpu {gg} xi {xi} a {ao}/{ag}")
             acc[0] = int(gg)
-        if not large:
+        if not large and not langevin:
             # the GPU adds round(a 2^32) of its binary32 a to A_{k(x)} (small steps)
             self.A_g[kx] += int(np.rint(np.float64(np.float32(ag)) * 4294967296.0))
             self.i_g[kx] += 1
@@ -275,15 +345,19 @@ class Replay:
         s = self.s
         return not (s["q_mismatch"] or s["large_mismatch"] or s["early_mismatch"] or s["f_mismatch"]
                     or s["a_mismatch"] or s["decision_mismatch"] or s["update_mismatch"]
-                    or s["lambda_mismatch"] or s["visits_mismatch"])
+                    or s["lambda_mismatch"] or s["visits_mismatch"] or s["proposal_mismatch"]
+                    or s["kind_mismatch"])
 
     def counts(self) -> dict:
         """What the windows let through, for the pinned ceilings of each test."""
         return {k: self.s[k] for k in ("f_bounded", "f_excluded", "decision_excluded", "update_excluded")}
 
+    def ok_proposals(self) -> bool:
+        return not (self.s["proposal_mismatch"] or self.s["kind_mismatch"])
+
     def summary(self) -> str:
         return (f"{self.s} f_max_rel={self.f_max_rel:.3g} a_max_rel={self.a_max_rel:.3g} "
-                f"bound_use={self.bound_use:.3g} failures={self.failures[:5]}")
+                f"bound_use={self.bound_use:.3g} prop_use={self.prop_use:.3g} failures={self.failures[:5]}")
 
 
 def adopt_initial_states(chains, q_gpu: np.ndarray, max_adopt: int) -> int:

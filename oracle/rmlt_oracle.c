@@ -1084,6 +1084,9 @@ struct or_ctx {
     int inited;
     or_mut_hook mh;
     or_upd_hook uh;
+    or_prop_hook ph;
+    /* the last Langevin move (tests): drift, normal draws, tau_x, sensitivity */
+    double lm_m[OR_MAX_GRAD], lm_z[OR_MAX_GRAD], lm_tau, lm_sens;
     void* user;
 };
 
@@ -1182,6 +1185,17 @@ void or_ctx_destroy(or_ctx* c)
 void or_set_hooks(or_ctx* c, or_mut_hook mh, or_upd_hook uh, void* user)
 {
     c->mh = mh; c->uh = uh; c->user = user;
+}
+
+void or_set_prop_hook(or_ctx* c, or_prop_hook ph) { c->ph = ph; }
+
+void or_last_mala(const or_ctx* c, double* m, double* z, double out2[2])
+{
+    for (int32_t d = 0; d < c->D && d < OR_MAX_GRAD; ++d) {
+        if (m) m[d] = c->lm_m[d];
+        if (z) z[d] = c->lm_z[d];
+    }
+    if (out2) { out2[0] = c->lm_tau; out2[1] = c->lm_sens; }
 }
 
 static void pixel_of(const or_ctx* c, const uint32_t* q, int32_t* px, int32_t* py)
@@ -1438,8 +1452,12 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
         double step = mx[d] + st * z[d];
         int64_t dq = (int64_t)llrint(step * 4294967296.0);
         qy[d] = qx[d] + (uint32_t)(uint64_t)dq;
-        delta[d] = (double)(int32_t)(qy[d] - qx[d]) * (1.0 / 4294967296.0);
+        c->lm_m[d] = mx[d];
+        c->lm_z[d] = z[d];
     }
+    c->lm_tau = tx;
+    if (c->ph) c->ph(c->user, chain, c->mut, 2, qy, D);
+    for (int32_t d = 0; d < D; ++d) delta[d] = (double)(int32_t)(qy[d] - qx[d]) * (1.0 / 4294967296.0);
     int32_t ky = or_region_of(c, qy);
     double fy[3];
     if (or_path_grad(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy, gy) != 1) {
@@ -1449,6 +1467,9 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
     }
     const double ty = dmin(c->p.mala_tau * (double)c->sig[ky] * (double)c->sig[ky], OR_MALA_TAU_MAX);
     mala_drift(c, gy, ty, my);
+    c->lm_sens = 0.0;
+    for (int32_t d = 0; d < D; ++d)
+        c->lm_sens += fabs(mx[d]) * fabs(delta[d] - mx[d]) / tx + fabs(my[d]) * fabs(delta[d] + my[d]) / ty;
     double piy = luminance(fy);
     double ptx = c->pi[chain] / weight_of(c, kx), pty = piy / weight_of(c, ky);
     double a;
@@ -1466,6 +1487,15 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
         a = lr >= 0 ? 1.0 : exp(lr);
     }
     int32_t acc = xi < a;
+    if (c->mh) {
+        /* the test hook sees a Langevin move as kind 2, with the path's
+         * binary32 error model */
+        or_err E;
+        double fe[3];
+        path_eval_impl(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fe, NULL, &E, NULL);
+        c->mh(c->user, chain, c->mut, qy, D, 2, 0, E.dec, E.ferr, xi, fy, &a, &acc);
+        piy = luminance(fy);
+    }
     c->mala_st[0]++;
     if (acc) {
         memcpy(qx, qy, sizeof(uint32_t) * (size_t)D);
@@ -1497,6 +1527,7 @@ static void mutate(or_ctx* c, uint32_t chain)
     int32_t kx = c->k[chain];
     if (large) large_step(c, chain, c->mut, qy);
     else small_step(c, chain, c->mut, kx, qx, qy);
+    if (c->ph) c->ph(c->user, chain, c->mut, large, qy, D);
     int32_t ky = or_region_of(c, qy);
     double R = kernel_ratio(c, large, kx, ky, qx, qy);
     if (c->p.debug_flags & 1) R = 1.0;   /* planted mistake for negative-control tests */

@@ -98,6 +98,11 @@ typedef void (*or_mut_hook)(void* user, uint32_t chain, uint64_t mut,
                             const uint32_t* qy, int32_t D, int32_t large,
                             int32_t early_reject, double dec, const double* ferr, double xi_accept,
                             double* f_y, double* a, int32_t* accept);
+/* Proposal hook (tests only): sees each proposal qy right after it is drawn
+ * (kind 0 small step, 1 large step, 2 Langevin move) and may replace its
+ * words; everything after (regions, kernel ratio, path, acceptance) uses the
+ * words it leaves. */
+typedef void (*or_prop_hook)(void* user, uint32_t chain, uint64_t mut, int32_t kind, uint32_t* qy, int32_t D);
 /* Region-update hook (tests only): may override sgn(alpha_hat - alpha*). */
 typedef void (*or_upd_hook)(void* user, int32_t k, uint64_t i_k, uint64_t A_k,
                             double alpha_hat, int32_t* sign);
@@ -152,6 +157,12 @@ int32_t or_path_eval_err(const or_scene* s, int32_t width, int32_t height, int32
 or_ctx*  or_ctx_create(const or_scene* s, const or_params* p);
 void     or_ctx_destroy(or_ctx* c);
 void     or_set_hooks(or_ctx* c, or_mut_hook mh, or_upd_hook uh, void* user);
+void     or_set_prop_hook(or_ctx* c, or_prop_hook ph);
+/* The last Langevin move's terms (tests): its drift m_x [D] and standard
+ * normal draws z [D] (as drawn, before a proposal hook), and out2 = {tau_x,
+ * S} with S = sum_d |m_x,d| |delta_d - m_x,d| / tau_x + |m_y,d| |delta_d +
+ * m_y,d| / tau_y, the sensitivity of ln a to relative errors of the drifts. */
+void     or_last_mala(const or_ctx* c, double* m, double* z, double out2[2]);
 int32_t  or_init(or_ctx* c);                       /* bootstrap + initial states */
 int32_t  or_init_tables(or_ctx* c);                /* region tables only (Alg. 1 lines 2-6) */
 void     or_refresh_sigma(or_ctx* c);              /* sigma_k from the current lambda_k */

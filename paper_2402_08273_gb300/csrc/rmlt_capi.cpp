@@ -94,6 +94,7 @@ struct rmlt_ctx {
 
     rmlt_trace_record* tr = nullptr;
     uint64_t tr_cap = 0, tr_epoch = 0;
+    uint32_t* tr_words = nullptr;    // the proposal words of each record (optional)
     double* tr_lam = nullptr;
     uint64_t tr_lam_cap = 0;
     uint32_t tr_stride = 1;
@@ -723,6 +724,7 @@ static rmlt_status epoch_kernels(rmlt_ctx* c)
         Ch.trace_cap = c->tr_cap;
         Ch.trace_stride = c->tr_stride;
         Ch.trace_base = c->tr_epoch * (unsigned long long)n_traced * E;
+        Ch.trace_words = c->tr_words;
     }
     const DevScene& S = c->S;
     rmlt_status st;
@@ -785,8 +787,8 @@ static rmlt_status check_steppable(rmlt_ctx* c)
 {
     if (!c->have_chains) return fail(RMLT_E_STATE, "rmlt_init_chains first");
     if (c->failed) return fail(RMLT_E_STATE, "context failed earlier: %s", g_err.c_str());
-    if (c->Ch.T_mala && (c->wavefront || c->tr))
-        return fail(RMLT_E_STATE, "the Langevin strategy runs in the chain kernel without the trace instrument");
+    if (c->Ch.T_mala && c->wavefront)
+        return fail(RMLT_E_STATE, "the Langevin strategy runs in the chain kernel");
     return RMLT_OK;
 }
 
@@ -877,6 +879,22 @@ rmlt_status rmlt_set_trace(rmlt_ctx* c, rmlt_trace_record* records, uint64_t cap
     c->tr_lam_cap = records ? lambda_capacity : 0;
     c->tr_stride = records ? chain_stride : 1;
     c->tr_epoch = 0;
+    c->tr_words = nullptr;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_trace_words(rmlt_ctx* c, uint32_t* words, uint64_t capacity_words)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (!words) {
+        c->tr_words = nullptr;
+        return RMLT_OK;
+    }
+    if (!c->tr || !c->have_chains) return fail(RMLT_E_STATE, "set the trace instrument (rmlt_set_trace) first");
+    if (capacity_words < c->tr_cap * (uint64_t)c->Ch.D)
+        return fail(RMLT_E_INVALID_ARG, "room for %llu words needed (capacity x D)",
+                    (unsigned long long)(c->tr_cap * (uint64_t)c->Ch.D));
+    c->tr_words = words;
     return RMLT_OK;
 }
 
@@ -1602,6 +1620,7 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
             bm.Ch.trace = c->tr;
             bm.Ch.trace_cap = c->tr_cap;
             bm.Ch.trace_stride = c->tr_stride;
+            bm.Ch.trace_words = c->tr_words;
             bm.trace_mut0 = c->mut - c->tr_epoch * (uint64_t)c->Ch.E;
             bm.tr_lam = c->tr_lam;
             bm.tr_lam_cap = c->tr_lam_cap;

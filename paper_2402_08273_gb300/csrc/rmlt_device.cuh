@@ -1121,8 +1121,11 @@ __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool
             r.f[2] = fy.z;
             r.a = a;
             r.qhash = hsh;
-            r.flags = (uint32_t)accept | ((uint32_t)L.large << 1) | ((uint32_t)L.early << 2) | ((uint32_t)invalid << 3);
+            r.flags = (uint32_t)accept | ((uint32_t)L.large << 1) | ((uint32_t)L.early << 2) | ((uint32_t)invalid << 3) |
+                      ((uint32_t)(MALA && L.mala) << 4);
             Ch.trace[idx] = r;
+            if (Ch.trace_words)
+                for (int d = 0; d < D; ++d) Ch.trace_words[idx * (unsigned long long)D + d] = y[d];
         }
     }
     if (accept) {

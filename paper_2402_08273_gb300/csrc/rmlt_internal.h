@@ -128,6 +128,7 @@ struct DevChains {
     rmlt_trace_record* trace = nullptr;
     unsigned long long trace_cap = 0, trace_base = 0;
     uint32_t trace_stride = 1;
+    uint32_t* trace_words = nullptr;   // optional: the D proposal words of each record, [record][D]
 };
 
 // Wavefront form of the chain epoch (rmlt_wavefront.cu).  Per chain, a

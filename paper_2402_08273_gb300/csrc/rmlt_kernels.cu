@@ -934,12 +934,12 @@ cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const Batch
 }
 
 template <bool B>
-static cudaError_t launch_mala_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, cudaStream_t st)
+static cudaError_t launch_mala_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace, cudaStream_t st)
 {
     constexpr int nt = epoch_block<B>();
     const int blocks = (c.C + nt - 1) / nt;
     const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
-    auto kern = chain_epoch_kernel<B, false, false, true>;
+    auto kern = trace ? chain_epoch_kernel<B, true, false, true> : chain_epoch_kernel<B, false, false, true>;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
@@ -1009,7 +1009,8 @@ cudaError_t launch_record_paths(const DevScene& s, const DevChains& c, const uin
 cudaError_t launch_chain_epoch(const DevScene& s, const DevChains& c, uint64_t mut0, bool trace, bool count_work,
                                cudaStream_t st)
 {
-    if (c.T_mala) return s.brute ? launch_mala_epoch<true>(s, c, mut0, st) : launch_mala_epoch<false>(s, c, mut0, st);
+    if (c.T_mala)
+        return s.brute ? launch_mala_epoch<true>(s, c, mut0, trace, st) : launch_mala_epoch<false>(s, c, mut0, trace, st);
     if (s.brute) {
         if (trace) return count_work ? launch_epoch_t<true, true, true>(s, c, mut0, st)
                                      : launch_epoch_t<true, true, false>(s, c, mut0, st);

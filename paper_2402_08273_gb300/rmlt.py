@@ -104,6 +104,7 @@ _SIGS = [
     ("rmlt_read_stats", C.c_int, [C.c_void_p, _P(Stats)]),
     ("rmlt_set_trace", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64,
                                  C.c_uint32]),
+    ("rmlt_set_trace_words", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     ("rmlt_memory_usage", C.c_int, [C.c_void_p, _P(C.c_uint64)]),
     ("rmlt_probe_peaks", C.c_int, [C.c_int, C.c_void_p, _P(C.c_double), _P(C.c_double)]),
     ("rmlt_path_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -440,6 +441,10 @@ class Renderer:
         cap = records.numel() * records.element_size() // TRACE_DTYPE.itemsize
         lcap = lambdas.numel() if lambdas is not None else 0
         _check(lib().rmlt_set_trace(self.h, _ptr(records), cap, _ptr(lambdas), lcap, chain_stride))
+
+    def set_trace_words(self, words=None):
+        """words: CUDA int32 tensor with room for D words per trace record (or None)."""
+        _check(lib().rmlt_set_trace_words(self.h, _ptr(words), words.numel() if words is not None else 0))
 
     # -- checkpoint ----------------------------------------------------------
     def save(self, path):

@@ -7,7 +7,7 @@ from paper_2402_08273_gb300 import rmlt
 
 
 def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bvh_width=0, tuning=None,
-               wavefront=None, **params):
+               wavefront=None, words=False, **params):
     """Initialise, trace `n_epochs` epochs of every `stride`-th chain, and
     return the trace together with the initial and final state.  `tuning`
     (keyword arguments of Renderer.set_tuning) and `wavefront` (of
@@ -31,6 +31,10 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
                       device="cuda")
     lam = torch.zeros(n_epochs * R.m, dtype=torch.float64, device="cuda")
     R.set_trace(rec, lam, stride)
+    wbuf = None
+    if words:   # every record's proposal words, for replays that adopt proposals
+        wbuf = torch.zeros(n_epochs * n_traced * E * R.D, dtype=torch.int32, device="cuda")
+        R.set_trace_words(wbuf)
     R.step(n_epochs * E)
     R.synchronize()
     R.set_trace(None)
@@ -49,6 +53,8 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
     }
     if p.get("partition", 0) == 1:
         out["quadtree"] = R.read_quadtree()
+    if wbuf is not None:
+        out["words"] = wbuf.cpu().numpy().view(np.uint32).reshape(n_epochs, n_traced, E, R.D)
     return out
 
 
@@ -56,7 +62,7 @@ def oracle_params(p: dict) -> dict:
     keys = ("n_chains", "width", "height", "region_px", "max_depth", "epoch_len", "L", "target_mode",
             "n_bootstrap", "seed", "p_large", "s1", "s2", "alpha_star", "gamma_max", "gamma_scale",
             "lambda_init", "lambda_min", "lambda_max", "w_floor", "partition", "qt_max_leaves",
-            "qt_max_depth", "qt_split", "qt_refine", "kernel", "dir_cells")
+            "qt_max_depth", "qt_split", "qt_refine", "kernel", "dir_cells", "p_mala", "mala_tau", "mala_drift_max")
     return {k: p[k] for k in keys}
 
 
@@ -67,7 +73,7 @@ def replay_full(oracle_mod, gpu, scene_obj, max_adopt=2, **replay_kw):
     ch = oracle_mod.Chains(scene_obj, **oracle_params(p))
     ch.init()
     adopted = adopt_initial_states(ch, gpu["init"]["q"], max_adopt)
-    rp = Replay(ch, gpu["trace"], gpu["lambdas"], init_f=gpu["init"]["f"], **replay_kw)
+    rp = Replay(ch, gpu["trace"], gpu["lambdas"], init_f=gpu["init"]["f"], words=gpu.get("words"), **replay_kw)
     rp.run_full(gpu["trace"].shape[0])
     return ch, rp, adopted
 

@@ -11,6 +11,13 @@ Langevin (MALA) strategy on the GPU.
   masses (the state-dependent proposal ratio is exercised by the regional
   steps tau sigma_k^2); on the Cornell box it renders the same image as the
   plain strategies; a checkpoint restores the gradients.
+- The oracle replays every mutation of a Langevin run: each Langevin
+  proposal is adopted from the GPU's recorded words after checking it against
+  the oracle's own (binary64 Box-Muller and forward-mode gradient) within the
+  first-order bound of the binary32 rounding and of the gradient's accuracy;
+  the path, the acceptance with the proposal-density ratio (including the
+  (D/2) ln(tau_x / tau_y) term), the decision, the region tables and the final
+  states are then compared as for the other strategies.
 """
 import math
 
@@ -200,3 +207,29 @@ def test_mala_rejections():
     R.set_tuning(wavefront=True)
     with pytest.raises(rmlt.RmltError):
         R.step(16)
+
+
+# the most mutations each window may let through, measured on a GB300
+PINS_REPLAY = {"toy": {}, "cornell": {}}
+
+
+@pytest.mark.parametrize("case", ["toy", "cornell"])
+def test_mala_oracle_replay(oracle_mod, case):
+    from gpu_run import check_counters, replay_full, traced_run
+    if case == "toy":
+        gpu = traced_run(toy=S.TOY_DEFAULT, words=True, n_epochs=30, n_chains=128, width=64, height=64, region_px=8,
+                         max_depth=0, n_bootstrap=1 << 13, p_large=0.1, p_mala=0.5, mala_tau=1e-3,
+                         mala_drift_max=0.1)
+        osc = oracle_mod.Scene(toy=S.TOY_DEFAULT)
+    else:
+        gpu = traced_run(scene=S.cornell_box(), words=True, n_epochs=10, n_chains=64, width=64, height=64,
+                         region_px=8, max_depth=5, n_bootstrap=1 << 13, p_large=0.3, p_mala=0.3, mala_tau=1e-3,
+                         mala_drift_max=0.1)
+        osc = oracle_mod.Scene(S.cornell_box(), use_bvh=False)
+    ch, rp, adopted = replay_full(oracle_mod, gpu, osc)
+    print("Langevin replay:", rp.summary())
+    check_counters(ch, gpu, rp, PINS_REPLAY[case], adopted, 0)
+    assert rp.s["langevin"] > 0.2 * rp.s["mutations"]
+    assert rp.s["proposal_adopted"] == rp.s["langevin"] and rp.s["proposal_mismatch"] == 0
+    st = gpu["stats"]
+    assert st["mala"] == rp.s["langevin"] and st["mala_accepted"] > 0

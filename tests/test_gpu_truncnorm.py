@@ -1,10 +1,13 @@
 """The truncated-normal small-step kernel (RMLT_KERNEL_TRUNCNORM) on the GPU.
 
 Its offsets come from binary32 erfinv, so they are not bit-identical to the
-oracle's binary64 ones; the kernel is checked through what it must preserve:
-with adaptation the toy's region histogram converges to the closed-form
-region masses (the density ratio of the state-dependent kernel is exercised
-by the per-region sigma_k), the Cornell box renders the image the Kelemen
+oracle's binary64 ones.  The oracle replays every mutation with the GPU's
+recorded proposal words, after checking each offset against its own within
+the first-order bound of that rounding, and compares the path, the
+acceptance probability with the kernel's density ratio, the decision and the
+region tables.  Beside that, the kernel is checked through what it must
+preserve: with adaptation the toy's region histogram converges to the
+closed-form region masses, the Cornell box renders the image the Kelemen
 kernel renders, and the wavefront form reproduces the chain kernel bit for
 bit.
 """
@@ -75,3 +78,26 @@ def test_truncnorm_parameter_checks():
         R.init_chains(n_chains=64, max_depth=0, kernel=1, lambda_max=3.0)   # above 2 ln 4
     with pytest.raises(rmlt.RmltError):
         R.init_chains(n_chains=64, max_depth=0, kernel=2)
+
+
+# the most mutations each window may let through, measured on a GB300
+PINS = {"toy": {}, "cornell": {}}
+
+
+@pytest.mark.parametrize("case", ["toy", "cornell"])
+def test_truncnorm_oracle_replay(oracle_mod, case):
+    from gpu_run import check_counters, replay_full, traced_run
+    if case == "toy":
+        gpu = traced_run(toy=S.TOY_DEFAULT, words=True, n_epochs=30, n_chains=128, width=64, height=64, region_px=8,
+                         max_depth=0, n_bootstrap=1 << 13, p_large=0.1, kernel=1, lambda_init=2 * np.log(0.1))
+        osc = oracle_mod.Scene(toy=S.TOY_DEFAULT)
+    else:
+        gpu = traced_run(scene=S.cornell_box(), words=True, n_epochs=12, n_chains=64, width=64, height=64,
+                         region_px=8, max_depth=5, n_bootstrap=1 << 13, kernel=1, lambda_init=2 * np.log(0.05))
+        osc = oracle_mod.Scene(S.cornell_box(), use_bvh=False)
+    ch, rp, adopted = replay_full(oracle_mod, gpu, osc)
+    print("truncnorm replay:", rp.summary())
+    check_counters(ch, gpu, rp, PINS[case], adopted, 0)
+    assert rp.s["proposal_adopted"] > 0 and rp.s["proposal_mismatch"] == 0
+    # adaptation moved the regions' scales apart, so the density ratio mattered
+    assert np.ptp(gpu["region"]["lambda"]) > 0
