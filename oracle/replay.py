@@ -148,11 +148,15 @@ class Replay:
             tol = 4.0 * (2.0 ** 32 * sigma * math.sqrt(2.0) * (0.5 * math.sqrt(math.pi) * amp * 6 * U * np.abs(x)
                                                                  + 6 * U * np.abs(y))) + 2.0
         else:
-            # step = m + sqrt(tau) z: the drift errs by EPS_G |m| (gradient), the
-            # Box-Muller normals by ~8 u |z|, the sum by ~4 u |step|
+            # step = m + sqrt(tau) z: the drift errs by EPS_G |m| (gradient); a
+            # Box-Muller pair z = rho (cos, sin), rho^2 = -2 ln u1, errs by ~8 u |z|
+            # plus the binary32 rounding of u1 = (x + 1/2) 2^-24 (up to u absolute),
+            # which ln u1 amplifies by 1 / |ln u1| = 2 / rho^2; the sum by ~4 u |step|
             m, z, tau, _ = self.ch.last_mala()
+            rho2 = np.array([z[d] ** 2 + (z[d ^ 1] ** 2 if (d ^ 1) < D else 0.0) for d in range(D)])
+            ez = np.abs(z) * (8 * U + U / np.maximum(rho2, 1e-300))
             step = m + math.sqrt(tau) * z
-            tol = 4.0 * 2.0 ** 32 * (EPS_G * np.abs(m) + math.sqrt(tau) * 8 * U * np.abs(z) + 4 * U * np.abs(step)) + 2.0
+            tol = 4.0 * 2.0 ** 32 * (EPS_G * np.abs(m) + math.sqrt(tau) * ez + 4 * U * np.abs(step)) + 2.0
         diff = np.abs(off_g - off_o)
         self.prop_use = max(self.prop_use, float(np.max(diff / tol)))
         if np.all(diff <= tol):

@@ -1533,7 +1533,11 @@ static void mutate(or_ctx* c, uint32_t chain)
     if (c->p.debug_flags & 1) R = 1.0;   /* planted mistake for negative-control tests */
     double fy[3] = {0, 0, 0};
     or_err E = {OR_INF, {0, 0, 0}};
-    if (R > 0) {
+    /* early rejection: a proposal outside the reverse Kelemen kernel's support
+     * has R = 0 by definition; the truncated normal's density ratio is
+     * positive (if it underflows, a = 0 but the path is still evaluated) */
+    const int early = c->p.kernel == 1 ? 0 : !(R > 0);
+    if (!early) {
         uint64_t cnt[3] = {0, 0, 0};
         if (!path_eval_impl(c->s, c->p.width, c->p.height, c->p.max_depth, qy, fy, NULL, c->mh ? &E : NULL, cnt))
             c->st[5]++;
@@ -1545,7 +1549,7 @@ static void mutate(or_ctx* c, uint32_t chain)
     double a = accept_prob(c, kx, ky, c->pi[chain], piy, R);
     int32_t acc = xi < a;
     if (c->mh) {
-        c->mh(c->user, chain, c->mut, qy, D, large, !(R > 0), E.dec, E.ferr, xi, fy, &a, &acc);
+        c->mh(c->user, chain, c->mut, qy, D, large, early, E.dec, E.ferr, xi, fy, &a, &acc);
         piy = luminance(fy);
     }
     if (large) {
