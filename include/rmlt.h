@@ -205,12 +205,15 @@ rmlt_status rmlt_load_scene(rmlt_ctx* ctx, const rmlt_scene_desc* scene);
 rmlt_status rmlt_load_toy_integrand(rmlt_ctx* ctx, const double* params);
 
 /* Allocate chain state and region tables, run the bootstrap (n_bootstrap
- * uniform samples -> b, Sec. 3.2 "preprocess"), choose each chain's initial
- * state by stratified inverse CDF of pi, and set lambda_k = lambda_init,
- * i_k = A_k = 0, n_k = 1 (Alg. 1 lines 2-6).  Errors: RMLT_E_INVALID_ARG
- * (non-positive sizes, max_depth out of range, s1 >= s2, p_large outside
- * [0,1], lambda bounds outside [-150, 2 ln(1/(2 s2))] ...), RMLT_E_STATE (no
- * scene), RMLT_E_OOM, RMLT_E_CUDA. */
+ * uniform samples -> b, Sec. 3.2 "preprocess"), give each chain g (global id)
+ * a starting state among its own K = n_bootstrap / chains samples [gK, (g+1)K)
+ * with probability pi_s / sum(pi) (weighted reservoir sampling), and set
+ * lambda_k = lambda_init, i_k = A_k = 0, n_k = 1 (Alg. 1 lines 2-6).
+ * Bootstrap paths dropped by a traversal-stack overflow are counted in
+ * rmlt_stats.boot_overflow.  On error the context keeps its previous chains.
+ * Errors: RMLT_E_INVALID_ARG (non-positive sizes, max_depth out of range,
+ * s1 >= s2, p_large outside [0,1], lambda bounds outside [-150, the kernel's
+ * maximum] ...), RMLT_E_STATE (no scene), RMLT_E_OOM, RMLT_E_CUDA. */
 rmlt_status rmlt_init_chains(rmlt_ctx* ctx, const rmlt_chain_params* params);
 
 /* Advance every chain by n_mutations Metropolis-Hastings mutations (Alg. 1

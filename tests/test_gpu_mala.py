@@ -210,7 +210,7 @@ def test_mala_rejections():
 
 
 # the most mutations each window may let through, measured on a GB300
-PINS_REPLAY = {"toy": {}, "cornell": {}}
+PINS_REPLAY = {"toy": {}, "cornell": {"f_bounded": 4}}
 
 
 @pytest.mark.parametrize("case", ["toy", "cornell"])

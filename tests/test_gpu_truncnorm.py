@@ -81,7 +81,7 @@ def test_truncnorm_parameter_checks():
 
 
 # the most mutations each window may let through, measured on a GB300
-PINS = {"toy": {}, "cornell": {}}
+PINS = {"toy": {}, "cornell": {"f_bounded": 2}}
 
 
 @pytest.mark.parametrize("case", ["toy", "cornell"])
