@@ -1704,8 +1704,17 @@ rmlt_status rmlt_batch_step(rmlt_batch* b, uint64_t n_mutations)
     } else {
         for (uint64_t ep = 0; ep < n_ep && e == cudaSuccess; ++ep) {
             e = cudaGraphLaunch(b->exec, b->stream);
-            for (int i = 0; i < n && e == cudaSuccess; ++i)
-                if (refine[(size_t)i * n_ep + ep]) e = launch_quadtree_refine(b->h[(size_t)i].Ch, b->stream);
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                if (!refine[(size_t)i * n_ep + ep]) continue;
+                e = launch_quadtree_refine(b->h[(size_t)i].Ch, b->stream);
+                // the trace instrument records lambda after the whole epoch
+                // boundary, as rmlt_step does: the split leaves' children too
+                rmlt_ctx* c = b->m[(size_t)i];
+                const uint64_t m = (uint64_t)c->Ch.m, te = c->tr_epoch + ep;
+                if (e == cudaSuccess && c->tr && c->tr_lam && (te + 1) * m <= c->tr_lam_cap)
+                    e = cudaMemcpyAsync(c->tr_lam + te * m, c->Ch.lam, sizeof(double) * m, cudaMemcpyDeviceToDevice,
+                                        b->stream);
+            }
         }
     }
     if (e != cudaSuccess) {
