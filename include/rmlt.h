@@ -383,6 +383,11 @@ rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup, int
  * cannot see into conditional graphs need it.  Speed only.  Defaults 0, 0, 16,
  * 0. */
 #define RMLT_WAVEFRONT_HOST_LOOP 1
+/* RMLT_WAVEFRONT_SHORT_STACK: the persistent trace kernel keeps 16 of each
+ * ray's 48 traversal-stack entries in shared memory and the deeper ones in a
+ * per-thread area of device memory (about 40 MB, part of the wavefront
+ * state), which leaves more of each SM's memory to the L1 cache.  Speed only. */
+#define RMLT_WAVEFRONT_SHORT_STACK 2
 rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_ctas_per_sm, int refill_lanes,
                                int flags);
 

@@ -19,6 +19,7 @@ CANDIDATES = (
     {"form": "chain", "batch_shade": 16, "batch_setup": 10},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "short_stack": True},
 )
 
 
@@ -30,7 +31,8 @@ def apply(R, cand: dict) -> None:
         R.set_tuning(wavefront=True)
         R.set_wavefront(trace_ctas_per_sm=cand.get("trace_ctas_per_sm", 0),
                         setup_ctas_per_sm=cand.get("setup_ctas_per_sm", 0),
-                        refill_lanes=cand.get("refill_lanes", 16))
+                        refill_lanes=cand.get("refill_lanes", 16), short_stack=cand.get("short_stack", False),
+                        host_loop=cand.get("host_loop", False))
 
 
 def autotune(R, epochs: int = 2, candidates=CANDIDATES, step=None):

@@ -738,6 +738,7 @@ static rmlt_status epoch_kernels(rmlt_ctx* c)
     if (err == cudaSuccess) {
         if (c->wavefront) {
             c->W.refill = c->wf_refill;
+            c->W.short_stack = (c->wf_flags & RMLT_WAVEFRONT_SHORT_STACK) != 0;
             c->wf_ran = true;
             err = wf_epoch(&c->wg, S, Ch, c->W, c->mut, Ch.trace_base, trace, c->count_work, c->wf_trace_cps,
                            c->wf_setup_cps, (c->wf_flags & RMLT_WAVEFRONT_HOST_LOOP) != 0, c->wave_limit,
@@ -1057,7 +1058,8 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* c, int trace_ctas_per_sm, int setup_cta
     if (trace_ctas_per_sm < 0 || trace_ctas_per_sm > 32 || setup_ctas_per_sm < 0 || setup_ctas_per_sm > 32)
         return fail(RMLT_E_INVALID_ARG, "blocks per SM must be in 0..32");
     if (refill_lanes < 1 || refill_lanes > 32) return fail(RMLT_E_INVALID_ARG, "refill_lanes must be in 1..32");
-    if (flags & ~RMLT_WAVEFRONT_HOST_LOOP) return fail(RMLT_E_INVALID_ARG, "unknown wavefront flag");
+    if (flags & ~(RMLT_WAVEFRONT_HOST_LOOP | RMLT_WAVEFRONT_SHORT_STACK))
+        return fail(RMLT_E_INVALID_ARG, "unknown wavefront flag");
     c->wf_flags = flags;
     c->wf_trace_cps = trace_ctas_per_sm;
     c->wf_setup_cps = setup_ctas_per_sm;

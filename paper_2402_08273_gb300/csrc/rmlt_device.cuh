@@ -232,9 +232,35 @@ __device__ __forceinline__ bool step_turn(bool live, const Trav& T)
     return live && (at_leaf == leaf_turn);
 }
 
+// The traversal stack: a thread's column of a shared-memory panel (all
+// kStackSize entries), or a split stack whose first SS entries sit in shared
+// memory and the rest in a per-thread area of global memory (entry j of the
+// thread at gl[(j - SS) * gstride]), which leaves more of the SM's memory to
+// the L1 cache.  Both hold kStackSize entries; the traversal is the same.
+__device__ __forceinline__ void stk_push(uint32_t* s, int sp, uint32_t v) { s[kStackStride * sp] = v; }
+__device__ __forceinline__ uint32_t stk_pop(uint32_t* s, int sp) { return s[kStackStride * sp]; }
+
+template <int SS>
+struct SplitStack {
+    uint32_t* sh;      // this thread's column of the shared panel (SS entries)
+    uint32_t* gl;      // this thread's first global entry
+    unsigned gstride;  // words between a thread's consecutive global entries
+};
+template <int SS>
+__device__ __forceinline__ void stk_push(const SplitStack<SS>& s, int sp, uint32_t v)
+{
+    if (sp < SS) s.sh[kStackStride * sp] = v;
+    else s.gl[(size_t)(sp - SS) * s.gstride] = v;
+}
+template <int SS>
+__device__ __forceinline__ uint32_t stk_pop(const SplitStack<SS>& s, int sp)
+{
+    return sp < SS ? s.sh[kStackStride * sp] : s.gl[(size_t)(sp - SS) * s.gstride];
+}
+
 // one step; returns true once the ray is resolved
-template <bool BRUTE>
-__device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevScene& S, const float4* s_tris,
+template <bool BRUTE, class STK = uint32_t*>
+__device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S, const float4* s_tris,
                                           unsigned& n_nodes, unsigned& n_tris)
 {
     if (BRUTE) {
@@ -302,12 +328,12 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
 #pragma unroll
         for (int k = 3; k >= 1; --k) {
             if (key[k] != INFINITY) {
-                if (T.sp < kStackSize) stack[kStackStride * T.sp++] = cr[k];
+                if (T.sp < kStackSize) stk_push(stack, T.sp++, cr[k]);
                 else T.overflow = 1;
             }
         }
 
-        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef);
+        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef);
     } else if (!(ref & kLeafBit)) {
         ++n_nodes;
         const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
@@ -330,7 +356,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (T.sp < kStackSize) stack[kStackStride * T.sp++] = first0 ? c1 : c0;
+            if (T.sp < kStackSize) stk_push(stack, T.sp++, first0 ? c1 : c0);
             else T.overflow = 1;
             next = first0 ? c0 : c1;
         } else if (h0) {
@@ -338,7 +364,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
         } else if (h1) {
             next = c1;
         } else {
-            next = T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef;
+            next = T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef;
         }
     } else {
         const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
@@ -371,7 +397,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, uint32_t* stack, const DevSce
                 }
             }
         }
-        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stack[kStackStride * --T.sp] : kNoRef);
+        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef);
     }
     T.ref = T.overflow ? kNoRef : next;
     return T.ref == kNoRef;

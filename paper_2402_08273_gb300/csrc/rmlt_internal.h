@@ -162,7 +162,12 @@ struct DevWave {
     unsigned long long cond = 0;  // cudaGraphConditionalHandle of the wave loop
     unsigned wave_cap = 0;        // E (max_depth + 1) + 2: more waves than any epoch needs
     int refill = 16;              // idle lanes of a trace warp that pull new rays together
+    int short_stack = 0;          // 1: the trace kernel keeps kShortStack stack entries per ray in shared
+                                  //    memory and the rest in `gstack`
+    uint32_t* gstack = nullptr;   // [kStackSize - kShortStack][kWfTraceThreadsPerSm x SMs]
 };
+constexpr int kShortStack = 16;
+constexpr int kWfTraceThreadsPerSm = 16 * kChainBlock;   // bound on the persistent trace kernel's threads per SM
 
 // device bytes of the wavefront state for C chains of D dimensions
 size_t wf_bytes(int C, int D);

@@ -387,12 +387,23 @@ __global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S,
 // ---------------------------------------------------------------------------
 // trace: persistent; one ray per lane, idle lanes pull rays together
 // ---------------------------------------------------------------------------
-template <bool BRUTE, bool COUNT>
+template <int SS>
+struct StackFor {
+    using type = SplitStack<SS>;
+};
+template <>
+struct StackFor<kStackSize> {
+    using type = uint32_t*;
+};
+
+// SS: traversal stack entries per ray kept in shared memory (kStackSize: all;
+// fewer: the rest in W.gstack, so more of the SM's memory serves as L1)
+template <bool BRUTE, bool COUNT, int SS = kStackSize>
 __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S, const DevWave W, int C,
                                                                unsigned long long* stats)
 {
     extern __shared__ float4 s_tris[];
-    __shared__ uint32_t s_stack[kStackSize * kChainBlock];
+    __shared__ uint32_t s_stack[SS * kChainBlock];
     if (BRUTE) stage_triangles(S, s_tris);
     const unsigned FULL = 0xFFFFFFFFu;
     const unsigned cap = 2u * (unsigned)C, n = min(W.ctr->trace_n, cap), buf = W.ctr->trace_buf;
@@ -401,7 +412,15 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const int refill = W.refill;
-    uint32_t* stack = thread_stack(s_stack);
+    uint32_t* col = s_stack + (threadIdx.x / kStackStride) * (SS * kStackStride) + threadIdx.x % kStackStride;
+    typename StackFor<SS>::type stack;
+    if constexpr (SS < kStackSize) {
+        stack.sh = col;
+        stack.gl = W.gstack + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        stack.gstride = gridDim.x * blockDim.x;
+    } else {
+        stack = col;
+    }
     unsigned nn = 0, nt = 0;
     Trav T;
     T.ref = kNoRef;
@@ -481,11 +500,24 @@ __global__ void __launch_bounds__(256) wf_end_kernel(const DevChains Ch, const D
 // ---------------------------------------------------------------------------
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+namespace {
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+size_t gstack_words() { return (size_t)(kStackSize - kShortStack) * kWfTraceThreadsPerSm * (size_t)sm_count(); }
+}  // namespace
+
 size_t wf_bytes(int C, int D)
 {
     const size_t c = (size_t)C;
     return align256(sizeof(uint32_t) * kWfSlots * c) + 2 * align256(sizeof(uint32_t) * (size_t)D * c) +
-           2 * align256(sizeof(float4) * 4 * c) + align256(sizeof(uint32_t) * c) + align256(sizeof(WfCounters));
+           2 * align256(sizeof(float4) * 4 * c) + align256(sizeof(uint32_t) * c) + align256(sizeof(WfCounters)) +
+           align256(sizeof(uint32_t) * gstack_words());
 }
 
 void wf_carve(void* base, int C, int D, DevWave& w)
@@ -505,6 +537,8 @@ void wf_carve(void* base, int C, int D, DevWave& w)
     w.fq = (uint32_t*)p;
     p += align256(sizeof(uint32_t) * c);
     w.ctr = (WfCounters*)p;
+    p += align256(sizeof(WfCounters));
+    w.gstack = (uint32_t*)p;
 }
 
 struct WfGraph {
@@ -530,12 +564,21 @@ void put(std::vector<unsigned char>& k, const T& v)
     k.insert(k.end(), b, b + sizeof v);
 }
 
-int sm_count()
+// the trace kernel for the wave state's stack layout, with its shared
+// memory carve-out set for the layout (the short stack leaves L1 the rest)
+template <bool B, bool K>
+void* trace_kernel(const DevWave& W)
 {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
+    if (!B && W.short_stack) {
+        void* k = (void*)wf_trace_kernel<B, K, kShortStack>;
+        static bool carved = false;
+        if (!carved) {
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 30);
+            carved = true;
+        }
+        return k;
+    }
+    return (void*)wf_trace_kernel<B, K>;
 }
 
 template <bool B, bool T, bool K>
@@ -557,7 +600,7 @@ cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevW
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
-    auto kt = wf_trace_kernel<B, K>;
+    void* kt = trace_kernel<B, K>(W);
     if (tshm > 48 * 1024) {
         if ((e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm)) != cudaSuccess)
             return e;
@@ -578,7 +621,7 @@ cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevW
     k2.gridDim = dim3((unsigned)setup_ctas);
     k2.blockDim = dim3(kChainBlock);
     k2.kernelParams = a_setup;
-    k3.func = (void*)kt;
+    k3.func = kt;
     k3.gridDim = dim3((unsigned)trace_ctas);
     k3.blockDim = dim3(kChainBlock);
     k3.sharedMemBytes = (unsigned)tshm;
@@ -591,13 +634,14 @@ cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevW
 }
 
 template <bool B, bool T, bool K>
-int trace_occupancy(const DevScene& S)
+int trace_occupancy(const DevScene& S, const DevWave& W)
 {
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
     int n = 0;
-    if (tshm > 48 * 1024)
-        cudaFuncSetAttribute(wf_trace_kernel<B, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, wf_trace_kernel<B, K>, kChainBlock, tshm);
+    void* kt = trace_kernel<B, K>(W);
+    if (tshm > 48 * 1024) cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kt, kChainBlock, tshm);
+    if (n > kWfTraceThreadsPerSm / kChainBlock) n = kWfTraceThreadsPerSm / kChainBlock;   // the global stack's room
     return n > 0 ? n : 1;
 }
 
@@ -617,9 +661,9 @@ cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int tr
 {
     W.cond = 0;
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
+    void* kt = trace_kernel<B, K>(W);
     if (tshm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(wf_trace_kernel<B, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tshm);
+        cudaError_t e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
         if (e != cudaSuccess) return e;
     }
     const unsigned g1 = (unsigned)((Ch.C + kChainBlock - 1) / kChainBlock);
@@ -627,8 +671,11 @@ cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int tr
         wf_shade_kernel<B><<<g1, kChainBlock, 0, st>>>(S, Ch, W);
         if (Ch.dcells > 1) wf_setup_kernel<T, true><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
         else wf_setup_kernel<T><<<(unsigned)setup_ctas, kChainBlock, 0, st>>>(S, Ch, W);
-        wf_trace_kernel<B, K><<<(unsigned)trace_ctas, kChainBlock, tshm, st>>>(S, W, Ch.C, Ch.stats);
-        cudaError_t e = cudaGetLastError();
+        int C = Ch.C;
+        unsigned long long* stats = Ch.stats;
+        void* args[] = {(void*)&S, (void*)&W, (void*)&C, (void*)&stats};
+        cudaError_t e = cudaLaunchKernel(kt, dim3((unsigned)trace_ctas), dim3(kChainBlock), args, tshm, st);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -640,7 +687,7 @@ cudaError_t epoch_t(WfGraph** gp, const DevScene& S, const DevChains& Ch, DevWav
                     cudaStream_t st)
 {
     const int sms = sm_count();
-    const int tocc = trace_occupancy<B, T, K>(S), socc = setup_occupancy<T>();
+    const int tocc = trace_occupancy<B, T, K>(S, W), socc = setup_occupancy<T>();
     const int tc = sms * (trace_cps > 0 && trace_cps < tocc ? trace_cps : tocc);
     const int max_setup = (Ch.C + kChainBlock - 1) / kChainBlock;
     int sc = sms * (setup_cps > 0 && setup_cps < socc ? setup_cps : socc);

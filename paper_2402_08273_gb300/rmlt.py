@@ -371,9 +371,10 @@ class Renderer:
         _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup), flags))
 
     def set_wavefront(self, trace_ctas_per_sm: int = 0, setup_ctas_per_sm: int = 0, refill_lanes: int = 16,
-                      host_loop: bool = False):
+                      host_loop: bool = False, short_stack: bool = False):
+        flags = (1 if host_loop else 0) | (2 if short_stack else 0)
         _check(lib().rmlt_set_wavefront(self.h, int(trace_ctas_per_sm), int(setup_ctas_per_sm),
-                                        int(refill_lanes), 1 if host_loop else 0))
+                                        int(refill_lanes), flags))
 
     def read_chain_grad(self) -> np.ndarray:
         """grad log pi of the current states, [D, n_chains] (Langevin runs)."""
