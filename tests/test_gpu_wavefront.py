@@ -96,7 +96,8 @@ def test_wavefront_identical_quadtree():
 
 @pytest.mark.parametrize("shape", [{"trace_ctas_per_sm": 1, "setup_ctas_per_sm": 1, "refill_lanes": 1},
                                    {"trace_ctas_per_sm": 3, "setup_ctas_per_sm": 0, "refill_lanes": 32},
-                                   {"host_loop": True}])
+                                   {"host_loop": True}, {"short_stack": True},
+                                   {"short_stack": True, "host_loop": True}])
 def test_wavefront_launch_shape_changes_nothing(shape):
     from gpu_run import traced_run
     kw = dict(scene=S.two_rooms(5_000, seed=3), n_epochs=2, n_chains=1000, width=64, height=64, region_px=8,
@@ -123,3 +124,14 @@ def test_wavefront_bench_size_stays_identical():
     ref, wf = _both(1, stride=97, scene=S.two_rooms(200_000, seed=0), n_chains=1 << 16, width=512,
                     height=512, region_px=16, max_depth=10, epoch_len=16, n_bootstrap=1 << 20, p_large=0.3)
     _assert_identical(ref, wf)
+
+
+def test_short_stack_identical_on_deep_stacks():
+    """The trace kernel's split stack (16 entries in shared memory, the rest
+    in device memory) on the glossy corridor's 2M-triangle BVH4, whose rays
+    use more than 16 entries: identical to the chain kernel."""
+    ref, wf = _both(1, stride=61, wf_shape={"short_stack": True}, scene=S.glossy_corridor(2_000_000, seed=0),
+                    n_chains=1 << 15, width=480, height=270, region_px=32, max_depth=12, epoch_len=16,
+                    n_bootstrap=1 << 17, p_large=0.3)
+    st = _assert_identical(ref, wf)
+    assert st["stack_overflow"] == 0 and st["rays"] > 0
