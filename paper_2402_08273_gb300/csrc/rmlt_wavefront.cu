@@ -397,12 +397,10 @@ struct StackFor<kStackSize> {
 };
 
 // SS: traversal stack entries per ray kept in shared memory (kStackSize: all;
-// fewer: the rest in W.gstack, so more of the SM's memory serves as L1, and
-// the kernel is compiled for 10 resident blocks per SM instead of 8: more
-// rays in flight at 48 registers)
+// fewer: the rest in W.gstack, so more of the SM's memory serves as L1)
 template <bool BRUTE, bool COUNT, int SS = kStackSize>
-__global__ void __launch_bounds__(kChainBlock, SS < kStackSize ? 10 : 1)
-    wf_trace_kernel(const DevScene S, const DevWave W, int C, unsigned long long* stats)
+__global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S, const DevWave W, int C,
+                                                               unsigned long long* stats)
 {
     extern __shared__ float4 s_tris[];
     __shared__ uint32_t s_stack[SS * kChainBlock];
