@@ -399,6 +399,11 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_c
  * marks the context failed. */
 rmlt_status rmlt_set_wave_limit(rmlt_ctx* ctx, uint32_t waves);
 
+/* Leaf turns of the wavefront form's trace kernel: a warp's lanes whose ray
+ * waits at a BVH leaf test its triangles together once at least leaf_batch
+ * of them are there (1..32; default 8).  Speed only. */
+rmlt_status rmlt_set_trace_leaf_batch(rmlt_ctx* ctx, int leaf_batch);
+
 /* Bootstrap without any device allocation.  Some callers cannot allocate
  * device memory at the point where they need starting states: code running
  * inside a memory-pool or arena callback, a process whose allocator is

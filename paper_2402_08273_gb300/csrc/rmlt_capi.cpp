@@ -102,7 +102,7 @@ struct rmlt_ctx {
     uint64_t since_refine = 0;   // mutations since the last quadtree pass
     int batch_shade = 12, batch_setup = 10;
     int large_ahead = 0, adaptive_batch = 0;
-    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0;
+    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0, wf_leaf_batch = kLeafBatch;
     unsigned wave_limit = 0;     // waves per epoch before the wavefront form stops (0: its default)
     bool wf_ran = false;         // an epoch ran in the wavefront form since the chains were set up
     uint64_t wave_hits_seen = 0; // epochs stopped by the wave limit, as of the last check
@@ -739,6 +739,7 @@ static rmlt_status epoch_kernels(rmlt_ctx* c)
         if (c->wavefront) {
             c->W.refill = c->wf_refill;
             c->W.short_stack = (c->wf_flags & RMLT_WAVEFRONT_SHORT_STACK) != 0;
+            c->W.leaf_batch = c->wf_leaf_batch;
             c->wf_ran = true;
             err = wf_epoch(&c->wg, S, Ch, c->W, c->mut, Ch.trace_base, trace, c->count_work, c->wf_trace_cps,
                            c->wf_setup_cps, (c->wf_flags & RMLT_WAVEFRONT_HOST_LOOP) != 0, c->wave_limit,
@@ -1026,6 +1027,14 @@ rmlt_status rmlt_read_params(rmlt_ctx* c, rmlt_chain_params* out)
     if (!c || !out) return fail(RMLT_E_INVALID_ARG, "null argument");
     if (!c->have_chains) return fail(RMLT_E_STATE, "no chains");
     *out = c->P;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_trace_leaf_batch(rmlt_ctx* c, int leaf_batch)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (leaf_batch < 1 || leaf_batch > 32) return fail(RMLT_E_INVALID_ARG, "leaf_batch must be in 1..32");
+    c->wf_leaf_batch = leaf_batch;
     return RMLT_OK;
 }
 

@@ -222,13 +222,13 @@ __device__ __forceinline__ YPanel thread_words(uint32_t* s_y)
 // A ray's own sequence of steps, and so its result, does not change.  Called
 // by all lanes of the warp; `live`: this lane has a ray in traversal.
 template <bool BRUTE>
-__device__ __forceinline__ bool step_turn(bool live, const Trav& T)
+__device__ __forceinline__ bool step_turn(bool live, const Trav& T, int leaf_batch = kLeafBatch)
 {
     if (BRUTE) return live;
     const bool at_leaf = live && (T.ref & kLeafBit);
     const unsigned m_leaf = __ballot_sync(0xFFFFFFFFu, at_leaf);
     const unsigned m_node = __ballot_sync(0xFFFFFFFFu, live && !at_leaf);
-    const bool leaf_turn = m_leaf && (!m_node || __popc(m_leaf) >= kLeafBatch);
+    const bool leaf_turn = m_leaf && (!m_node || __popc(m_leaf) >= leaf_batch);
     return live && (at_leaf == leaf_turn);
 }
 

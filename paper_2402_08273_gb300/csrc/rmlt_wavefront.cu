@@ -185,8 +185,10 @@ __global__ void wf_begin_kernel(const DevChains Ch, const DevWave W, unsigned lo
 // ---------------------------------------------------------------------------
 // shade: consume the rays traced in the previous wave
 // ---------------------------------------------------------------------------
+// compiled for 8 resident blocks per SM (64 registers): the kernel waits on
+// its slot loads, so more warps in flight pay for a few spilled words
 template <bool BRUTE>
-__global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S, const DevChains Ch, const DevWave W)
+__global__ void __launch_bounds__(kChainBlock, 8) wf_shade_kernel(const DevScene S, const DevChains Ch, const DevWave W)
 {
     const unsigned FULL = 0xFFFFFFFFu;
     const int C = Ch.C;
@@ -291,8 +293,10 @@ __global__ void __launch_bounds__(kChainBlock) wf_shade_kernel(const DevScene S,
 // ---------------------------------------------------------------------------
 // setup: finish the mutations whose path ended, draw the next proposals
 // ---------------------------------------------------------------------------
+// compiled for 6 resident blocks per SM (80 registers, no spills) instead of
+// the 3 that 152 registers allowed: the kernel is latency-bound
 template <bool TRACE, bool D4 = false>
-__global__ void __launch_bounds__(kChainBlock) wf_setup_kernel(const DevScene S, DevChains Ch, const DevWave W)
+__global__ void __launch_bounds__(kChainBlock, 6) wf_setup_kernel(const DevScene S, DevChains Ch, const DevWave W)
 {
     __shared__ uint32_t s_y[kMaxDim * kChainBlock];
     const int C = Ch.C;
@@ -444,7 +448,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
             }
         }
         if (dry && __all_sync(FULL, c < 0)) break;
-        if (step_turn<BRUTE>(c >= 0, T) && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        if (step_turn<BRUTE>(c >= 0, T, W.leaf_batch) && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
             if (T.any) {
                 W.s[(size_t)kWShd * C + c] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
             } else {

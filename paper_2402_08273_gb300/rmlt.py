@@ -94,6 +94,7 @@ _SIGS = [
     ("rmlt_epoch_update", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("rmlt_read_params", C.c_int, [C.c_void_p, _P(ChainParams)]),
     ("rmlt_set_wave_limit", C.c_int, [C.c_void_p, C.c_uint32]),
+    ("rmlt_set_trace_leaf_batch", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_read_image", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("rmlt_read_region_hist", C.c_int, [C.c_void_p, C.c_void_p]),
     ("rmlt_read_region_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -294,6 +295,9 @@ class Renderer:
 
     def epoch_update(self, counts, sums):
         _check(lib().rmlt_epoch_update(self.h, _ptr(counts), _ptr(sums)))
+
+    def set_trace_leaf_batch(self, leaf_batch: int = 8):
+        _check(lib().rmlt_set_trace_leaf_batch(self.h, int(leaf_batch)))
 
     def set_wave_limit(self, waves: int = 0):
         _check(lib().rmlt_set_wave_limit(self.h, int(waves)))

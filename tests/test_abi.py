@@ -48,6 +48,7 @@ def test_host_side_errors_without_gpu():
     assert L.rmlt_epoch_update(None, None, None) == -1
     assert L.rmlt_read_params(None, None) == -1
     assert L.rmlt_set_wave_limit(None, 0) == -1
+    assert L.rmlt_set_trace_leaf_batch(None, 8) == -1
     assert b"null" in L.rmlt_last_error()
     L.rmlt_destroy(None)
 
