@@ -208,7 +208,7 @@ rmlt_status rmlt_load_toy_integrand(rmlt_ctx* ctx, const double* params);
  * uniform samples -> b, Sec. 3.2 "preprocess"), give each chain g (global id)
  * a starting state among its own K = n_bootstrap / chains samples [gK, (g+1)K)
  * with probability pi_s / sum(pi) (weighted reservoir sampling), and set
- * lambda_k = lambda_init, i_k = A_k = 0, n_k = 1 (Alg. 1 lines 2-6).
+ * lambda_k = lambda_init, i_k = A_k = 0, n_k = 1 (Alg. 1, initialisation).
  * Bootstrap paths dropped by a traversal-stack overflow are counted in
  * rmlt_stats.boot_overflow.  On error the context keeps its previous chains.
  * Errors: RMLT_E_INVALID_ARG (non-positive sizes, max_depth out of range,
@@ -216,9 +216,9 @@ rmlt_status rmlt_load_toy_integrand(rmlt_ctx* ctx, const double* params);
  * maximum] ...), RMLT_E_STATE (no scene), RMLT_E_OOM, RMLT_E_CUDA. */
 rmlt_status rmlt_init_chains(rmlt_ctx* ctx, const rmlt_chain_params* params);
 
-/* Advance every chain by n_mutations Metropolis-Hastings mutations (Alg. 1
- * lines 8-19), rounded up to whole epochs of epoch_len, with the region
- * update (Alg. 1 lines 13-18; at most one per region per epoch) at each epoch
+/* Advance every chain by n_mutations Metropolis-Hastings mutations (Alg. 1,
+ * mutation loop), rounded up to whole epochs of epoch_len, with the region
+ * update (Alg. 1, region update; at most one per region per epoch) at each epoch
  * boundary.  Asynchronous on the context's stream (no host synchronisation);
  * launch errors are returned here, execution errors at the next synchronising
  * call.  A proposal whose ray overflows the traversal stack is given zero
@@ -231,16 +231,16 @@ rmlt_status rmlt_step(rmlt_ctx* ctx, uint64_t n_mutations);
  * chains_total; Sec. 6 "Implementation": all chains share i_k and A_k).
  *   rmlt_exchange_size: *n_counts u64 words and *n_sums doubles of the two
  *     exchange buffers (3 m + 1 and m, m the region capacity).
- *   rmlt_epoch_mutate: E mutations of every chain of this context (Alg. 1
- *     lines 8-12 and 19), then writes what this epoch added to the region
+ *   rmlt_epoch_mutate: E mutations of every chain of this context (Alg. 1,
+ *     mutation step), then writes what this epoch added to the region
  *     tables to the caller's device buffers: counts = [i_k (m)][A_k (m)]
  *     [h_k (m)][large steps (1)], sums = [sum of pi over the large-step
  *     proposals per region (m)].
  *   rmlt_epoch_update: takes the same buffers after the caller summed them
  *     over all contexts (an all-reduce; u64 sums wrap, so a signed 64-bit
  *     reduction gives the same bits), sets every table to its value at the
- *     start of the epoch plus the sums, and runs the region update (Alg. 1
- *     lines 13-18), the weight update of the weighted target and a due
+ *     start of the epoch plus the sums, and runs the region update (Alg. 1,
+ *     region update), the weight update of the weighted target and a due
  *     quadtree pass.  Every context then holds identical region tables.
  * An unsharded context may use them too (the buffers passed through
  * unchanged give exactly rmlt_step(epoch_len)).  Both are asynchronous on the
@@ -401,7 +401,7 @@ rmlt_status rmlt_set_wave_limit(rmlt_ctx* ctx, uint32_t waves);
 
 /* Leaf turns of the wavefront form's trace kernel: a warp's lanes whose ray
  * waits at a BVH leaf test its triangles together once at least leaf_batch
- * of them are there (1..32; default 8).  Speed only. */
+ * of them are there (1..32; default 4).  Speed only. */
 rmlt_status rmlt_set_trace_leaf_batch(rmlt_ctx* ctx, int leaf_batch);
 
 /* Bootstrap without any device allocation.  Some callers cannot allocate
@@ -438,8 +438,8 @@ rmlt_status rmlt_bootstrap_noalloc(rmlt_ctx* ctx, const rmlt_chain_params* param
 /* Batched stepping.  A batch advances several contexts (their own scenes,
  * resolutions, region grids and chain counts, of any size) together: per
  * epoch, one launch of the chain kernel covers the chains of every member,
- * block by block, and one launch runs every member's region update (Alg. 1
- * lines 13-18); the two are a CUDA graph captured once and replayed per
+ * block by block, and one launch runs every member's region update (Alg. 1,
+ * region update); the two are a CUDA graph captured once and replayed per
  * epoch.  Each member's trajectory is exactly the one rmlt_step gives it (the
  * same kernel body, Philox streams and order of updates); only the launch is
  * shared, so small populations fill the GPU together.  Members must be on

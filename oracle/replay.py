@@ -32,7 +32,7 @@ from the failures it removes:
   beyond it, `proposal_mismatch`); the Langevin acceptance may further differ
   by what a relative error `EPS_G` of the drifts (the adjoint's gradient
   against the oracle's) changes in it, ln a +- EPS_G S (S from the oracle);
-* the region update (Alg. 1 lines 13-18): with every chain traced, the GPU's
+* the region update (Alg. 1, region update): with every chain traced, the GPU's
   A_k is rebuilt exactly from its own recorded acceptance probabilities
   (sum of round(a 2^32) over the small steps of region k), and the GPU's
   lambda_k must equal the update computed from that A_k bit for bit.  The

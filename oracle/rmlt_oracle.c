@@ -1293,7 +1293,7 @@ static void large_step(const or_ctx* c, uint32_t chain, uint64_t mut, uint32_t* 
 }
 
 /* Small step: every dimension perturbed with the one scale sigma_{k(x)}
- * (Alg. 1 lines 8-10; Sec. 5.2 proposal of the current state's region). */
+ * (Alg. 1, region lookup, step size and proposal; Sec. 5.2 proposal of the current state's region). */
 static void small_step(const or_ctx* c, uint32_t chain, uint64_t mut, int32_t kx,
                        const uint32_t* qx, uint32_t* qy)
 {
@@ -1511,7 +1511,7 @@ static void mala_mutate(or_ctx* c, uint32_t chain, double xi)
     splat(c, chain);
 }
 
-/* One Metropolis-Hastings mutation of chain `chain` (Alg. 1 lines 8-12, 19). */
+/* One Metropolis-Hastings mutation of chain `chain` (Alg. 1, mutation step). */
 static void mutate(or_ctx* c, uint32_t chain)
 {
     int32_t D = c->D;
@@ -1557,7 +1557,7 @@ static void mutate(or_ctx* c, uint32_t chain)
         c->Bk[ky] += piy;
         c->nU++;
     } else {
-        /* adaptation statistics of the current state's region (Alg. 1 l. 11-12) */
+        /* adaptation statistics of the current state's region (Alg. 1, acceptance statistics) */
         c->st[3]++;
         c->i[kx] += 1;
         c->A[kx] += (uint64_t)llrint(a * 4294967296.0);
@@ -1579,7 +1579,7 @@ static void mutate(or_ctx* c, uint32_t chain)
     splat(c, chain);
 }
 
-/* Region-parameter update at an epoch boundary (Alg. 1 lines 13-18).
+/* Region-parameter update at an epoch boundary (Alg. 1, region update).
  * Reading: the trigger is i_k >= L and alpha_hat = A_k / i_k, which equals
  * eq. est_exp_acc (Alg. 1 tests i_k > L but divides by L).  The update follows
  * eq. update_lambda as printed: lambda grows when the acceptance estimate is
@@ -1686,7 +1686,7 @@ int32_t or_init(or_ctx* c)
     return or_init_tables(c);
 }
 
-/* Alg. 1 lines 2-6: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
+/* Alg. 1, initialisation: lambda_k = initial scale, i_k = A_k = 0, n_k = 1 */
 int32_t or_init_tables(or_ctx* c)
 {
     if (c->p.partition == 1) {
@@ -1741,7 +1741,7 @@ int32_t or_mutate_one(or_ctx* c, uint32_t chain, uint64_t mut)
     return 0;
 }
 
-/* E mutations of every chain of this context (Alg. 1 lines 8-12, 19) */
+/* E mutations of every chain of this context (Alg. 1, mutation step) */
 static void epoch_mutations(or_ctx* c)
 {
     uint64_t mut0 = c->mut;
@@ -1755,7 +1755,7 @@ static void epoch_mutations(or_ctx* c)
     c->mut = mut0 + (uint64_t)c->p.epoch_len;
 }
 
-/* the epoch boundary: Alg. 1 lines 13-18, the weighted target's weights, and
+/* the epoch boundary: Alg. 1, region update, the weighted target's weights, and
  * a quadtree pass every qt_refine mutations of the whole population */
 static void epoch_boundary(or_ctx* c)
 {

@@ -164,7 +164,7 @@ void     or_set_prop_hook(or_ctx* c, or_prop_hook ph);
  * m_y,d| / tau_y, the sensitivity of ln a to relative errors of the drifts. */
 void     or_last_mala(const or_ctx* c, double* m, double* z, double out2[2]);
 int32_t  or_init(or_ctx* c);                       /* bootstrap + initial states */
-int32_t  or_init_tables(or_ctx* c);                /* region tables only (Alg. 1 lines 2-6) */
+int32_t  or_init_tables(or_ctx* c);                /* region tables only (Alg. 1, initialisation) */
 void     or_refresh_sigma(or_ctx* c);              /* sigma_k from the current lambda_k */
 /* Set chain `chain` to state q; f, pi and k are recomputed by the oracle. */
 int32_t  or_set_state(or_ctx* c, uint32_t chain, const uint32_t* q);
@@ -177,7 +177,7 @@ int32_t  or_run_epochs(or_ctx* c, int64_t n_epochs);
  * of large steps; sums [cap] = the sum of pi over large-step proposals per
  * region.  or_epoch_update takes those arrays summed over every context of
  * the population, sets each table to its value at the start of the epoch
- * plus the sums, and runs the epoch boundary (Alg. 1 lines 13-18, weights,
+ * plus the sums, and runs the epoch boundary (Alg. 1, region update, weights,
  * quadtree).  cap = or_region_capacity(). */
 int32_t  or_epoch_mutate(or_ctx* c, uint64_t* counts, double* sums);
 int32_t  or_epoch_update(or_ctx* c, const uint64_t* counts, const double* sums);

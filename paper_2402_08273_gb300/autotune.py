@@ -20,9 +20,8 @@ CANDIDATES = (
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "short_stack": True},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 4},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 12},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 16},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 2},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 8},
 )
 
 
@@ -32,7 +31,7 @@ def apply(R, cand: dict) -> None:
         R.set_tuning(batch_shade=cand.get("batch_shade", 12), batch_setup=cand.get("batch_setup", 10))
     else:
         R.set_tuning(wavefront=True)
-        R.set_trace_leaf_batch(cand.get("leaf_batch", 8))
+        R.set_trace_leaf_batch(cand.get("leaf_batch", 4))
         R.set_wavefront(trace_ctas_per_sm=cand.get("trace_ctas_per_sm", 0),
                         setup_ctas_per_sm=cand.get("setup_ctas_per_sm", 0),
                         refill_lanes=cand.get("refill_lanes", 16), short_stack=cand.get("short_stack", False),

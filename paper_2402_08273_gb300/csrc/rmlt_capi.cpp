@@ -102,7 +102,7 @@ struct rmlt_ctx {
     uint64_t since_refine = 0;   // mutations since the last quadtree pass
     int batch_shade = 12, batch_setup = 10;
     int large_ahead = 0, adaptive_batch = 0;
-    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0, wf_leaf_batch = kLeafBatch;
+    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0, wf_leaf_batch = kWfLeafBatch;
     unsigned wave_limit = 0;     // waves per epoch before the wavefront form stops (0: its default)
     bool wf_ran = false;         // an epoch ran in the wavefront form since the chains were set up
     uint64_t wave_hits_seen = 0; // epochs stopped by the wave limit, as of the last check
@@ -708,7 +708,7 @@ rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* pin)
     return RMLT_OK;
 }
 
-// One epoch's chain kernel (Alg. 1 lines 8-12, 19 for every chain).
+// One epoch's chain kernel (Alg. 1, mutation step for every chain).
 static rmlt_status epoch_kernels(rmlt_ctx* c)
 {
     const uint64_t E = (uint64_t)c->Ch.E;
@@ -755,7 +755,7 @@ static rmlt_status epoch_kernels(rmlt_ctx* c)
     return RMLT_OK;
 }
 
-// The epoch boundary (Alg. 1 lines 13-18), a due quadtree pass, the trace
+// The epoch boundary (Alg. 1, region update), a due quadtree pass, the trace
 // instrument's lambda record; the epoch is then complete.
 static rmlt_status epoch_boundary(rmlt_ctx* c)
 {

@@ -237,8 +237,15 @@ __device__ __forceinline__ bool step_turn(bool live, const Trav& T, int leaf_bat
 // memory and the rest in a per-thread area of global memory (entry j of the
 // thread at gl[(j - SS) * gstride]), which leaves more of the SM's memory to
 // the L1 cache.  Both hold kStackSize entries; the traversal is the same.
-__device__ __forceinline__ void stk_push(uint32_t* s, int sp, uint32_t v) { s[kStackStride * sp] = v; }
-__device__ __forceinline__ uint32_t stk_pop(uint32_t* s, int sp) { return s[kStackStride * sp]; }
+// stk_push takes the distance at which the ray enters the entry's box and
+// stk_next the current bound on the closest hit, for a stack that would drop
+// entries beyond it; neither stack keeps them (the keys cost more time than
+// the node visits they save).
+__device__ __forceinline__ void stk_push(uint32_t* s, int sp, uint32_t v, float) { s[kStackStride * sp] = v; }
+__device__ __forceinline__ uint32_t stk_next(uint32_t* s, int& sp, float)
+{
+    return sp > 0 ? s[kStackStride * --sp] : kNoRef;
+}
 
 template <int SS>
 struct SplitStack {
@@ -247,14 +254,16 @@ struct SplitStack {
     unsigned gstride;  // words between a thread's consecutive global entries
 };
 template <int SS>
-__device__ __forceinline__ void stk_push(const SplitStack<SS>& s, int sp, uint32_t v)
+__device__ __forceinline__ void stk_push(const SplitStack<SS>& s, int sp, uint32_t v, float)
 {
     if (sp < SS) s.sh[kStackStride * sp] = v;
     else s.gl[(size_t)(sp - SS) * s.gstride] = v;
 }
 template <int SS>
-__device__ __forceinline__ uint32_t stk_pop(const SplitStack<SS>& s, int sp)
+__device__ __forceinline__ uint32_t stk_next(const SplitStack<SS>& s, int& sp, float)
 {
+    if (sp == 0) return kNoRef;
+    --sp;
     return sp < SS ? s.sh[kStackStride * sp] : s.gl[(size_t)(sp - SS) * s.gstride];
 }
 
@@ -328,12 +337,12 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
 #pragma unroll
         for (int k = 3; k >= 1; --k) {
             if (key[k] != INFINITY) {
-                if (T.sp < kStackSize) stk_push(stack, T.sp++, cr[k]);
+                if (T.sp < kStackSize) stk_push(stack, T.sp++, cr[k], key[k]);
                 else T.overflow = 1;
             }
         }
 
-        next = key[0] != INFINITY ? cr[0] : (T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef);
+        next = key[0] != INFINITY ? cr[0] : stk_next(stack, T.sp, tcap);
     } else if (!(ref & kLeafBit)) {
         ++n_nodes;
         const float4 n0 = __ldg(&S.nodes[4 * ref + 0]);
@@ -356,7 +365,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
         const uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
         if (h0 && h1) {
             const bool first0 = tn0 <= tn1;
-            if (T.sp < kStackSize) stk_push(stack, T.sp++, first0 ? c1 : c0);
+            if (T.sp < kStackSize) stk_push(stack, T.sp++, first0 ? c1 : c0, first0 ? tn1 : tn0);
             else T.overflow = 1;
             next = first0 ? c0 : c1;
         } else if (h0) {
@@ -364,7 +373,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
         } else if (h1) {
             next = c1;
         } else {
-            next = T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef;
+            next = stk_next(stack, T.sp, tcap);
         }
     } else {
         const uint32_t first = ref & 0x0FFFFFFFu, cnt = ((ref >> 28) & 7u) + 1u;
@@ -397,7 +406,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
                 }
             }
         }
-        next = (T.any && found) ? kNoRef : (T.sp > 0 ? stk_pop(stack, --T.sp) : kNoRef);
+        next = (T.any && found) ? kNoRef : stk_next(stack, T.sp, T.t * 1.00000036f);
     }
     T.ref = T.overflow ? kNoRef : next;
     return T.ref == kNoRef;
@@ -789,7 +798,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
 }
 
 // ---------------------------------------------------------------------------
-// the chain step: E mutations per chain (Alg. 1 lines 8-19)
+// the chain step: E mutations per chain (Alg. 1, mutation loop)
 // ---------------------------------------------------------------------------
 struct ChainLane {
     // cached current state x
@@ -934,8 +943,8 @@ __device__ __forceinline__ void mala_setup(const DevScene& S, const DevChains& C
         for (int d = 0; d < D; ++d) Ch.G[(size_t)d * C + c] = gy[d];
 }
 
-// Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1 line
-// 10) and decide the reverse-kernel support; returns false when the proposal
+// Draw the proposal y of mutation mut0 + j (large or small step, Alg. 1,
+// proposal) and decide the reverse-kernel support; returns false when the proposal
 // needs no path (rejected early, or the toy integrand evaluated directly).
 template <bool MALA = false, bool BRUTE = false, bool D4 = false, class Y>
 __device__ __forceinline__ bool mutation_setup(const DevScene& S, const DevChains& Ch, int c, uint64_t mut0,
@@ -1092,12 +1101,12 @@ __device__ __forceinline__ void flush_state(const DevChains& Ch, ChainLane& L)
 }
 
 // acceptance (Sec. 3.2 with the mixture of Sec. 5.2), adaptation statistics
-// of the current region (Alg. 1 lines 11-12), MH update (line 19), splat
+// of the current region (Alg. 1, acceptance statistics), MH update (Alg. 1, state update), splat
 template <bool TRACE, bool MALA = false, class Y>
 __device__ __forceinline__ void mutation_finish(const DevChains& Ch, int c, bool traced, ChainLane& L,
                                                 Y y, unsigned (&st)[7])
 {
-    const int C = Ch.C, D = Ch.D;
+    const int D = Ch.D;
     V3 fy = L.fy;
     float piy = lum(fy.x, fy.y, fy.z);
     int invalid = 0;

@@ -18,6 +18,7 @@ constexpr int kEpochBlock = 64;                     // threads per block of the 
 constexpr int kStackStride = 64;                    // traversal stacks: panels of 64 threads, one column each
 static_assert(kChainBlock % kStackStride == 0 && kEpochBlock % kStackStride == 0, "stack panels");
 constexpr int kLeafBatch = 8;                       // lanes of a warp at leaves before they test them together
+constexpr int kWfLeafBatch = 4;                     // ... in the wavefront form's trace kernel (measured)
 
 // statistic slots in DevChains::stats
 enum StatSlot {
@@ -162,7 +163,7 @@ struct DevWave {
     unsigned long long cond = 0;  // cudaGraphConditionalHandle of the wave loop
     unsigned wave_cap = 0;        // E (max_depth + 1) + 2: more waves than any epoch needs
     int refill = 16;              // idle lanes of a trace warp that pull new rays together
-    int leaf_batch = kLeafBatch;  // lanes of a trace warp at leaves before they test them together
+    int leaf_batch = kWfLeafBatch;  // lanes of a trace warp at leaves before they test them together
     int short_stack = 0;          // 1: the trace kernel keeps kShortStack stack entries per ray in shared
                                   //    memory and the rest in `gstack`
     uint32_t* gstack = nullptr;   // [kStackSize - kShortStack][kWfTraceThreadsPerSm x SMs]

@@ -1,6 +1,6 @@
 // CUDA kernels of librmlt (sm_103a): the regional adaptive PSS-MLT chain step.
 //
-// One thread owns one chain for an epoch of E mutations (Alg. 1 lines 8-19).
+// One thread owns one chain for an epoch of E mutations (Alg. 1, mutation loop).
 // Each loop iteration traces exactly one ray (camera/extension closest hit,
 // or a next-event shadow any-hit), so the threads of a warp meet at the same
 // traversal code whatever mutation or bounce each one is at.  Chain state is
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kChainBlock) large_trace_kernel(const DevScene
 }
 
 // ---------------------------------------------------------------------------
-// region update at the epoch boundary (Alg. 1 lines 13-18; eqs.
+// region update at the epoch boundary (Alg. 1, region update; eqs.
 // est_exp_acc, update_lambda, step_size_n), binary64 with explicit rounding
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void region_update_body(const DevChains& Ch, int init_only)

@@ -13,8 +13,8 @@
 //           shadow and extension rays, or hand the chain to `setup` when its
 //           path has ended;
 //   setup   persistent, over the chains whose path ended (all chains in the
-//           first wave): accept or reject (Sec. 3.2, Alg. 1 lines 11-12, 19),
-//           then draw the next proposal (Alg. 1 line 10) and queue its camera
+//           first wave): accept or reject (Sec. 3.2, Alg. 1, acceptance statistics and state update),
+//           then draw the next proposal (Alg. 1, proposal) and queue its camera
 //           ray; proposals that need no path finish at once;
 //   trace   persistent, one ray per lane: lanes whose ray is resolved pull
 //           new rays from the queue together, so warps stay full until the
@@ -141,9 +141,10 @@ __device__ __forceinline__ void append_rays(const DevWave& W, int C, unsigned bu
     if (lane == 31 && total > 0) base = atomicAdd(&W.ctr->cnt[buf], (unsigned)total);
     base = __shfl_sync(FULL, base, 31);
     const unsigned at = base + (unsigned)(incl - n), cap = 2u * (unsigned)C;
-    float4* q = W.rq[buf];
-    for (int i = 0; i < n; ++i) {
-        if (at + i < cap) {
+    float4* q = buf ? W.rq[1] : W.rq[0];   // a runtime index would copy W to local memory
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {   // constant indices keep r in registers
+        if (i < n && at + i < cap) {
             q[2 * (size_t)(at + i)] = r[2 * i];
             q[2 * (size_t)(at + i) + 1] = r[2 * i + 1];
         }
@@ -268,8 +269,13 @@ __global__ void __launch_bounds__(kChainBlock, 8) wf_shade_kernel(const DevScene
                 }
                 if (emit & 2) {
                     s.setv(kWP, p.P);
-                    r[2 * nr] = sh0;
-                    r[2 * nr + 1] = sh1;
+                    if (nr) {   // constant indices keep r in registers
+                        r[2] = sh0;
+                        r[3] = sh1;
+                    } else {
+                        r[0] = sh0;
+                        r[1] = sh1;
+                    }
                     ++nr;
                 }
             } else {
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     if (BRUTE) stage_triangles(S, s_tris);
     const unsigned FULL = 0xFFFFFFFFu;
     const unsigned cap = 2u * (unsigned)C, n = min(W.ctr->trace_n, cap), buf = W.ctr->trace_buf;
-    const float4* q = W.rq[buf];
+    const float4* q = buf ? W.rq[1] : W.rq[0];
     unsigned* pull = &W.ctr->fetch[buf];
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -419,9 +425,10 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     uint32_t* col = s_stack + (threadIdx.x / kStackStride) * (SS * kStackStride) + threadIdx.x % kStackStride;
     typename StackFor<SS>::type stack;
     if constexpr (SS < kStackSize) {
+        const size_t nthr = (size_t)gridDim.x * blockDim.x, g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
         stack.sh = col;
-        stack.gl = W.gstack + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-        stack.gstride = gridDim.x * blockDim.x;
+        stack.gl = W.gstack + g;
+        stack.gstride = (unsigned)nthr;
     } else {
         stack = col;
     }
@@ -513,6 +520,7 @@ int sm_count()
     return n > 0 ? n : 1;
 }
 
+// the deeper entries of every trace thread
 size_t gstack_words() { return (size_t)(kStackSize - kShortStack) * kWfTraceThreadsPerSm * (size_t)sm_count(); }
 }  // namespace
 

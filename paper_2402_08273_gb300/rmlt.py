@@ -296,7 +296,7 @@ class Renderer:
     def epoch_update(self, counts, sums):
         _check(lib().rmlt_epoch_update(self.h, _ptr(counts), _ptr(sums)))
 
-    def set_trace_leaf_batch(self, leaf_batch: int = 8):
+    def set_trace_leaf_batch(self, leaf_batch: int = 4):
         _check(lib().rmlt_set_trace_leaf_batch(self.h, int(leaf_batch)))
 
     def set_wave_limit(self, waves: int = 0):

@@ -11,7 +11,8 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
     """Initialise, trace `n_epochs` epochs of every `stride`-th chain, and
     return the trace together with the initial and final state.  `tuning`
     (keyword arguments of Renderer.set_tuning) and `wavefront` (of
-    Renderer.set_wavefront) select the execution form."""
+    Renderer.set_wavefront, and `leaf_batch` of set_trace_leaf_batch) select
+    the execution form."""
     import torch
     R = rmlt.Renderer()
     if toy is not None:
@@ -21,6 +22,9 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
     if tuning:
         R.set_tuning(**tuning)
     if wavefront:
+        wavefront = dict(wavefront)
+        if "leaf_batch" in wavefront:
+            R.set_trace_leaf_batch(wavefront.pop("leaf_batch"))
         R.set_wavefront(**wavefront)
     R.init_chains(**params)
     p = R.params

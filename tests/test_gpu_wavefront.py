@@ -97,7 +97,8 @@ def test_wavefront_identical_quadtree():
 @pytest.mark.parametrize("shape", [{"trace_ctas_per_sm": 1, "setup_ctas_per_sm": 1, "refill_lanes": 1},
                                    {"trace_ctas_per_sm": 3, "setup_ctas_per_sm": 0, "refill_lanes": 32},
                                    {"host_loop": True}, {"short_stack": True},
-                                   {"short_stack": True, "host_loop": True}])
+                                   {"short_stack": True, "host_loop": True}, {"leaf_batch": 1},
+                                   {"leaf_batch": 32, "short_stack": True}])
 def test_wavefront_launch_shape_changes_nothing(shape):
     from gpu_run import traced_run
     kw = dict(scene=S.two_rooms(5_000, seed=3), n_epochs=2, n_chains=1000, width=64, height=64, region_px=8,

@@ -5,7 +5,7 @@ by the global id, every rank drawing the whole bootstrap).  Each epoch every
 rank runs its chains, the region statistics the epoch added (i_k, A_k, h_k
 and the large-step count as integers; the large-step sums of pi per region as
 doubles) are summed over ranks by an all-reduce, and every rank runs the same
-epoch boundary (Alg. 1 lines 13-18) on the summed tables -- the paper's
+epoch boundary (Alg. 1, region update) on the summed tables -- the paper's
 threads share i_k and A_k the same way (Sec. 6).  Here each rank runs the CPU
 oracle's shard through bench.py's own epoch loop (`step_sharded`), and the
 result must equal one unsharded oracle run bit for bit: region tables, lambda,

@@ -131,9 +131,10 @@ def test_lambda_trajectory_closed_form(oracle_mod):
 
 def test_sequential_alg1_special_case(oracle_mod):
     """One chain and one mutation per epoch reduce the epoch-parallel update to
-    the sequential Algorithm 1 (with the i_k >= L reading).  The test keeps its
-    own literal transcription of Alg. 1 lines 8-18 from the observed
-    proposals and compares lambda_k, n_k, i_k after every mutation."""
+    the sequential Algorithm 1 (with the i_k >= L reading).  The test restates
+    Algorithm 1's acceptance statistics, region update and state update in its
+    own code, driven by the observed proposals, and compares lambda_k, n_k,
+    i_k after every mutation."""
     sc = oracle_mod.Scene(toy=TOY)
     L = 10
     ch = oracle_mod.Chains(sc, n_chains=1, width=64, height=64, region_px=16, max_depth=0,
@@ -158,17 +159,17 @@ def test_sequential_alg1_special_case(oracle_mod):
         ch.run_epochs(1)
         large, a, acc, y = seen[0]
         k = ch.region_of(state["x"])
-        if not large:                      # Alg. 1 lines 11-12 (small steps)
+        if not large:                      # Alg. 1, acceptance statistics (small steps)
             Ak[k] += a
             ik[k] += 1
-            if ik[k] >= L:                 # lines 13-18
+            if ik[k] >= L:                 # Alg. 1, region update
                 ahat = Ak[k] / ik[k]
                 g = min(1.0, 5.0 / math.sqrt(nk[k]))
                 lam[k] = min(lmax, max(-30.0, lam[k] + g * np.sign(ahat - 0.5)))
                 ik[k] = 0
                 Ak[k] = 0.0
                 nk[k] += 1
-        if acc:                            # line 19
+        if acc:                            # Alg. 1, state update
             state["x"] = y
         assert np.array_equal(ch.q[0], state["x"])
         np.testing.assert_allclose(ch.lam, lam, rtol=0, atol=1e-12)
