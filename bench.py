@@ -41,14 +41,16 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-# FP32 operations the traversal needs per BVH4 node visit (four child boxes:
-# 6 FMA + 6 min + 6 max per slab test, one compare each, and a 5-comparator
-# sort) and per ray-triangle test (Moller-Trumbore: two cross products, three
-# dot products, sign scaling, 5 compares, one division for a hit); an FMA
-# counts as 2 floating-point operations.
-FLOPS_PER_NODE = 4 * (6 * 2 + 12 + 1) + 5 * 2   # 110
+# FP32 operations the traversal needs per BVH4 node visit (the node grid's
+# three scales and offsets along the ray, 3 mul + 3 FMA; four child boxes:
+# 6 grid-index decodes (an add each), 6 FMA + 6 min + 6 max per slab test,
+# one compare each; a 5-comparator sort) and per ray-triangle test
+# (Moller-Trumbore: two cross products, three dot products, sign scaling, 5
+# compares, one division for a hit); an FMA counts as 2 floating-point
+# operations.
+FLOPS_PER_NODE = 3 + 3 * 2 + 4 * (6 + 6 * 2 + 12 + 1) + 5 * 2   # 143
 FLOPS_PER_TRI = 2 * (6 * 2) + 3 * 5 + 3 + 5 + 1  # 48
-BYTES_PER_NODE = 128   # BVH4 node: six float4 of child bounds, one of child refs, one unused
+BYTES_PER_NODE = 64    # BVH4 node: the node grid, the children's 8-bit grid boxes, their refs
 BYTES_PER_TRI = 48
 SM_COUNT = 152
 FP32_LANES = 128

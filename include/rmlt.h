@@ -380,7 +380,7 @@ rmlt_status rmlt_set_tuning(rmlt_ctx* ctx, int batch_shade, int batch_setup, int
  * pull new rays together (1..32).  flags: RMLT_WAVEFRONT_HOST_LOOP launches
  * the waves from the host (a fixed E (max_depth + 1) + 2 waves per epoch, the
  * surplus ones empty) instead of the graph's device-side loop; profilers that
- * cannot see into conditional graphs need it.  Speed only.  Defaults 0, 0, 16,
+ * cannot see into conditional graphs need it.  Speed only.  Defaults 0, 0, 8,
  * 0. */
 #define RMLT_WAVEFRONT_HOST_LOOP 1
 /* RMLT_WAVEFRONT_SHORT_STACK: the persistent trace kernel keeps 16 of each
@@ -401,7 +401,7 @@ rmlt_status rmlt_set_wave_limit(rmlt_ctx* ctx, uint32_t waves);
 
 /* Leaf turns of the wavefront form's trace kernel: a warp's lanes whose ray
  * waits at a BVH leaf test its triangles together once at least leaf_batch
- * of them are there (1..32; default 4).  Speed only. */
+ * of them are there (1..32; default 8).  Speed only. */
 rmlt_status rmlt_set_trace_leaf_batch(rmlt_ctx* ctx, int leaf_batch);
 
 /* Bootstrap without any device allocation.  Some callers cannot allocate

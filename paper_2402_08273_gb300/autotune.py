@@ -17,11 +17,12 @@ CANDIDATES = (
     {"form": "chain", "batch_shade": 12, "batch_setup": 12},
     {"form": "chain", "batch_shade": 8, "batch_setup": 10},
     {"form": "chain", "batch_shade": 16, "batch_setup": 10},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
     {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "short_stack": True},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 2},
-    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16, "leaf_batch": 8},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 6},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 16},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8, "short_stack": True},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8, "leaf_batch": 6},
+    {"form": "wavefront", "trace_ctas_per_sm": 0, "refill_lanes": 8, "leaf_batch": 10},
 )
 
 
@@ -31,10 +32,10 @@ def apply(R, cand: dict) -> None:
         R.set_tuning(batch_shade=cand.get("batch_shade", 12), batch_setup=cand.get("batch_setup", 10))
     else:
         R.set_tuning(wavefront=True)
-        R.set_trace_leaf_batch(cand.get("leaf_batch", 4))
+        R.set_trace_leaf_batch(cand.get("leaf_batch", 8))
         R.set_wavefront(trace_ctas_per_sm=cand.get("trace_ctas_per_sm", 0),
                         setup_ctas_per_sm=cand.get("setup_ctas_per_sm", 0),
-                        refill_lanes=cand.get("refill_lanes", 16), short_stack=cand.get("short_stack", False),
+                        refill_lanes=cand.get("refill_lanes", 8), short_stack=cand.get("short_stack", False),
                         host_loop=cand.get("host_loop", False))
 
 

@@ -12,11 +12,21 @@
 //   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   n3 = (ref c0, ref c1, 0, 0)                      (uint bits)
-// BVH4 (8 float4 per node, children in the four lanes of each float4):
-//   lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, refs (uint bits), unused
+// BVH4 (4 float4 per node, the children's boxes quantised to 8 bits on a
+// per-node grid):
+//   n0 = (p.x, p.y, p.z, s.x)
+//   n1 = (s.y, s.z, qlo.z, qhi.z)                    (q words as uint bits)
+//   n2 = (qlo.x, qhi.x, qlo.y, qhi.y)
+//   n3 = (ref c0, ref c1, ref c2, ref c3)            (uint bits)
+// Byte k of a q word belongs to child k; child k's box on axis a is
+// [p.a + qlo.a[k] s.a, p.a + qhi.a[k] s.a] in exact arithmetic.  p is the
+// lower corner of the union of the children's boxes and s.a = its extent on
+// axis a / 255, rounded up, so every grid value lies in the node; lo planes
+// are rounded down and hi planes up, so each decoded box contains the
+// child's box.
 // A ref is an internal node index, a leaf (kLeafBit | (count-1) << 28 |
-// first triangle in build order), or kEmptyRef for an unused BVH4 slot, whose
-// box is inverted (lo = +inf, hi = -inf) so that no slab test accepts it.
+// first triangle in build order), or kEmptyRef for an unused BVH4 slot (its q
+// bytes 255 / 0: an inverted box; the traversal skips it by the reference).
 // Boxes are widened by `pad` and rounded outward so that binary32 traversal
 // never culls a box a ray grazes.
 #include <algorithm>
@@ -214,28 +224,62 @@ struct Emitter {
             ch[pick] = c.left;
             ch[nc++] = c.right;
         }
-        const uint32_t id = (uint32_t)(out.size() / 8);
-        out.resize(out.size() + 8);
+        const uint32_t id = (uint32_t)(out.size() / 4);
+        out.resize(out.size() + 4);
         uint32_t refs[4] = {kEmptyRef, kEmptyRef, kEmptyRef, kEmptyRef};
         Box boxes[4];
-        for (int k = 0; k < 4; ++k) {
-            // an unused slot gets an inverted infinite box, which every slab
-            // test rejects whatever the ray's direction
-            for (int a = 0; a < 3; ++a) { boxes[k].lo[a] = INFINITY; boxes[k].hi[a] = -INFINITY; }
-            if (k < nc) {
-                refs[k] = emit4(ch[k]);
-                boxes[k] = padded(bn[(size_t)ch[k]].box);
+        for (int k = 0; k < nc; ++k) {
+            refs[k] = emit4(ch[k]);
+            boxes[k] = padded(bn[(size_t)ch[k]].box);
+        }
+        float p[3], s[3];
+        uint32_t qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+            float lo = INFINITY, hi = -INFINITY;
+            for (int k = 0; k < nc; ++k) { lo = std::min(lo, boxes[k].lo[a]); hi = std::max(hi, boxes[k].hi[a]); }
+            p[a] = lo;
+            s[a] = grid_step((double)hi - (double)lo);
+            for (int k = 0; k < 4; ++k) {
+                uint32_t l = 255u, h = 0u;   // an unused slot: inverted
+                if (k < nc) {
+                    l = quantise(p[a], s[a], boxes[k].lo[a], false);
+                    h = quantise(p[a], s[a], boxes[k].hi[a], true);
+                }
+                qlo[a] |= l << (8 * k);
+                qhi[a] |= h << (8 * k);
             }
         }
-        float4* nd = &out[8 * (size_t)id];
-        for (int a = 0; a < 3; ++a) {
-            nd[2 * a] = make_float4(boxes[0].lo[a], boxes[1].lo[a], boxes[2].lo[a], boxes[3].lo[a]);
-            nd[2 * a + 1] = make_float4(boxes[0].hi[a], boxes[1].hi[a], boxes[2].hi[a], boxes[3].hi[a]);
-        }
-        nd[6] = make_float4(bitsf(refs[0]), bitsf(refs[1]), bitsf(refs[2]), bitsf(refs[3]));
-        nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4* nd = &out[4 * (size_t)id];
+        nd[0] = make_float4(p[0], p[1], p[2], s[0]);
+        nd[1] = make_float4(s[1], s[2], bitsf(qlo[2]), bitsf(qhi[2]));
+        nd[2] = make_float4(bitsf(qlo[0]), bitsf(qhi[0]), bitsf(qlo[1]), bitsf(qhi[1]));
+        nd[3] = make_float4(bitsf(refs[0]), bitsf(refs[1]), bitsf(refs[2]), bitsf(refs[3]));
         --depth;
         return id;
+    }
+
+    // the grid step of an axis whose children span `extent`: extent / 255
+    // rounded up to a float (1 for a flat axis, where every plane is p)
+    static float grid_step(double extent)
+    {
+        if (!(extent > 0.0)) return 1.0f;
+        float s = (float)(extent / 255.0);
+        while ((double)s * 255.0 < extent) s = std::nextafter(s, INFINITY);
+        return s;
+    }
+    // the grid index of plane x: the largest with p + q s <= x (a lower
+    // plane) or the smallest with p + q s >= x (an upper plane), in 0..255
+    static uint32_t quantise(float p, float s, float x, bool upper)
+    {
+        const double d = ((double)x - (double)p) / (double)s;
+        long q = upper ? (long)std::ceil(d) : (long)std::floor(d);
+        q = std::max(0L, std::min(255L, q));
+        if (upper) {
+            while (q < 255 && (double)p + (double)q * (double)s < (double)x) ++q;
+        } else {
+            while (q > 0 && (double)p + (double)q * (double)s > (double)x) --q;
+        }
+        return (uint32_t)q;
     }
 };
 

@@ -102,7 +102,7 @@ struct rmlt_ctx {
     uint64_t since_refine = 0;   // mutations since the last quadtree pass
     int batch_shade = 12, batch_setup = 10;
     int large_ahead = 0, adaptive_batch = 0;
-    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 16, wf_flags = 0, wf_leaf_batch = kWfLeafBatch;
+    int wavefront = 0, wf_trace_cps = 0, wf_setup_cps = 0, wf_refill = 8, wf_flags = 0, wf_leaf_batch = kLeafBatch;
     unsigned wave_limit = 0;     // waves per epoch before the wavefront form stops (0: its default)
     bool wf_ran = false;         // an epoch ran in the wavefront form since the chains were set up
     uint64_t wave_hits_seen = 0; // epochs stopped by the wave limit, as of the last check
@@ -399,7 +399,7 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     S.light_tri = d_lt;
     S.light_cdf = d_lc;
     S.n_tris = nt;
-    S.n_nodes = (int32_t)(bvh.nodes.size() / (width == 4 ? 8 : 4));
+    S.n_nodes = (int32_t)(bvh.nodes.size() / 4);
     S.bvh4 = width == 4 ? 1 : 0;
     S.n_mats = s->n_mats;
     S.n_lights = (int32_t)ltri.size();

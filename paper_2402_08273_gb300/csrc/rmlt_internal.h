@@ -18,7 +18,6 @@ constexpr int kEpochBlock = 64;                     // threads per block of the 
 constexpr int kStackStride = 64;                    // traversal stacks: panels of 64 threads, one column each
 static_assert(kChainBlock % kStackStride == 0 && kEpochBlock % kStackStride == 0, "stack panels");
 constexpr int kLeafBatch = 8;                       // lanes of a warp at leaves before they test them together
-constexpr int kWfLeafBatch = 4;                     // ... in the wavefront form's trace kernel (measured)
 
 // statistic slots in DevChains::stats
 enum StatSlot {
@@ -46,9 +45,11 @@ constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kEmptyRef = 0xFFFFFFFEu;
 
 // Device view of a loaded scene.  Triangles: 3 float4 each (v0 | mat id bits,
-// e1 | original index bits, e2 | 0); nodes: 4 float4 each (child 0 x/y
-// bounds, child 1 x/y bounds, both z bounds, child refs); materials: 3 float4
-// each (albedo | type, emission | roughness, emissive flag | black flag).
+// e1 | original index bits, e2 | 0); nodes: 4 float4 each (BVH2: child 0 x/y
+// bounds, child 1 x/y bounds, both z bounds, child refs; BVH4: a node grid
+// and the four children's boxes as 8-bit grid indices, then their refs, as
+// bvh_build.cpp describes); materials: 3 float4 each (albedo | type,
+// emission | roughness, emissive flag | black flag).
 struct DevScene {
     const float4* tris = nullptr;
     const float4* nodes = nullptr;
@@ -56,7 +57,7 @@ struct DevScene {
     const int32_t* light_tri = nullptr;
     const float* light_cdf = nullptr;
     int32_t n_tris = 0, n_nodes = 0, n_mats = 0, n_lights = 0, brute = 1;
-    int32_t bvh4 = 1;                 // node layout: 1 = BVH4 (8 float4), 0 = BVH2 (4 float4)
+    int32_t bvh4 = 1;                 // node layout (4 float4 each): 1 = quantised BVH4, 0 = BVH2
     float light_area = 0.f;
     float cam_pos[3] = {0, 0, 0}, cam_fwd[3] = {0, 0, 1}, cam_right[3] = {1, 0, 0}, cam_up[3] = {0, 1, 0};
     float tan_x = 1.f, tan_y = 1.f;   // tan(vfov / 2) * aspect, tan(vfov / 2)
@@ -162,8 +163,8 @@ struct DevWave {
     WfCounters* ctr = nullptr;
     unsigned long long cond = 0;  // cudaGraphConditionalHandle of the wave loop
     unsigned wave_cap = 0;        // E (max_depth + 1) + 2: more waves than any epoch needs
-    int refill = 16;              // idle lanes of a trace warp that pull new rays together
-    int leaf_batch = kWfLeafBatch;  // lanes of a trace warp at leaves before they test them together
+    int refill = 8;               // idle lanes of a trace warp that pull new rays together
+    int leaf_batch = kLeafBatch;  // lanes of a trace warp at leaves before they test them together
     int short_stack = 0;          // 1: the trace kernel keeps kShortStack stack entries per ray in shared
                                   //    memory and the rest in `gstack`
     uint32_t* gstack = nullptr;   // [kStackSize - kShortStack][kWfTraceThreadsPerSm x SMs]
@@ -262,7 +263,7 @@ cudaError_t noalloc_scratch(int device, NoAllocScratch& out);
 
 // host-side BVH build (bvh_build.cpp)
 struct HostBVH {
-    std::vector<float4> nodes;    // 4 (BVH2) or 8 (BVH4) per node
+    std::vector<float4> nodes;    // 4 per node (BVH2, or quantised BVH4)
     std::vector<uint32_t> order;  // triangle order after the build
     int width = 4;
     int max_depth = 0;

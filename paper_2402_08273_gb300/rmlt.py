@@ -296,7 +296,7 @@ class Renderer:
     def epoch_update(self, counts, sums):
         _check(lib().rmlt_epoch_update(self.h, _ptr(counts), _ptr(sums)))
 
-    def set_trace_leaf_batch(self, leaf_batch: int = 4):
+    def set_trace_leaf_batch(self, leaf_batch: int = 8):
         _check(lib().rmlt_set_trace_leaf_batch(self.h, int(leaf_batch)))
 
     def set_wave_limit(self, waves: int = 0):
@@ -374,7 +374,7 @@ class Renderer:
         flags = (1 if large_ahead else 0) | (2 if adaptive_batch else 0) | (4 if wavefront else 0)
         _check(lib().rmlt_set_tuning(self.h, int(batch_shade), int(batch_setup), flags))
 
-    def set_wavefront(self, trace_ctas_per_sm: int = 0, setup_ctas_per_sm: int = 0, refill_lanes: int = 16,
+    def set_wavefront(self, trace_ctas_per_sm: int = 0, setup_ctas_per_sm: int = 0, refill_lanes: int = 8,
                       host_loop: bool = False, short_stack: bool = False):
         flags = (1 if host_loop else 0) | (2 if short_stack else 0)
         _check(lib().rmlt_set_wavefront(self.h, int(trace_ctas_per_sm), int(setup_ctas_per_sm),

@@ -5,9 +5,10 @@
 //   - the leaves cover every position of that order exactly once and hold at
 //     most `leaf_max` triangles;
 //   - every vertex of a leaf's triangles lies inside every box on the path
-//     from the root (the boxes are conservative);
-//   - an unused BVH4 slot has the empty reference and an inverted infinite
-//     box, so every slab test rejects it;
+//     from the root (the boxes are conservative; a BVH4 box is decoded from
+//     its node's grid, p + q s, in binary64);
+//   - a used BVH4 slot has lo <= hi grid indices on every axis; an unused one
+//     has the empty reference and the inverted indices 255 / 0;
 //   - the depth the builder reports is the depth walked.
 // Usage: bvh_check <width 2|4> <n_tris> <mode 0 random | 1 identical | 2 slivers> <seed> <leaf_max>
 #include <algorithm>
@@ -22,7 +23,7 @@
 namespace {
 
 struct Box3 {
-    float lo[3], hi[3];
+    double lo[3], hi[3];
 };
 
 uint32_t lcg(uint64_t& s)
@@ -75,18 +76,24 @@ struct Walker {
     void node(uint32_t id, std::vector<Box3>& path, int depth)
     {
         depth_seen = std::max(depth_seen, depth);
-        const float4* nd = &b.nodes[(size_t)(b.width == 4 ? 8 : 4) * id];
+        const float4* nd = &b.nodes[(size_t)4 * id];
         const int nc = b.width == 4 ? 4 : 2;
         for (int k = 0; k < nc; ++k) {
             Box3 bx;
             uint32_t ref;
+            uint32_t ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0};
             if (b.width == 4) {
-                const float* f = reinterpret_cast<const float*>(nd);
+                const double p[3] = {nd[0].x, nd[0].y, nd[0].z}, s[3] = {nd[0].w, nd[1].x, nd[1].y};
+                const uint32_t wl[3] = {fbits(nd[2].x), fbits(nd[2].z), fbits(nd[1].z)};
+                const uint32_t wh[3] = {fbits(nd[2].y), fbits(nd[2].w), fbits(nd[1].w)};
                 for (int a = 0; a < 3; ++a) {
-                    bx.lo[a] = f[4 * (2 * a) + k];
-                    bx.hi[a] = f[4 * (2 * a + 1) + k];
+                    if (!(s[a] > 0.0)) fail("grid step not positive", id, a);
+                    ql[a] = (wl[a] >> (8 * k)) & 255u;
+                    qh[a] = (wh[a] >> (8 * k)) & 255u;
+                    bx.lo[a] = p[a] + (double)ql[a] * s[a];
+                    bx.hi[a] = p[a] + (double)qh[a] * s[a];
                 }
-                ref = fbits(f[4 * 6 + k]);
+                ref = fbits((&nd[3].x)[k]);
             } else {
                 const float4 xy = nd[k], z = nd[2];
                 bx = {{xy.x, xy.z, k ? z.z : z.x}, {xy.y, xy.w, k ? z.w : z.y}};
@@ -95,12 +102,15 @@ struct Walker {
             if (ref == rmlt::kEmptyRef) {
                 if (b.width != 4) fail("empty slot in a BVH2 node", id, k);
                 for (int a = 0; a < 3; ++a)
-                    if (!(bx.lo[a] == INFINITY && bx.hi[a] == -INFINITY)) fail("empty slot without an inverted box", id, k);
+                    if (ql[a] != 255u || qh[a] != 0u) fail("empty slot without inverted grid indices", id, k);
                 continue;
             }
+            if (b.width == 4)
+                for (int a = 0; a < 3; ++a)
+                    if (ql[a] > qh[a]) fail("used slot with inverted grid indices", id, k);
             path.push_back(bx);
             if (ref & rmlt::kLeafBit) leaf(ref, path);
-            else if (ref <= id || (size_t)ref * (b.width == 4 ? 8 : 4) >= b.nodes.size()) fail("bad child node", id, ref);
+            else if (ref <= id || (size_t)ref * 4 >= b.nodes.size()) fail("bad child node", id, ref);
             else node(ref, path, depth + 1);
             path.pop_back();
         }
@@ -145,6 +155,6 @@ int main(int argc, char** argv)
         if (w.covered[(size_t)i] != 1) w.fail("position not covered exactly once", i, w.covered[(size_t)i]);
     if (width == 4 && w.depth_seen != b.max_depth) w.fail("reported depth differs", b.max_depth, w.depth_seen);
     if (w.errors) return 1;
-    std::printf("ok nodes=%zu depth=%d\n", b.nodes.size() / (width == 4 ? 8 : 4), w.depth_seen);
+    std::printf("ok nodes=%zu depth=%d\n", b.nodes.size() / 4, w.depth_seen);
     return 0;
 }

@@ -3,9 +3,10 @@
 `tests/bvh_check.cpp` is compiled with the host compiler against the
 library's builder (`csrc/bvh_build.cpp`) and walks the emitted node array:
 the triangle order is a permutation, leaves cover it exactly once with at
-most two triangles each, every vertex lies inside every box above its leaf,
-and unused BVH4 slots hold the empty reference with an inverted infinite box
-(which the traversal relies on to skip them without a test).  Cases: random
+most two triangles each, every vertex lies inside every box above its leaf
+(BVH4 boxes decoded from their node's 8-bit grid in binary64), and unused
+BVH4 slots hold the empty reference (which the traversal skips them by) and
+inverted grid indices.  Cases: random
 small triangles, triangles with one shared centroid (the builder splits by
 count), long slivers, and a tiny scene; both node widths.
 
