@@ -159,7 +159,10 @@ typedef struct {
     uint64_t node_visits;      /* BVH internal nodes visited (only while work counters are on) */
     uint64_t tri_tests;        /* ray-triangle tests in BVH leaves (only while work counters are on) */
     uint64_t sched[6];         /* work counters on: warp loop iterations, traversing lanes summed over
-                                  them, shade batches, lanes shaded, setup batches, lanes set up */
+                                  them, shade batches, lanes shaded, setup batches, lanes set up;
+                                  wavefront form, of the trace kernel's warp loop: iterations, lanes
+                                  stepping, lanes holding a ray, leaf turns, lanes waiting at a leaf
+                                  during node turns, iterations after the ray queue ran dry */
     uint64_t cycles[5];        /* work counters on: SM cycles warps spent in traversal steps, shade
                                   batches, finish/setup batches; warp lifetimes (sum, max) */
     uint64_t waves;            /* wavefront form: waves run (one trace pass each), summed over epochs */

@@ -28,6 +28,7 @@
 // condition the last `setup` block sets from the number of rays queued.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
         stack = col;
     }
     unsigned nn = 0, nt = 0;
+    unsigned long long sc[6] = {0, 0, 0, 0, 0, 0};   // scheduling counters (COUNT)
     Trav T;
     T.ref = kNoRef;
     int c = -1;
@@ -455,7 +457,19 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
             }
         }
         if (dry && __all_sync(FULL, c < 0)) break;
-        if (step_turn<BRUTE>(c >= 0, T, W.leaf_batch) && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        const bool go = step_turn<BRUTE>(c >= 0, T, W.leaf_batch);
+        if (COUNT) {
+            const unsigned live = __ballot_sync(FULL, c >= 0), stepping = __ballot_sync(FULL, go);
+            const unsigned at_leaf = __ballot_sync(FULL, c >= 0 && (T.ref & kLeafBit));
+            const bool leaf_turn = (stepping & at_leaf) != 0u;
+            sc[0] += 1;
+            sc[1] += __popc(stepping);
+            sc[2] += __popc(live);
+            sc[3] += leaf_turn ? 1 : 0;
+            sc[4] += leaf_turn ? 0 : __popc(at_leaf);
+            sc[5] += dry ? 1 : 0;
+        }
+        if (go && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
             if (T.any) {
                 W.s[(size_t)kWShd * C + c] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
             } else {
@@ -470,6 +484,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
         if (lane == 0) {
             if (a) atomicAdd(&stats[kStNodes], a);
             if (b) atomicAdd(&stats[kStTris], b);
+            for (int s = 0; s < 6; ++s) atomicAdd(&stats[kStIters + s], sc[s]);
         }
     }
 }
@@ -577,7 +592,9 @@ void put(std::vector<unsigned char>& k, const T& v)
 }
 
 // the trace kernel for the wave state's stack layout, with its shared
-// memory carve-out set for the layout (the short stack leaves L1 the rest)
+// memory carve-out set for the layout: the short stack asks for just the
+// shared memory of as many resident blocks as the full-stack kernel gets
+// (registers bound both), and leaves L1 the rest
 template <bool B, bool K>
 void* trace_kernel(const DevWave& W)
 {
@@ -585,7 +602,15 @@ void* trace_kernel(const DevWave& W)
         void* k = (void*)wf_trace_kernel<B, K, kShortStack>;
         static bool carved = false;
         if (!carved) {
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 30);
+            int dev = 0, nb = 0, smem_sm = 0;
+            cudaFuncAttributes fa{};
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wf_trace_kernel<B, K>, kChainBlock, 0);
+            cudaFuncGetAttributes(&fa, k);
+            const size_t need = (size_t)(nb > 0 ? nb : 1) * (fa.sharedSizeBytes + 1024);
+            const int pct = smem_sm > 0 ? (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / smem_sm + 1) : 100;
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             carved = true;
         }
         return k;
