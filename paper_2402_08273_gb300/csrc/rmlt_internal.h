@@ -133,19 +133,30 @@ struct DevChains {
     uint32_t* trace_words = nullptr;   // optional: the D proposal words of each record, [record][D]
 };
 
-// Wavefront form of the chain epoch (rmlt_wavefront.cu).  Per chain, a
-// column of kWfSlots 32-bit words holds the mutation in flight, the path
-// state between waves and the ray results; the proposal y lives in [D][C].
+// Wavefront form of the chain epoch (rmlt_wavefront.cu).  Per chain,
+// kWfSlots 32-bit words hold the mutation in flight, the path state between
+// waves and the ray results.  The words only the finish / setup kernel uses
+// (the chain's lane state and its statistics, [0, kWRowEnd)) sit in a row
+// of kWfRow words per chain: that kernel visits the chains of a compacted
+// list, scattered over the population, and reads a line per chain instead
+// of a sector per word.  The rest sit in columns ([word][C]), coalesced for
+// the shade kernel, which visits every chain in order.  The proposal y lives
+// in [C][D].
 // A wave is three kernels: shade (consume the ray results of the chains with
 // rays in flight, emit the next rays), finish / set up (the chains whose path
 // ended: accept or reject, the next proposal, its camera ray), and trace (a
 // persistent kernel that pulls rays from the queue).  A CUDA graph repeats
 // the wave under a device-side while condition until no chain has a ray.
 enum WfSlot {
+    // row block: lane state and the statistics the finish / setup kernel counts
     kWKx = 0, kWPx, kWPy, kWPix, kWFx, kWPendN = kWFx + 3, kWPendI, kWPendA, kWJ = kWPendA + 2, kWFlags, kWKy,
-    kWXi, kWR, kWFy, kWT = kWFy + 3, kWL = kWT + 3, kWP = kWL + 3, kWB = kWP + 3, kWO, kWD = kWO + 3,
-    kWPfl = kWD + 3, kWSt, kWPhase = kWSt + 7, kWHitT, kWHitTri, kWShd, kWfSlots
+    kWXi, kWR, kWFy, kWSt = kWFy + 3, kWRowEnd = kWSt + 5,
+    // column block: path state, ray counters and ray results
+    kWT = kWRowEnd, kWL = kWT + 3, kWP = kWL + 3, kWB = kWP + 3, kWO, kWD = kWO + 3, kWPfl = kWD + 3,
+    kWRays, kWDropped, kWPhase, kWHitT, kWHitTri, kWShd, kWfSlots
 };
+constexpr int kWfRow = 32;   // words per row (one 128-byte line)
+static_assert(kWRowEnd <= kWfRow, "the row block fits a row");
 
 struct WfCounters {
     unsigned wave, ticket, fq_count, err;
@@ -155,7 +166,7 @@ struct WfCounters {
 };
 
 struct DevWave {
-    uint32_t* s = nullptr;        // [kWfSlots][C]
+    uint32_t* s = nullptr;        // [C][kWfRow] row block, then [kWfSlots - kWRowEnd][C] columns
     uint32_t* y = nullptr;        // [C][D] proposals, one chain's words contiguous
     uint32_t* qa = nullptr;       // [C][D] the states during an epoch (transposed in and out)
     float4* rq[2] = {nullptr, nullptr};   // two queues of 2C rays, 2 float4 each

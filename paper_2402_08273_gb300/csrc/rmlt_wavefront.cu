@@ -74,7 +74,10 @@ cudaError_t transpose(const uint32_t* src, uint32_t* dst, int rows, int cols, cu
 struct Slots {
     uint32_t* s;
     int C, c;
-    __device__ __forceinline__ uint32_t& operator[](int k) const { return s[(size_t)k * C + c]; }
+    __device__ __forceinline__ uint32_t& operator[](int k) const
+    {
+        return k < kWRowEnd ? s[(size_t)c * kWfRow + k] : s[(size_t)C * kWfRow + (size_t)(k - kWRowEnd) * C + c];
+    }
     __device__ __forceinline__ float f(int k) const { return __uint_as_float((*this)[k]); }
     __device__ __forceinline__ void setf(int k, float v) const { (*this)[k] = __float_as_uint(v); }
     __device__ __forceinline__ V3 v(int k) const { return {f(k), f(k + 1), f(k + 2)}; }
@@ -179,7 +182,9 @@ __global__ void wf_begin_kernel(const DevChains Ch, const DevWave W, unsigned lo
     s.setv(kWFx, {Ch.f[c], Ch.f[(size_t)C + c], Ch.f[2 * (size_t)C + c]});
     s[kWPendN] = s[kWPendI] = s[kWPendA] = s[kWPendA + 1] = 0u;
     s[kWJ] = 0u;
-    for (int k = 0; k < 7; ++k) s[kWSt + k] = 0u;
+    for (int k = 0; k < 5; ++k) s[kWSt + k] = 0u;
+    s[kWRays] = 0u;
+    s[kWDropped] = 0u;
     s[kWPhase] = Ch.E > 0 ? kWfStart : kWfIdle;
     W.fq[c] = (uint32_t)c;
 }
@@ -253,9 +258,9 @@ __global__ void __launch_bounds__(kChainBlock, 8) wf_shade_kernel(const DevScene
             if (dropped) {   // a traversal stack overflowed: the path contributes nothing
                 p.L = {0.f, 0.f, 0.f};
                 emit = 0;
-                s[kWSt + 6] += 1u;
+                s[kWDropped] += 1u;
             }
-            s[kWSt + 5] += rays;
+            s[kWRays] += rays;
             if (emit) {
                 s.setv(kWT, p.T);
                 s.setv(kWL, p.L);
@@ -327,7 +332,8 @@ __global__ void __launch_bounds__(kChainBlock, 6) wf_setup_kernel(const DevScene
             ChainLane L;
             load_lane(s, L);
             unsigned st[7];
-            for (int k = 0; k < 7; ++k) st[k] = s[kWSt + k];
+            for (int k = 0; k < 5; ++k) st[k] = s[kWSt + k];
+            st[5] = st[6] = 0u;   // ray counters: the shade kernel's
             Path p;
             if (s[kWPhase] != kWfStart) {
                 mutation_finish<TRACE>(Ch, c, traced, L, y, st);
@@ -368,7 +374,7 @@ __global__ void __launch_bounds__(kChainBlock, 6) wf_setup_kernel(const DevScene
                 s[kWPhase] = kWfIdle;
             }
             store_lane(s, L);
-            for (int k = 0; k < 7; ++k) s[kWSt + k] = st[k];
+            for (int k = 0; k < 5; ++k) s[kWSt + k] = st[k];
         }
         append_rays(W, C, buf, nr, r);
     }
@@ -471,10 +477,10 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
         }
         if (go && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
             if (T.any) {
-                W.s[(size_t)kWShd * C + c] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
+                Slots{W.s, C, c}[kWShd] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
             } else {
-                W.s[(size_t)kWHitTri * C + c] = T.overflow ? (uint32_t)-2 : (uint32_t)T.tri;
-                W.s[(size_t)kWHitT * C + c] = __float_as_uint(T.t);
+                Slots{W.s, C, c}[kWHitTri] = T.overflow ? (uint32_t)-2 : (uint32_t)T.tri;
+                Slots{W.s, C, c}[kWHitT] = __float_as_uint(T.t);
             }
             c = -1;
         }
@@ -500,7 +506,9 @@ __global__ void __launch_bounds__(256) wf_end_kernel(const DevChains Ch, const D
     unsigned long long v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (c < C) {
         const Slots s{W.s, C, c};
-        for (int k = 0; k < 7; ++k) v[k] = s[kWSt + k];
+        for (int k = 0; k < 5; ++k) v[k] = s[kWSt + k];
+        v[5] = s[kWRays];
+        v[6] = s[kWDropped];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < 7; ++k) {
@@ -542,7 +550,7 @@ size_t gstack_words() { return (size_t)(kStackSize - kShortStack) * kWfTraceThre
 size_t wf_bytes(int C, int D)
 {
     const size_t c = (size_t)C;
-    return align256(sizeof(uint32_t) * kWfSlots * c) + 2 * align256(sizeof(uint32_t) * (size_t)D * c) +
+    return align256(sizeof(uint32_t) * ((size_t)kWfRow + kWfSlots - kWRowEnd) * c) + 2 * align256(sizeof(uint32_t) * (size_t)D * c) +
            2 * align256(sizeof(float4) * 4 * c) + align256(sizeof(uint32_t) * c) + align256(sizeof(WfCounters)) +
            align256(sizeof(uint32_t) * gstack_words());
 }
@@ -552,7 +560,7 @@ void wf_carve(void* base, int C, int D, DevWave& w)
     const size_t c = (size_t)C;
     char* p = (char*)base;
     w.s = (uint32_t*)p;
-    p += align256(sizeof(uint32_t) * kWfSlots * c);
+    p += align256(sizeof(uint32_t) * ((size_t)kWfRow + kWfSlots - kWRowEnd) * c);
     w.y = (uint32_t*)p;
     p += align256(sizeof(uint32_t) * (size_t)D * c);
     w.qa = (uint32_t*)p;
