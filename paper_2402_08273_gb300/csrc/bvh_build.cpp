@@ -25,8 +25,9 @@
 // are rounded down and hi planes up, so each decoded box contains the
 // child's box.
 // A ref is an internal node index, a leaf (kLeafBit | (count-1) << 28 |
-// first triangle in build order), or kEmptyRef for an unused BVH4 slot (its q
-// bytes 255 / 0: an inverted box; the traversal skips it by the reference).
+// first triangle in build order), or, for an unused BVH4 slot, empty_ref(n):
+// a one-triangle leaf past the scene's triangles (the upload's zero-area
+// sentinel), with q bytes 255 / 0, an inverted box no slab test accepts.
 // Boxes are widened by `pad` and rounded outward so that binary32 traversal
 // never culls a box a ray grazes.
 #include <algorithm>
@@ -174,6 +175,7 @@ struct Emitter {
     const std::vector<BNode>& bn;
     std::vector<float4>& out;
     float pad;
+    uint32_t empty;   // the reference of an unused BVH4 slot
     int depth = 0, max_depth = 0;
 
     Box padded(const Box& b) const
@@ -226,7 +228,7 @@ struct Emitter {
         }
         const uint32_t id = (uint32_t)(out.size() / 4);
         out.resize(out.size() + 4);
-        uint32_t refs[4] = {kEmptyRef, kEmptyRef, kEmptyRef, kEmptyRef};
+        uint32_t refs[4] = {empty, empty, empty, empty};
         Box boxes[4];
         for (int k = 0; k < nc; ++k) {
             refs[k] = emit4(ch[k]);
@@ -305,7 +307,7 @@ void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width
     bld.build(0, n_tris, 0);
     out.nodes.clear();
     out.width = width;
-    Emitter em{bld.nodes, out.nodes, pad};
+    Emitter em{bld.nodes, out.nodes, pad, empty_ref((uint32_t)n_tris)};
     if (width == 4) {
         em.emit4(0);
         out.max_depth = em.max_depth;

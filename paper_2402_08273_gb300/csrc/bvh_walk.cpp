@@ -124,7 +124,6 @@ WalkResult walk_ray(const std::vector<float4>& nodes, int width, const std::vect
                 const uint32_t qh[3] = {bits(nd[2].y), bits(nd[2].w), bits(nd[1].w)};
                 const uint32_t rf[4] = {bits(nd[3].x), bits(nd[3].y), bits(nd[3].z), bits(nd[3].w)};
                 for (int k = 0; k < 4; ++k) {
-                    if (rf[k] == kEmptyRef) continue;
                     double lo[3], hi[3];
                     for (int a = 0; a < 3; ++a) {
                         lo[a] = p[a] + (double)((ql[a] >> (8 * k)) & 255u) * s[a];

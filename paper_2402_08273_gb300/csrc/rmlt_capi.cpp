@@ -326,7 +326,9 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     std::vector<uint32_t> order((size_t)nt), inv((size_t)nt);
     for (int i = 0; i < nt; ++i) order[(size_t)i] = brute ? (uint32_t)i : bvh.order[(size_t)i];
     for (int i = 0; i < nt; ++i) inv[order[(size_t)i]] = (uint32_t)i;
-    std::vector<float4> tri4((size_t)3 * nt);
+    // with a BVH, a zero-area sentinel triangle after the scene's (the leaf
+    // that unused BVH4 slots reference)
+    std::vector<float4> tri4((size_t)3 * (nt + (brute ? 0 : 1)), make_float4(0.f, 0.f, 0.f, 0.f));
     for (int j = 0; j < nt; ++j) {
         const uint32_t i = order[(size_t)j];
         const float* p = &tv[(size_t)9 * i];

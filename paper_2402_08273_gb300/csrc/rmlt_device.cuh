@@ -332,7 +332,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
             const float a2 = fmaf(qbyte(nwz, k), Az, Bz), b2 = fmaf(qbyte(fwz, k), Az, Bz);
             const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
             const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
-            const bool hit = tn <= tf && rr[k] != kEmptyRef;
+            const bool hit = tn <= tf;   // an unused slot's inverted box never passes
             key[k] = hit ? tn : INFINITY;
             cr[k] = rr[k];
         }

@@ -41,8 +41,12 @@ enum StatSlot {
 
 // Leaf references in the BVH: bit 31 set, bits 28..30 = count - 1, bits 0..27 = first triangle.
 constexpr uint32_t kLeafBit = 0x80000000u;
-// unused child slot of a BVH4 node
-constexpr uint32_t kEmptyRef = 0xFFFFFFFEu;
+// An unused child slot of a BVH4 node references a one-triangle leaf at
+// position n_tris, just past the scene's triangles, where the upload puts a
+// zero-area sentinel triangle.  The slot's box is inverted, so no slab test
+// accepts it; were one to, the sentinel's test finds no hit, and no
+// reference ever leaves the triangle array.
+constexpr uint32_t empty_ref(uint32_t n_tris) { return kLeafBit | n_tris; }
 
 // Device view of a loaded scene.  Triangles: 3 float4 each (v0 | mat id bits,
 // e1 | original index bits, e2 | 0); nodes: 4 float4 each (BVH2: child 0 x/y

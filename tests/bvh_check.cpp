@@ -8,7 +8,8 @@
 //     from the root (the boxes are conservative; a BVH4 box is decoded from
 //     its node's grid, p + q s, in binary64);
 //   - a used BVH4 slot has lo <= hi grid indices on every axis; an unused one
-//     has the empty reference and the inverted indices 255 / 0;
+//     references the sentinel leaf past the triangles and has the inverted
+//     indices 255 / 0;
 //   - the depth the builder reports is the depth walked.
 // Usage: bvh_check <width 2|4> <n_tris> <mode 0 random | 1 identical | 2 slivers> <seed> <leaf_max>
 #include <algorithm>
@@ -99,7 +100,7 @@ struct Walker {
                 bx = {{xy.x, xy.z, k ? z.z : z.x}, {xy.y, xy.w, k ? z.w : z.y}};
                 ref = fbits(k ? nd[3].y : nd[3].x);
             }
-            if (ref == rmlt::kEmptyRef) {
+            if (ref == rmlt::empty_ref((uint32_t)covered.size())) {
                 if (b.width != 4) fail("empty slot in a BVH2 node", id, k);
                 for (int a = 0; a < 3; ++a)
                     if (ql[a] != 255u || qh[a] != 0u) fail("empty slot without inverted grid indices", id, k);

@@ -5,8 +5,8 @@ library's builder (`csrc/bvh_build.cpp`) and walks the emitted node array:
 the triangle order is a permutation, leaves cover it exactly once with at
 most two triangles each, every vertex lies inside every box above its leaf
 (BVH4 boxes decoded from their node's 8-bit grid in binary64), and unused
-BVH4 slots hold the empty reference (which the traversal skips them by) and
-inverted grid indices.  Cases: random
+BVH4 slots reference the sentinel leaf past the triangles with inverted grid
+indices (which no slab test accepts).  Cases: random
 small triangles, triangles with one shared centroid (the builder splits by
 count), long slivers, and a tiny scene; both node widths.
 
