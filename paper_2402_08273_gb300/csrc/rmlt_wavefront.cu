@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     unsigned* pull = &W.ctr->fetch[buf];
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    const int refill = W.refill;
+    const int refill = W.refill, leaf_batch = W.leaf_batch;
     uint32_t* col = s_stack + (threadIdx.x / kStackStride) * (SS * kStackStride) + threadIdx.x % kStackStride;
     typename StackFor<SS>::type stack;
     if constexpr (SS < kStackSize) {
@@ -446,7 +446,13 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
     int c = -1;
     bool dry = n == 0u;
     while (true) {
-        const unsigned idle = __ballot_sync(FULL, c < 0);
+        // the lanes at a leaf and at an inner node (the others are idle):
+        // the leaf-turn rule of step_turn, and the refill and exit tests,
+        // from the same two votes
+        const bool at_leaf = c >= 0 && !BRUTE && (T.ref & kLeafBit);
+        const unsigned m_leaf = __ballot_sync(FULL, at_leaf);
+        unsigned m_node = __ballot_sync(FULL, c >= 0 && !at_leaf);
+        const unsigned idle = ~(m_leaf | m_node);
         if (!dry && __popc(idle) >= refill) {
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(pull, (unsigned)__popc(idle));
@@ -461,9 +467,13 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
                     trav_begin(T, v3(r0.x, r0.y, r0.z), v3(r1.x, r1.y, r1.z), r0.w, (tag & kAnyBit) ? 1 : 0);
                 }
             }
+            m_node |= __ballot_sync(FULL, c >= 0) & idle;   // new rays start at the root, an inner node
         }
-        if (dry && __all_sync(FULL, c < 0)) break;
-        const bool go = step_turn<BRUTE>(c >= 0, T, W.leaf_batch);
+        if (dry && (m_leaf | m_node) == 0u) break;
+        // as step_turn: leaves take their turn once leaf_batch lanes (or
+        // every lane with a ray) wait at one
+        const bool leaf_turn = m_leaf && (!m_node || __popc(m_leaf) >= leaf_batch);
+        const bool go = c >= 0 && at_leaf == leaf_turn;
         if (COUNT) {
             const unsigned live = __ballot_sync(FULL, c >= 0), stepping = __ballot_sync(FULL, go);
             const unsigned at_leaf = __ballot_sync(FULL, c >= 0 && (T.ref & kLeafBit));
