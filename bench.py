@@ -87,9 +87,11 @@ SECONDARY = {"corridor": "two_rooms"}
 
 
 def measured_traffic(workload: str, form: str):
-    """DRAM bytes per launch of the workload's dominant kernel from the
-    committed ncu capture (profiles/traffic.json), or None when there is no
-    capture for this workload and form or the kernel source changed since."""
+    """DRAM traffic of the workload's dominant kernel from the committed ncu
+    capture (profiles/traffic.json): bytes per launch, or bytes per ray for a
+    kernel launched once per wave (scaled to the step by its rays); None when
+    there is no capture for this workload and form or the kernel source
+    changed since."""
     import hashlib
     try:
         rec = json.loads((ROOT / "profiles" / "traffic.json").read_text())[f"{workload}/{form}"]
@@ -97,8 +99,8 @@ def measured_traffic(workload: str, form: str):
         src = b"".join((csrc / f).read_bytes() for f in ("rmlt_kernels.cu", "rmlt_device.cuh", "rmlt_wavefront.cu"))
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
             return None
-        return {"bytes_per_launch": rec["dram_bytes_per_launch"], "kernel": rec["kernel"],
-                "scaled_from": rec.get("scaled_from")}
+        return {"bytes_per_launch": rec.get("dram_bytes_per_launch"), "bytes_per_ray": rec.get("dram_bytes_per_ray"),
+                "kernel": rec["kernel"], "scaled_from": rec.get("scaled_from")}
     except (OSError, KeyError, ValueError):
         return None
 
@@ -528,9 +530,17 @@ def measure(wname, steps, warmup, form_arg, world=1, rank=0, local=0, dist=None,
     bound, achieved, peak, unit = ("l2", l2["achieved_gbs"], l2_gbs, "GB/s") if l2_max <= alu_max else \
         ("alu", alu["achieved_tflops"], fp32_tflops, "TFLOP/s")
     tr = measured_traffic(wname, form)
+    traffic, traffic_per = None, None
+    if tr and tr["bytes_per_ray"] is not None:
+        # every trace launch of one step: the captured bytes per ray times the step's rays (per GPU)
+        traffic, traffic_per = tr["bytes_per_ray"] * rays / world / steps, "step (all of the kernel's launches)"
+    elif tr:
+        traffic, traffic_per = tr["bytes_per_launch"], "launch"
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": (tr["bytes_per_launch"] if tr else None),
+                "traffic": traffic, "traffic_per": traffic_per,
+                "traffic_algorithmic": bytes_ray * rays / world / steps,
                 "traffic_kernel": (tr["kernel"] if tr else None),
+                "traffic_source": (tr["scaled_from"] if tr else None),
                 "kernel": "chain_epoch_kernel" if form == "chain" else "wavefront waves (shade, setup, trace)",
                 "achieved_over": "the whole step's device time (every kernel of the step), so the dominant "
                                  "kernel's own rate is higher by its share of the step",
