@@ -209,8 +209,10 @@ rmlt_status rmlt_load_toy_integrand(rmlt_ctx* ctx, const double* params);
 
 /* Allocate chain state and region tables, run the bootstrap (n_bootstrap
  * uniform samples -> b, Sec. 3.2 "preprocess"), give each chain g (global id)
- * a starting state among its own K = n_bootstrap / chains samples [gK, (g+1)K)
- * with probability pi_s / sum(pi) (weighted reservoir sampling), and set
+ * the sample where the cumulative sum of pi over all K C samples (K =
+ * n_bootstrap / chains) first exceeds (g + u_g) / chains of the total, u_g a
+ * uniform of its own (systematic resampling in proportion to pi, so no chain
+ * starts on a path that contributes nothing while any sample does), and set
  * lambda_k = lambda_init, i_k = A_k = 0, n_k = 1 (Alg. 1, initialisation).
  * Bootstrap paths dropped by a traversal-stack overflow are counted in
  * rmlt_stats.boot_overflow.  On error the context keeps its previous chains.
@@ -420,7 +422,7 @@ rmlt_status rmlt_set_trace_leaf_batch(rmlt_ctx* ctx, int leaf_batch);
  *   out_f     device, [3][n_chains] float contributions of those states
  *   out_bhat  host or device, one double: b
  * Its intermediate values live in one fixed array inside the library (about
- * 5.3 MB, held on every GPU that loads the library until the process exits),
+ * 5.9 MB, held on every GPU that loads the library until the process exits),
  * so it calls no cudaMalloc, cudaFree or allocating library routine.  Limits:
  * (n_bootstrap / n_chains) * n_chains <= RMLT_NOALLOC_MAX_SAMPLES, n_chains <=
  * RMLT_NOALLOC_MAX_CHAINS, regions <= RMLT_NOALLOC_MAX_REGIONS; larger sizes

@@ -54,7 +54,8 @@ static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
 /* Counter layout of the draws (the paper does not specify its RNG):
  *   mutation draws  ctr = {mut lo, mut hi, chain, call}, key = {seed lo, seed hi}
- *   bootstrap draws ctr = {sample lo, sample hi, 0xFFFFFFFF, 0x8000 + call}   */
+ *   bootstrap draws ctr = {sample lo, sample hi, 0xFFFFFFFF, 0x8000 + call}
+ *   starting state  ctr = {chain g, 0, 0xFFFFFFFF, 0x7FFE} (its point u_g)   */
 static void draw(uint64_t seed, uint64_t a, uint32_t b, uint32_t call, uint32_t out[4])
 {
     uint32_t ctr[4] = {(uint32_t)a, (uint32_t)(a >> 32), b, call};
@@ -1635,40 +1636,58 @@ static void boot_sample(const or_ctx* c, uint64_t s, uint32_t* q)
 
 /* Bootstrap (Sec. 3.2: b estimated by independent Monte Carlo in a
  * preprocess) and the initial states.  Reading: the paper does not say how
- * the initial paths are chosen.  Chain c owns the K = n_boot / C uniform
- * samples s in [cK, (c+1)K) and picks one of them with probability
- * pi_s / sum(pi) by weighted reservoir sampling (keep s when v_s cum_s < pi_s,
- * v_s a uniform of its own).  b = sum of all pi / (K C). */
+ * the initial paths are chosen.  Every chain g of the population takes the
+ * uniform sample s where the cumulative sum of pi over all n = K C samples
+ * (K = n_boot / C) first exceeds t_g = (g + u_g) / C * sum(pi), u_g a
+ * uniform of its own: systematic resampling in proportion to pi, so each
+ * chain starts on a contributing path and the starting states follow pi.
+ * Without a contributing sample, chain g starts at sample g K.
+ * b = sum of all pi / n. */
 int32_t or_init(or_ctx* c)
 {
     const or_params* p = &c->p;
     const int32_t C_all = chains_all(c);
     int64_t K = p->n_bootstrap / C_all;
     if (K <= 0) return -1;
+    const int64_t n = K * (int64_t)C_all;
     if (p->partition == 1) or_init_tables(c);   /* the region lookup needs the root */
     uint32_t q[OR_MAX_DIM];
     double f[3], total = 0.0;
+    double* pis = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!pis) return -1;
     memset(c->Bk, 0, sizeof(double) * (size_t)c->m);
-    /* every chain of the population (all shards): b needs every slice; only
-     * this context's chains take a starting state */
-    for (int32_t g = 0; g < C_all; ++g) {
-        double cum = 0.0;
-        int64_t sel = -1;
-        for (int64_t i = 0; i < K; ++i) {
-            uint64_t s = (uint64_t)g * (uint64_t)K + (uint64_t)i;
-            boot_sample(c, s, q);
-            if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
-            double pis = luminance(f);
-            c->Bk[or_region_of(c, q)] += pis;
-            cum += pis;
+    /* every sample of the population (all shards): b and the distribution
+     * need all of them; only this context's chains take a starting state */
+    double* cum = (double*)malloc(sizeof(double) * (size_t)n);   /* inclusive cumulative sums */
+    if (!cum) {
+        free(pis);
+        return -1;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        boot_sample(c, (uint64_t)s, q);
+        if (!or_path_eval(c->s, p->width, p->height, p->max_depth, q, f, NULL, NULL)) c->st[5]++;
+        pis[s] = luminance(f);
+        c->Bk[or_region_of(c, q)] += pis[s];
+        total += pis[s];
+        cum[s] = total;
+    }
+    for (int32_t ch = 0; ch < p->n_chains; ++ch) {
+        const int32_t g = p->chain_first + ch;
+        int64_t sel = (int64_t)g * K;
+        if (total > 0.0) {
             uint32_t r[4];
-            draw(p->seed, s, 0xFFFFFFFFu, 0x7FFFu, r);
-            if (pis > 0 && u24(r[0]) * cum < pis) sel = (int64_t)s;
+            draw(p->seed, (uint64_t)g, 0xFFFFFFFFu, 0x7FFEu, r);
+            const double t = ((double)g + u24(r[0])) / (double)C_all * total;
+            int64_t lo = 0, hi = n;   /* the first s with cum[s] > t, n if none */
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (cum[mid] > t) hi = mid;
+                else lo = mid + 1;
+            }
+            sel = lo < n ? lo : -1;
+            for (int64_t s = n - 1; s >= 0 && sel < 0; --s)   /* t at the very end: rounding */
+                if (pis[s] > 0.0) sel = s;
         }
-        if (sel < 0) sel = (int64_t)g * K;
-        total += cum;
-        const int32_t ch = g - p->chain_first;
-        if (ch < 0 || ch >= p->n_chains) continue;
         c->boot[ch] = sel;
         uint32_t* qc = &c->q[(size_t)ch * c->D];
         boot_sample(c, (uint64_t)sel, qc);
@@ -1680,6 +1699,8 @@ int32_t or_init(or_ctx* c)
             or_path_grad(c->s, p->width, p->height, p->max_depth, qc, fg, &c->g[(size_t)ch * c->D]);
         }
     }
+    free(cum);
+    free(pis);
     c->st[7] = (uint64_t)(K * C_all);
     c->nU = (uint64_t)(K * C_all);
     c->bhat = total / (double)(K * C_all);

@@ -682,7 +682,8 @@ rmlt_status rmlt_init_chains(rmlt_ctx* c, const rmlt_chain_params* pin)
     const int64_t K = p->n_bootstrap / Ch.C_all;
     const int64_t nb = K * Ch.C_all;
     if ((st = c->alloc_n(scratch, (size_t)nb, &B.pi)) || (st = c->alloc_n(scratch, (size_t)nb * 3, &B.f)) ||
-        (st = c->alloc_n(scratch, (size_t)Ch.C_all, &B.partial))) {
+        (st = c->alloc_n(scratch, (size_t)Ch.C_all, &B.partial)) ||
+        (st = c->alloc_n(scratch, (size_t)Ch.C_all + 1, &B.prefix))) {
         c->release(scratch);
         c->release(A.pool);
         return st;

@@ -231,6 +231,7 @@ struct BootScratch {
     float* pi = nullptr;          // [n]
     float* f = nullptr;           // [3][n]
     double* partial = nullptr;    // [C_all] per-chain slice sums
+    double* prefix = nullptr;     // [C_all + 1] exclusive prefix of the slice sums, then their total
     double* total = nullptr;      // [1] sum of pi over all samples (kept)
     unsigned long long* overflow = nullptr;   // [1] paths dropped by a traversal-stack overflow (added to)
 };

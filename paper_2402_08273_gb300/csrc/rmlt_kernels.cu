@@ -752,7 +752,7 @@ __global__ void fill_regions_kernel(const DevChains Ch, double lambda_init)
 
 // ---------------------------------------------------------------------------
 // bootstrap (Sec. 3.2: b by independent Monte Carlo in a preprocess) and the
-// initial states (stratified inverse CDF of pi)
+// initial states (systematic resampling of the samples in proportion to pi)
 // ---------------------------------------------------------------------------
 template <bool BRUTE>
 __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevScene S, const DevChains Ch,
@@ -808,31 +808,86 @@ __global__ void __launch_bounds__(kChainBlock) bootstrap_eval_kernel(const DevSc
     if (pv != 0.f) atomicAdd(&Ch.Bk[k], (double)pv);
 }
 
-// Initial state of chain g (global id): weighted reservoir sampling over its
-// own K uniform samples s in [gK, (g+1)K): keep s when v_s cum_s < pi_s, which
-// picks s with probability pi_s / sum(pi) (v_s a uniform of its own).  The
-// slice sum goes to `partial` for the normaliser b.  Every chain of the
-// population computes its slice sum; only this context's chains
-// [chain0, chain0 + C) write a state.
-__global__ void bootstrap_select_kernel(const DevChains Ch, long long K, const BootScratch B)
+// Sum of pi over each chain's slice of K uniform samples [gK, (g+1)K): the
+// terms of the normaliser b and of the cumulative distribution below.
+__global__ void bootstrap_slice_kernel(const DevChains Ch, long long K, const BootScratch B)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= Ch.C_all) return;
-    const long long n_eff = K * Ch.C_all;
     double cum = 0.0;
-    long long sel = -1;
-    for (long long i = 0; i < K; ++i) {
-        const long long s = (long long)g * K + i;
-        const double v = (double)B.pi[s];
-        cum += v;
-        const uint4 r = philox((uint32_t)s, (uint32_t)((unsigned long long)s >> 32), 0xFFFFFFFFu, 0x7FFFu,
-                               Ch.seed_lo, Ch.seed_hi);
-        if (v > 0.0 && (double)u24(r.x) * cum < v) sel = s;
-    }
-    if (sel < 0) sel = (long long)g * K;
+    for (long long i = 0; i < K; ++i) cum += (double)B.pi[(long long)g * K + i];
     B.partial[g] = cum;
-    const int c = g - (int)Ch.chain0;
-    if (c < 0 || c >= Ch.C) return;
+}
+
+// Exclusive prefix of the slice sums in a fixed order (thread t scans its
+// contiguous chunk after thread 0 has scanned the chunk sums), and their
+// total at prefix[C_all]: the cumulative distribution of pi over all
+// samples, slice by slice.  One block.
+__global__ void __launch_bounds__(1024) bootstrap_scan_kernel(int C_all, const BootScratch B)
+{
+    __shared__ double chunk[1024];
+    const int t = threadIdx.x, per = (C_all + 1023) / 1024;
+    const int b = t * per, e = min(b + per, C_all);
+    double acc = 0.0;
+    for (int g = b; g < e; ++g) acc += B.partial[g];
+    chunk[t] = acc;
+    __syncthreads();
+    if (t == 0) {
+        double run = 0.0;
+        for (int k = 0; k < 1024; ++k) {
+            const double v = chunk[k];
+            chunk[k] = run;
+            run += v;
+        }
+        B.prefix[C_all] = run;
+    }
+    __syncthreads();
+    double run = chunk[t];
+    for (int g = b; g < e; ++g) {
+        B.prefix[g] = run;
+        run += B.partial[g];
+    }
+}
+
+// Initial state of chain g (global id): systematic resampling of all uniform
+// samples in proportion to pi.  Its point t = (g + u_g) / C_all of the total
+// (u_g a uniform of its own) falls in the sample s whose cumulative sum first
+// exceeds t; so every chain starts on a path that contributes, and the
+// starting states together follow pi.  Only this context's chains
+// [chain0, chain0 + C) write a state.
+__global__ void bootstrap_pick_kernel(const DevChains Ch, long long K, const BootScratch B)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Ch.C) return;
+    const int g = (int)Ch.chain0 + c;
+    const int C_all = Ch.C_all;
+    const long long n_eff = K * C_all;
+    const double total = B.prefix[C_all];
+    long long sel = (long long)g * K;   // no sample contributes: the slice's first
+    if (total > 0.0) {
+        const uint4 r = philox((uint32_t)g, 0u, 0xFFFFFFFFu, 0x7FFEu, Ch.seed_lo, Ch.seed_hi);
+        const double tc = ((double)g + (double)u24(r.x)) / (double)C_all * total;
+        // the last slice whose prefix is at most tc
+        int lo = 0, hi = C_all - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (B.prefix[mid] <= tc) lo = mid;
+            else hi = mid - 1;
+        }
+        double cum = B.prefix[lo];
+        long long s = (long long)lo * K;
+        sel = -1;
+        for (; s < n_eff; ++s) {
+            cum += (double)B.pi[s];
+            if (cum > tc) {
+                sel = s;
+                break;
+            }
+        }
+        if (sel < 0)   // tc at the very end (rounding): the last contributing sample
+            for (s = n_eff - 1; s >= 0 && sel < 0; --s)
+                if (B.pi[s] > 0.f) sel = s;
+    }
     const int D = Ch.D, C = Ch.C;
     uint32_t q0 = 0, q1 = 0, q5 = 0, q6 = 0;
     for (int jj = 0; 4 * jj < D; ++jj) {
@@ -1143,9 +1198,13 @@ cudaError_t launch_bootstrap(const DevScene& s, const DevChains& c, int64_t n_bo
         bootstrap_eval_kernel<false><<<(unsigned)blocks, kChainBlock, 0, st>>>(s, c, n_eff, b);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bootstrap_select_kernel<<<(c.C_all + 127) / 128, 128, 0, st>>>(c, K, b);
+    bootstrap_slice_kernel<<<(c.C_all + 127) / 128, 128, 0, st>>>(c, K, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     bootstrap_total_kernel<<<1, 256, 0, st>>>(c.C_all, b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bootstrap_scan_kernel<<<1, 1024, 0, st>>>(c.C_all, b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bootstrap_pick_kernel<<<(c.C + 127) / 128, 128, 0, st>>>(c, K, b);
     return cudaGetLastError();
 }
 
@@ -1158,7 +1217,8 @@ constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kNaPi = 0;
 constexpr size_t kNaF = na_align(kNaPi + sizeof(float) * RMLT_NOALLOC_MAX_SAMPLES);
 constexpr size_t kNaPartial = na_align(kNaF + sizeof(float) * 3 * (size_t)RMLT_NOALLOC_MAX_SAMPLES);
-constexpr size_t kNaTotal = na_align(kNaPartial + sizeof(double) * RMLT_NOALLOC_MAX_CHAINS);
+constexpr size_t kNaPrefix = na_align(kNaPartial + sizeof(double) * RMLT_NOALLOC_MAX_CHAINS);
+constexpr size_t kNaTotal = na_align(kNaPrefix + sizeof(double) * (RMLT_NOALLOC_MAX_CHAINS + 1));
 constexpr size_t kNaChainPi = na_align(kNaTotal + sizeof(double));
 constexpr size_t kNaChainK = na_align(kNaChainPi + sizeof(float) * RMLT_NOALLOC_MAX_CHAINS);
 constexpr size_t kNaBk = na_align(kNaChainK + sizeof(int32_t) * RMLT_NOALLOC_MAX_CHAINS);
@@ -1191,6 +1251,7 @@ cudaError_t noalloc_scratch(int device, NoAllocScratch& out)
     out.boot.pi = (float*)(base + kNaPi);
     out.boot.f = (float*)(base + kNaF);
     out.boot.partial = (double*)(base + kNaPartial);
+    out.boot.prefix = (double*)(base + kNaPrefix);
     out.boot.total = (double*)(base + kNaTotal);
     out.chain_pi = (float*)(base + kNaChainPi);
     out.chain_k = (int32_t*)(base + kNaChainK);

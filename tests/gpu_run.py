@@ -107,7 +107,12 @@ def check_counters(ch, gpu, rp, pins: dict | None = None, adopted: int = 0, max_
     i_k = reg["i"].astype(np.float64)
     assert np.all(np.abs(A_g - A_o) <= 2.0 ** 32 * i_k * rp.a_max_rel + i_k + 1), "A_k differs"
     raw_o = ch.image_acc
-    np.testing.assert_allclose(gpu["image_raw"], raw_o, rtol=1e-5, atol=1e-7 * max(1.0, raw_o.max()))
+    # each splat is a state's f / pi, and f may differ from the oracle's by up
+    # to the replay's largest relative difference (within its binary32
+    # bound): a pixel's sum of positive splats then differs by at most twice
+    # that (f and its luminance)
+    rtol = 2.0 * max(rp.f_max_rel, 5e-6) + 1e-9
+    np.testing.assert_allclose(gpu["image_raw"], raw_o, rtol=rtol, atol=1e-7 * max(1.0, raw_o.max()))
     pins = pins or {}
     for key, n in rp.counts().items():
         assert n <= pins.get(key, 0), (key, n, pins.get(key, 0))

@@ -113,7 +113,7 @@ def test_batch_rejects_unsupported_members():
 
 
 # the most mutations each window may let through, measured on a GB300
-PINS_REPLAY = {0: {"f_bounded": 1, "f_excluded": 1}, 1: {"f_excluded": 1}}
+PINS_REPLAY = {0: {"f_bounded": 1, "f_excluded": 1}, 1: {"f_bounded": 1, "f_excluded": 1}}
 
 
 def test_batched_members_replayed_by_the_oracle(oracle_mod):

@@ -34,9 +34,10 @@ def _check_counters(ch, gpu, rp, pins=None, adopted=0, max_adopted=0):
 # the most mutations each window may let through, measured on a GB300
 PINS = {
     "toy": {"update_excluded": 2},
+    "toy_weighted": {"update_excluded": 1},
     "cornell": {"f_bounded": 59, "f_excluded": 1},
 }
-PINS_SAMPLED = {"two_rooms": {}}
+PINS_SAMPLED = {"two_rooms": {"f_bounded": 2}}
 
 
 @pytest.mark.parametrize("n_chains,target_mode", [(200, 0), (64, 1)])
@@ -47,7 +48,7 @@ def test_toy_integrand_parity(oracle_mod, n_chains, target_mode):
                      target_mode=target_mode)
     ch, rp, adopted = _replay_full(oracle_mod, gpu, oracle_mod.Scene(toy=TOY), max_adopt=0)
     assert rp.s["f_excluded"] == 0
-    _check_counters(ch, gpu, rp, PINS["toy"] if target_mode == 0 else {})
+    _check_counters(ch, gpu, rp, PINS["toy"] if target_mode == 0 else PINS["toy_weighted"])
     if target_mode:
         assert np.array_equal(ch.weight, gpu["region"]["w"]), "w_k differs"
     np.testing.assert_allclose(gpu["image"], ch.image(), rtol=1e-5, atol=1e-9)

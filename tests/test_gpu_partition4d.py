@@ -10,7 +10,7 @@ from paper_2402_08273_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 # the most mutations each window may let through, measured on a GB300
-PINS = {"f_bounded": 14}
+PINS = {"f_bounded": 16}
 
 
 def test_partition4d_full_trajectory(oracle_mod):

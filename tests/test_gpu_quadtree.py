@@ -9,7 +9,7 @@ from paper_2402_08273_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 # the most mutations each window may let through, measured on a GB300
-PINS = {"toy": {}, "cornell": {"f_bounded": 6}}
+PINS = {"toy": {}, "cornell": {"f_bounded": 10}}
 
 QT = dict(partition=1, qt_max_leaves=256, qt_max_depth=6)
 

@@ -16,7 +16,7 @@ from paper_2402_08273_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 # the most mutations each window may let through, measured on a GB300
-PINS = {"f_bounded": 9}
+PINS = {"f_bounded": 12}
 
 WF = {"wavefront": True}
 STAT_KEYS = ("mutations", "accepted", "large", "small", "early_reject", "invalid_paths", "rays",
