@@ -41,16 +41,18 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-# FP32 operations the traversal needs per BVH4 node visit (the node grid's
-# three scales and offsets along the ray, 3 mul + 3 FMA; four child boxes:
-# 6 grid-index decodes (an add each), 6 FMA + 6 min + 6 max per slab test,
-# one compare each; a 5-comparator sort) and per ray-triangle test
-# (Moller-Trumbore: two cross products, three dot products, sign scaling, 5
-# compares, one division for a hit); an FMA counts as 2 floating-point
-# operations.
-FLOPS_PER_NODE = 3 + 3 * 2 + 4 * (6 + 6 * 2 + 12 + 1) + 5 * 2   # 143
+# FP32 operations the traversal needs per BVH4 node visit, by node size (128
+# bytes, binary32 bounds: four child boxes of 6 FMA + 6 min + 6 max per slab
+# test, one compare each, and a 5-comparator sort; 64 bytes, quantised: the
+# node grid's three scales and offsets along the ray, 3 mul + 3 FMA, and 6
+# grid-index decodes per child, an add each, on top) and per ray-triangle
+# test (Moller-Trumbore: two cross products, three dot products, sign
+# scaling, 5 compares, one division for a hit); an FMA counts as 2
+# floating-point operations.
+FLOPS_PER_NODE = {128: 4 * (6 * 2 + 12 + 1) + 5 * 2,                         # 110
+                  64: 3 + 3 * 2 + 4 * (6 + 6 * 2 + 12 + 1) + 5 * 2}          # 143
 FLOPS_PER_TRI = 2 * (6 * 2) + 3 * 5 + 3 + 5 + 1  # 48
-BYTES_PER_NODE = 64    # BVH4 node: the node grid, the children's 8-bit grid boxes, their refs
+BYTES_PER_NODE = 64    # quantised BVH4 node (the library reports the loaded scene's own: 128 for binary32 nodes)
 BYTES_PER_TRI = 48
 SM_COUNT = 152
 FP32_LANES = 128
@@ -515,8 +517,9 @@ def measure(wname, steps, warmup, form_arg, world=1, rank=0, local=0, dist=None,
     dr = max(1, sb["rays"] - sa["rays"])
     nodes_per_ray = (sb["node_visits"] - sa["node_visits"]) / dr
     tris_per_ray = (sb["tri_tests"] - sa["tri_tests"]) / dr
-    flops_ray = nodes_per_ray * FLOPS_PER_NODE + tris_per_ray * FLOPS_PER_TRI
-    bytes_ray = nodes_per_ray * BYTES_PER_NODE + tris_per_ray * BYTES_PER_TRI
+    node_bytes = sb["node_bytes"] or BYTES_PER_NODE
+    flops_ray = nodes_per_ray * FLOPS_PER_NODE[node_bytes] + tris_per_ray * FLOPS_PER_TRI
+    bytes_ray = nodes_per_ray * node_bytes + tris_per_ray * BYTES_PER_TRI
     rays_per_s_gpu = rays / world / t_max   # per GPU, for the per-kernel roofline
     l2_gbs, fp32_tflops = peaks["l2_gbs"], peaks["fp32_tflops"]
     # traversal roofline: rays/s_max = min(P_fp32 / flops_ray, BW / bytes_ray)
@@ -551,6 +554,7 @@ def measure(wname, steps, warmup, form_arg, world=1, rank=0, local=0, dist=None,
                 "ceilings": {"l2": l2, "alu": alu,
                              "alu_nominal_tflops": SM_COUNT * FP32_LANES * 2 * (clk["sm_mhz"] or 2070.0) / 1e6},
                 "per_ray": {"nodes": nodes_per_ray, "tris": tris_per_ray, "flops": flops_ray, "bytes": bytes_ray,
+                            "node_bytes": node_bytes,
                             "source": "the kernels' work counters over every ray of four epochs"}}
     if peaks.get("hbm_gbs"):
         hbm = peaks["hbm_gbs"]

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define RMLT_ABI_VERSION 6
+#define RMLT_ABI_VERSION 7
 #define RMLT_MAX_DEPTH 12          /* D = 2 + 5 d <= 62 primary-sample dimensions */
 
 typedef struct rmlt_ctx rmlt_ctx;
@@ -169,6 +169,9 @@ typedef struct {
     uint64_t wave_limit_hits;  /* wavefront form: epochs stopped by the wave limit (0 unless a bug) */
     uint64_t mala, mala_accepted;   /* Langevin moves proposed and accepted */
     uint64_t boot_overflow;    /* bootstrap paths dropped because the traversal stack overflowed */
+    uint32_t node_bytes;       /* bytes per BVH node of the loaded scene (128 BVH4, 64 quantised BVH4 or
+                                  BVH2; 0 without a BVH) */
+    uint32_t pad_;
 } rmlt_stats;
 
 /* One record per traced mutation (test instrument, see rmlt_set_trace). */
@@ -403,6 +406,21 @@ rmlt_status rmlt_set_wavefront(rmlt_ctx* ctx, int trace_ctas_per_sm, int setup_c
  * (rmlt_synchronize, rmlt_read_*, rmlt_save) then returns RMLT_E_OVERFLOW and
  * marks the context failed. */
 rmlt_status rmlt_set_wave_limit(rmlt_ctx* ctx, uint32_t waves);
+
+/* Node layout of the BVH4 that the next rmlt_load_scene builds (no counterpart
+ * in the paper).  RMLT_NODES_FLOAT: 128-byte nodes with the children's
+ * binary32 bounds.  RMLT_NODES_QUANTISED: 64-byte nodes, the children's boxes
+ * as 8-bit indices on a per-node grid, rounded outward (more boxes pass, the
+ * same hits are found), which halves the node bytes a ray reads for a decode
+ * per plane.  RMLT_NODES_AUTO (the default): quantised when the binary32 nodes
+ * and the triangles would take more than 48 MB, a third of the GPU's L2,
+ * where node loads miss the cache often enough for the halving to pay.
+ * Results do not depend on the layout beyond which of two triangles at the
+ * same distance is reported.  Errors: RMLT_E_INVALID_ARG. */
+#define RMLT_NODES_AUTO 0
+#define RMLT_NODES_FLOAT 1
+#define RMLT_NODES_QUANTISED 2
+rmlt_status rmlt_set_node_format(rmlt_ctx* ctx, int format);
 
 /* Leaf turns of the wavefront form's trace kernel: a warp's lanes whose ray
  * waits at a BVH leaf test its triangles together once at least leaf_batch

@@ -12,8 +12,10 @@
 //   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   n3 = (ref c0, ref c1, 0, 0)                      (uint bits)
-// BVH4 (4 float4 per node, the children's boxes quantised to 8 bits on a
-// per-node grid):
+// BVH4 (8 float4 per node, children in the four lanes of each float4):
+//   lo.x, hi.x, lo.y, hi.y, lo.z, hi.z, refs (uint bits), unused
+// or, quantised, BVH4Q (4 float4 per node, the children's boxes as 8-bit
+// indices on a per-node grid):
 //   n0 = (p.x, p.y, p.z, s.x)
 //   n1 = (s.y, s.z, qlo.z, qhi.z)                    (q words as uint bits)
 //   n2 = (qlo.x, qhi.x, qlo.y, qhi.y)
@@ -27,7 +29,8 @@
 // A ref is an internal node index, a leaf (kLeafBit | (count-1) << 28 |
 // first triangle in build order), or, for an unused BVH4 slot, empty_ref(n):
 // a one-triangle leaf past the scene's triangles (the upload's zero-area
-// sentinel), with q bytes 255 / 0, an inverted box no slab test accepts.
+// sentinel), with an inverted box no slab test accepts (BVH4: lo = +inf,
+// hi = -inf; BVH4Q: q bytes 255 / 0).
 // Boxes are widened by `pad` and rounded outward so that binary32 traversal
 // never culls a box a ray grazes.
 #include <algorithm>
@@ -176,6 +179,7 @@ struct Emitter {
     std::vector<float4>& out;
     float pad;
     uint32_t empty;   // the reference of an unused BVH4 slot
+    bool quant;       // BVH4Q nodes
     int depth = 0, max_depth = 0;
 
     Box padded(const Box& b) const
@@ -226,13 +230,29 @@ struct Emitter {
             ch[pick] = c.left;
             ch[nc++] = c.right;
         }
-        const uint32_t id = (uint32_t)(out.size() / 4);
-        out.resize(out.size() + 4);
+        const size_t words = quant ? 4 : 8;
+        const uint32_t id = (uint32_t)(out.size() / words);
+        out.resize(out.size() + words);
         uint32_t refs[4] = {empty, empty, empty, empty};
         Box boxes[4];
-        for (int k = 0; k < nc; ++k) {
-            refs[k] = emit4(ch[k]);
-            boxes[k] = padded(bn[(size_t)ch[k]].box);
+        for (int k = 0; k < 4; ++k) {
+            // an unused slot's inverted infinite box: every slab test rejects it
+            for (int a = 0; a < 3; ++a) { boxes[k].lo[a] = INFINITY; boxes[k].hi[a] = -INFINITY; }
+            if (k < nc) {
+                refs[k] = emit4(ch[k]);
+                boxes[k] = padded(bn[(size_t)ch[k]].box);
+            }
+        }
+        if (!quant) {
+            float4* nd = &out[8 * (size_t)id];
+            for (int a = 0; a < 3; ++a) {
+                nd[2 * a] = make_float4(boxes[0].lo[a], boxes[1].lo[a], boxes[2].lo[a], boxes[3].lo[a]);
+                nd[2 * a + 1] = make_float4(boxes[0].hi[a], boxes[1].hi[a], boxes[2].hi[a], boxes[3].hi[a]);
+            }
+            nd[6] = make_float4(bitsf(refs[0]), bitsf(refs[1]), bitsf(refs[2]), bitsf(refs[3]));
+            nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+            --depth;
+            return id;
         }
         float p[3], s[3];
         uint32_t qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
@@ -287,7 +307,7 @@ struct Emitter {
 
 }  // namespace
 
-void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out)
+void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out, int quantise)
 {
     std::vector<Prim> prims((size_t)n_tris);
     for (int i = 0; i < n_tris; ++i) {
@@ -307,13 +327,25 @@ void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width
     bld.build(0, n_tris, 0);
     out.nodes.clear();
     out.width = width;
-    Emitter em{bld.nodes, out.nodes, pad, empty_ref((uint32_t)n_tris)};
+    Emitter em{bld.nodes, out.nodes, pad, empty_ref((uint32_t)n_tris), quantise == 1};
     if (width == 4) {
         em.emit4(0);
         out.max_depth = em.max_depth;
+        out.fmt = kNodeBvh4;
+        const double bytes = sizeof(float4) * ((double)out.nodes.size() + 3.0 * n_tris);
+        if (quantise == 1 || (quantise < 0 && bytes > kQuantiseBytes)) {
+            if (!em.quant) {   // emitted as binary32 to size it: again, quantised
+                out.nodes.clear();
+                em.quant = true;
+                em.depth = em.max_depth = 0;
+                em.emit4(0);
+            }
+            out.fmt = kNodeBvh4Q;
+        }
     } else {
         em.emit2(0);
         out.max_depth = bld.max_depth;
+        out.fmt = kNodeBvh2;
     }
     out.order.resize((size_t)n_tris);
     for (int i = 0; i < n_tris; ++i) out.order[(size_t)i] = prims[(size_t)i].id;

@@ -1,10 +1,12 @@
 // Reference traversal of the uploaded BVH on the host, in binary64: the
 // yardstick for the chain kernel's traversal work counters.  It reads the
-// same node and triangle arrays the kernels read (four float4 per node; BVH4:
-// the node grid p, s and each child's box as 8-bit grid indices, decoded to
-// p + q s in binary64, and the four references; BVH2: both children's boxes
-// and references; leaves referenced with bit 31, the count - 1 in bits
-// 28..30 and the first triangle below), and walks them the textbook
+// same node and triangle arrays the kernels read (BVH4: eight float4 per
+// node, rows lo.x hi.x lo.y hi.y lo.z hi.z of the four children and their
+// references; BVH4Q: four float4, the node grid p, s and each child's box as
+// 8-bit grid indices, decoded to p + q s in binary64, and the references;
+// BVH2: four float4, both children's boxes and references; leaves
+// referenced with bit 31, the count - 1 in bits 28..30 and the first
+// triangle below), and walks them the textbook
 // way: at an internal node every child box is slab-tested against the ray
 // segment [0, t] (t the closest hit so far), the hit children are visited
 // nearest entry first (the rest stacked), a leaf's triangles are tested with
@@ -67,7 +69,7 @@ bool tri_hit(const Ray& r, const float4* T, double tmax, double& t)
 
 }  // namespace
 
-WalkResult walk_ray(const std::vector<float4>& nodes, int width, const std::vector<float4>& tris, bool brute,
+WalkResult walk_ray(const std::vector<float4>& nodes, int fmt, const std::vector<float4>& tris, bool brute,
                     const float ray[8])
 {
     Ray r;
@@ -117,7 +119,18 @@ WalkResult walk_ray(const std::vector<float4>& nodes, int width, const std::vect
             double key[4];
             uint32_t cref[4];
             int nc = 0;
-            if (width == 4) {
+            if (fmt == kNodeBvh4) {
+                const float4* nd = &nodes[8 * (size_t)ref];
+                const float lx[4] = {nd[0].x, nd[0].y, nd[0].z, nd[0].w}, hx[4] = {nd[1].x, nd[1].y, nd[1].z, nd[1].w};
+                const float ly[4] = {nd[2].x, nd[2].y, nd[2].z, nd[2].w}, hy[4] = {nd[3].x, nd[3].y, nd[3].z, nd[3].w};
+                const float lz[4] = {nd[4].x, nd[4].y, nd[4].z, nd[4].w}, hz[4] = {nd[5].x, nd[5].y, nd[5].z, nd[5].w};
+                const uint32_t rf[4] = {bits(nd[6].x), bits(nd[6].y), bits(nd[6].z), bits(nd[6].w)};
+                for (int k = 0; k < 4; ++k) {
+                    const double lo[3] = {lx[k], ly[k], lz[k]}, hi[3] = {hx[k], hy[k], hz[k]};
+                    const double tn = slab(r, lo, hi, t);
+                    if (tn >= 0.0) { key[nc] = tn; cref[nc++] = rf[k]; }
+                }
+            } else if (fmt == kNodeBvh4Q) {
                 const float4* nd = &nodes[4 * (size_t)ref];
                 const double p[3] = {nd[0].x, nd[0].y, nd[0].z}, s[3] = {nd[0].w, nd[1].x, nd[1].y};
                 const uint32_t ql[3] = {bits(nd[2].x), bits(nd[2].z), bits(nd[1].z)};

@@ -79,7 +79,8 @@ struct rmlt_ctx {
 
     bool have_scene = false, have_chains = false, failed = false;
     std::vector<float4> h_nodes, h_tris;   // host copies of the uploaded BVH nodes and triangles
-    int h_width = 4;
+    int h_fmt = kNodeBvh4;       // node layout of h_nodes
+    int node_format = RMLT_NODES_AUTO;   // BVH4 layout of the next rmlt_load_scene
     bool scene_lambert = true;   // every material Lambertian: the path map is differentiable (Langevin strategy)
     DevScene S;
     double tan_half = 1.0;
@@ -322,7 +323,9 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     // triangle order: BVH build order, or input order for brute force
     const bool brute = nt <= brute_max || nt <= 4;
     HostBVH bvh;
-    if (!brute) build_bvh(tv, nt, (float)(1e-6 * scale), width, bvh);
+    if (!brute)
+        build_bvh(tv, nt, (float)(1e-6 * scale), width, bvh,
+                  c->node_format == RMLT_NODES_QUANTISED ? 1 : c->node_format == RMLT_NODES_FLOAT ? 0 : -1);
     std::vector<uint32_t> order((size_t)nt), inv((size_t)nt);
     for (int i = 0; i < nt; ++i) order[(size_t)i] = brute ? (uint32_t)i : bvh.order[(size_t)i];
     for (int i = 0; i < nt; ++i) inv[order[(size_t)i]] = (uint32_t)i;
@@ -401,8 +404,8 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     S.light_tri = d_lt;
     S.light_cdf = d_lc;
     S.n_tris = nt;
-    S.n_nodes = (int32_t)(bvh.nodes.size() / 4);
-    S.bvh4 = width == 4 ? 1 : 0;
+    S.node_fmt = brute ? kNodeBvh4 : bvh.fmt;
+    S.n_nodes = (int32_t)(bvh.nodes.size() / node_float4s(S.node_fmt));
     S.n_mats = s->n_mats;
     S.n_lights = (int32_t)ltri.size();
     S.brute = brute ? 1 : 0;
@@ -422,7 +425,7 @@ rmlt_status rmlt_load_scene(rmlt_ctx* c, const rmlt_scene_desc* s)
     c->scene_mem = std::move(fresh);
     c->h_nodes = std::move(bvh.nodes);
     c->h_tris = std::move(tri4);
-    c->h_width = width;
+    c->h_fmt = S.node_fmt;
     c->tan_half = std::tan((double)cam.vfov_deg * 3.14159265358979323846 / 360.0);
     c->S = S;
     uint64_t h = fnv64(tv.data(), tv.size() * sizeof(float), 1469598103934665603ull);
@@ -1022,6 +1025,7 @@ rmlt_status rmlt_read_stats(rmlt_ctx* c, rmlt_stats* out)
     out->mala = s[kStMala];
     out->mala_accepted = s[kStMalaAcc];
     out->boot_overflow = s[kStBootOverflow];
+    out->node_bytes = c->have_scene && !c->S.brute && !c->S.toy ? 16u * (uint32_t)node_float4s(c->S.node_fmt) : 0u;
     return RMLT_OK;
 }
 
@@ -1030,6 +1034,15 @@ rmlt_status rmlt_read_params(rmlt_ctx* c, rmlt_chain_params* out)
     if (!c || !out) return fail(RMLT_E_INVALID_ARG, "null argument");
     if (!c->have_chains) return fail(RMLT_E_STATE, "no chains");
     *out = c->P;
+    return RMLT_OK;
+}
+
+rmlt_status rmlt_set_node_format(rmlt_ctx* c, int format)
+{
+    if (!c) return fail(RMLT_E_INVALID_ARG, "null context");
+    if (format != RMLT_NODES_AUTO && format != RMLT_NODES_FLOAT && format != RMLT_NODES_QUANTISED)
+        return fail(RMLT_E_INVALID_ARG, "node format must be RMLT_NODES_AUTO, _FLOAT or _QUANTISED");
+    c->node_format = format;
     return RMLT_OK;
 }
 
@@ -1138,7 +1151,7 @@ rmlt_status rmlt_walk_rays_host(rmlt_ctx* c, const float* rays, int64_t n, uint3
             o[1] = o[2] = o[3] = 0u;
             continue;
         }
-        const WalkResult w = walk_ray(c->h_nodes, c->h_width, c->h_tris, brute, r);
+        const WalkResult w = walk_ray(c->h_nodes, c->h_fmt, c->h_tris, brute, r);
         const float tf = (float)w.t;
         o[0] = w.tri >= 0 ? (uint32_t)w.tri : 0xFFFFFFFFu;
         std::memcpy(&o[1], &tf, 4);

@@ -301,40 +301,66 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
     }
     uint32_t next;
     const uint32_t ref = T.ref;
-    if (!(ref & kLeafBit) && S.bvh4) {
-        // four children: slab tests of their quantised boxes, nearest hit
-        // child next, the others pushed far to near
+    if (!(ref & kLeafBit) && S.node_fmt != kNodeBvh2) {
+        // four children: slab tests, nearest hit child next, the others
+        // pushed far to near
         ++n_nodes;
-        const float4* nd = &S.nodes[4 * (size_t)ref];
-        const float4 h0 = __ldg(nd), h1 = __ldg(nd + 1), qw = __ldg(nd + 2), rf = __ldg(nd + 3);
         const float tcap = T.t * 1.00000036f;
         const V3 id = T.id, ood = T.ood;
-        // plane p + q s of axis a at distance (p + q s - o) / d = q (s / d) + (p - o) / d
-        const float Ax = h0.w * id.x, Ay = h1.x * id.y, Az = h1.y * id.z;
-        const float Bx = fmaf(h0.x, id.x, -ood.x), By = fmaf(h0.y, id.y, -ood.y), Bz = fmaf(h0.z, id.z, -ood.z);
-        // the near and far planes of each axis are picked by the ray's octant:
-        // the distance is monotone in q with the direction's sign, so the
-        // slab test needs no min / max of the two planes
-        const uint32_t qlx = __float_as_uint(qw.x), qhx = __float_as_uint(qw.y);
-        const uint32_t qly = __float_as_uint(qw.z), qhy = __float_as_uint(qw.w);
-        const uint32_t qlz = __float_as_uint(h1.z), qhz = __float_as_uint(h1.w);
-        const uint32_t nwx = (T.oct & 1) ? qhx : qlx, fwx = (T.oct & 1) ? qlx : qhx;
-        const uint32_t nwy = (T.oct & 2) ? qhy : qly, fwy = (T.oct & 2) ? qly : qhy;
-        const uint32_t nwz = (T.oct & 4) ? qhz : qlz, fwz = (T.oct & 4) ? qlz : qhz;
         float key[4];
         uint32_t cr[4];
-        const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
-                                __float_as_uint(rf.w)};
+        // the near and far planes of each axis are picked by the ray's octant:
+        // the distance (plane - o) / d is monotone in the plane with the
+        // direction's sign, so the slab test needs no min / max of the two
+        if (S.node_fmt == kNodeBvh4Q) {
+            // 64-byte node: plane p + q s of axis a at distance
+            // (p + q s - o) / d = q (s / d) + (p - o) / d
+            const float4* nd = &S.nodes[4 * (size_t)ref];
+            const float4 h0 = __ldg(nd), h1 = __ldg(nd + 1), qw = __ldg(nd + 2), rf = __ldg(nd + 3);
+            const float Ax = h0.w * id.x, Ay = h1.x * id.y, Az = h1.y * id.z;
+            const float Bx = fmaf(h0.x, id.x, -ood.x), By = fmaf(h0.y, id.y, -ood.y), Bz = fmaf(h0.z, id.z, -ood.z);
+            const uint32_t qlx = __float_as_uint(qw.x), qhx = __float_as_uint(qw.y);
+            const uint32_t qly = __float_as_uint(qw.z), qhy = __float_as_uint(qw.w);
+            const uint32_t qlz = __float_as_uint(h1.z), qhz = __float_as_uint(h1.w);
+            const uint32_t nwx = (T.oct & 1) ? qhx : qlx, fwx = (T.oct & 1) ? qlx : qhx;
+            const uint32_t nwy = (T.oct & 2) ? qhy : qly, fwy = (T.oct & 2) ? qly : qhy;
+            const uint32_t nwz = (T.oct & 4) ? qhz : qlz, fwz = (T.oct & 4) ? qlz : qhz;
+            const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                                    __float_as_uint(rf.w)};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float a0 = fmaf(qbyte(nwx, k), Ax, Bx), b0 = fmaf(qbyte(fwx, k), Ax, Bx);
-            const float a1 = fmaf(qbyte(nwy, k), Ay, By), b1 = fmaf(qbyte(fwy, k), Ay, By);
-            const float a2 = fmaf(qbyte(nwz, k), Az, Bz), b2 = fmaf(qbyte(fwz, k), Az, Bz);
-            const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
-            const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
-            const bool hit = tn <= tf;   // an unused slot's inverted box never passes
-            key[k] = hit ? tn : INFINITY;
-            cr[k] = rr[k];
+            for (int k = 0; k < 4; ++k) {
+                const float a0 = fmaf(qbyte(nwx, k), Ax, Bx), b0 = fmaf(qbyte(fwx, k), Ax, Bx);
+                const float a1 = fmaf(qbyte(nwy, k), Ay, By), b1 = fmaf(qbyte(fwy, k), Ay, By);
+                const float a2 = fmaf(qbyte(nwz, k), Az, Bz), b2 = fmaf(qbyte(fwz, k), Az, Bz);
+                const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
+                const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
+                const bool hit = tn <= tf;   // an unused slot's inverted box never passes
+                key[k] = hit ? tn : INFINITY;
+                cr[k] = rr[k];
+            }
+        } else {
+            // 128-byte node: the bounds of the four children in the lanes of
+            // six float4 rows, the near / far row of each axis loaded by octant
+            const float4* nd = &S.nodes[8 * (size_t)ref];
+            const int ox = T.oct & 1, oy = (T.oct >> 1) & 1, oz = (T.oct >> 2) & 1;
+            const float4 nx = __ldg(nd + ox), fx = __ldg(nd + 1 - ox), ny = __ldg(nd + 2 + oy), fy = __ldg(nd + 3 - oy);
+            const float4 nz = __ldg(nd + 4 + oz), fz = __ldg(nd + 5 - oz), rf = __ldg(nd + 6);
+            const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+            const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+            const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+            const uint32_t rr[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                                    __float_as_uint(rf.w)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float a0 = fmaf(nxs[k], id.x, -ood.x), b0 = fmaf(fxs[k], id.x, -ood.x);
+                const float a1 = fmaf(nys[k], id.y, -ood.y), b1 = fmaf(fys[k], id.y, -ood.y);
+                const float a2 = fmaf(nzs[k], id.z, -ood.z), b2 = fmaf(fzs[k], id.z, -ood.z);
+                const float tn = fmaxf(fmaxf(a0, a1), fmaxf(a2, 0.0f));
+                const float tf = fminf(fminf(b0, b1), fminf(b2, tcap));
+                const bool hit = tn <= tf;   // an unused slot's inverted infinite box never passes
+                key[k] = hit ? tn : INFINITY;
+                cr[k] = rr[k];
+            }
         }
         // sorting network on (key, ref): (0,1) (2,3) (0,2) (1,3) (1,2)
 #define RMLT_CSWAP(i, j)                                                    \

@@ -48,12 +48,20 @@ constexpr uint32_t kLeafBit = 0x80000000u;
 // reference ever leaves the triangle array.
 constexpr uint32_t empty_ref(uint32_t n_tris) { return kLeafBit | n_tris; }
 
+// BVH node layouts (bvh_build.cpp describes them): BVH2, 4 float4 per node;
+// BVH4 with binary32 child bounds, 8 float4; BVH4 with the child boxes
+// quantised to 8 bits on a per-node grid, 4 float4.
+enum NodeFormat { kNodeBvh2 = 0, kNodeBvh4 = 1, kNodeBvh4Q = 2 };
+constexpr int node_float4s(int fmt) { return fmt == kNodeBvh4 ? 8 : 4; }
+// a BVH4 whose binary32 nodes and triangles would take more device memory
+// than this gets quantised nodes: past a third of the L2, node loads miss it
+// often enough that half the bytes per node pays for the decode
+constexpr double kQuantiseBytes = 48.0e6;
+
 // Device view of a loaded scene.  Triangles: 3 float4 each (v0 | mat id bits,
-// e1 | original index bits, e2 | 0); nodes: 4 float4 each (BVH2: child 0 x/y
-// bounds, child 1 x/y bounds, both z bounds, child refs; BVH4: a node grid
-// and the four children's boxes as 8-bit grid indices, then their refs, as
-// bvh_build.cpp describes); materials: 3 float4 each (albedo | type,
-// emission | roughness, emissive flag | black flag).
+// e1 | original index bits, e2 | 0); nodes: node_float4s(node_fmt) float4
+// each; materials: 3 float4 each (albedo | type, emission | roughness,
+// emissive flag | black flag).
 struct DevScene {
     const float4* tris = nullptr;
     const float4* nodes = nullptr;
@@ -61,7 +69,7 @@ struct DevScene {
     const int32_t* light_tri = nullptr;
     const float* light_cdf = nullptr;
     int32_t n_tris = 0, n_nodes = 0, n_mats = 0, n_lights = 0, brute = 1;
-    int32_t bvh4 = 1;                 // node layout (4 float4 each): 1 = quantised BVH4, 0 = BVH2
+    int32_t node_fmt = kNodeBvh4;     // node layout (NodeFormat)
     float light_area = 0.f;
     float cam_pos[3] = {0, 0, 0}, cam_fwd[3] = {0, 0, 1}, cam_right[3] = {1, 0, 0}, cam_up[3] = {0, 1, 0};
     float tan_x = 1.f, tan_y = 1.f;   // tan(vfov / 2) * aspect, tan(vfov / 2)
@@ -279,12 +287,17 @@ cudaError_t noalloc_scratch(int device, NoAllocScratch& out);
 
 // host-side BVH build (bvh_build.cpp)
 struct HostBVH {
-    std::vector<float4> nodes;    // 4 per node (BVH2, or quantised BVH4)
+    std::vector<float4> nodes;    // node_float4s(fmt) per node
     std::vector<uint32_t> order;  // triangle order after the build
     int width = 4;
+    int fmt = kNodeBvh4;
     int max_depth = 0;
 };
-void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out);
+// width 2: BVH2; width 4: BVH4 with binary32 bounds, or quantised bounds when
+// `quantise` is 1, or when it is -1 and the binary32 nodes and the triangles
+// would exceed kQuantiseBytes
+void build_bvh(const std::vector<float>& tri_v, int n_tris, float pad, int width, HostBVH& out,
+               int quantise = -1);
 
 // Reference traversal on the host (bvh_walk.cpp): the uploaded node and
 // triangle arrays walked in binary64, nearest child first, counting the
@@ -294,7 +307,7 @@ struct WalkResult {
     double t;
     uint32_t nodes, tris;
 };
-WalkResult walk_ray(const std::vector<float4>& nodes, int width, const std::vector<float4>& tris, bool brute,
+WalkResult walk_ray(const std::vector<float4>& nodes, int fmt, const std::vector<float4>& tris, bool brute,
                     const float ray[8]);
 
 }  // namespace rmlt

@@ -68,7 +68,8 @@ class Stats(C.Structure):
                 ("bhat", C.c_double), ("n_regions", C.c_int32), ("dims", C.c_int32),
                 ("node_visits", C.c_uint64), ("tri_tests", C.c_uint64), ("sched", C.c_uint64 * 6),
                 ("cycles", C.c_uint64 * 5), ("waves", C.c_uint64), ("wave_limit_hits", C.c_uint64),
-                ("mala", C.c_uint64), ("mala_accepted", C.c_uint64), ("boot_overflow", C.c_uint64)]
+                ("mala", C.c_uint64), ("mala_accepted", C.c_uint64), ("boot_overflow", C.c_uint64),
+                ("node_bytes", C.c_uint32), ("pad_", C.c_uint32)]
 
 
 TRACE_DTYPE = np.dtype([("f", np.float32, 3), ("a", np.float32), ("qhash", np.uint32),
@@ -95,6 +96,7 @@ _SIGS = [
     ("rmlt_read_params", C.c_int, [C.c_void_p, _P(ChainParams)]),
     ("rmlt_set_wave_limit", C.c_int, [C.c_void_p, C.c_uint32]),
     ("rmlt_set_trace_leaf_batch", C.c_int, [C.c_void_p, C.c_int]),
+    ("rmlt_set_node_format", C.c_int, [C.c_void_p, C.c_int]),
     ("rmlt_read_image", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("rmlt_read_region_hist", C.c_int, [C.c_void_p, C.c_void_p]),
     ("rmlt_read_region_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -232,7 +234,13 @@ class Renderer:
         self.close()
 
     # -- scene ---------------------------------------------------------------
-    def load_scene(self, scene: dict, brute_force_max: int = 0, bvh_width: int = 0):
+    NODE_FORMATS = {"auto": 0, "float": 1, "quantised": 2}
+
+    def load_scene(self, scene: dict, brute_force_max: int = 0, bvh_width: int = 0, node_format: str = "auto"):
+        """node_format: the BVH4 node layout, "float" (128-byte nodes),
+        "quantised" (64-byte nodes) or "auto" (quantised for scenes whose
+        binary32 nodes and triangles exceed 48 MB)."""
+        _check(lib().rmlt_set_node_format(self.h, self.NODE_FORMATS[node_format]))
         v = np.ascontiguousarray(scene["verts"], np.float32)
         t = np.ascontiguousarray(scene["tris"], np.uint32)
         mid = np.ascontiguousarray(scene["mat_id"], np.uint32)

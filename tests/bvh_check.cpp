@@ -7,11 +7,11 @@
 //   - every vertex of a leaf's triangles lies inside every box on the path
 //     from the root (the boxes are conservative; a BVH4 box is decoded from
 //     its node's grid, p + q s, in binary64);
-//   - a used BVH4 slot has lo <= hi grid indices on every axis; an unused one
-//     references the sentinel leaf past the triangles and has the inverted
-//     indices 255 / 0;
+//   - a used quantised BVH4 slot has lo <= hi grid indices on every axis; an
+//     unused BVH4 slot references the sentinel leaf past the triangles and
+//     has an inverted box (binary32: +inf / -inf; quantised: indices 255 / 0);
 //   - the depth the builder reports is the depth walked.
-// Usage: bvh_check <width 2|4> <n_tris> <mode 0 random | 1 identical | 2 slivers> <seed> <leaf_max>
+// Usage: bvh_check <layout 2|4|4q> <n_tris> <mode 0 random | 1 identical | 2 slivers> <seed> <leaf_max>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -77,13 +77,20 @@ struct Walker {
     void node(uint32_t id, std::vector<Box3>& path, int depth)
     {
         depth_seen = std::max(depth_seen, depth);
-        const float4* nd = &b.nodes[(size_t)4 * id];
+        const float4* nd = &b.nodes[(size_t)rmlt::node_float4s(b.fmt) * id];
         const int nc = b.width == 4 ? 4 : 2;
         for (int k = 0; k < nc; ++k) {
             Box3 bx;
             uint32_t ref;
             uint32_t ql[3] = {0, 0, 0}, qh[3] = {0, 0, 0};
-            if (b.width == 4) {
+            if (b.fmt == rmlt::kNodeBvh4) {
+                const float* f = reinterpret_cast<const float*>(nd);
+                for (int a = 0; a < 3; ++a) {
+                    bx.lo[a] = f[4 * (2 * a) + k];
+                    bx.hi[a] = f[4 * (2 * a + 1) + k];
+                }
+                ref = fbits(f[4 * 6 + k]);
+            } else if (b.fmt == rmlt::kNodeBvh4Q) {
                 const double p[3] = {nd[0].x, nd[0].y, nd[0].z}, s[3] = {nd[0].w, nd[1].x, nd[1].y};
                 const uint32_t wl[3] = {fbits(nd[2].x), fbits(nd[2].z), fbits(nd[1].z)};
                 const uint32_t wh[3] = {fbits(nd[2].y), fbits(nd[2].w), fbits(nd[1].w)};
@@ -102,16 +109,20 @@ struct Walker {
             }
             if (ref == rmlt::empty_ref((uint32_t)covered.size())) {
                 if (b.width != 4) fail("empty slot in a BVH2 node", id, k);
-                for (int a = 0; a < 3; ++a)
-                    if (ql[a] != 255u || qh[a] != 0u) fail("empty slot without inverted grid indices", id, k);
+                for (int a = 0; a < 3; ++a) {
+                    if (b.fmt == rmlt::kNodeBvh4Q && (ql[a] != 255u || qh[a] != 0u))
+                        fail("empty slot without inverted grid indices", id, k);
+                    if (b.fmt == rmlt::kNodeBvh4 && !(bx.lo[a] == INFINITY && bx.hi[a] == -INFINITY))
+                        fail("empty slot without an inverted infinite box", id, k);
+                }
                 continue;
             }
-            if (b.width == 4)
+            if (b.fmt == rmlt::kNodeBvh4Q)
                 for (int a = 0; a < 3; ++a)
                     if (ql[a] > qh[a]) fail("used slot with inverted grid indices", id, k);
             path.push_back(bx);
             if (ref & rmlt::kLeafBit) leaf(ref, path);
-            else if (ref <= id || (size_t)ref * 4 >= b.nodes.size()) fail("bad child node", id, ref);
+            else if (ref <= id || (size_t)ref * rmlt::node_float4s(b.fmt) >= b.nodes.size()) fail("bad child node", id, ref);
             else node(ref, path, depth + 1);
             path.pop_back();
         }
@@ -123,10 +134,11 @@ struct Walker {
 int main(int argc, char** argv)
 {
     if (argc != 6) {
-        std::printf("usage: bvh_check width n_tris mode seed leaf_max\n");
+        std::printf("usage: bvh_check layout n_tris mode seed leaf_max   (layout 2, 4 or 4q)\n");
         return 2;
     }
     const int width = std::atoi(argv[1]), n = std::atoi(argv[2]), mode = std::atoi(argv[3]);
+    const int quant = std::strcmp(argv[1], "4q") == 0 ? 1 : 0;
     const int leaf_max = std::atoi(argv[5]);
     uint64_t s = (uint64_t)std::atoll(argv[4]) * 0x9E3779B97F4A7C15ull + 1u;
     std::vector<float> v((size_t)9 * n);
@@ -142,7 +154,11 @@ int main(int argc, char** argv)
             }
     }
     rmlt::HostBVH b;
-    rmlt::build_bvh(v, n, 1e-6f * 10.f, width, b);
+    rmlt::build_bvh(v, n, 1e-6f * 10.f, width, b, quant);
+    if (b.fmt != (width == 2 ? rmlt::kNodeBvh2 : quant ? rmlt::kNodeBvh4Q : rmlt::kNodeBvh4)) {
+        std::printf("error: layout %d not the one asked for\n", b.fmt);
+        return 1;
+    }
     Walker w{b, v, leaf_max, std::vector<int>((size_t)n, 0)};
     if ((int)b.order.size() != n) w.fail("order has the wrong length", (long)b.order.size(), n);
     std::vector<int> seen((size_t)n, 0);
@@ -156,6 +172,6 @@ int main(int argc, char** argv)
         if (w.covered[(size_t)i] != 1) w.fail("position not covered exactly once", i, w.covered[(size_t)i]);
     if (width == 4 && w.depth_seen != b.max_depth) w.fail("reported depth differs", b.max_depth, w.depth_seen);
     if (w.errors) return 1;
-    std::printf("ok nodes=%zu depth=%d\n", b.nodes.size() / 4, w.depth_seen);
+    std::printf("ok nodes=%zu depth=%d\n", b.nodes.size() / rmlt::node_float4s(b.fmt), w.depth_seen);
     return 0;
 }

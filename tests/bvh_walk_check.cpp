@@ -4,7 +4,7 @@
 // distance as a brute-force loop over every triangle; any-hit rays agree on
 // occlusion; every ray visits at least the root; and a ray that misses the
 // scene's box visits the root only.
-// Usage: bvh_walk_check <width 2|4> <n_tris> <seed>
+// Usage: bvh_walk_check <layout 2|4|4q> <n_tris> <seed>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -26,6 +26,7 @@ int main(int argc, char** argv)
 {
     if (argc < 4) return 2;
     const int width = std::atoi(argv[1]), n = std::atoi(argv[2]);
+    const int quant = std::strcmp(argv[1], "4q") == 0 ? 1 : 0;
     uint64_t s = (uint64_t)std::atoll(argv[3]) * 7919u + 1u;
     std::vector<float> tv((size_t)9 * n);
     for (int i = 0; i < n; ++i) {
@@ -34,7 +35,7 @@ int main(int argc, char** argv)
             for (int a = 0; a < 3; ++a) tv[(size_t)9 * i + 3 * v + a] = c[a] + 0.05f * (unit(s) - 0.5f);
     }
     rmlt::HostBVH bvh;
-    rmlt::build_bvh(tv, n, 1e-6f, width, bvh);
+    rmlt::build_bvh(tv, n, 1e-6f, width, bvh, quant);
     // triangles in leaf order as the library uploads them: v0 | -, e1 | original index, e2
     std::vector<float4> tris((size_t)3 * n);
     for (int j = 0; j < n; ++j) {
@@ -56,8 +57,8 @@ int main(int argc, char** argv)
         ray[3] = 3.0e38f;
         ray[7] = (k % 3 == 0) ? 1.0f : 0.0f;
         if (ray[7] != 0.0f) ray[3] = 0.5f;
-        const rmlt::WalkResult a = rmlt::walk_ray(bvh.nodes, width, tris, false, ray);
-        const rmlt::WalkResult b = rmlt::walk_ray(bvh.nodes, width, tris, true, ray);
+        const rmlt::WalkResult a = rmlt::walk_ray(bvh.nodes, bvh.fmt, tris, false, ray);
+        const rmlt::WalkResult b = rmlt::walk_ray(bvh.nodes, bvh.fmt, tris, true, ray);
         if (a.nodes < 1) ++errors;
         if (ray[7] != 0.0f) {
             if ((a.tri >= 0) != (b.tri >= 0)) ++errors;
@@ -70,7 +71,7 @@ int main(int argc, char** argv)
     }
     // a ray that leaves the scene's box: the root only
     const float away[8] = {5.f, 5.f, 5.f, 3.0e38f, 1.f, 0.f, 0.f, 0.f};
-    const rmlt::WalkResult w = rmlt::walk_ray(bvh.nodes, width, tris, false, away);
+    const rmlt::WalkResult w = rmlt::walk_ray(bvh.nodes, bvh.fmt, tris, false, away);
     if (w.nodes != 1 || w.tris != 0 || w.tri != -1) ++errors;
     if (errors) {
         std::printf("errors %d\n", errors);

@@ -7,7 +7,7 @@ from paper_2402_08273_gb300 import rmlt
 
 
 def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bvh_width=0, tuning=None,
-               wavefront=None, words=False, **params):
+               wavefront=None, words=False, node_format="auto", **params):
     """Initialise, trace `n_epochs` epochs of every `stride`-th chain, and
     return the trace together with the initial and final state.  `tuning`
     (keyword arguments of Renderer.set_tuning) and `wavefront` (of
@@ -18,7 +18,7 @@ def traced_run(scene=None, toy=None, n_epochs=4, stride=1, brute_force_max=0, bv
     if toy is not None:
         R.load_toy_integrand(toy)
     else:
-        R.load_scene(scene, brute_force_max=brute_force_max, bvh_width=bvh_width)
+        R.load_scene(scene, brute_force_max=brute_force_max, bvh_width=bvh_width, node_format=node_format)
     if tuning:
         R.set_tuning(**tuning)
     if wavefront:

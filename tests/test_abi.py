@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 def test_host_side_errors_without_gpu():
     from paper_2402_08273_gb300 import rmlt
     L = rmlt.lib()
-    assert L.rmlt_abi_version() == 6
+    assert L.rmlt_abi_version() == 7
     # NULL context / NULL out: argument errors, no device needed
     assert L.rmlt_create(None, 0, None) == -1
     assert L.rmlt_step(None, 1) == -1
@@ -49,6 +49,7 @@ def test_host_side_errors_without_gpu():
     assert L.rmlt_read_params(None, None) == -1
     assert L.rmlt_set_wave_limit(None, 0) == -1
     assert L.rmlt_set_trace_leaf_batch(None, 8) == -1
+    assert L.rmlt_set_node_format(None, 0) == -1
     assert b"null" in L.rmlt_last_error()
     L.rmlt_destroy(None)
 

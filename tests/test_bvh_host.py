@@ -4,11 +4,12 @@
 library's builder (`csrc/bvh_build.cpp`) and walks the emitted node array:
 the triangle order is a permutation, leaves cover it exactly once with at
 most two triangles each, every vertex lies inside every box above its leaf
-(BVH4 boxes decoded from their node's 8-bit grid in binary64), and unused
-BVH4 slots reference the sentinel leaf past the triangles with inverted grid
-indices (which no slab test accepts).  Cases: random
+(quantised BVH4 boxes decoded from their node's 8-bit grid in binary64), and
+unused BVH4 slots reference the sentinel leaf past the triangles with an
+inverted box (which no slab test accepts).  Cases: random
 small triangles, triangles with one shared centroid (the builder splits by
-count), long slivers, and a tiny scene; both node widths.
+count), long slivers, and a tiny scene; BVH4 with binary32 and with
+quantised bounds, and BVH2.
 
 `tests/bvh_walk_check.cpp` checks the reference traversal the bench measures
 the kernel's traversal work against (`csrc/bvh_walk.cpp`): through the
@@ -39,10 +40,10 @@ def checker(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("width", [4, 2])
+@pytest.mark.parametrize("layout", ["4", "4q", "2"])
 @pytest.mark.parametrize("n_tris,mode,seed", [(20_000, 0, 1), (300, 1, 2), (5_000, 2, 3), (5, 0, 4), (777, 0, 5)])
-def test_bvh_structure(checker, width, n_tris, mode, seed):
-    r = subprocess.run([str(checker), str(width), str(n_tris), str(mode), str(seed), str(LEAF_MAX)],
+def test_bvh_structure(checker, layout, n_tris, mode, seed):
+    r = subprocess.run([str(checker), layout, str(n_tris), str(mode), str(seed), str(LEAF_MAX)],
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok ")
@@ -61,10 +62,10 @@ def walker(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("width", [4, 2])
+@pytest.mark.parametrize("layout", ["4", "4q", "2"])
 @pytest.mark.parametrize("n_tris,seed", [(3000, 1), (40, 2)])
-def test_reference_traversal_matches_brute_force(walker, width, n_tris, seed):
-    r = subprocess.run([str(walker), str(width), str(n_tris), str(seed)], capture_output=True, text=True,
+def test_reference_traversal_matches_brute_force(walker, layout, n_tris, seed):
+    r = subprocess.run([str(walker), layout, str(n_tris), str(seed)], capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.startswith("ok ") and int(r.stdout.split()[1]) > (100 if n_tris > 1000 else 0)

@@ -61,13 +61,14 @@ def test_weighted_target_cornell(oracle_mod):
     assert np.array_equal(ch.weight, gpu["region"]["w"])
 
 
-@pytest.mark.parametrize("bvh_width", [4, 2])
-def test_bvh_scene_full_trajectory(oracle_mod, bvh_width):
-    """A 20k-triangle two-rooms scene through the BVH path, every mutation
-    replayed (the oracle uses its own median-split BVH)."""
+@pytest.mark.parametrize("bvh_width,node_format", [(4, "float"), (4, "quantised"), (2, "auto")])
+def test_bvh_scene_full_trajectory(oracle_mod, bvh_width, node_format):
+    """A 20k-triangle two-rooms scene through the BVH path (BVH4 with binary32
+    and with quantised bounds, BVH2), every mutation replayed (the oracle uses
+    its own median-split BVH)."""
     gpu, ch, rp = _full(oracle_mod, scene=S.two_rooms(20_000, seed=4), use_bvh=True, n_epochs=6,
-                        bvh_width=bvh_width, n_chains=64, width=128, height=128, region_px=16,
-                        max_depth=8, n_bootstrap=1 << 12, pin=f"bvh{bvh_width}")
+                        bvh_width=bvh_width, node_format=node_format, n_chains=64, width=128, height=128,
+                        region_px=16, max_depth=8, n_bootstrap=1 << 12, pin=f"bvh{bvh_width}")
     assert gpu["stats"]["stack_overflow"] == 0
 
 

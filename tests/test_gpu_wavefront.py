@@ -57,11 +57,15 @@ def test_wavefront_identical_cornell_brute_force():
     assert ref["stats"]["waves"] == 0
 
 
-def test_wavefront_identical_bvh_scene():
-    """Two-rooms geometry (BVH4), 4096 chains, depth 10, three epochs."""
-    ref, wf = _both(3, stride=3, scene=S.two_rooms(20_000, seed=1), n_chains=4096, width=128, height=96,
-                    region_px=16, max_depth=10, epoch_len=16, n_bootstrap=1 << 16, p_large=0.3, seed=5)
+@pytest.mark.parametrize("node_format", ["float", "quantised"])
+def test_wavefront_identical_bvh_scene(node_format):
+    """Two-rooms geometry (BVH4, both node layouts), 4096 chains, depth 10,
+    three epochs."""
+    ref, wf = _both(3, stride=3, scene=S.two_rooms(20_000, seed=1), node_format=node_format, n_chains=4096,
+                    width=128, height=96, region_px=16, max_depth=10, epoch_len=16, n_bootstrap=1 << 16,
+                    p_large=0.3, seed=5)
     st = _assert_identical(ref, wf)
+    assert st["node_bytes"] == (128 if node_format == "float" else 64)
     assert st["rays"] > 0 and st["stack_overflow"] == 0
     # a wave per camera ray, bounce and last shadow ray at most
     assert st["waves"] <= 3 * (16 * 11 + 2)
@@ -136,3 +140,4 @@ def test_short_stack_identical_on_deep_stacks():
                     n_bootstrap=1 << 17, p_large=0.3)
     st = _assert_identical(ref, wf)
     assert st["stack_overflow"] == 0 and st["rays"] > 0
+    assert st["node_bytes"] == 64   # 2M triangles: quantised nodes by default
