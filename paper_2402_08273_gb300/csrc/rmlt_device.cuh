@@ -275,10 +275,13 @@ __device__ __forceinline__ float qbyte(uint32_t w, int k)
 }
 
 // one step; returns true once the ray is resolved
-template <bool BRUTE, class STK = uint32_t*>
+// FMT: the scene's node layout when the kernel was compiled for it (the hot
+// kernels are, per layout), or -1 to read it from the scene
+template <bool BRUTE, class STK = uint32_t*, int FMT = -1>
 __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S, const float4* s_tris,
                                           unsigned& n_nodes, unsigned& n_tris)
 {
+    const int fmt = FMT >= 0 ? FMT : S.node_fmt;
     if (BRUTE) {
         const int n = S.n_tris;
         const int i0 = (int)T.ref;
@@ -301,7 +304,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
     }
     uint32_t next;
     const uint32_t ref = T.ref;
-    if (!(ref & kLeafBit) && S.node_fmt != kNodeBvh2) {
+    if (!(ref & kLeafBit) && fmt != kNodeBvh2) {
         // four children: slab tests, nearest hit child next, the others
         // pushed far to near
         ++n_nodes;
@@ -312,7 +315,7 @@ __device__ __forceinline__ bool trav_step(Trav& T, STK stack, const DevScene& S,
         // the near and far planes of each axis are picked by the ray's octant:
         // the distance (plane - o) / d is monotone in the plane with the
         // direction's sign, so the slab test needs no min / max of the two
-        if (S.node_fmt == kNodeBvh4Q) {
+        if (fmt == kNodeBvh4Q) {
             // 64-byte node: plane p + q s of axis a at distance
             // (p + q s - o) / d = q (s / d) + (p - o) / d
             const float4* nd = &S.nodes[4 * (size_t)ref];

@@ -63,7 +63,7 @@ struct ProposalWords<false> {
 // The epoch of chain c (one thread); s_tris holds the staged triangles of a
 // brute-force scene, s_stack the block's traversal stacks.
 template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false, bool YSM = false,
-          int NT = kChainBlock>
+          int NT = kChainBlock, int FMT = -1>
 __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevChains& Ch, uint64_t mut0, int c,
                                                  const float4* s_tris, uint32_t* s_stack)
 {
@@ -117,7 +117,7 @@ __device__ __forceinline__ void chain_epoch_body(const DevScene& S, const DevCha
         while (true) {
             __syncwarp();
             if (step_turn<BRUTE>(phase == kTraverse, T)) {
-                if (trav_step<BRUTE>(T, stack, S, s_tris, n_nodes, n_tris)) {
+                if (trav_step<BRUTE, decltype(stack), FMT>(T, stack, S, s_tris, n_nodes, n_tris)) {
                     if (T.any) {
                         // the shadow ray of the last interaction: its contribution
                         // now, then straight on with the extension ray that the
@@ -304,7 +304,9 @@ __host__ __device__ constexpr int epoch_block() { return BRUTE ? kChainBlock : k
 
 // mut0_dev, when set, holds the epoch's first mutation index on the device
 // (a graph replayed over several epochs advances it there)
-template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false>
+// FMT: the node layout the kernel is compiled for (-1: the scene's, read at
+// each node)
+template <bool BRUTE, bool TRACE, bool COUNT, bool MALA = false, bool D4 = false, int FMT = -1>
 __global__ void __launch_bounds__(epoch_block<BRUTE>(), BRUTE ? 4 : 8)
     chain_epoch_kernel(const DevScene S, const DevChains Ch, uint64_t mut0, const unsigned long long* mut0_dev)
 {
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(epoch_block<BRUTE>(), BRUTE ? 4 : 8)
     if (mut0_dev) mut0 = *mut0_dev;
     // proposal words in shared memory on BVH scenes; a brute-force scene's
     // staged triangles may fill shared memory, so it keeps them local
-    chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4, !BRUTE, epoch_block<BRUTE>()>(
+    chain_epoch_body<BRUTE, TRACE, COUNT, MALA, D4, !BRUTE, epoch_block<BRUTE>(), FMT>(
         S, Ch, mut0, blockIdx.x * blockDim.x + threadIdx.x, s_tris, s_stack);
 }
 
@@ -967,8 +969,13 @@ static cudaError_t launch_epoch_t(const DevScene& s, const DevChains& c, uint64_
     constexpr int nt = epoch_block<B>();
     const int blocks = (c.C + nt - 1) / nt;
     const size_t shm = B ? sizeof(float4) * 3 * (size_t)s.n_tris : 0;
-    // the 4-D partition has its own instance, so the screen-only kernel carries none of its code
+    // the 4-D partition has its own instance, so the screen-only kernel carries none of its code;
+    // the plain BVH epoch one per BVH4 node layout, so its node step carries one layout's code
     auto kern = c.dcells > 1 ? chain_epoch_kernel<B, T, K, false, true> : chain_epoch_kernel<B, T, K>;
+    if (!B && !T && !K && c.dcells <= 1 && s.node_fmt == kNodeBvh4)
+        kern = chain_epoch_kernel<B, T, K, false, false, (B || T || K) ? -1 : kNodeBvh4>;
+    if (!B && !T && !K && c.dcells <= 1 && s.node_fmt == kNodeBvh4Q)
+        kern = chain_epoch_kernel<B, T, K, false, false, (B || T || K) ? -1 : kNodeBvh4Q>;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;

@@ -415,7 +415,8 @@ struct StackFor<kStackSize> {
 
 // SS: traversal stack entries per ray kept in shared memory (kStackSize: all;
 // fewer: the rest in W.gstack, so more of the SM's memory serves as L1)
-template <bool BRUTE, bool COUNT, int SS = kStackSize>
+// FMT: the node layout compiled in (-1: the scene's, read at each node)
+template <bool BRUTE, bool COUNT, int SS = kStackSize, int FMT = -1>
 __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S, const DevWave W, int C,
                                                                unsigned long long* stats)
 {
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(kChainBlock) wf_trace_kernel(const DevScene S,
             sc[4] += leaf_turn ? 0 : __popc(at_leaf);
             sc[5] += dry ? 1 : 0;
         }
-        if (go && trav_step<BRUTE>(T, stack, S, s_tris, nn, nt)) {
+        if (go && trav_step<BRUTE, decltype(stack), FMT>(T, stack, S, s_tris, nn, nt)) {
             if (T.any) {
                 Slots{W.s, C, c}[kWShd] = T.overflow ? 2u : (T.tri >= 0 ? 1u : 0u);
             } else {
@@ -614,8 +615,13 @@ void put(std::vector<unsigned char>& k, const T& v)
 // shared memory of as many resident blocks as the full-stack kernel gets
 // (registers bound both), and leaves L1 the rest
 template <bool B, bool K>
-void* trace_kernel(const DevWave& W)
+void* trace_kernel(const DevScene& S, const DevWave& W)
 {
+    // the plain BVH kernel one per BVH4 node layout, so its node step carries one layout's code
+    if (!B && !K && !W.short_stack && S.node_fmt == kNodeBvh4)
+        return (void*)wf_trace_kernel<B, K, kStackSize, (B || K) ? -1 : kNodeBvh4>;
+    if (!B && !K && !W.short_stack && S.node_fmt == kNodeBvh4Q)
+        return (void*)wf_trace_kernel<B, K, kStackSize, (B || K) ? -1 : kNodeBvh4Q>;
     if (!B && W.short_stack) {
         void* k = (void*)wf_trace_kernel<B, K, kShortStack>;
         static bool carved = false;
@@ -655,7 +661,7 @@ cudaError_t build_graph(WfGraph& G, const DevScene& S, const DevChains& Ch, DevW
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
-    void* kt = trace_kernel<B, K>(W);
+    void* kt = trace_kernel<B, K>(S, W);
     if (tshm > 48 * 1024) {
         if ((e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm)) != cudaSuccess)
             return e;
@@ -693,7 +699,7 @@ int trace_occupancy(const DevScene& S, const DevWave& W)
 {
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
     int n = 0;
-    void* kt = trace_kernel<B, K>(W);
+    void* kt = trace_kernel<B, K>(S, W);
     if (tshm > 48 * 1024) cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kt, kChainBlock, tshm);
     if (n > kWfTraceThreadsPerSm / kChainBlock) n = kWfTraceThreadsPerSm / kChainBlock;   // the global stack's room
@@ -716,7 +722,7 @@ cudaError_t host_waves(const DevScene& S, const DevChains& Ch, DevWave W, int tr
 {
     W.cond = 0;
     const size_t tshm = B ? sizeof(float4) * 3 * (size_t)S.n_tris : 0;
-    void* kt = trace_kernel<B, K>(W);
+    void* kt = trace_kernel<B, K>(S, W);
     if (tshm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tshm);
         if (e != cudaSuccess) return e;
