@@ -990,8 +990,14 @@ cudaError_t launch_chain_epoch_member(const BatchMember* member_dev, const Batch
     constexpr int nt = epoch_block<false>();
     const int blocks = (member.Ch.C + nt - 1) / nt;
     const unsigned long long* m0 = &member_dev->mut0;
-    if (count_work) chain_epoch_kernel<false, false, true><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
-    else chain_epoch_kernel<false, false, false><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
+    if (count_work)
+        chain_epoch_kernel<false, false, true><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
+    else if (member.Ch.dcells <= 1 && member.S.node_fmt == kNodeBvh4)
+        chain_epoch_kernel<false, false, false, false, false, kNodeBvh4><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
+    else if (member.Ch.dcells <= 1 && member.S.node_fmt == kNodeBvh4Q)
+        chain_epoch_kernel<false, false, false, false, false, kNodeBvh4Q><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
+    else
+        chain_epoch_kernel<false, false, false><<<blocks, nt, 0, st>>>(member.S, member.Ch, 0, m0);
     return cudaGetLastError();
 }
 
