@@ -98,7 +98,9 @@ def measured_traffic(workload: str, form: str):
     try:
         rec = json.loads((ROOT / "profiles" / "traffic.json").read_text())[f"{workload}/{form}"]
         csrc = ROOT / "paper_2402_08273_gb300" / "csrc"
-        src = b"".join((csrc / f).read_bytes() for f in ("rmlt_kernels.cu", "rmlt_device.cuh", "rmlt_wavefront.cu"))
+        # the files that hold the kernel's device code
+        files = rec.get("kernel_sources", ("rmlt_kernels.cu", "rmlt_device.cuh", "rmlt_wavefront.cu"))
+        src = b"".join((csrc / f).read_bytes() for f in files)
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
             return None
         return {"bytes_per_launch": rec.get("dram_bytes_per_launch"), "bytes_per_ray": rec.get("dram_bytes_per_ray"),
