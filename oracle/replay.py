@@ -367,10 +367,12 @@ class Replay:
 def adopt_initial_states(chains, q_gpu: np.ndarray, max_adopt: int) -> int:
     """Compare the oracle's initial states with the GPU's ([D][C] words).
 
-    Each chain picks its start from its own bootstrap slice; a path that
-    binary32 and binary64 evaluate differently (a triangle edge) can move one
-    chain's pick.  Up to ``max_adopt`` such chains are given the GPU's
-    starting state (the oracle recomputes f itself); returns how many."""
+    Each chain takes the sample where the cumulative sum of pi over all
+    bootstrap samples crosses its point; a path that binary32 and binary64
+    evaluate differently shifts that sum by its rounding error, which can move
+    a pick whose point lies that close to a sample boundary.  Up to
+    ``max_adopt`` such chains are given the GPU's starting state (the oracle
+    recomputes f itself); returns how many."""
     q_o = chains.q
     diff = np.flatnonzero(np.any(q_o != q_gpu.T, axis=1))
     if len(diff) > max_adopt:

@@ -14,9 +14,9 @@
 * Next-event light choice in proportion to triangle area: a furnace cube whose
   faces are split into triangles of very different areas keeps the closed form
   le sum rho^i; choosing triangles uniformly (planted) is biased and fails.
-* Starting states: the reservoir choice over each chain's bootstrap slice
-  puts the chains in region k with probability b_k / b; chi-square on the toy
-  integrand against its closed-form region masses.
+* Starting states: systematic resampling of all bootstrap samples in
+  proportion to pi puts the chains in region k with probability b_k / b;
+  chi-square on the toy integrand against its closed-form region masses.
 """
 import numpy as np
 import pytest
@@ -148,11 +148,11 @@ def test_light_choice_by_area(oracle_mod, plant):
 
 
 def test_starting_states_follow_the_target(oracle_mod):
-    """Chains pick their start among K = n_bootstrap / C uniform samples of
-    their own slice with probability pi_s / sum pi (weighted reservoir).  For
-    large K the chains' regions are distributed as the region masses b_k / b
-    of the toy integrand (closed form): chi-square test.  The uniform samples
-    themselves (no weighting) fail the same test."""
+    """Chains take their start by systematic resampling of the n_bootstrap
+    uniform samples in proportion to pi.  The chains' regions are then
+    distributed as the region masses b_k / b of the toy integrand (closed
+    form): chi-square test.  Unweighted picks of uniform samples fail the same
+    test."""
     from scipy import stats
     C, K = 4096, 256
     ch = oracle_mod.Chains(oracle_mod.Scene(toy=S.TOY_DEFAULT), n_chains=C, width=32, height=32, region_px=8,
@@ -163,7 +163,7 @@ def test_starting_states_follow_the_target(oracle_mod):
     obs = np.bincount(ch.k, minlength=len(p))
     chi2 = ((obs - C * p) ** 2 / (C * p)).sum()
     assert stats.chi2.sf(chi2, len(p) - 1) > 1e-3, chi2
-    # power: the chains' slices' first samples (what an unweighted pick gives)
+    # power: one uniform sample per chain (what an unweighted pick gives)
     first = np.array([ch.region_of(_boot_sample(oracle_mod, 21, c * K, 2)) for c in range(C)])
     obs_u = np.bincount(first, minlength=len(p))
     chi2_u = ((obs_u - C * p) ** 2 / (C * p)).sum()
